@@ -1,0 +1,225 @@
+/*
+ * tlda.h — C ABI of the GB300 online Tensor LDA library (libtlda).
+ *
+ * The library runs the data-parallel hot path of online Tensor LDA
+ * (Kangaslahti et al., "Analyzing Political Text at Scale with Online Tensor
+ * LDA"): demean and whiten bag-of-words minibatches into D dimensions, take the
+ * implicit third-order-moment CP gradient (eq. vec_deriv) and apply the SGD
+ * factor update (section "Online Learning of the Third Moment").  The moments
+ * (M1, M2, whitening W) and the recovery of topics (section "Recovering the
+ * Topic Model Parameters") sit on either side of that loop.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Plain pointers and sizes only.  "device" pointers address CUDA global
+ *    memory of the context's device; "host" pointers address CPU memory.
+ *  - Ownership: every array is owned by the caller; the context owns only its
+ *    workspace.  No call keeps a pointer after it returns.
+ *  - Streams: work is enqueued on the context's stream (tlda_create) and is
+ *    asynchronous unless the entry point says it synchronises.
+ *  - Errors: no exception crosses the ABI.  Each call returns a tlda_status;
+ *    tlda_last_error() gives a message for the last failure on that context.
+ *    Device-side validation failures (a corrupt CSR batch, a bounded wait
+ *    that expired) are sticky: they stop later updates of Phi and are
+ *    reported by the next synchronising call (tlda_sync, or any call that
+ *    documents that it synchronises), which also clears them.
+ *  - A context is used by one host thread at a time.
+ *
+ * Notation: V vocabulary size, D whitening dimension (D >= K), K topics,
+ * B documents in a batch.  Matrices are row-major with the stated shape.
+ */
+#ifndef TLDA_H
+#define TLDA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tlda_ctx tlda_ctx;
+
+typedef enum {
+  TLDA_OK = 0,
+  TLDA_ERR_INVALID = 1,        /* bad argument, or a corrupt CSR batch          */
+  TLDA_ERR_CUDA = 2,           /* a CUDA runtime call failed                    */
+  TLDA_ERR_NUMERIC = 3,        /* e.g. M2 has fewer than D positive eigenvalues */
+  TLDA_ERR_TIMEOUT = 4,        /* a bounded device-side wait expired            */
+  TLDA_ERR_OOM = 5,            /* workspace allocation failed / size limit      */
+  TLDA_ERR_STATE = 6,          /* call out of order (e.g. cp_step before fit)   */
+  TLDA_ERR_UNIMPLEMENTED = 7
+} tlda_status;
+
+typedef enum { TLDA_FP32 = 0, TLDA_BF16 = 1 } tlda_precision;
+
+/* A batch (or chunk) of documents as a count CSR, the document-term matrix F
+ * of section "Computing the Centered Cumulants" restricted to these rows.
+ * Row d holds the distinct words indices[indptr[d] .. indptr[d+1]) with their
+ * counts.  indptr entries are absolute offsets into indices/counts, so a batch
+ * may be a view into a larger corpus CSR: indptr must be non-decreasing with
+ * indptr[0] >= 0.  Within a row indices are strictly ascending and in [0, V);
+ * counts are > 0.  Documents with fewer than three tokens are legal: they
+ * carry no ordered triple of distinct tokens and contribute nothing to the
+ * third moment (pooled normalisation by S3 = sum_d L_d(L_d-1)(L_d-2)).
+ * All three arrays are DEVICE pointers unless an entry point says otherwise. */
+typedef struct {
+  int32_t n_docs;
+  int32_t vocab;               /* must equal the context's V */
+  const int32_t *indptr;       /* n_docs + 1 */
+  const int32_t *indices;
+  const int32_t *counts;
+} tlda_csr;
+
+/* Method parameters (section "Hyperparameter Tuning"; D from section
+ * "Online Decomposition of the Second Moment"). */
+typedef struct {
+  int32_t k;                   /* topics K (>= 1)                                  */
+  int32_t dim;                 /* whitening dimension D (0 means D = K; D >= K)    */
+  double alpha0;               /* topic mixing alpha0 > 0                          */
+  float theta;                 /* orthogonality penalty theta (> -1)               */
+  int32_t precision;           /* tlda_precision of the CP-step contractions       */
+  int32_t same_token_correction; /* 1: triples of distinct tokens (default);
+                                    0: drop the same-token terms                   */
+  uint64_t seed;               /* seed of the randomised subspace start (fit)      */
+  int32_t max_batch;           /* largest n_docs of a cp_step / whiten call;
+                                  0 means 8192 (sizes the workspace)               */
+} tlda_params;
+
+/* Fills *p with defaults: k=K given, D=K, alpha0=1, theta=0, FP32, correction
+ * on, seed 0, max_batch 8192. */
+void tlda_default_params(tlda_params *p, int32_t k);
+
+/* Creates a context for vocabulary size `vocab` on the current CUDA device,
+ * with all work enqueued on `cuda_stream` (a cudaStream_t; NULL = the legacy
+ * default stream).  Allocates the workspace (device memory linear in V and
+ * max_batch).  Returns TLDA_ERR_INVALID for bad sizes/parameters, TLDA_ERR_OOM
+ * if the workspace cannot be allocated. */
+tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, void *cuda_stream);
+
+/* Frees the context and its workspace (synchronises the stream first). */
+tlda_status tlda_destroy(tlda_ctx *ctx);
+
+/* Message of the last failure on ctx ("" if none).  Owned by ctx. */
+const char *tlda_last_error(const tlda_ctx *ctx);
+
+/* Synchronises the context's stream and returns (then clears) any sticky
+ * device-side status: TLDA_ERR_INVALID for a corrupt batch, TLDA_ERR_TIMEOUT
+ * for an expired bounded wait. */
+tlda_status tlda_sync(tlda_ctx *ctx);
+
+/* ---------------------------------------------------------------- moments */
+#define TLDA_ACCUMULATE 1u
+#define TLDA_FINALIZE 2u
+
+/* Moment estimation (section "Computing the Centered Cumulants" and appendix
+ * "Uncentered cumulants"; whitening of section "Online Decomposition of the
+ * Second Moment", read as W^T M2 W = I with the uncentred M2).
+ * With TLDA_ACCUMULATE, adds `chunk` (device CSR) to the running integer
+ * statistics: word totals C_m, T = sum L, S2 = sum L(L-1), S3, and the exact
+ * pair counts P = sum_d (f_d f_d^T - diag f_d) (a V x V FP64 accumulator held
+ * on the device; V <= 65536).  With TLDA_FINALIZE (chunk may be NULL), forms
+ * M1 = C/T and M2 = (alpha0+1) P/S2 - alpha0 M1 M1^T, finds the top-D
+ * eigenpairs by randomised subspace iteration (FP32 products, FP64
+ * orthonormalisation, FP64 Rayleigh-Ritz with a Jacobi eigensolver on the
+ * device), and sets W = U_D Lambda_D^-1/2 and m1 = W^T M1.  FINALIZE
+ * synchronises and returns TLDA_ERR_NUMERIC if lambda_D <= 1e-12 lambda_1,
+ * TLDA_ERR_INVALID if any accumulated chunk was corrupt.  Both flags may be
+ * given together.  A later ACCUMULATE after FINALIZE starts a new fit. */
+tlda_status tlda_fit_moments(tlda_ctx *ctx, const tlda_csr *chunk, uint32_t flags);
+
+/* Copies the whitening out: W (V x D FP32, device), m1 = W^T M1 (D FP32,
+ * device), eigenvalues lambda_1 >= ... >= lambda_D (D FP64, host).  Any
+ * pointer may be NULL.  Synchronises.  TLDA_ERR_STATE before a fit. */
+tlda_status tlda_get_whitening(const tlda_ctx *ctx, float *W, float *m1, double *eigvals);
+
+/* Integer statistics of the accumulated fit (host outputs, any may be NULL):
+ * C (V int64 word totals), T, S2, S3.  Synchronises. */
+tlda_status tlda_get_counts(const tlda_ctx *ctx, int64_t *C, int64_t *T, int64_t *S2, int64_t *S3);
+
+/* Installs a whitening instead of fitting one: W (V x D FP32, device) and
+ * m1 (D FP32, device).  The CP step uses whitened M2 = I by definition, so its
+ * arithmetic does not depend on how W was obtained. */
+tlda_status tlda_set_whitening(tlda_ctx *ctx, const float *W, const float *m1);
+
+/* ------------------------------------------------------------- hot path */
+
+/* Whitened, centred counts of a batch (section "Online Decomposition of the
+ * Second Moment", x = W (f - M1) in the paper's notation):
+ *   X[d,:] = sum_m f_dm W[m,:] - L_d m1,   L_d = sum_m f_dm,
+ * i.e. X = F U with U = W - 1 m1^T; the demeaned counts are never densified.
+ * X_out: B x D FP32, device, caller-allocated.  Asynchronous; a corrupt batch
+ * is reported by tlda_sync.  TLDA_ERR_STATE without a whitening. */
+tlda_status tlda_whiten_batch(tlda_ctx *ctx, const tlda_csr *batch, float *X_out);
+
+/* One stochastic tensor gradient step on one minibatch (eq. vec_deriv and
+ * the update Phi_{t+1} = Phi_t - beta dL/dPhi), in place on Phi (D x K FP32,
+ * device), with lr = beta.  The gradient is
+ *   grad = 3(1+theta) Phi (Phi^T Phi * Phi^T Phi) - 3 [c3/S3 (G1 + G2) + G3],
+ *   c3 = (alpha0+1)(alpha0+2)/2, X = F U, Y = X Phi, Q = U Phi,
+ *   G1 = X^T (Y*Y - F(Q*Q)),  G2 = U^T [Q * (2 c*Q - 2 F^T Y)], c = F^T 1,
+ *   G3_i = 2 phi_i (m1.phi_i) + m1 ||phi_i||^2 - 2 m1 (m1.phi_i)^2,
+ * the gradient of (1+theta)/2 ||sum phi_i^3||^2 - <sum phi_i^3, T_B> for the
+ * batch's whitened third moment written in centred form through Theorem 1
+ * (distinct-token triples; G2 and the F(Q*Q) term are the same-token terms,
+ * dropped when same_token_correction = 0).  lr = 0 gives the gradient only.
+ * grad_out (D x K FP32, device) may be NULL.  loss_out (host) may be NULL;
+ * when given, the call synchronises, writes the loss
+ *   (1+theta)/2 sum_ij (phi_i.phi_j)^3 - sum_i T_B(phi_i, phi_i, phi_i)
+ * at the incoming Phi and returns any sticky status.  A batch with S3 = 0
+ * leaves Phi unchanged (grad 0, loss 0).  A corrupt batch leaves Phi
+ * unchanged.  TLDA_ERR_STATE without a whitening; TLDA_ERR_INVALID if
+ * n_docs > max_batch. */
+tlda_status tlda_cp_step(tlda_ctx *ctx, const tlda_csr *batch, float *Phi, float lr,
+                         float *grad_out, double *loss_out);
+
+/* The data term of the same step without the update (diagnostics and
+ * parity): G_data = c3/S3 (G1 + G2) + G3 (D x K FP32, device) at Phi, and
+ * S3 (host, may be NULL).  Synchronises. */
+tlda_status tlda_cp_data_term(tlda_ctx *ctx, const tlda_csr *batch, const float *Phi,
+                              float *G_data_out, int64_t *S3_out);
+
+#define TLDA_HOST_INPUT 1u     /* corpus arrays are in host memory (pinned for overlap) */
+
+/* One online pass (section "Fully Online Implementation", with W fixed):
+ * batch b is documents [batch_offsets[b], batch_offsets[b+1]) of `corpus`;
+ * one CP step per batch, in order, on Phi (D x K FP32, device).
+ * batch_offsets: host, n_batches + 1 non-decreasing document offsets.
+ * With TLDA_HOST_INPUT the corpus CSR is in host memory and each batch is
+ * copied to the device inside the call (double-buffered, overlapped with the
+ * previous batch's compute); otherwise it is in device memory.
+ * loss_out (host, n_batches doubles) may be NULL; if given, each step's loss
+ * is copied back as the pass runs.  Synchronises at the end and returns any
+ * sticky status. */
+tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets,
+                         int32_t n_batches, float *Phi, float lr, uint32_t flags,
+                         double *loss_out);
+
+/* --------------------------------------------------------------- recovery */
+#define TLDA_HOST_OUTPUT 1u    /* mu_out / alpha_out are host pointers */
+
+/* Topic recovery (section "Recovering the Topic Model Parameters"), in FP64
+ * on the device: with lambda_i = ||phi_i||^3, v_i = phi_i/||phi_i||,
+ *   mu_i = lambda_i (W^T)^dagger v_i,  (W^T)^dagger = W (W^T W)^-1,
+ *   alpha_i proportional to lambda_i^-2, normalised to sum 1,
+ * then each mu_i is clipped at 0 and normalised to sum 1.  No "+ M1"
+ * re-centring: the whitening is by the uncentred M2, so the CP factors are
+ * already the uncentred topics (Theorem 1).  Phi: D x K FP32, device.
+ * mu_out: V x K FP64 (column i = topic i); alpha_out: K FP64.  Device
+ * pointers, or host with TLDA_HOST_OUTPUT (then the call synchronises). */
+tlda_status tlda_unwhiten_topics(tlda_ctx *ctx, const float *Phi, double *mu_out,
+                                 double *alpha_out, uint32_t flags);
+
+/* --------------------------------------------------------------- state */
+
+/* Checkpoint / resume of the fitted state (integer statistics, whitening,
+ * eigenvalues) to a flat binary file with a version word and a CRC-32.
+ * Synchronises.  tlda_load_state checks V, D and the CRC and returns
+ * TLDA_ERR_INVALID on a mismatch. */
+tlda_status tlda_save_state(const tlda_ctx *ctx, const char *path);
+tlda_status tlda_load_state(tlda_ctx *ctx, const char *path);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLDA_H */

@@ -1,0 +1,552 @@
+// Hot-path kernels of the online Tensor LDA CP step (eq. vec_deriv and the SGD
+// update of section "Online Learning of the Third Moment"), plain FP32 form,
+// plus the pieces both precisions share: batch scan + whitening, the
+// touched-word compaction, the Phi-only terms and the final reduction/update.
+//
+// Per step, with U = W - 1 m1^T (V x D), X = F U, Y = X Phi, Q = U Phi:
+//   a1  L_d, S3, c_m = sum_d f_dm, CSR validation         k_scan_whiten
+//   a2  X = F U (= F W - L m1^T)                           k_scan_whiten
+//       touched words {m : c_m > 0}                        k_compact
+//   a3  Y = X Phi;  a4 Q = U Phi (touched rows)            k_qy_f32
+//   a4  R_d = sum_m f_dm Q_m^2,  Z = Y*Y - R;  H = F^T Y   k_rz
+//   a6  Zc_m = Q_m * (2 c_m Q_m - 2 H_m)                   k_zh_f32
+//   a5+a6  G1 + G2 = X^T Z + U^T Zc (split reduction)      k_g_f32
+//   a7/a8  G3, P = Phi (Phi^T Phi * Phi^T Phi)             k_phi_gram, k_phi_terms
+//   a9  grad = E - 3 c3/S3 (G1 + G2), Phi -= lr grad       k_reduce_update
+// where E = 3(1+theta) P - 3 G3.  Words a batch does not touch have c_m = 0
+// and H_m = 0, so they contribute nothing to G2 and are skipped.
+#include <cstdio>
+
+#include "tlda_internal.h"
+
+namespace tlda {
+
+__device__ __forceinline__ float4 f4(float x) { return make_float4(x, x, x, x); }
+__device__ __forceinline__ float4 fma4(float s, float4 a, float4 c) {
+  return make_float4(fmaf(s, a.x, c.x), fmaf(s, a.y, c.y), fmaf(s, a.z, c.z), fmaf(s, a.w, c.w));
+}
+
+// ------------------------------------------------------------ batch descriptor
+__global__ void k_set_desc(DevState *st, BatchDesc b) { st->cur = b; }
+
+__global__ void k_begin_pass(DevState *st, const BatchDesc *descs, int n) {
+  st->descs = descs;
+  st->n_descs = n;
+  st->pass_pos = 1;
+  st->cur = descs[0];
+}
+
+void launch_set_desc(DevState *st, const BatchDesc &b, cudaStream_t s) {
+  k_set_desc<<<1, 1, 0, s>>>(st, b);
+}
+void launch_begin_pass(DevState *st, const BatchDesc *descs, int n, cudaStream_t s) {
+  k_begin_pass<<<1, 1, 0, s>>>(st, descs, n);
+}
+
+// ------------------------------------------------------------ U = W - 1 m1^T
+__global__ void k_make_u(const float *W, const float *m1, int V, int D, int Dp, float *U32,
+                         __nv_bfloat16 *U16) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)V * Dp) return;
+  const int m = (int)(e / Dp), i = (int)(e % Dp);
+  const float u = i < D ? W[(long long)m * D + i] - m1[i] : 0.f;
+  U32[e] = u;
+  if (U16) U16[e] = __float2bfloat16_rn(u);
+}
+
+void launch_make_u(const float *W, const float *m1, int V, int D, int Dp, float *U32,
+                   __nv_bfloat16 *U16, cudaStream_t s) {
+  const long long n = (long long)V * Dp;
+  k_make_u<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(W, m1, V, D, Dp, U32, U16);
+}
+
+// ------------------------------------------------------------ a1 + a2: scan and whiten
+// One warp per document: validates the row, accumulates L_d and
+// x_d = sum_m f_dm u_m (FP32) with float4 loads of the U rows, adds c_m and
+// the block's share of S3.  TC=true also writes X in BF16 row-major (X16)
+// and transposed (AT16 columns, via shared memory) for the tensor-core chain.
+template <int NV, bool TC>
+__global__ void __launch_bounds__(32 * kDocsPerBlock)
+    k_scan_whiten(StepArgs a, float *X_out, int stats) {
+  const BatchDesc b = a.st->cur;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int d0 = blockIdx.x * kDocsPerBlock;
+  if (d0 >= (TC ? round_up(b.n_docs, 64) : b.n_docs)) return;
+  const int d = d0 + warp;
+  __shared__ unsigned long long s3;
+  __shared__ __nv_bfloat16 xs[TC ? kDocsPerBlock * kMaxDim : 1];
+  if (threadIdx.x == 0) s3 = 0;
+  __syncthreads();
+  float4 acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = f4(0.f);
+  if (d < b.n_docs) {
+    const int lo = b.indptr[d], hi = b.indptr[d + 1];
+    bool bad = (lo < b.nz_base) || (hi < lo);
+    long long L = 0;
+    int prev = -1;
+    if (!bad) {
+      for (int j = lo; j < hi; ++j) {
+        const long long o = (long long)j - b.nz_base;
+        const int m = __ldg(b.indices + o), f = __ldg(b.counts + o);
+        if (m < 0 || m >= a.V || f <= 0) {
+          bad = true;
+          continue;
+        }
+        if (m <= prev) bad = true;
+        prev = m;
+        L += f;
+        if (stats && a.same_token && lane == 0) atomicAdd(a.cnt + m, f);
+        const float ff = (float)f;
+        const float *urow = a.U32 + (long long)m * a.Dp;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int col = v * 128 + lane * 4;
+          if (col < a.Dp) acc[v] = fma4(ff, __ldg(reinterpret_cast<const float4 *>(urow + col)), acc[v]);
+        }
+      }
+    }
+    if (bad && lane == 0) atomicOr(&a.st->err, kErrCsr);
+    if (stats && lane == 0 && L >= 3) atomicAdd(&s3, (unsigned long long)(L * (L - 1) * (L - 2)));
+    if (X_out) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int col = v * 128 + lane * 4;
+        const float c[4] = {acc[v].x, acc[v].y, acc[v].z, acc[v].w};
+        for (int q = 0; q < 4; ++q)
+          if (col + q < a.D) X_out[(long long)d * a.D + col + q] = c[q];
+      }
+    } else if (!TC) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int col = v * 128 + lane * 4;
+        if (col < a.Dp) *reinterpret_cast<float4 *>(a.X32 + (long long)d * a.Dp + col) = acc[v];
+      }
+    }
+  }
+  if constexpr (TC) {
+    if (!X_out) {
+      // row-major BF16 copy (A operand of Y = X Phi) and a staging copy for X^T
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int col = v * 128 + lane * 4;
+        if (col < a.Dp) {
+          __nv_bfloat162 lo2 = __floats2bfloat162_rn(acc[v].x, acc[v].y);
+          __nv_bfloat162 hi2 = __floats2bfloat162_rn(acc[v].z, acc[v].w);
+          if (d < b.n_docs) {
+            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(a.X16 + (long long)d * a.Dp + col);
+            dst[0] = lo2;
+            dst[1] = hi2;
+          }
+          __nv_bfloat162 *sx = reinterpret_cast<__nv_bfloat162 *>(xs + warp * a.Dp + col);
+          sx[0] = lo2;
+          sx[1] = hi2;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if constexpr (TC) {
+    if (!X_out) {
+      // X^T: AT16[i][d0 .. d0+16) = 32 contiguous bytes per feature row i
+      for (int i = threadIdx.x; i < a.Dp; i += blockDim.x) {
+        __align__(16) __nv_bfloat16 col[kDocsPerBlock];
+#pragma unroll
+        for (int q = 0; q < kDocsPerBlock; ++q) col[q] = xs[q * a.Dp + i];
+        uint4 *dst = reinterpret_cast<uint4 *>(a.AT16 + (long long)i * a.ldT + d0);
+        dst[0] = reinterpret_cast<const uint4 *>(col)[0];
+        dst[1] = reinterpret_cast<const uint4 *>(col)[1];
+      }
+    }
+  }
+  if (stats && threadIdx.x == 0 && s3) atomicAdd(&a.st->S3, s3);
+}
+
+void launch_whiten(const StepArgs &a, cudaStream_t s, float *X_out, bool stats) {
+  const int grid = round_up(a.Bmax, 64) / kDocsPerBlock;
+  const int nv = (a.Dp + 127) / 128;
+  const bool tc = a.precision == TLDA_BF16 && X_out == nullptr;
+#define TLDA_WHITEN(NVv)                                                                        \
+  if (nv == NVv) {                                                                              \
+    if (tc) k_scan_whiten<NVv, true><<<grid, 32 * kDocsPerBlock, 0, s>>>(a, X_out, stats);     \
+    else k_scan_whiten<NVv, false><<<grid, 32 * kDocsPerBlock, 0, s>>>(a, X_out, stats);       \
+    return;                                                                                     \
+  }
+  TLDA_WHITEN(1) TLDA_WHITEN(2) TLDA_WHITEN(3) TLDA_WHITEN(4)
+#undef TLDA_WHITEN
+}
+
+// ------------------------------------------------------------ touched words
+// Compact list of the batch's distinct words (c_m > 0), warp-aggregated.
+__global__ void k_compact(StepArgs a) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool hit = m < a.V && a.cnt[m] > 0;
+  const unsigned mask = __ballot_sync(0xffffffffu, hit);
+  int base = 0;
+  if (lane == 0 && mask) base = atomicAdd(&a.st->n_touched, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (hit) a.widx[base + __popc(mask & ((1u << lane) - 1u))] = m;
+}
+
+// ------------------------------------------------------------ a7/a8: Phi-only terms
+// Gram = Phi^T Phi (K x K, padded Kp) and a = m1^T Phi (extra block row).
+__global__ void k_phi_gram(StepArgs a) {
+  const int j = blockIdx.x * 16 + threadIdx.x;
+  const int i = blockIdx.y * 16 + threadIdx.y;
+  if ((int)blockIdx.y == (int)gridDim.y - 1) {
+    if (threadIdx.y == 0 && j < a.Kp) {
+      float s = 0.f;
+      if (j < a.K)
+        for (int r = 0; r < a.D; ++r) s = fmaf(a.m1[r], a.Phi[(long long)r * a.K + j], s);
+      a.avec[j] = s;
+    }
+    return;
+  }
+  if (i >= a.Kp || j >= a.Kp) return;
+  float s = 0.f;
+  if (i < a.K && j < a.K)
+    for (int r = 0; r < a.D; ++r)
+      s = fmaf(a.Phi[(long long)r * a.K + i], a.Phi[(long long)r * a.K + j], s);
+  a.Gram[i * a.Kp + j] = s;
+}
+
+// E = 3(1+theta) P - 3 G3 and G3 per entry (r, i); block 0 also forms the
+// Phi-only part of the loss.
+__global__ void k_phi_terms(StepArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < a.D * a.K) {
+    const int r = e / a.K, i = e % a.K;
+    float p = 0.f;
+    for (int j = 0; j < a.K; ++j) {
+      const float g = a.Gram[j * a.Kp + i];
+      p = fmaf(a.Phi[(long long)r * a.K + j], g * g, p);
+    }
+    const float ai = a.avec[i], n2 = a.Gram[i * a.Kp + i], mr = a.m1[r];
+    const float g3 = 2.f * a.Phi[(long long)r * a.K + i] * ai + mr * n2 - 2.f * mr * ai * ai;
+    a.G3[r * a.Kp + i] = g3;
+    a.E[r * a.Kp + i] = 3.f * (1.f + a.theta) * p - 3.f * g3;
+  }
+  if (blockIdx.x == 0 && a.want_loss) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int q = threadIdx.x; q < a.K * a.K; q += blockDim.x) {
+      const double g = a.Gram[(q / a.K) * a.Kp + (q % a.K)];
+      s += 0.5 * (1.0 + a.theta) * g * g * g;
+    }
+    for (int i = threadIdx.x; i < a.K; i += blockDim.x) {
+      const double ai = a.avec[i], n2 = a.Gram[i * a.Kp + i];
+      s -= 3.0 * ai * n2 - 2.0 * ai * ai * ai;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) a.st->loss_phi = red[0];
+  }
+}
+
+void launch_phi_terms(const StepArgs &a, cudaStream_t s) {
+  dim3 g1(a.Kp / 16, a.Kp / 16 + 1), b1(16, 16);
+  k_phi_gram<<<g1, b1, 0, s>>>(a);
+  k_phi_terms<<<(a.D * a.K + 255) / 256, 256, 0, s>>>(a);
+}
+
+// ------------------------------------------------------------ a3/a4: Q and Y (FP32)
+// Rows t < n_touched: Q[widx[t]] = U[widx[t]] Phi; then Y[d] = X[d] Phi.
+// 64 x 64 output tile per block, 4 x 4 per thread, Phi read with bounds
+// straight from the caller's D x K layout (zero padding).
+__global__ void __launch_bounds__(256) k_qy_f32(StepArgs a) {
+  const int nt = a.same_token ? a.st->n_touched : 0;
+  const int rows = nt + a.st->cur.n_docs;
+  const int r0 = blockIdx.x * 64;
+  if (r0 >= rows) return;
+  const int n0 = blockIdx.y * 64;
+  __shared__ __align__(16) float As[32][68];
+  __shared__ __align__(16) float Bs[32][64];
+  __shared__ const float *arow[64];
+  __shared__ float *orow[64];
+  const int tid = threadIdx.x;
+  if (tid < 64) {
+    const int r = r0 + tid;
+    const float *ap = nullptr;
+    float *op = nullptr;
+    if (r < nt) {
+      const int m = a.widx[r];
+      ap = a.U32 + (long long)m * a.Dp;
+      op = a.Q32 + (long long)m * a.Kp;
+    } else if (r < rows) {
+      const int d = r - nt;
+      ap = a.X32 + (long long)d * a.Dp;
+      op = a.Y32 + (long long)d * a.Kp;
+    }
+    arow[tid] = ap;
+    orow[tid] = op;
+  }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < a.Dp; k0 += 32) {
+    {
+      const int r = tid >> 2, kk = (tid & 3) * 8;
+      const float *ap = arow[r];
+      float4 v0 = f4(0.f), v1 = f4(0.f);
+      if (ap) {
+        v0 = *reinterpret_cast<const float4 *>(ap + k0 + kk);
+        v1 = *reinterpret_cast<const float4 *>(ap + k0 + kk + 4);
+      }
+      As[kk + 0][r] = v0.x; As[kk + 1][r] = v0.y; As[kk + 2][r] = v0.z; As[kk + 3][r] = v0.w;
+      As[kk + 4][r] = v1.x; As[kk + 5][r] = v1.y; As[kk + 6][r] = v1.z; As[kk + 7][r] = v1.w;
+    }
+    for (int e = tid; e < 32 * 64; e += 256) {
+      const int kk = e >> 6, n = e & 63, gi = k0 + kk, gn = n0 + n;
+      Bs[kk][n] = (gi < a.D && gn < a.K) ? a.Phi[(long long)gi * a.K + gn] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const float4 av = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+      const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+      const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float *op = orow[ty * 4 + i];
+    if (op) *reinterpret_cast<float4 *>(op + n0 + tx * 4) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  }
+}
+
+// ------------------------------------------------------------ a4 + a6 scatter: R, Z, H
+// One warp per document: r_d = sum_m f_dm q_m^2 (gathered Q rows), z_d = y_d^2 - r_d,
+// H_m += f_dm y_d (vector atomics), and the document part of the loss.
+template <int NK, bool TC>
+__global__ void __launch_bounds__(256) k_rz(StepArgs a) {
+  const BatchDesc b = a.st->cur;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int d = blockIdx.x * 8 + warp;
+  if (d >= b.n_docs) return;
+  float4 y[NK], r[NK];
+#pragma unroll
+  for (int v = 0; v < NK; ++v) {
+    const int col = v * 128 + lane * 4;
+    y[v] = col < a.Kp ? *reinterpret_cast<const float4 *>(a.Y32 + (long long)d * a.Kp + col) : f4(0.f);
+    r[v] = f4(0.f);
+  }
+  if (a.same_token) {
+    const int lo = b.indptr[d], hi = b.indptr[d + 1];
+    if (lo >= b.nz_base)
+      for (int j = lo; j < hi; ++j) {
+        const long long o = (long long)j - b.nz_base;
+        const int m = __ldg(b.indices + o), f = __ldg(b.counts + o);
+        if (m < 0 || m >= a.V || f <= 0) continue;
+        const float ff = (float)f;
+#pragma unroll
+        for (int v = 0; v < NK; ++v) {
+          const int col = v * 128 + lane * 4;
+          if (col < a.Kp) {
+            const float4 q = *reinterpret_cast<const float4 *>(a.Q32 + (long long)m * a.Kp + col);
+            r[v].x = fmaf(ff * q.x, q.x, r[v].x);
+            r[v].y = fmaf(ff * q.y, q.y, r[v].y);
+            r[v].z = fmaf(ff * q.z, q.z, r[v].z);
+            r[v].w = fmaf(ff * q.w, q.w, r[v].w);
+            atomicAdd(reinterpret_cast<float4 *>(a.H32 + (long long)m * a.Kp + col),
+                      make_float4(ff * y[v].x, ff * y[v].y, ff * y[v].z, ff * y[v].w));
+          }
+        }
+      }
+  }
+  float ls = 0.f;
+#pragma unroll
+  for (int v = 0; v < NK; ++v) {
+    const int col = v * 128 + lane * 4;
+    if (col < a.Kp) {
+      const float4 z = make_float4(y[v].x * y[v].x - r[v].x, y[v].y * y[v].y - r[v].y,
+                                   y[v].z * y[v].z - r[v].z, y[v].w * y[v].w - r[v].w);
+      if constexpr (TC) {
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+        for (int q = 0; q < 4; ++q) a.BT16[(long long)(col + q) * a.ldT + d] = __float2bfloat16_rn(zz[q]);
+      } else {
+        *reinterpret_cast<float4 *>(a.Z32 + (long long)d * a.Kp + col) = z;
+      }
+      if (a.want_loss)
+        ls += y[v].x * (y[v].x * y[v].x - 3.f * r[v].x) + y[v].y * (y[v].y * y[v].y - 3.f * r[v].y) +
+              y[v].z * (y[v].z * y[v].z - 3.f * r[v].z) + y[v].w * (y[v].w * y[v].w - 3.f * r[v].w);
+    }
+  }
+  if (a.want_loss) {
+    for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
+    if (lane == 0) atomicAdd(&a.st->loss_data, (double)ls);
+  }
+}
+
+// ------------------------------------------------------------ a6: Zc rows
+// One warp per touched word (compact slot t): Zc_t = q * (2 c q - 2 H_m); then
+// H_m and c_m are cleared for the next batch (this warp is their only reader).
+template <int NK>
+__global__ void __launch_bounds__(256) k_zh_f32(StepArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= a.st->n_touched) return;
+  const int m = a.widx[t];
+  const float c = (float)a.cnt[m];
+  float ls = 0.f;
+#pragma unroll
+  for (int v = 0; v < NK; ++v) {
+    const int col = v * 128 + lane * 4;
+    if (col < a.Kp) {
+      float4 *hp = reinterpret_cast<float4 *>(a.H32 + (long long)m * a.Kp + col);
+      const float4 q = *reinterpret_cast<const float4 *>(a.Q32 + (long long)m * a.Kp + col);
+      const float4 h = *hp;
+      const float4 z = make_float4(q.x * (2.f * c * q.x - 2.f * h.x), q.y * (2.f * c * q.y - 2.f * h.y),
+                                   q.z * (2.f * c * q.z - 2.f * h.z), q.w * (2.f * c * q.w - 2.f * h.w));
+      *reinterpret_cast<float4 *>(a.Zc32 + (long long)t * a.Kp + col) = z;
+      *hp = f4(0.f);
+      ls += q.x * q.x * q.x + q.y * q.y * q.y + q.z * q.z * q.z + q.w * q.w * q.w;
+    }
+  }
+  if (a.want_loss) {
+    for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
+    if (lane == 0) atomicAdd(&a.st->loss_data, 2.0 * (double)c * (double)ls);
+  }
+  __syncwarp();
+  if (lane == 0) a.cnt[m] = 0;
+}
+
+// ------------------------------------------------------------ a5 + a6: G1 + G2 (FP32)
+// Split reduction over the rows [docs: (X, Z)] ++ [touched words: (U, Zc)]:
+// block (s, ti, tn) sums rows of split s into the 64 x 64 tile (ti, tn) of
+// partial s, 4 x 4 outputs per thread.
+__global__ void __launch_bounds__(256) k_g_f32(StepArgs a) {
+  const int nd = a.st->cur.n_docs, nt = a.same_token ? a.st->n_touched : 0;
+  const int R = nd + nt;
+  const int s = blockIdx.x, i0 = blockIdx.y * 64, n0 = blockIdx.z * 64;
+  const int rb = (int)((long long)R * s / a.nsplit), re = (int)((long long)R * (s + 1) / a.nsplit);
+  __shared__ __align__(16) float As[32][64];
+  __shared__ __align__(16) float Bs[32][64];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int r0 = rb; r0 < re; r0 += 32) {
+    {
+      const int rr = tid >> 3, cc = (tid & 7) * 8, r = r0 + rr;
+      float4 a0 = f4(0.f), a1 = f4(0.f), b0 = f4(0.f), b1 = f4(0.f);
+      if (r < re) {
+        const float *ap, *bp;
+        if (r < nd) {
+          ap = a.X32 + (long long)r * a.Dp;
+          bp = a.Z32 + (long long)r * a.Kp;
+        } else {
+          const int t = r - nd;
+          ap = a.U32 + (long long)a.widx[t] * a.Dp;
+          bp = a.Zc32 + (long long)t * a.Kp;
+        }
+        a0 = *reinterpret_cast<const float4 *>(ap + i0 + cc);
+        a1 = *reinterpret_cast<const float4 *>(ap + i0 + cc + 4);
+        b0 = *reinterpret_cast<const float4 *>(bp + n0 + cc);
+        b1 = *reinterpret_cast<const float4 *>(bp + n0 + cc + 4);
+      }
+      *reinterpret_cast<float4 *>(&As[rr][cc]) = a0;
+      *reinterpret_cast<float4 *>(&As[rr][cc + 4]) = a1;
+      *reinterpret_cast<float4 *>(&Bs[rr][cc]) = b0;
+      *reinterpret_cast<float4 *>(&Bs[rr][cc + 4]) = b1;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+      const float4 av = *reinterpret_cast<const float4 *>(&As[rr][ty * 4]);
+      const float4 bv = *reinterpret_cast<const float4 *>(&Bs[rr][tx * 4]);
+      const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float *gp = a.Gpart + (long long)s * a.Dp * a.Kp;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<float4 *>(gp + (long long)(i0 + ty * 4 + i) * a.Kp + n0 + tx * 4) =
+        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+}
+
+void launch_chain_f32(const StepArgs &a, cudaStream_t s) {
+  const int nk = (a.Kp + 127) / 128;
+  if (a.same_token) k_compact<<<(a.V + 255) / 256, 256, 0, s>>>(a);
+  {
+    dim3 g((a.V + a.Bmax + 63) / 64, a.Kp / 64);
+    k_qy_f32<<<g, 256, 0, s>>>(a);
+  }
+#define TLDA_RZ(NKv)                                                              \
+  if (nk == NKv) {                                                                \
+    k_rz<NKv, false><<<(a.Bmax + 7) / 8, 256, 0, s>>>(a);                          \
+    if (a.same_token) k_zh_f32<NKv><<<(a.V + 7) / 8, 256, 0, s>>>(a);            \
+  }
+  TLDA_RZ(1) TLDA_RZ(2) TLDA_RZ(3) TLDA_RZ(4)
+#undef TLDA_RZ
+  {
+    dim3 g(a.nsplit, a.Dp / 64, a.Kp / 64);
+    k_g_f32<<<g, 256, 0, s>>>(a);
+  }
+}
+
+// ------------------------------------------------------------ a9: reduce + update
+// Entry (i, n): g = sum over partials; grad = E - 3 c3/S3 g; Phi -= lr grad
+// (skipped on a sticky error or S3 = 0).  The last block (ticket) writes the
+// loss, clears the per-step sums and advances the pass descriptor.
+__global__ void __launch_bounds__(256) k_reduce_update(StepArgs a) {
+  DevState *st = a.st;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long S3 = st->S3;
+  const int err = st->err;
+  const double scale = S3 ? a.c3 / (double)S3 : 0.0;
+  if (e < a.D * a.K) {
+    const int i = e / a.K, n = e % a.K;
+    const long long off = (long long)i * a.Kp + n, stride = (long long)a.Dp * a.Kp;
+    float g = 0.f;
+    for (int s = 0; s < a.nsplit; ++s) g += a.Gpart[s * stride + off];
+    if (a.mode == 1) {
+      a.gdata_out[e] = S3 ? (float)(scale * (double)g) + a.G3[off] : 0.f;
+    } else {
+      const float grad = S3 ? a.E[off] - (float)(3.0 * scale * (double)g) : 0.f;
+      if (a.grad_out) a.grad_out[e] = grad;
+      if (!err && S3) a.Phi[e] -= a.lr * grad;
+    }
+  }
+  __threadfence();
+  __shared__ bool last;
+  if (threadIdx.x == 0) last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    st->loss = S3 ? st->loss_phi - scale * st->loss_data : 0.0;
+    st->last_S3 = S3;
+    st->S3 = 0;
+    st->loss_data = 0.0;
+    st->n_touched = 0;
+    st->ticket = 0;
+    st->step += 1;
+    if (st->descs && st->pass_pos < st->n_descs) st->cur = st->descs[st->pass_pos++];
+  }
+}
+
+void launch_reduce_update(const StepArgs &a, cudaStream_t s) {
+  k_reduce_update<<<(a.D * a.K + 255) / 256, 256, 0, s>>>(a);
+}
+
+}  // namespace tlda

@@ -1,0 +1,530 @@
+// C ABI of libtlda (declared in include/tlda.h): context and workspace
+// management, argument checks, and the orchestration of the per-batch kernel
+// chain on the context's stream.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "tlda_internal.h"
+
+using namespace tlda;
+
+namespace {
+
+tlda_status fail(tlda_ctx *c, tlda_status s, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+#define CK(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? TLDA_ERR_OOM : TLDA_ERR_CUDA,       \
+                  "%s: %s", #call, cudaGetErrorString(e_));                                  \
+  } while (0)
+
+#define CKL()                                                                                \
+  do {                                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                                     \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(ctx, TLDA_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e_));          \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t n, bool zero = false) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+  if (e == cudaSuccess && zero) e = cudaMemset(*p, 0, n * sizeof(T));
+  return e;
+}
+
+template <class T>
+void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+StepArgs make_args(tlda_ctx *c) {
+  StepArgs a{};
+  a.V = c->V;
+  a.D = c->D;
+  a.K = c->K;
+  a.Dp = c->Dp;
+  a.Kp = c->Kp;
+  a.Bmax = c->Bmax;
+  a.nsplit = c->nsplit;
+  a.theta = c->p.theta;
+  a.lr = 0.f;
+  a.c3 = (c->p.alpha0 + 1.0) * (c->p.alpha0 + 2.0) / 2.0;
+  a.same_token = c->p.same_token_correction ? 1 : 0;
+  a.want_loss = 0;
+  a.mode = 0;
+  a.st = c->st;
+  a.U32 = c->U32;
+  a.m1 = c->m1;
+  a.X32 = c->X32;
+  a.Q32 = c->Q32;
+  a.Y32 = c->Y32;
+  a.Z32 = c->Z32;
+  a.Zc32 = c->Zc32;
+  a.H32 = c->H32;
+  a.cnt = c->cnt;
+  a.widx = c->widx;
+  a.Gpart = c->Gpart;
+  a.Gram = c->Gram;
+  a.avec = c->avec;
+  a.E = c->E;
+  a.G3 = c->G3;
+  a.U16 = c->U16;
+  a.X16 = c->X16;
+  a.AT16 = c->AT16;
+  a.BT16 = c->BT16;
+  a.ldT = c->ldT;
+  a.precision = c->p.precision;
+  return a;
+}
+
+tlda_status check_csr(tlda_ctx *ctx, const tlda_csr *b, bool allow_empty_ptrs = false) {
+  if (!b) return fail(ctx, TLDA_ERR_INVALID, "batch is NULL");
+  if (b->vocab != ctx->V) return fail(ctx, TLDA_ERR_INVALID, "batch vocab %d != context V %d", b->vocab, ctx->V);
+  if (b->n_docs < 0) return fail(ctx, TLDA_ERR_INVALID, "n_docs < 0");
+  if (!allow_empty_ptrs && (!b->indptr || (b->n_docs > 0 && (!b->indices || !b->counts))))
+    return fail(ctx, TLDA_ERR_INVALID, "NULL CSR array");
+  return TLDA_OK;
+}
+
+BatchDesc desc_of(const tlda_csr *b) {
+  BatchDesc d{};
+  d.indptr = b->indptr;
+  d.indices = b->indices;
+  d.counts = b->counts;
+  d.nz_base = 0;
+  d.n_docs = b->n_docs;
+  return d;
+}
+
+// Enqueues one CP step on ctx->stream for the batch in st->cur.
+tlda_status enqueue_step(tlda_ctx *ctx, const StepArgs &a) {
+  CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  launch_phi_terms(a, ctx->side);
+  CKL();
+  CK(cudaEventRecord(ctx->ev_join, ctx->side));
+  launch_whiten(a, ctx->stream, nullptr, true);
+  CKL();
+  if (a.precision == TLDA_BF16) launch_chain_bf16(a, ctx->stream);
+  else launch_chain_f32(a, ctx->stream);
+  CKL();
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+  launch_reduce_update(a, ctx->stream);
+  CKL();
+  return TLDA_OK;
+}
+
+tlda_status read_state(tlda_ctx *ctx) {
+  CK(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return TLDA_OK;
+}
+
+tlda_status take_sticky(tlda_ctx *ctx) {
+  const int e = ctx->st_host->err;
+  if (e) {
+    const int zero = 0;
+    CK(cudaMemcpy(&ctx->st->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    if (e & kErrTimeout) return fail(ctx, TLDA_ERR_TIMEOUT, "a bounded device wait expired");
+    return fail(ctx, TLDA_ERR_INVALID, "corrupt CSR batch (indptr, index, order or count)");
+  }
+  return TLDA_OK;
+}
+
+const uint32_t kStateMagic = 0x41444C54u;  // "TLDA"
+const uint32_t kStateVersion = 1;
+
+uint32_t crc32_update(uint32_t crc, const void *data, size_t n) {
+  const unsigned char *p = static_cast<const unsigned char *>(data);
+  crc = ~crc;
+  for (size_t i = 0; i < n; ++i) {
+    crc ^= p[i];
+    for (int b = 0; b < 8; ++b) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+  }
+  return ~crc;
+}
+
+}  // namespace
+
+// ============================================================================ ABI
+
+extern "C" {
+
+void tlda_default_params(tlda_params *p, int32_t k) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->k = k;
+  p->dim = 0;
+  p->alpha0 = 1.0;
+  p->theta = 0.f;
+  p->precision = TLDA_FP32;
+  p->same_token_correction = 1;
+  p->seed = 0;
+  p->max_batch = 8192;
+}
+
+const char *tlda_last_error(const tlda_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, void *cuda_stream) {
+  if (!out || !p) return TLDA_ERR_INVALID;
+  *out = nullptr;
+  const int K = p->k, D = p->dim > 0 ? p->dim : p->k;
+  if (vocab < 1 || K < 1 || D < K || round_up(D, 64) > kMaxDim || round_up(K, 64) > kMaxDim ||
+      D > vocab || !(p->alpha0 > 0.0) || !(p->theta > -1.f) ||
+      (p->precision != TLDA_FP32 && p->precision != TLDA_BF16) || p->max_batch < 0 ||
+      p->max_batch > (1 << 20))
+    return TLDA_ERR_INVALID;
+  if (p->precision == TLDA_BF16) return TLDA_ERR_UNIMPLEMENTED;
+  tlda_ctx *ctx = new tlda_ctx();
+  ctx->p = *p;
+  ctx->p.dim = D;
+  if (ctx->p.max_batch == 0) ctx->p.max_batch = 8192;
+  ctx->V = vocab;
+  ctx->D = D;
+  ctx->K = K;
+  ctx->Dp = round_up(D, 64);
+  ctx->Kp = round_up(K, 64);
+  ctx->Bmax = round_up(ctx->p.max_batch, 128);
+  ctx->ldT = ctx->Bmax + round_up(vocab, 128);
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  auto bail = [&](tlda_status s, const char *what, cudaError_t e) {
+    fprintf(stderr, "tlda_create: %s: %s\n", what, cudaGetErrorString(e));
+    tlda_destroy(ctx);
+    return s;
+  };
+  cudaError_t e;
+#define CA(call)                                                                            \
+  if ((e = (call)) != cudaSuccess)                                                          \
+    return bail(e == cudaErrorMemoryAllocation ? TLDA_ERR_OOM : TLDA_ERR_CUDA, #call, e);
+  CA(cudaGetDevice(&ctx->device));
+  CA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  CA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+  CA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+  CA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  const size_t V = vocab, Dp = ctx->Dp, Kp = ctx->Kp, Bm = ctx->Bmax;
+  const int tiles = (ctx->Dp / 64) * (ctx->Kp / 64);
+  ctx->nsplit = std::max(8, std::min(256, 2 * ctx->num_sms / tiles));
+  CA(dalloc(&ctx->W32, V * D, true));
+  CA(dalloc(&ctx->m1, Dp, true));
+  CA(dalloc(&ctx->U32, V * Dp, true));
+  CA(dalloc(&ctx->X32, Bm * Dp, true));
+  CA(dalloc(&ctx->Q32, V * Kp, true));
+  CA(dalloc(&ctx->Y32, Bm * Kp, true));
+  CA(dalloc(&ctx->Z32, Bm * Kp, true));
+  CA(dalloc(&ctx->Zc32, V * Kp, true));
+  CA(dalloc(&ctx->H32, V * Kp, true));
+  CA(dalloc(&ctx->cnt, V, true));
+  CA(dalloc(&ctx->widx, V, true));
+  CA(dalloc(&ctx->Gpart, (size_t)ctx->nsplit * Dp * Kp, true));
+  CA(dalloc(&ctx->Gram, Kp * Kp, true));
+  CA(dalloc(&ctx->avec, Kp, true));
+  CA(dalloc(&ctx->E, Dp * Kp, true));
+  CA(dalloc(&ctx->G3, Dp * Kp, true));
+  CA(dalloc(&ctx->st, 1, true));
+  CA(cudaMallocHost(reinterpret_cast<void **>(&ctx->st_host), sizeof(DevState)));
+  std::memset(ctx->st_host, 0, sizeof(DevState));
+  if (p->precision == TLDA_BF16) {
+    CA(dalloc(&ctx->U16, V * Dp, true));
+    CA(dalloc(&ctx->X16, Bm * Dp, true));
+    CA(dalloc(&ctx->AT16, Dp * (size_t)ctx->ldT, true));
+    CA(dalloc(&ctx->BT16, Kp * (size_t)ctx->ldT, true));
+  }
+#undef CA
+  CK(cudaDeviceSynchronize());
+  *out = ctx;
+  return TLDA_OK;
+}
+
+tlda_status tlda_destroy(tlda_ctx *ctx) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  if (ctx->stream || ctx->side) cudaDeviceSynchronize();
+  dfree(ctx->W32); dfree(ctx->m1); dfree(ctx->U32); dfree(ctx->U16);
+  dfree(ctx->X32); dfree(ctx->Q32); dfree(ctx->Y32); dfree(ctx->Z32); dfree(ctx->Zc32);
+  dfree(ctx->H32); dfree(ctx->cnt); dfree(ctx->widx); dfree(ctx->Gpart); dfree(ctx->Gram);
+  dfree(ctx->avec); dfree(ctx->E); dfree(ctx->G3); dfree(ctx->X16); dfree(ctx->AT16);
+  dfree(ctx->BT16); dfree(ctx->st); dfree(ctx->descs); dfree(ctx->P64); dfree(ctx->Ccnt);
+  dfree(ctx->TS); dfree(ctx->fit_err); dfree(ctx->stage[0]); dfree(ctx->stage[1]);
+  if (ctx->st_host) cudaFreeHost(ctx->st_host);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  delete ctx;
+  return TLDA_OK;
+}
+
+tlda_status tlda_sync(tlda_ctx *ctx) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  tlda_status s = read_state(ctx);
+  if (s != TLDA_OK) return s;
+  return take_sticky(ctx);
+}
+
+tlda_status tlda_set_whitening(tlda_ctx *ctx, const float *W, const float *m1) {
+  if (!ctx || !W || !m1) return fail(ctx, TLDA_ERR_INVALID, "NULL argument");
+  CK(cudaMemcpyAsync(ctx->W32, W, sizeof(float) * (size_t)ctx->V * ctx->D, cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  CK(cudaMemsetAsync(ctx->m1, 0, sizeof(float) * ctx->Dp, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->m1, m1, sizeof(float) * ctx->D, cudaMemcpyDeviceToDevice, ctx->stream));
+  launch_make_u(ctx->W32, ctx->m1, ctx->V, ctx->D, ctx->Dp, ctx->U32, ctx->U16, ctx->stream);
+  CKL();
+  ctx->eig.assign(ctx->D, 0.0);
+  ctx->whitened = true;
+  return TLDA_OK;
+}
+
+tlda_status tlda_get_whitening(const tlda_ctx *cctx, float *W, float *m1, double *eigvals) {
+  tlda_ctx *ctx = const_cast<tlda_ctx *>(cctx);
+  if (!ctx) return TLDA_ERR_INVALID;
+  if (!ctx->whitened) return fail(ctx, TLDA_ERR_STATE, "no whitening: fit or set one first");
+  if (W) CK(cudaMemcpyAsync(W, ctx->W32, sizeof(float) * (size_t)ctx->V * ctx->D, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (m1) CK(cudaMemcpyAsync(m1, ctx->m1, sizeof(float) * ctx->D, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (eigvals) std::memcpy(eigvals, ctx->eig.data(), sizeof(double) * ctx->D);
+  CK(cudaStreamSynchronize(ctx->stream));
+  return TLDA_OK;
+}
+
+tlda_status tlda_whiten_batch(tlda_ctx *ctx, const tlda_csr *batch, float *X_out) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  tlda_status s = check_csr(ctx, batch);
+  if (s) return s;
+  if (!X_out && batch->n_docs > 0) return fail(ctx, TLDA_ERR_INVALID, "X_out is NULL");
+  if (!ctx->whitened) return fail(ctx, TLDA_ERR_STATE, "no whitening: fit or set one first");
+  if (batch->n_docs > ctx->Bmax) return fail(ctx, TLDA_ERR_INVALID, "n_docs %d > max_batch %d", batch->n_docs, ctx->Bmax);
+  if (batch->n_docs == 0) return TLDA_OK;
+  launch_set_desc(ctx->st, desc_of(batch), ctx->stream);
+  StepArgs a = make_args(ctx);
+  launch_whiten(a, ctx->stream, X_out, false);
+  CKL();
+  return TLDA_OK;
+}
+
+static tlda_status step_common(tlda_ctx *ctx, const tlda_csr *batch, float *Phi, float lr,
+                               float *grad_out, double *loss_out, int mode, float *gdata_out,
+                               int64_t *S3_out) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  tlda_status s = check_csr(ctx, batch);
+  if (s) return s;
+  if (!Phi) return fail(ctx, TLDA_ERR_INVALID, "Phi is NULL");
+  if (!ctx->whitened) return fail(ctx, TLDA_ERR_STATE, "no whitening: fit or set one first");
+  if (batch->n_docs > ctx->Bmax) return fail(ctx, TLDA_ERR_INVALID, "n_docs %d > max_batch %d", batch->n_docs, ctx->Bmax);
+  StepArgs a = make_args(ctx);
+  a.lr = lr;
+  a.Phi = Phi;
+  a.grad_out = grad_out;
+  a.gdata_out = gdata_out;
+  a.mode = mode;
+  a.want_loss = loss_out ? 1 : 0;
+  launch_set_desc(ctx->st, desc_of(batch), ctx->stream);
+  CKL();
+  s = enqueue_step(ctx, a);
+  if (s) return s;
+  if (loss_out || mode == 1) {
+    s = read_state(ctx);
+    if (s) return s;
+    if (loss_out) *loss_out = ctx->st_host->loss;
+    if (S3_out) *S3_out = (int64_t)ctx->st_host->last_S3;
+    return take_sticky(ctx);
+  }
+  return TLDA_OK;
+}
+
+tlda_status tlda_cp_step(tlda_ctx *ctx, const tlda_csr *batch, float *Phi, float lr, float *grad_out,
+                         double *loss_out) {
+  return step_common(ctx, batch, Phi, lr, grad_out, loss_out, 0, nullptr, nullptr);
+}
+
+tlda_status tlda_cp_data_term(tlda_ctx *ctx, const tlda_csr *batch, const float *Phi, float *G_data_out,
+                              int64_t *S3_out) {
+  if (ctx && !G_data_out) return fail(ctx, TLDA_ERR_INVALID, "G_data_out is NULL");
+  return step_common(ctx, batch, const_cast<float *>(Phi), 0.f, nullptr, nullptr, 1, G_data_out, S3_out);
+}
+
+tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets,
+                         int32_t n_batches, float *Phi, float lr, uint32_t flags, double *loss_out) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  tlda_status s = check_csr(ctx, corpus);
+  if (s) return s;
+  if (!Phi || !batch_offsets || n_batches < 0) return fail(ctx, TLDA_ERR_INVALID, "bad pass arguments");
+  if (!ctx->whitened) return fail(ctx, TLDA_ERR_STATE, "no whitening: fit or set one first");
+  if (n_batches == 0) return TLDA_OK;
+  const bool host = flags & TLDA_HOST_INPUT;
+  for (int b = 0; b < n_batches; ++b) {
+    const int64_t d0 = batch_offsets[b], d1 = batch_offsets[b + 1];
+    if (d0 < 0 || d1 < d0 || d1 > corpus->n_docs) return fail(ctx, TLDA_ERR_INVALID, "batch_offsets[%d] out of range", b);
+    if (d1 - d0 > ctx->Bmax) return fail(ctx, TLDA_ERR_INVALID, "batch %d has %lld docs > max_batch", b, (long long)(d1 - d0));
+  }
+  // descriptors
+  if (ctx->descs_cap < n_batches) {
+    dfree(ctx->descs);
+    CK(dalloc(&ctx->descs, (size_t)n_batches));
+    ctx->descs_cap = n_batches;
+  }
+  std::vector<BatchDesc> hd(n_batches);
+  long long max_nnz = 0;
+  if (host) {
+    for (int b = 0; b < n_batches; ++b) {
+      const int64_t d0 = batch_offsets[b], d1 = batch_offsets[b + 1];
+      const long long lo = corpus->indptr[d0], hi = corpus->indptr[d1];
+      if (lo < 0 || hi < lo) return fail(ctx, TLDA_ERR_INVALID, "host indptr not monotone at batch %d", b);
+      max_nnz = std::max(max_nnz, hi - lo);
+    }
+    const long long need = (long long)(ctx->Bmax + 1) + 2 * max_nnz;
+    if (ctx->stage_cap < need) {
+      dfree(ctx->stage[0]);
+      dfree(ctx->stage[1]);
+      CK(dalloc(&ctx->stage[0], (size_t)need));
+      CK(dalloc(&ctx->stage[1], (size_t)need));
+      ctx->stage_cap = need;
+    }
+  }
+  for (int b = 0; b < n_batches; ++b) {
+    const int64_t d0 = batch_offsets[b], d1 = batch_offsets[b + 1];
+    BatchDesc d{};
+    d.n_docs = (int32_t)(d1 - d0);
+    if (host) {
+      int32_t *sg = ctx->stage[b & 1];
+      d.indptr = sg;
+      d.indices = sg + (ctx->Bmax + 1);
+      d.counts = sg + (ctx->Bmax + 1) + max_nnz;
+      d.nz_base = corpus->indptr[d0];
+    } else {
+      d.indptr = corpus->indptr + d0;
+      d.indices = corpus->indices;
+      d.counts = corpus->counts;
+      d.nz_base = 0;
+    }
+    hd[b] = d;
+  }
+  CK(cudaMemcpyAsync(ctx->descs, hd.data(), sizeof(BatchDesc) * n_batches, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));  // hd is pageable: keep it alive until copied
+  StepArgs a = make_args(ctx);
+  a.lr = lr;
+  a.Phi = Phi;
+  a.want_loss = loss_out ? 1 : 0;
+  double *losses = nullptr;
+  if (loss_out) CK(cudaMallocHost(reinterpret_cast<void **>(&losses), sizeof(double) * n_batches));
+  launch_begin_pass(ctx->st, ctx->descs, n_batches, ctx->stream);
+  CKL();
+  for (int b = 0; b < n_batches && s == TLDA_OK; ++b) {
+    if (host) {
+      // the slot was last read by step b-2; the stream orders the copy after it
+      const int64_t d0 = batch_offsets[b], d1 = batch_offsets[b + 1];
+      const long long lo = corpus->indptr[d0], hi = corpus->indptr[d1];
+      const BatchDesc &d = hd[b];
+      CK(cudaMemcpyAsync(const_cast<int32_t *>(d.indptr), corpus->indptr + d0, sizeof(int32_t) * (d1 - d0 + 1),
+                         cudaMemcpyHostToDevice, ctx->stream));
+      if (hi > lo) {
+        CK(cudaMemcpyAsync(const_cast<int32_t *>(d.indices), corpus->indices + lo, sizeof(int32_t) * (hi - lo),
+                           cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(const_cast<int32_t *>(d.counts), corpus->counts + lo, sizeof(int32_t) * (hi - lo),
+                           cudaMemcpyHostToDevice, ctx->stream));
+      }
+    }
+    s = enqueue_step(ctx, a);
+    if (loss_out && s == TLDA_OK)
+      CK(cudaMemcpyAsync(losses + b, &ctx->st->loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (s) {
+    if (losses) cudaFreeHost(losses);
+    return s;
+  }
+  s = read_state(ctx);
+  if (s == TLDA_OK) {
+    if (loss_out) std::memcpy(loss_out, losses, sizeof(double) * n_batches);
+    s = take_sticky(ctx);
+  }
+  if (losses) cudaFreeHost(losses);
+  return s;
+}
+
+tlda_status tlda_save_state(const tlda_ctx *cctx, const char *path) {
+  tlda_ctx *ctx = const_cast<tlda_ctx *>(cctx);
+  if (!ctx || !path) return TLDA_ERR_INVALID;
+  if (!ctx->whitened) return fail(ctx, TLDA_ERR_STATE, "nothing to save: no whitening");
+  std::vector<float> W((size_t)ctx->V * ctx->D), m1(ctx->D);
+  std::vector<unsigned long long> C(ctx->V, 0), TS(3, 0);
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(W.data(), ctx->W32, sizeof(float) * W.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(m1.data(), ctx->m1, sizeof(float) * ctx->D, cudaMemcpyDeviceToHost));
+  if (ctx->Ccnt) CK(cudaMemcpy(C.data(), ctx->Ccnt, sizeof(unsigned long long) * ctx->V, cudaMemcpyDeviceToHost));
+  if (ctx->TS) CK(cudaMemcpy(TS.data(), ctx->TS, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost));
+  FILE *f = fopen(path, "wb");
+  if (!f) return fail(ctx, TLDA_ERR_INVALID, "cannot open %s for writing", path);
+  uint32_t hdr[4] = {kStateMagic, kStateVersion, (uint32_t)ctx->V, (uint32_t)ctx->D};
+  uint32_t crc = 0;
+  auto put = [&](const void *p, size_t n) {
+    fwrite(p, 1, n, f);
+    crc = crc32_update(crc, p, n);
+  };
+  put(hdr, sizeof hdr);
+  put(W.data(), sizeof(float) * W.size());
+  put(m1.data(), sizeof(float) * m1.size());
+  put(ctx->eig.data(), sizeof(double) * ctx->D);
+  put(C.data(), sizeof(unsigned long long) * C.size());
+  put(TS.data(), sizeof(unsigned long long) * 3);
+  fwrite(&crc, sizeof crc, 1, f);
+  const bool ok = fflush(f) == 0;
+  fclose(f);
+  return ok ? TLDA_OK : fail(ctx, TLDA_ERR_INVALID, "write to %s failed", path);
+}
+
+tlda_status tlda_load_state(tlda_ctx *ctx, const char *path) {
+  if (!ctx || !path) return TLDA_ERR_INVALID;
+  FILE *f = fopen(path, "rb");
+  if (!f) return fail(ctx, TLDA_ERR_INVALID, "cannot open %s", path);
+  std::vector<unsigned char> buf;
+  unsigned char tmp[65536];
+  size_t n;
+  while ((n = fread(tmp, 1, sizeof tmp, f)) > 0) buf.insert(buf.end(), tmp, tmp + n);
+  fclose(f);
+  const size_t nW = (size_t)ctx->V * ctx->D;
+  const size_t body = 16 + 4 * nW + 4 * ctx->D + 8 * ctx->D + 8 * (size_t)ctx->V + 24;
+  if (buf.size() != body + 4) return fail(ctx, TLDA_ERR_INVALID, "state file size mismatch");
+  uint32_t hdr[4], crc;
+  std::memcpy(hdr, buf.data(), 16);
+  std::memcpy(&crc, buf.data() + body, 4);
+  if (hdr[0] != kStateMagic || hdr[1] != kStateVersion) return fail(ctx, TLDA_ERR_INVALID, "not a tlda state file");
+  if ((int)hdr[2] != ctx->V || (int)hdr[3] != ctx->D) return fail(ctx, TLDA_ERR_INVALID, "state V/D mismatch");
+  if (crc32_update(0, buf.data(), body) != crc) return fail(ctx, TLDA_ERR_INVALID, "state CRC mismatch");
+  const unsigned char *p = buf.data() + 16;
+  float *dW = nullptr, *dm = nullptr;
+  CK(dalloc(&dW, nW));
+  CK(dalloc(&dm, ctx->D));
+  CK(cudaMemcpy(dW, p, 4 * nW, cudaMemcpyHostToDevice));
+  p += 4 * nW;
+  CK(cudaMemcpy(dm, p, 4 * ctx->D, cudaMemcpyHostToDevice));
+  p += 4 * ctx->D;
+  tlda_status s = tlda_set_whitening(ctx, dW, dm);
+  CK(cudaStreamSynchronize(ctx->stream));
+  cudaFree(dW);
+  cudaFree(dm);
+  if (s) return s;
+  std::memcpy(ctx->eig.data(), p, 8 * ctx->D);
+  p += 8 * ctx->D;
+  if (!ctx->Ccnt) CK(dalloc(&ctx->Ccnt, ctx->V, true));
+  if (!ctx->TS) CK(dalloc(&ctx->TS, 3, true));
+  CK(cudaMemcpy(ctx->Ccnt, p, 8 * (size_t)ctx->V, cudaMemcpyHostToDevice));
+  p += 8 * (size_t)ctx->V;
+  CK(cudaMemcpy(ctx->TS, p, 24, cudaMemcpyHostToDevice));
+  ctx->fitted = true;
+  return TLDA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// Internal declarations of libtlda: device-side state, batch descriptors,
+// the context workspace and the kernel launchers shared by the .cu files.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "tlda.h"
+
+namespace tlda {
+
+constexpr int kMaxDim = 512;     // D and K are padded to multiples of 64, at most 512
+constexpr int kErrCsr = 1;       // sticky device error bits
+constexpr int kErrTimeout = 2;
+constexpr int kDocsPerBlock = 16; // whitening: one warp per document
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// One batch of documents as the kernels see it.  Nonzero j of the batch (an
+// absolute offset read from indptr) lives at indices[j - nz_base].
+struct BatchDesc {
+  const int32_t *indptr;
+  const int32_t *indices;
+  const int32_t *counts;
+  long long nz_base;
+  int32_t n_docs;
+  int32_t pad;
+};
+
+// Device-resident per-context state of the CP step.  Every step kernel reads
+// the current batch from `cur`, so one step sequence (or a captured graph of
+// it) can be replayed over a whole pass: the last block of the reduction
+// kernel advances `cur` to descs[pass_pos] and clears the per-step sums.
+struct DevState {
+  BatchDesc cur;
+  const BatchDesc *descs;        // pass descriptors (device) or null
+  int32_t n_descs;
+  int32_t pass_pos;              // next descriptor of the pass
+  int32_t step;                  // steps completed on this context
+  int32_t err;                   // sticky error bits (kErr*)
+  unsigned int ticket;           // last-block ticket of the reduction kernel
+  int32_t n_touched;             // distinct words of the current batch
+  unsigned long long S3;         // sum_d L(L-1)(L-2) of the current batch
+  unsigned long long last_S3;    // S3 of the last completed step
+  double loss_data;              // sum_d sum_i (y^3 - 3 y r) + 2 sum_m c_m sum_i q^3
+  double loss_phi;               // (1+theta)/2 sum G^3 - sum_i (3 a_i |phi_i|^2 - 2 a_i^3)
+  double loss;                   // loss of the last completed step
+};
+
+// Kernel-side view of the workspace for one CP step.
+struct StepArgs {
+  int V, D, K, Dp, Kp, Bmax;
+  int nsplit;                    // partial sums of the data-term reduction
+  float theta, lr;
+  double c3;
+  int same_token, want_loss, mode;   // mode 0: update Phi; 1: data term only
+  DevState *st;
+  // whitening (U = W - 1 m1^T, padded to Dp columns)
+  const float *U32;              // V x Dp
+  const float *m1;               // Dp
+  // FP32 work
+  float *X32;                    // Bmax x Dp
+  float *Q32;                    // V x Kp   (rows of the batch's words only)
+  float *Y32;                    // Bmax x Kp
+  float *Z32;                    // Bmax x Kp: Y*Y - R
+  float *Zc32;                   // V x Kp: compact rows Q*(2cQ - 2H) of the touched words
+  float *H32;                    // V x Kp, zero between steps
+  int *cnt;                      // V, zero between steps (c_m = sum_d f_dm)
+  int *widx;                     // V: touched words of the batch, compact
+  float *Gpart;                  // nsplit x Dp x Kp
+  float *Gram;                   // Kp x Kp: Phi^T Phi
+  float *avec;                   // Kp: m1^T Phi
+  float *E;                      // Dp x Kp: 3(1+theta) P - 3 G3
+  float *G3;                     // Dp x Kp
+  // BF16 tensor-core work
+  const __nv_bfloat16 *U16;      // V x Dp
+  __nv_bfloat16 *X16;            // Bmax x Dp
+  __nv_bfloat16 *AT16;           // Dp x ldT: X^T (docs) then U^T (touched words)
+  __nv_bfloat16 *BT16;           // Kp x ldT: Z^T (docs) then Zc^T (touched words)
+  int ldT;                       // Bmax + V rounded up
+  int precision;
+  // caller buffers
+  float *Phi;                    // D x K (user layout), updated in place
+  float *grad_out;               // D x K or null
+  float *gdata_out;              // D x K or null (mode 1)
+};
+
+}  // namespace tlda
+
+struct tlda_ctx {
+  int V = 0, D = 0, K = 0, Dp = 0, Kp = 0, Bmax = 0, ldT = 0;
+  tlda_params p{};
+  cudaStream_t stream = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int device = 0, num_sms = 0;
+  std::string err;
+  bool whitened = false;
+  // whitening state
+  float *W32 = nullptr;          // V x D (as set/fitted)
+  float *m1 = nullptr;           // Dp (zero padded)
+  float *U32 = nullptr;          // V x Dp
+  __nv_bfloat16 *U16 = nullptr;  // V x Dp
+  std::vector<double> eig;       // D eigenvalues (host copy)
+  // step workspace
+  float *X32 = nullptr, *Q32 = nullptr, *Y32 = nullptr, *Z32 = nullptr, *Zc32 = nullptr;
+  float *H32 = nullptr;
+  int *cnt = nullptr, *widx = nullptr;
+  float *Gpart = nullptr, *Gram = nullptr, *avec = nullptr, *E = nullptr, *G3 = nullptr;
+  int nsplit = 0;
+  __nv_bfloat16 *X16 = nullptr, *AT16 = nullptr, *BT16 = nullptr;
+  tlda::DevState *st = nullptr;
+  tlda::DevState *st_host = nullptr;   // pinned mirror for reads
+  tlda::BatchDesc *descs = nullptr;    // pass descriptors (device)
+  int descs_cap = 0;
+  // fit state
+  double *P64 = nullptr;               // V x V pair counts (allocated on first ACCUMULATE)
+  unsigned long long *Ccnt = nullptr;  // V word totals
+  unsigned long long *TS = nullptr;    // T, S2, S3 of the fit
+  int *fit_err = nullptr;
+  bool fit_open = false, fitted = false;
+  // pass staging (host input)
+  int32_t *stage[2] = {nullptr, nullptr};
+  long long stage_cap = 0;
+};
+
+namespace tlda {
+// k_step.cu
+void launch_set_desc(DevState *st, const BatchDesc &b, cudaStream_t s);
+void launch_begin_pass(DevState *st, const BatchDesc *descs, int n, cudaStream_t s);
+void launch_whiten(const StepArgs &a, cudaStream_t s, float *X_out, bool stats);
+void launch_phi_terms(const StepArgs &a, cudaStream_t s);
+void launch_chain_f32(const StepArgs &a, cudaStream_t s);
+void launch_reduce_update(const StepArgs &a, cudaStream_t s);
+void launch_make_u(const float *W, const float *m1, int V, int D, int Dp, float *U32,
+                   __nv_bfloat16 *U16, cudaStream_t s);
+// k_tc.cu
+void launch_chain_bf16(const StepArgs &a, cudaStream_t s);
+}  // namespace tlda

@@ -1,0 +1,268 @@
+"""Python binding of libtlda (include/tlda.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; this module
+passes pointers of torch CUDA tensors (and numpy host arrays) through ctypes.
+There is no fallback: if libtlda.so cannot be built or loaded, importing this
+module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _build
+
+# ---------------------------------------------------------------------------- library
+_LIB = None
+
+OK, ERR_INVALID, ERR_CUDA, ERR_NUMERIC, ERR_TIMEOUT, ERR_OOM, ERR_STATE, ERR_UNIMPLEMENTED = range(8)
+FP32, BF16 = 0, 1
+ACCUMULATE, FINALIZE = 1, 2
+HOST_INPUT = 1
+HOST_OUTPUT = 1
+
+STATUS_NAMES = {OK: "TLDA_OK", ERR_INVALID: "TLDA_ERR_INVALID", ERR_CUDA: "TLDA_ERR_CUDA",
+                ERR_NUMERIC: "TLDA_ERR_NUMERIC", ERR_TIMEOUT: "TLDA_ERR_TIMEOUT",
+                ERR_OOM: "TLDA_ERR_OOM", ERR_STATE: "TLDA_ERR_STATE",
+                ERR_UNIMPLEMENTED: "TLDA_ERR_UNIMPLEMENTED"}
+
+#: every entry point declared in include/tlda.h
+ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last_error",
+                "tlda_sync", "tlda_fit_moments", "tlda_get_whitening", "tlda_get_counts",
+                "tlda_set_whitening", "tlda_whiten_batch", "tlda_cp_step",
+                "tlda_cp_data_term", "tlda_cp_pass", "tlda_unwhiten_topics",
+                "tlda_save_state", "tlda_load_state")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("dim", ctypes.c_int32), ("alpha0", ctypes.c_double),
+                ("theta", ctypes.c_float), ("precision", ctypes.c_int32),
+                ("same_token_correction", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("max_batch", ctypes.c_int32)]
+
+
+class CSR(ctypes.Structure):
+    _fields_ = [("n_docs", ctypes.c_int32), ("vocab", ctypes.c_int32),
+                ("indptr", ctypes.c_void_p), ("indices", ctypes.c_void_p),
+                ("counts", ctypes.c_void_p)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Builds (if stale) and loads libtlda.so; raises if either fails."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libtlda.so not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, f32, f64, u32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                   ctypes.c_float, ctypes.c_double, ctypes.c_uint32)
+    P = ctypes.POINTER
+    sig = {
+        "tlda_default_params": (None, [P(Params), i32]),
+        "tlda_create": (i32, [P(vp), i32, P(Params), vp]),
+        "tlda_destroy": (i32, [vp]),
+        "tlda_last_error": (ctypes.c_char_p, [vp]),
+        "tlda_sync": (i32, [vp]),
+        "tlda_fit_moments": (i32, [vp, P(CSR), u32]),
+        "tlda_get_whitening": (i32, [vp, vp, vp, vp]),
+        "tlda_get_counts": (i32, [vp, vp, vp, vp, vp]),
+        "tlda_set_whitening": (i32, [vp, vp, vp]),
+        "tlda_whiten_batch": (i32, [vp, P(CSR), vp]),
+        "tlda_cp_step": (i32, [vp, P(CSR), vp, f32, vp, vp]),
+        "tlda_cp_data_term": (i32, [vp, P(CSR), vp, vp, vp]),
+        "tlda_cp_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, u32, vp]),
+        "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
+        "tlda_save_state": (i32, [vp, ctypes.c_char_p]),
+        "tlda_load_state": (i32, [vp, ctypes.c_char_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class TLDAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+# ---------------------------------------------------------------------------- data
+@dataclass
+class DeviceCSR:
+    """A batch/corpus CSR whose arrays live in torch int32 tensors (CUDA, or
+    pinned host memory for host-input passes)."""
+    indptr: torch.Tensor
+    indices: torch.Tensor
+    counts: torch.Tensor
+    vocab: int
+
+    @property
+    def n_docs(self) -> int:
+        return self.indptr.numel() - 1
+
+    @staticmethod
+    def from_arrays(indptr, indices, counts, vocab, device="cuda", pin=False) -> "DeviceCSR":
+        def t(a):
+            x = torch.as_tensor(np.ascontiguousarray(np.asarray(a, dtype=np.int32)))
+            if device == "cpu":
+                return x.pin_memory() if pin else x
+            return x.to(device)
+        return DeviceCSR(t(indptr), t(indices), t(counts), int(vocab))
+
+    @staticmethod
+    def from_corpus(c, device="cuda", pin=False) -> "DeviceCSR":
+        if int(c.indptr[-1]) >= 2 ** 31:
+            raise ValueError("corpus too large for int32 offsets")
+        return DeviceCSR.from_arrays(c.indptr, c.indices, c.counts, c.V, device=device, pin=pin)
+
+    def struct(self) -> CSR:
+        return CSR(self.n_docs, self.vocab, self.indptr.data_ptr(),
+                   self.indices.data_ptr() if self.indices.numel() else 0,
+                   self.counts.data_ptr() if self.counts.numel() else 0)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+# ---------------------------------------------------------------------------- context
+class TLDA:
+    """A libtlda context: vocabulary size V, K topics, whitening dimension D."""
+
+    def __init__(self, vocab: int, k: int, dim: int = 0, alpha0: float = 1.0, theta: float = 0.0,
+                 precision: str = "fp32", same_token: bool = True, seed: int = 0,
+                 max_batch: int = 8192, stream: torch.cuda.Stream | None = None):
+        self.lib = load()
+        p = Params()
+        self.lib.tlda_default_params(ctypes.byref(p), int(k))
+        p.dim, p.alpha0, p.theta = int(dim), float(alpha0), float(theta)
+        p.precision = BF16 if precision == "bf16" else FP32
+        p.same_token_correction = 1 if same_token else 0
+        p.seed, p.max_batch = int(seed), int(max_batch)
+        self.params = p
+        self.V, self.K = int(vocab), int(k)
+        self.D = int(dim) if dim else int(k)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = self.lib.tlda_create(ctypes.byref(h), int(vocab), ctypes.byref(p),
+                                  ctypes.c_void_p(self.stream.cuda_stream))
+        if st != OK:
+            raise TLDAError(st, "tlda_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tlda_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != OK:
+            raise TLDAError(st, self.lib.tlda_last_error(self.h).decode())
+
+    # ------------------------------------------------------------ moments
+    def fit_moments(self, chunk: DeviceCSR | None, flags: int):
+        s = chunk.struct() if chunk is not None else None
+        self._check(self.lib.tlda_fit_moments(self.h, ctypes.byref(s) if s is not None else None,
+                                              int(flags)))
+
+    def fit(self, chunks) -> None:
+        for c in chunks:
+            self.fit_moments(c, ACCUMULATE)
+        self.fit_moments(None, FINALIZE)
+
+    def get_whitening(self):
+        W = torch.empty((self.V, self.D), dtype=torch.float32, device="cuda")
+        m1 = torch.empty(self.D, dtype=torch.float32, device="cuda")
+        ev = np.zeros(self.D, dtype=np.float64)
+        self._check(self.lib.tlda_get_whitening(self.h, W.data_ptr(), m1.data_ptr(),
+                                                ev.ctypes.data))
+        return W, m1, ev
+
+    def get_counts(self):
+        C = np.zeros(self.V, dtype=np.int64)
+        T, S2, S3 = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.tlda_get_counts(self.h, C.ctypes.data, ctypes.byref(T),
+                                             ctypes.byref(S2), ctypes.byref(S3)))
+        return C, T.value, S2.value, S3.value
+
+    def set_whitening(self, W: torch.Tensor, m1: torch.Tensor):
+        W = W.to(device="cuda", dtype=torch.float32).contiguous()
+        m1 = m1.to(device="cuda", dtype=torch.float32).contiguous()
+        assert W.shape == (self.V, self.D) and m1.shape == (self.D,)
+        self._check(self.lib.tlda_set_whitening(self.h, W.data_ptr(), m1.data_ptr()))
+        self.stream.synchronize()
+
+    # ------------------------------------------------------------ hot path
+    def whiten_batch(self, batch: DeviceCSR, out: torch.Tensor | None = None) -> torch.Tensor:
+        X = out if out is not None else torch.empty((batch.n_docs, self.D), dtype=torch.float32,
+                                                    device="cuda")
+        s = batch.struct()
+        self._check(self.lib.tlda_whiten_batch(self.h, ctypes.byref(s), _ptr(X)))
+        return X
+
+    def cp_step(self, batch: DeviceCSR, Phi: torch.Tensor, lr: float, grad: torch.Tensor | None = None,
+                want_loss: bool = False):
+        """One CP-SGD step in place on Phi (D x K float32 CUDA). Returns the
+        loss at the incoming Phi if want_loss (then the call synchronises)."""
+        assert Phi.dtype == torch.float32 and Phi.is_cuda and Phi.is_contiguous()
+        s = batch.struct()
+        loss = ctypes.c_double()
+        self._check(self.lib.tlda_cp_step(self.h, ctypes.byref(s), Phi.data_ptr(), float(lr),
+                                          _ptr(grad), ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def cp_data_term(self, batch: DeviceCSR, Phi: torch.Tensor):
+        G = torch.empty((self.D, self.K), dtype=torch.float32, device="cuda")
+        S3 = ctypes.c_int64()
+        s = batch.struct()
+        self._check(self.lib.tlda_cp_data_term(self.h, ctypes.byref(s), Phi.data_ptr(),
+                                               G.data_ptr(), ctypes.byref(S3)))
+        return G, S3.value
+
+    def cp_pass(self, corpus: DeviceCSR, batch_offsets, Phi: torch.Tensor, lr: float,
+                host_input: bool = False, losses: bool = False):
+        off = np.ascontiguousarray(np.asarray(batch_offsets, dtype=np.int64))
+        nb = len(off) - 1
+        out = np.zeros(max(nb, 1), dtype=np.float64) if losses else None
+        s = corpus.struct()
+        self._check(self.lib.tlda_cp_pass(self.h, ctypes.byref(s), off.ctypes.data, nb,
+                                          Phi.data_ptr(), float(lr),
+                                          HOST_INPUT if host_input else 0,
+                                          out.ctypes.data if losses else None))
+        return out[:nb] if losses else None
+
+    def sync(self):
+        self._check(self.lib.tlda_sync(self.h))
+
+    # ------------------------------------------------------------ recovery / state
+    def unwhiten_topics(self, Phi: torch.Tensor):
+        mu = np.zeros((self.V, self.K), dtype=np.float64)
+        al = np.zeros(self.K, dtype=np.float64)
+        self._check(self.lib.tlda_unwhiten_topics(self.h, Phi.data_ptr(), mu.ctypes.data,
+                                                  al.ctypes.data, HOST_OUTPUT))
+        return mu, al
+
+    def save_state(self, path: str):
+        self._check(self.lib.tlda_save_state(self.h, str(path).encode()))
+
+    def load_state(self, path: str):
+        self._check(self.lib.tlda_load_state(self.h, str(path).encode()))

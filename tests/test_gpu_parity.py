@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle, on
+seeded synthetic corpora.  Tolerances: relative Frobenius error 1e-5 for the
+FP32 form; integer statistics bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import tlda_synth as ts
+from oracle import tlda_oracle as O
+from tests import _cases as C
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+
+def _ctx(lib, name, precision="fp32", same_token=True, dim=0, theta=0.0, max_batch=8192, W=None):
+    sp = ts.WORKLOADS[name]
+    t = lib.TLDA(sp.V, sp.K, dim=dim, alpha0=float(sp.alpha0), theta=theta, precision=precision,
+                 same_token=same_token, max_batch=max_batch)
+    if W is None:
+        W, m1 = C.population_whitening(name)
+    else:
+        W, m1 = W
+    t.set_whitening(torch.tensor(W, dtype=torch.float32), torch.tensor(m1, dtype=torch.float32))
+    return t, W, m1
+
+
+def _phi0(sp, D=None):
+    D = D or sp.K
+    return ts.initial_factors(sp.seed + 1, D, sp.K)
+
+
+def _oracle_grad(batch, sp, W, m1, Phi, theta=0.0, same_token=True):
+    return O.cp_grad_implicit(batch.indptr, batch.indices, batch.counts, sp.V, W, m1, Phi,
+                              float(sp.alpha0), theta, same_token)
+
+
+# ----------------------------------------------------------------------------- whitening
+@pytest.mark.parametrize("name,n", [("small_v500_k10", 1000), ("stream_v20k_k100", 3001)])
+def test_whiten_batch(lib, name, n):
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name)
+    c = C.corpus(name, n)
+    X = t.whiten_batch(lib.DeviceCSR.from_corpus(c)).cpu().numpy()
+    F = O.csr_matrix(c.indptr, c.indices, c.counts, sp.V)
+    Xo = F @ W - c.lengths[:, None].astype(np.float64) * m1[None, :]
+    assert C.rel(X, Xo) < TOL32
+    t.sync()
+
+
+# ----------------------------------------------------------------------------- data term / step
+@pytest.mark.parametrize("name,n", [("small_v500_k10", 1000), ("small_v500_k10", 37),
+                                    ("tweet_v5k_k50", 2048), ("stream_v20k_k100", 4099)])
+def test_data_term_fp32(lib, name, n):
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name)
+    c = C.corpus(name, n)
+    Phi = _phi0(sp)
+    G, S3 = t.cp_data_term(lib.DeviceCSR.from_corpus(c), torch.tensor(Phi, dtype=torch.float32, device="cuda"))
+    g = _oracle_grad(c, sp, W, m1, Phi)
+    assert S3 == g["S3"]
+    assert C.rel(G.cpu().numpy(), g["G_data"]) < TOL32
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.5])
+@pytest.mark.parametrize("same_token", [True, False])
+def test_cp_step_fp32(lib, theta, same_token):
+    name = "small_v500_k10"
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name, theta=theta, same_token=same_token)
+    c = C.corpus(name, 1000)
+    Phi0 = _phi0(sp)
+    Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(Phi)
+    lr = 0.01
+    loss = t.cp_step(lib.DeviceCSR.from_corpus(c), Phi, lr, grad=grad, want_loss=True)
+    g = _oracle_grad(c, sp, W, m1, Phi0, theta, same_token)
+    assert C.rel(grad.cpu().numpy(), g["grad"]) < TOL32
+    assert C.rel(Phi.cpu().numpy(), Phi0 - lr * g["grad"]) < TOL32
+    assert abs(loss - g["loss"]) <= TOL32 * abs(g["loss"])
+
+
+def test_ragged_and_tiny_batches(lib):
+    name = "tweet_v5k_k50"
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name, max_batch=600)
+    c = C.corpus(name, 700)
+    Phi0 = _phi0(sp)
+    for d0, d1 in [(0, 1), (1, 8), (8, 137), (137, 737 - 137), (100, 600)]:
+        b = c.rows(d0, min(d1, c.n_docs))
+        G, S3 = t.cp_data_term(lib.DeviceCSR.from_corpus(b), torch.tensor(Phi0, dtype=torch.float32, device="cuda"))
+        g = _oracle_grad(b, sp, W, m1, Phi0)
+        assert S3 == g["S3"]
+        assert C.rel(G.cpu().numpy(), g["G_data"]) < TOL32, (d0, d1)
+
+
+def test_short_documents_and_empty_batch_are_noops(lib):
+    name = "small_v500_k10"
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name)
+    Phi0 = _phi0(sp)
+    Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+    grad = torch.ones_like(Phi)
+    short = lib.DeviceCSR.from_arrays([0, 1, 3, 3, 4], [5, 1, 7, 9], [2, 1, 1, 1], sp.V)  # L = 2,2,0,1
+    loss = t.cp_step(short, Phi, 0.1, grad=grad, want_loss=True)
+    assert loss == 0.0 and torch.all(grad == 0) and np.array_equal(Phi.cpu().numpy(), Phi0.astype(np.float32))
+    empty = lib.DeviceCSR.from_arrays([0], [], [], sp.V)
+    t.cp_step(empty, Phi, 0.1, want_loss=True)
+    assert np.array_equal(Phi.cpu().numpy(), Phi0.astype(np.float32))
+
+
+@pytest.mark.parametrize("corrupt", ["index_ge_V", "count_zero", "not_ascending", "indptr_decreasing"])
+def test_corrupt_batch_is_rejected_and_phi_kept(lib, corrupt):
+    name = "small_v500_k10"
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name)
+    c = C.corpus(name, 50)
+    indptr, indices, counts = c.indptr.copy(), c.indices.copy(), c.counts.copy()
+    j = int(indptr[10]) + 1
+    if corrupt == "index_ge_V":
+        indices[j] = sp.V + 3
+    elif corrupt == "count_zero":
+        counts[j] = 0
+    elif corrupt == "not_ascending":
+        indices[j], indices[j + 1] = indices[j + 1], indices[j]
+    else:
+        indptr[11], indptr[12] = indptr[12], indptr[11]   # stays within [0, nnz]
+    Phi0 = _phi0(sp)
+    Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+    b = lib.DeviceCSR.from_arrays(indptr, indices, counts, sp.V)
+    t.cp_step(b, Phi, 0.1)
+    with pytest.raises(lib.TLDAError) as ei:
+        t.sync()
+    assert ei.value.status == lib.ERR_INVALID
+    assert np.array_equal(Phi.cpu().numpy(), Phi0.astype(np.float32))
+    # the error is cleared by the synchronising call; a good batch works again
+    t.cp_step(lib.DeviceCSR.from_corpus(c), Phi, 0.1)
+    t.sync()
+
+
+def test_whitening_dimension_above_topics(lib):
+    """D > K: the whitening of the empirical M2 of the small workload to D = 16."""
+    name = "small_v500_k10"
+    sp = ts.WORKLOADS[name]
+    c = C.corpus(name, 4000)
+    st = O.ingest(c.indptr, c.indices, c.counts, sp.V)
+    M1 = O.first_moment(st["C"], st["T"])
+    M2 = O.second_moment(O.pair_counts(c.indptr, c.indices, c.counts, sp.V), st["S2"], M1, 1.0)
+    Wd, _, _ = O.whitening(M2, 16)
+    W = Wd.astype(np.float32).astype(np.float64)
+    m1 = (W.T @ M1).astype(np.float32).astype(np.float64)
+    t, _, _ = _ctx(lib, name, dim=16, W=(W, m1))
+    Phi0 = ts.initial_factors(7, 16, sp.K)
+    b = c.rows(0, 1000)
+    G, S3 = t.cp_data_term(lib.DeviceCSR.from_corpus(b), torch.tensor(Phi0, dtype=torch.float32, device="cuda"))
+    g = O.cp_grad_implicit(b.indptr, b.indices, b.counts, sp.V, W, m1, Phi0, 1.0, 0.0)
+    assert C.rel(G.cpu().numpy(), g["G_data"]) < TOL32
+
+
+# ----------------------------------------------------------------------------- pass
+@pytest.mark.parametrize("host_input", [False, True])
+def test_pass_equals_sequential_oracle_steps(lib, host_input):
+    name = "tweet_v5k_k50"
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name, max_batch=1024)
+    c = C.corpus(name, 3000)
+    offs = [0, 700, 1024 + 700, 1724, 2500, 3000]
+    Phi0 = _phi0(sp)
+    Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+    corpus = lib.DeviceCSR.from_corpus(c, device="cpu" if host_input else "cuda", pin=host_input)
+    lr = 0.002
+    losses = t.cp_pass(corpus, offs, Phi, lr, host_input=host_input, losses=True)
+    P = Phi0.copy()
+    for b in range(len(offs) - 1):
+        r = c.rows(offs[b], offs[b + 1])
+        P, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, lr, float(sp.alpha0), 0.0)
+        assert abs(losses[b] - g["loss"]) <= 1e-5 * abs(g["loss"]), b
+    assert C.rel(Phi.cpu().numpy(), P) < TOL32
+
+
+# ----------------------------------------------------------------------------- moments
+def test_fit_moments_small(lib):
+    name = "small_v500_k10"
+    sp = ts.WORKLOADS[name]
+    c = C.corpus(name, sp.n_docs)
+    t = lib.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), seed=3)
+    for d0 in range(0, c.n_docs, 3000):
+        t.fit_moments(lib.DeviceCSR.from_corpus(c.rows(d0, min(d0 + 3000, c.n_docs))), lib.ACCUMULATE)
+    t.fit_moments(None, lib.FINALIZE)
+    Cg, T, S2, S3 = t.get_counts()
+    st = O.ingest(c.indptr, c.indices, c.counts, sp.V)
+    assert np.array_equal(Cg, st["C"]) and (T, S2, S3) == (st["T"], st["S2"], st["S3"])
+    Wg, m1g, lam_g = t.get_whitening()
+    Wg = Wg.cpu().numpy().astype(np.float64)
+    M1 = O.first_moment(st["C"], st["T"])
+    M2 = O.second_moment(O.pair_counts(c.indptr, c.indices, c.counts, sp.V), st["S2"], M1, 1.0)
+    Wo, Uo, lam_o = O.whitening(M2, sp.K)
+    assert np.allclose(lam_g, lam_o, rtol=1e-6)
+    assert C.rel(Wg.T @ M2 @ Wg, np.eye(sp.K)) < 1e-5
+    # same subspace and same signed eigenvectors (eigengap here is well above 1e-6 lambda_1)
+    assert C.rel(Wg, Wo) < 1e-4
+    assert C.rel(m1g.cpu().numpy(), Wo.T @ M1) < 1e-4
+
+
+def test_unwhiten_population_factors(lib):
+    name = "small_v500_k10"
+    sp = ts.WORKLOADS[name]
+    _, mu = C.topics(name)
+    h = np.full(sp.K, 1.0 / sp.K)
+    t, W, m1 = _ctx(lib, name)
+    Phi = O.population_factors(mu, h, W).astype(np.float32).astype(np.float64)
+    mu_g, al_g = t.unwhiten_topics(torch.tensor(Phi, dtype=torch.float32, device="cuda"))
+    mu_o, al_o = O.unwhiten_cp(Phi, W)
+    mu_o, _ = O.clip_normalise(mu_o)
+    assert C.rel(mu_g, mu_o) < 1e-6
+    assert C.rel(al_g, al_o) < 1e-6
+    perm, l1, _ = O.match_topics(mu_g, mu)
+    assert l1.max() < 1e-3
+
+
+def test_state_roundtrip(lib, tmp_path):
+    name = "small_v500_k10"
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name)
+    p = tmp_path / "state.bin"
+    t.save_state(str(p))
+    t2 = lib.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0))
+    t2.load_state(str(p))
+    W2, m12, _ = t2.get_whitening()
+    assert np.array_equal(W2.cpu().numpy(), W.astype(np.float32))
+    raw = bytearray(p.read_bytes())
+    raw[100] ^= 0xFF
+    p.write_bytes(bytes(raw))
+    with pytest.raises(lib.TLDAError):
+        t2.load_state(str(p))
