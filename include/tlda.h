@@ -210,6 +210,20 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
 tlda_status tlda_unwhiten_topics(tlda_ctx *ctx, const float *Phi, double *mu_out,
                                  double *alpha_out, uint32_t flags);
 
+/* ------------------------------------------------------------ profiling */
+
+/* Per-kernel device time, from CUDA events recorded around each launch on
+ * the stream it is launched on.  Kernels of one CP step, in launch order:
+ *   0 scan_whiten  1 compact  2 qy  3 rz  4 zh  5 g_reduce  6 reduce_update
+ *   7 phi_gram  8 phi_terms (7 and 8 run on the context's side stream).
+ * tlda_profile sets the mask of bracketed kernels (bit i = kernel i; 0 turns
+ * profiling off) and clears the totals.  tlda_profile_read synchronises and
+ * returns the kernel's name (static string), launch count and summed
+ * milliseconds since the last tlda_profile; TLDA_ERR_INVALID past the last id. */
+tlda_status tlda_profile(tlda_ctx *ctx, uint32_t mask);
+tlda_status tlda_profile_read(tlda_ctx *ctx, int32_t kernel, const char **name, int64_t *launches,
+                              double *total_ms);
+
 /* --------------------------------------------------------------- state */
 
 /* Checkpoint / resume of the fitted state (integer statistics, whitening,

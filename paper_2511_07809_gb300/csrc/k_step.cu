@@ -248,9 +248,12 @@ __global__ void k_phi_terms(StepArgs a) {
   }
 }
 
-void launch_phi_terms(const StepArgs &a, cudaStream_t s) {
+void launch_phi_gram(const StepArgs &a, cudaStream_t s) {
   dim3 g1(a.Kp / 16, a.Kp / 16 + 1), b1(16, 16);
   k_phi_gram<<<g1, b1, 0, s>>>(a);
+}
+
+void launch_phi_terms(const StepArgs &a, cudaStream_t s) {
   k_phi_terms<<<(a.D * a.K + 255) / 256, 256, 0, s>>>(a);
 }
 
@@ -485,24 +488,37 @@ __global__ void __launch_bounds__(256) k_g_f32(StepArgs a) {
         make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
 }
 
-void launch_chain_f32(const StepArgs &a, cudaStream_t s) {
+void launch_compact(const StepArgs &a, cudaStream_t s) { k_compact<<<(a.V + 255) / 256, 256, 0, s>>>(a); }
+
+void launch_qy_f32(const StepArgs &a, cudaStream_t s) {
+  dim3 g((a.V + a.Bmax + 63) / 64, a.Kp / 64);
+  k_qy_f32<<<g, 256, 0, s>>>(a);
+}
+
+void launch_rz(const StepArgs &a, cudaStream_t s) {
   const int nk = (a.Kp + 127) / 128;
-  if (a.same_token) k_compact<<<(a.V + 255) / 256, 256, 0, s>>>(a);
-  {
-    dim3 g((a.V + a.Bmax + 63) / 64, a.Kp / 64);
-    k_qy_f32<<<g, 256, 0, s>>>(a);
-  }
-#define TLDA_RZ(NKv)                                                              \
-  if (nk == NKv) {                                                                \
-    k_rz<NKv, false><<<(a.Bmax + 7) / 8, 256, 0, s>>>(a);                          \
-    if (a.same_token) k_zh_f32<NKv><<<(a.V + 7) / 8, 256, 0, s>>>(a);            \
+  const bool tc = a.precision == TLDA_BF16;
+#define TLDA_RZ(NKv)                                                                      \
+  if (nk == NKv) {                                                                        \
+    if (tc) k_rz<NKv, true><<<(a.Bmax + 7) / 8, 256, 0, s>>>(a);                          \
+    else k_rz<NKv, false><<<(a.Bmax + 7) / 8, 256, 0, s>>>(a);                            \
+    return;                                                                               \
   }
   TLDA_RZ(1) TLDA_RZ(2) TLDA_RZ(3) TLDA_RZ(4)
 #undef TLDA_RZ
-  {
-    dim3 g(a.nsplit, a.Dp / 64, a.Kp / 64);
-    k_g_f32<<<g, 256, 0, s>>>(a);
-  }
+}
+
+void launch_zh_f32(const StepArgs &a, cudaStream_t s) {
+  const int nk = (a.Kp + 127) / 128;
+  if (nk == 1) k_zh_f32<1><<<(a.V + 7) / 8, 256, 0, s>>>(a);
+  else if (nk == 2) k_zh_f32<2><<<(a.V + 7) / 8, 256, 0, s>>>(a);
+  else if (nk == 3) k_zh_f32<3><<<(a.V + 7) / 8, 256, 0, s>>>(a);
+  else k_zh_f32<4><<<(a.V + 7) / 8, 256, 0, s>>>(a);
+}
+
+void launch_g_f32(const StepArgs &a, cudaStream_t s) {
+  dim3 g(a.nsplit, a.Dp / 64, a.Kp / 64);
+  k_g_f32<<<g, 256, 0, s>>>(a);
 }
 
 // ------------------------------------------------------------ a9: reduce + update

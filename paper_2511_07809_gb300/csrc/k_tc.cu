@@ -2,5 +2,7 @@
 #include "tlda_internal.h"
 
 namespace tlda {
-void launch_chain_bf16(const StepArgs &, cudaStream_t) {}
+void launch_qy_tc(const StepArgs &, cudaStream_t) {}
+void launch_zh_tc(const StepArgs &, cudaStream_t) {}
+void launch_g_tc(const StepArgs &, cudaStream_t) {}
 }  // namespace tlda

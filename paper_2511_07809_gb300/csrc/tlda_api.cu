@@ -11,6 +11,11 @@
 
 using namespace tlda;
 
+namespace tlda {
+const char *const kKernelNames[kNumKernels] = {"scan_whiten", "compact", "qy", "rz", "zh",
+                                                "g_reduce", "reduce_update", "phi_gram", "phi_terms"};
+}
+
 namespace {
 
 tlda_status fail(tlda_ctx *c, tlda_status s, const char *fmt, ...) {
@@ -113,21 +118,69 @@ BatchDesc desc_of(const tlda_csr *b) {
   return d;
 }
 
-// Enqueues one CP step on ctx->stream for the batch in st->cur.
+// Event bracket around one kernel launch when its profiler bit is set.
+struct Prof {
+  tlda_ctx *c;
+  int id;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Prof(tlda_ctx *c_, int id_, cudaStream_t s_) : c(c_), id(id_), s(s_) {
+    if (!(c->prof_mask & (1u << id))) return;
+    for (cudaEvent_t *e : {&a, &b}) {
+      if (!c->prof_pool.empty()) {
+        *e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+      } else if (cudaEventCreate(e) != cudaSuccess) {
+        *e = nullptr;
+      }
+    }
+    if (a) cudaEventRecord(a, s);
+  }
+  ~Prof() {
+    if (!a || !b) return;
+    cudaEventRecord(b, s);
+    c->prof_pending.push_back({id, a, b});
+  }
+};
+
+// Enqueues one CP step on ctx->stream for the batch in st->cur: the Phi-only
+// terms on the side stream, the data-term chain on the main stream, then the
+// reduction and update once both are done.
 tlda_status enqueue_step(tlda_ctx *ctx, const StepArgs &a) {
+  const bool tc = a.precision == TLDA_BF16;
   CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
   CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-  launch_phi_terms(a, ctx->side);
+  { Prof p(ctx, kPhiGram, ctx->side); launch_phi_gram(a, ctx->side); }
+  { Prof p(ctx, kPhiTerms, ctx->side); launch_phi_terms(a, ctx->side); }
   CKL();
   CK(cudaEventRecord(ctx->ev_join, ctx->side));
-  launch_whiten(a, ctx->stream, nullptr, true);
-  CKL();
-  if (a.precision == TLDA_BF16) launch_chain_bf16(a, ctx->stream);
-  else launch_chain_f32(a, ctx->stream);
+  { Prof p(ctx, kWhiten, ctx->stream); launch_whiten(a, ctx->stream, nullptr, true); }
+  if (a.same_token) { Prof p(ctx, kCompact, ctx->stream); launch_compact(a, ctx->stream); }
+  { Prof p(ctx, kQY, ctx->stream); if (tc) launch_qy_tc(a, ctx->stream); else launch_qy_f32(a, ctx->stream); }
+  { Prof p(ctx, kRZ, ctx->stream); launch_rz(a, ctx->stream); }
+  if (a.same_token) { Prof p(ctx, kZH, ctx->stream); if (tc) launch_zh_tc(a, ctx->stream); else launch_zh_f32(a, ctx->stream); }
+  { Prof p(ctx, kG, ctx->stream); if (tc) launch_g_tc(a, ctx->stream); else launch_g_f32(a, ctx->stream); }
   CKL();
   CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-  launch_reduce_update(a, ctx->stream);
+  { Prof p(ctx, kReduceUpdate, ctx->stream); launch_reduce_update(a, ctx->stream); }
   CKL();
+  return TLDA_OK;
+}
+
+// Folds finished event brackets into the per-kernel totals (synchronises).
+tlda_status harvest_profile(tlda_ctx *ctx) {
+  if (ctx->prof_pending.empty()) return TLDA_OK;
+  CK(cudaDeviceSynchronize());
+  for (auto &r : ctx->prof_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      ctx->prof_ms[r.id] += ms;
+      ctx->prof_launches[r.id] += 1;
+    }
+    ctx->prof_pool.push_back(r.a);
+    ctx->prof_pool.push_back(r.b);
+  }
+  ctx->prof_pending.clear();
   return TLDA_OK;
 }
 
@@ -262,6 +315,11 @@ tlda_status tlda_destroy(tlda_ctx *ctx) {
   dfree(ctx->BT16); dfree(ctx->st); dfree(ctx->descs); dfree(ctx->P64); dfree(ctx->Ccnt);
   dfree(ctx->TS); dfree(ctx->fit_err); dfree(ctx->stage[0]); dfree(ctx->stage[1]);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
+  for (auto &r : ctx->prof_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side) cudaStreamDestroy(ctx->side);
@@ -452,6 +510,30 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
   }
   if (losses) cudaFreeHost(losses);
   return s;
+}
+
+tlda_status tlda_profile(tlda_ctx *ctx, uint32_t mask) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  tlda_status s = harvest_profile(ctx);
+  if (s) return s;
+  ctx->prof_mask = mask & ((1u << kNumKernels) - 1u);
+  for (int i = 0; i < 16; ++i) {
+    ctx->prof_ms[i] = 0.0;
+    ctx->prof_launches[i] = 0;
+  }
+  return TLDA_OK;
+}
+
+tlda_status tlda_profile_read(tlda_ctx *ctx, int32_t kernel, const char **name, int64_t *launches,
+                              double *total_ms) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  if (kernel < 0 || kernel >= kNumKernels) return fail(ctx, TLDA_ERR_INVALID, "no kernel %d", kernel);
+  tlda_status s = harvest_profile(ctx);
+  if (s) return s;
+  if (name) *name = kKernelNames[kernel];
+  if (launches) *launches = ctx->prof_launches[kernel];
+  if (total_ms) *total_ms = ctx->prof_ms[kernel];
+  return TLDA_OK;
 }
 
 tlda_status tlda_save_state(const tlda_ctx *cctx, const char *path) {

@@ -125,18 +125,38 @@ struct tlda_ctx {
   // pass staging (host input)
   int32_t *stage[2] = {nullptr, nullptr};
   long long stage_cap = 0;
+  // event profiler: kernels whose bit is set in prof_mask are bracketed by events
+  uint32_t prof_mask = 0;
+  struct ProfRec { int id; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  long long prof_launches[16] = {};
+  double prof_ms[16] = {};
 };
 
 namespace tlda {
+// Kernels of one CP step, in launch order (ids used by the event profiler).
+enum KernelId {
+  kWhiten = 0, kCompact, kQY, kRZ, kZH, kG, kReduceUpdate, kPhiGram, kPhiTerms, kNumKernels
+};
+extern const char *const kKernelNames[kNumKernels];
+
 // k_step.cu
 void launch_set_desc(DevState *st, const BatchDesc &b, cudaStream_t s);
 void launch_begin_pass(DevState *st, const BatchDesc *descs, int n, cudaStream_t s);
 void launch_whiten(const StepArgs &a, cudaStream_t s, float *X_out, bool stats);
+void launch_compact(const StepArgs &a, cudaStream_t s);
+void launch_qy_f32(const StepArgs &a, cudaStream_t s);
+void launch_rz(const StepArgs &a, cudaStream_t s);
+void launch_zh_f32(const StepArgs &a, cudaStream_t s);
+void launch_g_f32(const StepArgs &a, cudaStream_t s);
+void launch_phi_gram(const StepArgs &a, cudaStream_t s);
 void launch_phi_terms(const StepArgs &a, cudaStream_t s);
-void launch_chain_f32(const StepArgs &a, cudaStream_t s);
 void launch_reduce_update(const StepArgs &a, cudaStream_t s);
 void launch_make_u(const float *W, const float *m1, int V, int D, int Dp, float *U32,
                    __nv_bfloat16 *U16, cudaStream_t s);
-// k_tc.cu
-void launch_chain_bf16(const StepArgs &a, cudaStream_t s);
+// k_tc.cu (BF16 tensor-core form)
+void launch_qy_tc(const StepArgs &a, cudaStream_t s);
+void launch_zh_tc(const StepArgs &a, cudaStream_t s);
+void launch_g_tc(const StepArgs &a, cudaStream_t s);
 }  // namespace tlda

@@ -35,7 +35,7 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_sync", "tlda_fit_moments", "tlda_get_whitening", "tlda_get_counts",
                 "tlda_set_whitening", "tlda_whiten_batch", "tlda_cp_step",
                 "tlda_cp_data_term", "tlda_cp_pass", "tlda_unwhiten_topics",
-                "tlda_save_state", "tlda_load_state")
+                "tlda_profile", "tlda_profile_read", "tlda_save_state", "tlda_load_state")
 
 
 class Params(ctypes.Structure):
@@ -82,6 +82,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "tlda_cp_data_term": (i32, [vp, P(CSR), vp, vp, vp]),
         "tlda_cp_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, u32, vp]),
         "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
+        "tlda_profile": (i32, [vp, u32]),
+        "tlda_profile_read": (i32, [vp, i32, P(ctypes.c_char_p), P(i64), P(f64)]),
         "tlda_save_state": (i32, [vp, ctypes.c_char_p]),
         "tlda_load_state": (i32, [vp, ctypes.c_char_p]),
     }
@@ -252,6 +254,27 @@ class TLDA:
 
     def sync(self):
         self._check(self.lib.tlda_sync(self.h))
+
+    # ------------------------------------------------------------ profiling
+    KERNELS = ("scan_whiten", "compact", "qy", "rz", "zh", "g_reduce", "reduce_update",
+               "phi_gram", "phi_terms")
+
+    def profile(self, kernels=()):
+        """Bracket the named kernels with CUDA events from now on (empty: off)."""
+        mask = 0
+        for k in kernels:
+            mask |= 1 << self.KERNELS.index(k)
+        self._check(self.lib.tlda_profile(self.h, mask))
+
+    def profile_read(self):
+        """{kernel: (launches, total_ms)} since the last profile() call."""
+        out = {}
+        for i, _ in enumerate(self.KERNELS):
+            name, n, ms = ctypes.c_char_p(), ctypes.c_int64(), ctypes.c_double()
+            self._check(self.lib.tlda_profile_read(self.h, i, ctypes.byref(name), ctypes.byref(n),
+                                                   ctypes.byref(ms)))
+            out[name.value.decode()] = (n.value, ms.value)
+        return out
 
     # ------------------------------------------------------------ recovery / state
     def unwhiten_topics(self, Phi: torch.Tensor):
