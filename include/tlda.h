@@ -210,6 +210,40 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
 tlda_status tlda_unwhiten_topics(tlda_ctx *ctx, const float *Phi, double *mu_out,
                                  double *alpha_out, uint32_t flags);
 
+/* ------------------------------------------------------- allocation-free */
+
+/* The paper has no counterpart of this entry point: it serves callers that
+ * cannot allocate device memory.  Examples are code embedded in a host that
+ * owns the whole device-memory budget (a framework's caching allocator, a
+ * fixed arena that forbids further cudaMalloc), and latency-critical loops
+ * where cudaMalloc/cudaFree would synchronise the device.
+ *
+ * It computes one CP-SGD step with the same arithmetic as tlda_cp_step (FP32
+ * form, same-token correction on), without a context.  Inputs:
+ *   batch (host struct of device CSR pointers; V = batch->vocab),
+ *   W (V x D FP32), m1 = W^T M1 (D FP32), Phi (D x K FP32, updated in place),
+ *   grad_out (D x K FP32, may be NULL), err_out (one int32, may be NULL),
+ *   all device pointers, dim = D (0 means K), k = K, alpha0, theta, lr = beta.
+ * The work is enqueued on cuda_stream and the call returns without waiting.
+ * If err_out is given, it receives the device-side validation bits (0 = the
+ * batch was valid; non-zero = corrupt CSR, and Phi was left unchanged).
+ *
+ * Memory: calls no cudaMalloc, cudaFree or allocating library routine.  All
+ * scratch is one file-scope __device__ array of 8 MiB that every GPU which
+ * loads the library holds until the process exits.  Sizes whose scratch does
+ * not fit are rejected with TLDA_ERR_OOM and a one-line message on stderr.
+ * For example, V = 4096, D = K = 64 and n_docs = 2048 fit.
+ * Set-up: the first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with that device current.  Make that first call
+ * before any stream capture.
+ * Sharing: every call uses the same array.  The array keeps the last call's
+ * contents, so each call clears what must start at zero.  Calls that overlap
+ * on the GPU (on different streams, or from different host threads) race on
+ * it.  Order them on one stream. */
+tlda_status tlda_cp_step_noalloc(const tlda_csr *batch, const float *W, const float *m1,
+                                 int32_t dim, int32_t k, double alpha0, float theta, float *Phi,
+                                 float lr, float *grad_out, int32_t *err_out, void *cuda_stream);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Per-kernel device time, from CUDA events recorded around each launch on

@@ -35,7 +35,8 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_sync", "tlda_fit_moments", "tlda_get_whitening", "tlda_get_counts",
                 "tlda_set_whitening", "tlda_whiten_batch", "tlda_cp_step",
                 "tlda_cp_data_term", "tlda_cp_pass", "tlda_unwhiten_topics",
-                "tlda_profile", "tlda_profile_read", "tlda_save_state", "tlda_load_state")
+                "tlda_profile", "tlda_profile_read", "tlda_save_state", "tlda_load_state",
+                "tlda_cp_step_noalloc")
 
 
 class Params(ctypes.Structure):
@@ -82,6 +83,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "tlda_cp_data_term": (i32, [vp, P(CSR), vp, vp, vp]),
         "tlda_cp_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, u32, vp]),
         "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
+        "tlda_cp_step_noalloc": (i32, [P(CSR), vp, vp, i32, i32, f64, f32, vp, f32, vp, vp, vp]),
         "tlda_profile": (i32, [vp, u32]),
         "tlda_profile_read": (i32, [vp, i32, P(ctypes.c_char_p), P(i64), P(f64)]),
         "tlda_save_state": (i32, [vp, ctypes.c_char_p]),
