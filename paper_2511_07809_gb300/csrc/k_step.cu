@@ -339,7 +339,13 @@ __global__ void __launch_bounds__(256) k_rz(StepArgs a) {
   const BatchDesc b = a.st->cur;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int d = blockIdx.x * 8 + warp;
-  if (d >= b.n_docs) return;
+  if (d >= b.n_docs) {
+    if constexpr (TC) {  // zero Z^T columns up to the 64-column reduction chunk
+      if (d < round_up(b.n_docs, 64))
+        for (int i = lane; i < a.Kp; i += 32) a.BT16[(long long)i * a.ldT + d] = __float2bfloat16_rn(0.f);
+    }
+    return;
+  }
   float4 y[NK], r[NK];
 #pragma unroll
   for (int v = 0; v < NK; ++v) {

@@ -1,8 +1,473 @@
-// BF16 tensor-core (tcgen05 / TMEM) form of the CP-step contractions.
+// BF16 tensor-core form of the CP-step contractions on sm_103a: tcgen05 MMAs
+// issued by one thread, operands staged in shared memory (TMA for the large
+// operands, 128-byte swizzle, K-major), FP32 accumulators in TMEM read back
+// with tcgen05.ld.
+//
+//   k_qy_tc  [Q; Y] = [U; X] Phi   (eq. vec_deriv: Y = X Phi; the same-token
+//            term needs Q = U Phi).  M = 128 rows of [U; X] per CTA, N = Kp,
+//            K = Dp.  A by TMA from the BF16 copy UX16; B = Phi^T built in
+//            shared memory from the FP32 factors.
+//   k_g_tc   G1 + G2 = [X; U_t]^T [Z; Zc] as a split reduction over the
+//            reduction-major copies AT16 (Dp x ldT) and BT16 (Kp x ldT):
+//            each CTA streams 64-column chunks through a 4-stage TMA ring and
+//            accumulates a 128 x Kp tile in TMEM, then writes its partial.
+//   k_zh_tc  Zc rows of the touched words, written transposed (BF16) next to
+//            the touched words' U^T columns.
+// Every wait on an mbarrier is bounded (about one second of clock cycles);
+// on expiry the kernel sets the context's timeout bit and leaves.
+#include <cuda.h>
+
+#include <cstdio>
+
 #include "tlda_internal.h"
 
 namespace tlda {
-void launch_qy_tc(const StepArgs &, cudaStream_t) {}
-void launch_zh_tc(const StepArgs &, cudaStream_t) {}
-void launch_g_tc(const StepArgs &, cudaStream_t) {}
+namespace {
+
+constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// whole warp
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulate.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred P;\n\t"
+      "setp.ne.b32 P, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, P;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrives on the mbarrier once all previously issued MMAs of this thread are done.
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
+// layout (rows of 64 BF16 = 128 B, 8-row groups 1024 B apart).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(1) << 16) |
+         (static_cast<uint64_t>(1024 >> 4) << 32) | (static_cast<uint64_t>(1) << 46) |
+         (static_cast<uint64_t>(2) << 61);
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__host__ __device__ constexpr int tmem_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : 256; }
+
+// Byte offset of element (row, k) inside a [rows x 64] BF16 sub-tile stored in
+// the 128-byte swizzle layout (16-byte chunk index XOR row mod 8).
+__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
+  return static_cast<uint32_t>(row * 128 + ((((k >> 3) ^ (row & 7)) & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
+  return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// ------------------------------------------------------------------ Q and Y
+template <int KA, int KP>
+__global__ void __launch_bounds__(128) k_qy_tc(StepArgs a, const __grid_constant__ CUtensorMap tmA) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = align1024(smem_raw);
+  unsigned char *sA = smem;                      // KA x [128 x 64] BF16
+  unsigned char *sB = smem + KA * 16384;         // KA x [KP x 64] BF16
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sB + KA * KP * 128);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nd = a.st->cur.n_docs;
+  const int rows = a.V + nd;
+  const int r0 = blockIdx.x * 128;
+  if (r0 >= rows) return;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(tslot, tmem_cols(KP));
+  // B = Phi^T (KP x Dp, K-major), built from the FP32 factors (zero padded)
+  for (int g = tid; g < KP * KA * 8; g += 128) {
+    const int n = g % KP, kc = g / KP;  // kc: 8-element chunk along Dp
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = kc * 8 + j;
+      v[j] = __float2bfloat16_rn((k < a.D && n < a.K) ? a.Phi[(long long)k * a.K + n] : 0.f);
+    }
+    const int sub = kc >> 3;
+    *reinterpret_cast<uint4 *>(sB + sub * KP * 128 + sw128_offset(n, (kc & 7) * 8)) =
+        *reinterpret_cast<const uint4 *>(v);
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  __shared__ int failed;
+  if (tid == 0) failed = 0;
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bars[0], KA * 16384);
+#pragma unroll
+    for (int kb = 0; kb < KA; ++kb) tma_load_2d(sA + kb * 16384, &tmA, &bars[0], kb * 64, r0);
+    if (mbar_wait(&bars[0], 0)) {
+      tc_fence_after();
+      const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
+#pragma unroll
+      for (int kk = 0; kk < KA * 4; ++kk) {
+        const uint64_t ad = sdesc_sw128(aBase + (kk >> 2) * 16384 + (kk & 3) * 32);
+        const uint64_t bd = sdesc_sw128(bBase + (kk >> 2) * KP * 128 + (kk & 3) * 32);
+        mma_bf16(tmem, ad, bd, idesc_bf16(128, KP), kk > 0 ? 1u : 0u);
+      }
+      mma_commit(&bars[1]);
+    } else {
+      atomicOr(&a.st->err, kErrTimeout);
+      failed = 1;
+    }
+  }
+  __syncthreads();
+  // warp-uniform decision: tcgen05.ld below is .sync.aligned
+  const bool ok = __all_sync(0xffffffffu, !failed && mbar_wait(&bars[1], 0));
+  if (ok) {
+    tc_fence_after();
+    const int row = r0 + warp * 32 + lane;
+    float *out = nullptr;
+    if (row < a.V) out = a.Q32 + (long long)row * a.Kp;
+    else if (row < rows) out = a.Y32 + (long long)(row - a.V) * a.Kp;
+#pragma unroll
+    for (int c0 = 0; c0 < KP; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+      if (out) {
+#pragma unroll
+        for (int q = 0; q < 16; q += 4)
+          *reinterpret_cast<float4 *>(out + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      }
+    }
+  } else if (lane == 0 && !failed) {
+    atomicOr(&a.st->err, kErrTimeout);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, tmem_cols(KP));
+}
+
+// ------------------------------------------------------------------ G1 + G2
+constexpr int kStages = 4;
+
+template <int KP>
+__global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant__ CUtensorMap tmA,
+                                              const __grid_constant__ CUtensorMap tmB) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = align1024(smem_raw);
+  constexpr int A_BYTES = 128 * 128, B_BYTES = KP * 128, STAGE = A_BYTES + B_BYTES;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * STAGE);
+  uint64_t *empty = full + kStages;
+  uint64_t *done = empty + kStages;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nd = a.st->cur.n_docs, nt = a.same_token ? a.st->n_touched : 0;
+  const int cB = (nd + 63) / 64, cT = (nt + 63) / 64, C = cB + cT;
+  const int s = blockIdx.x;
+  const int c0 = (int)((long long)C * s / a.nsplit), c1 = (int)((long long)C * (s + 1) / a.nsplit);
+  const int n = c1 - c0;
+  float *gp = a.Gpart + (long long)s * a.Dp * a.Kp;
+  if (n <= 0) {
+    for (int e = tid; e < a.Dp * a.Kp; e += 128) gp[e] = 0.f;
+    return;
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(tslot, tmem_cols(KP));
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  __shared__ int failed;
+  if (tid == 0) failed = 0;
+  __syncthreads();
+  if (tid == 0) {  // TMA producer
+    for (int i = 0; i < n; ++i) {
+      const int st = i % kStages;
+      if (i >= kStages && !mbar_wait(&empty[st], ((i / kStages) - 1) & 1)) {
+        failed = 1;
+        break;
+      }
+      const int c = c0 + i;
+      const int col = c < cB ? c * 64 : a.Bmax + (c - cB) * 64;
+      unsigned char *sa = smem + st * STAGE, *sb = sa + A_BYTES;
+      mbar_arrive_expect_tx(&full[st], STAGE);
+      tma_load_2d(sa, &tmA, &full[st], col, 0);
+      tma_load_2d(sb, &tmB, &full[st], col, 0);
+    }
+  } else if (tid == 32) {  // MMA issuer
+    for (int i = 0; i < n; ++i) {
+      const int st = i % kStages;
+      if (!mbar_wait(&full[st], (i / kStages) & 1)) {
+        failed = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t aBase = smem_u32(smem + st * STAGE), bBase = aBase + A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma_bf16(tmem, sdesc_sw128(aBase + kk * 32), sdesc_sw128(bBase + kk * 32), idesc_bf16(128, KP),
+                 (i > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[st]);
+    }
+    mma_commit(done);
+  }
+  __syncthreads();
+  const bool ok = __all_sync(0xffffffffu, !failed && mbar_wait(done, 0));
+  if (ok) {
+    tc_fence_after();
+    const int row = warp * 32 + lane;
+#pragma unroll
+    for (int q0 = 0; q0 < KP; q0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + q0, v);
+      if (row < a.Dp) {
+#pragma unroll
+        for (int q = 0; q < 16; q += 4)
+          *reinterpret_cast<float4 *>(gp + (long long)row * a.Kp + q0 + q) =
+              make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(&a.st->err, kErrTimeout);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, tmem_cols(KP));
+}
+
+// ------------------------------------------------------------------ Zc (BF16, transposed)
+// One warp per compact slot t: Zc_t = q (2 c q - 2 H_m) into BT16 column
+// Bmax + t and U_m into AT16 column Bmax + t; H_m, c_m cleared.  Slots in
+// [n_touched, round_up(n_touched, 64)) write zero columns (reduction padding).
+template <int NK>
+__global__ void __launch_bounds__(256) k_zh_tc(StepArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  const int nt = a.st->n_touched;
+  if (t >= round_up(nt, 64)) return;
+  const long long colT = (long long)a.Bmax + t;
+  if (t >= nt) {
+    for (int i = lane; i < a.Dp; i += 32) a.AT16[(long long)i * a.ldT + colT] = __float2bfloat16_rn(0.f);
+    for (int i = lane; i < a.Kp; i += 32) a.BT16[(long long)i * a.ldT + colT] = __float2bfloat16_rn(0.f);
+    return;
+  }
+  const int m = a.widx[t];
+  const float c = (float)a.cnt[m];
+  float ls = 0.f;
+#pragma unroll
+  for (int v = 0; v < NK; ++v) {
+    const int col = v * 128 + lane * 4;
+    if (col < a.Kp) {
+      float4 *hp = reinterpret_cast<float4 *>(a.H32 + (long long)m * a.Kp + col);
+      const float4 q = *reinterpret_cast<const float4 *>(a.Q32 + (long long)m * a.Kp + col);
+      const float4 h = *hp;
+      const float z[4] = {q.x * (2.f * c * q.x - 2.f * h.x), q.y * (2.f * c * q.y - 2.f * h.y),
+                          q.z * (2.f * c * q.z - 2.f * h.z), q.w * (2.f * c * q.w - 2.f * h.w)};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a.BT16[(long long)(col + j) * a.ldT + colT] = __float2bfloat16_rn(z[j]);
+      *hp = make_float4(0.f, 0.f, 0.f, 0.f);
+      ls += q.x * q.x * q.x + q.y * q.y * q.y + q.z * q.z * q.z + q.w * q.w * q.w;
+    }
+  }
+  for (int i = lane; i < a.Dp; i += 32) a.AT16[(long long)i * a.ldT + colT] = a.U16[(long long)m * a.Dp + i];
+  if (a.want_loss) {
+    for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
+    if (lane == 0) atomicAdd(&a.st->loss_data, 2.0 * (double)c * (double)ls);
+  }
+  __syncwarp();
+  if (lane == 0) a.cnt[m] = 0;
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2D BF16 tensor [outer x inner] (row pitch in bytes), box [box_outer x 64], 128-byte swizzle.
+bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
+              uint32_t box_outer) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {pitch_bytes};
+  cuuint32_t box[2] = {64, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct TcMaps {
+  CUtensorMap ux;  // UX16: (V + Bmax) x Dp, box 128 rows x 64
+  CUtensorMap at;  // AT16: Dp x ldT, box 128 rows x 64 (rows >= Dp read as zero)
+  CUtensorMap bt;  // BT16: Kp x ldT, box Kp rows x 64
+};
+
+template <int KA, int KP>
+void qy_launch(const StepArgs &a, const TcMaps &m, cudaStream_t s) {
+  const int smem = 1024 + KA * 16384 + KA * KP * 128 + 64;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_qy_tc<KA, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  k_qy_tc<KA, KP><<<(a.V + a.Bmax + 127) / 128, 128, smem, s>>>(a, m.ux);
+}
+
+template <int KP>
+void g_launch(const StepArgs &a, const TcMaps &m, cudaStream_t s) {
+  const int smem = 1024 + kStages * (128 * 128 + KP * 128) + 128;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_g_tc<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  k_g_tc<KP><<<a.nsplit, 128, smem, s>>>(a, m.at, m.bt);
+}
+
+}  // namespace
+
+bool tc_supported(int Dp, int Kp) { return Dp <= 128 && Kp <= 256; }
+
+void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const __nv_bfloat16 *BT16, int V,
+                   int Bmax, int Dp, int Kp, int ldT) {
+  TcMaps *m = new TcMaps();
+  bool ok = make_map(&m->ux, UX16, Dp, (uint64_t)V + Bmax, (uint64_t)Dp * 2, 128) &&
+            make_map(&m->at, AT16, ldT, Dp, (uint64_t)ldT * 2, 128) &&
+            make_map(&m->bt, BT16, ldT, Kp, (uint64_t)ldT * 2, Kp);
+  if (!ok) {
+    delete m;
+    return nullptr;
+  }
+  return m;
+}
+
+void tc_free_maps(void *p) { delete static_cast<TcMaps *>(p); }
+
+void launch_qy_tc(const StepArgs &a, cudaStream_t s) {
+  const TcMaps &m = *static_cast<const TcMaps *>(a.tc_maps);
+  const int ka = a.Dp / 64;
+#define TLDA_QY(KAv, KPv) \
+  if (ka == KAv && a.Kp == KPv) return qy_launch<KAv, KPv>(a, m, s);
+  TLDA_QY(1, 64) TLDA_QY(1, 128) TLDA_QY(1, 192) TLDA_QY(1, 256)
+  TLDA_QY(2, 64) TLDA_QY(2, 128) TLDA_QY(2, 192) TLDA_QY(2, 256)
+#undef TLDA_QY
+}
+
+void launch_g_tc(const StepArgs &a, cudaStream_t s) {
+  const TcMaps &m = *static_cast<const TcMaps *>(a.tc_maps);
+  if (a.Kp == 64) return g_launch<64>(a, m, s);
+  if (a.Kp == 128) return g_launch<128>(a, m, s);
+  if (a.Kp == 192) return g_launch<192>(a, m, s);
+  return g_launch<256>(a, m, s);
+}
+
+void launch_zh_tc(const StepArgs &a, cudaStream_t s) {
+  const int nk = (a.Kp + 127) / 128;
+  const int grid = round_up(a.V, 64) / 8;
+  if (nk == 1) k_zh_tc<1><<<grid, 256, 0, s>>>(a);
+  else k_zh_tc<2><<<grid, 256, 0, s>>>(a);
+}
+
 }  // namespace tlda

@@ -96,6 +96,8 @@ StepArgs make_args(tlda_ctx *c) {
   a.BT16 = c->BT16;
   a.ldT = c->ldT;
   a.precision = c->p.precision;
+  a.tc_maps = c->tc_maps;
+  if (a.precision == TLDA_BF16) a.nsplit = c->nsplit_tc;
   return a;
 }
 
@@ -244,7 +246,7 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
       (p->precision != TLDA_FP32 && p->precision != TLDA_BF16) || p->max_batch < 0 ||
       p->max_batch > (1 << 20))
     return TLDA_ERR_INVALID;
-  if (p->precision == TLDA_BF16) return TLDA_ERR_UNIMPLEMENTED;
+  if (p->precision == TLDA_BF16 && !tc_supported(round_up(D, 64), round_up(K, 64))) return TLDA_ERR_UNIMPLEMENTED;
   tlda_ctx *ctx = new tlda_ctx();
   ctx->p = *p;
   ctx->p.dim = D;
@@ -274,6 +276,7 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
   const size_t V = vocab, Dp = ctx->Dp, Kp = ctx->Kp, Bm = ctx->Bmax;
   const int tiles = (ctx->Dp / 64) * (ctx->Kp / 64);
   ctx->nsplit = std::max(8, std::min(256, 2 * ctx->num_sms / tiles));
+  ctx->nsplit_tc = 48;
   CA(dalloc(&ctx->W32, V * D, true));
   CA(dalloc(&ctx->m1, Dp, true));
   CA(dalloc(&ctx->U32, V * Dp, true));
@@ -285,7 +288,7 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
   CA(dalloc(&ctx->H32, V * Kp, true));
   CA(dalloc(&ctx->cnt, V, true));
   CA(dalloc(&ctx->widx, V, true));
-  CA(dalloc(&ctx->Gpart, (size_t)ctx->nsplit * Dp * Kp, true));
+  CA(dalloc(&ctx->Gpart, (size_t)std::max(ctx->nsplit, ctx->nsplit_tc) * Dp * Kp, true));
   CA(dalloc(&ctx->Gram, Kp * Kp, true));
   CA(dalloc(&ctx->avec, Kp, true));
   CA(dalloc(&ctx->E, Dp * Kp, true));
@@ -294,10 +297,14 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
   CA(cudaMallocHost(reinterpret_cast<void **>(&ctx->st_host), sizeof(DevState)));
   std::memset(ctx->st_host, 0, sizeof(DevState));
   if (p->precision == TLDA_BF16) {
-    CA(dalloc(&ctx->U16, V * Dp, true));
-    CA(dalloc(&ctx->X16, Bm * Dp, true));
+    // U rows then X rows in one BF16 matrix: one TMA map covers [U; X]
+    CA(dalloc(&ctx->UX16, (V + Bm) * Dp, true));
+    ctx->U16 = ctx->UX16;
+    ctx->X16 = ctx->UX16 + V * Dp;
     CA(dalloc(&ctx->AT16, Dp * (size_t)ctx->ldT, true));
     CA(dalloc(&ctx->BT16, Kp * (size_t)ctx->ldT, true));
+    ctx->tc_maps = tc_make_maps(ctx->UX16, ctx->AT16, ctx->BT16, vocab, ctx->Bmax, ctx->Dp, ctx->Kp, ctx->ldT);
+    if (!ctx->tc_maps) return bail(TLDA_ERR_CUDA, "cuTensorMapEncodeTiled", cudaErrorUnknown);
   }
 #undef CA
   CK(cudaDeviceSynchronize());
@@ -308,10 +315,12 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
 tlda_status tlda_destroy(tlda_ctx *ctx) {
   if (!ctx) return TLDA_ERR_INVALID;
   if (ctx->stream || ctx->side) cudaDeviceSynchronize();
-  dfree(ctx->W32); dfree(ctx->m1); dfree(ctx->U32); dfree(ctx->U16);
+  dfree(ctx->W32); dfree(ctx->m1); dfree(ctx->U32); dfree(ctx->UX16);
+  ctx->U16 = nullptr;
+  if (ctx->tc_maps) tc_free_maps(ctx->tc_maps);
   dfree(ctx->X32); dfree(ctx->Q32); dfree(ctx->Y32); dfree(ctx->Z32); dfree(ctx->Zc32);
   dfree(ctx->H32); dfree(ctx->cnt); dfree(ctx->widx); dfree(ctx->Gpart); dfree(ctx->Gram);
-  dfree(ctx->avec); dfree(ctx->E); dfree(ctx->G3); dfree(ctx->X16); dfree(ctx->AT16);
+  dfree(ctx->avec); dfree(ctx->E); dfree(ctx->G3); dfree(ctx->AT16);
   dfree(ctx->BT16); dfree(ctx->st); dfree(ctx->descs); dfree(ctx->P64); dfree(ctx->Ccnt);
   dfree(ctx->TS); dfree(ctx->fit_err); dfree(ctx->stage[0]); dfree(ctx->stage[1]);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);

@@ -83,6 +83,7 @@ struct StepArgs {
   __nv_bfloat16 *BT16;           // Kp x ldT: Z^T (docs) then Zc^T (touched words)
   int ldT;                       // Bmax + V rounded up
   int precision;
+  const void *tc_maps;           // host pointer to the TMA tensor maps (BF16 form)
   // caller buffers
   float *Phi;                    // D x K (user layout), updated in place
   float *grad_out;               // D x K or null
@@ -110,8 +111,9 @@ struct tlda_ctx {
   float *H32 = nullptr;
   int *cnt = nullptr, *widx = nullptr;
   float *Gpart = nullptr, *Gram = nullptr, *avec = nullptr, *E = nullptr, *G3 = nullptr;
-  int nsplit = 0;
-  __nv_bfloat16 *X16 = nullptr, *AT16 = nullptr, *BT16 = nullptr;
+  int nsplit = 0, nsplit_tc = 0;
+  __nv_bfloat16 *UX16 = nullptr, *X16 = nullptr, *AT16 = nullptr, *BT16 = nullptr;
+  void *tc_maps = nullptr;
   tlda::DevState *st = nullptr;
   tlda::DevState *st_host = nullptr;   // pinned mirror for reads
   tlda::BatchDesc *descs = nullptr;    // pass descriptors (device)
@@ -156,6 +158,10 @@ void launch_reduce_update(const StepArgs &a, cudaStream_t s);
 void launch_make_u(const float *W, const float *m1, int V, int D, int Dp, float *U32,
                    __nv_bfloat16 *U16, cudaStream_t s);
 // k_tc.cu (BF16 tensor-core form)
+bool tc_supported(int Dp, int Kp);
+void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const __nv_bfloat16 *BT16, int V,
+                   int Bmax, int Dp, int Kp, int ldT);
+void tc_free_maps(void *maps);
 void launch_qy_tc(const StepArgs &a, cudaStream_t s);
 void launch_zh_tc(const StepArgs &a, cudaStream_t s);
 void launch_g_tc(const StepArgs &a, cudaStream_t s);

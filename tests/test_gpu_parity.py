@@ -12,6 +12,7 @@ from tests import _cases as C
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-5
+TOL16 = 2e-2
 
 
 def _ctx(lib, name, precision="fp32", same_token=True, dim=0, theta=0.0, max_batch=8192, W=None):
@@ -177,6 +178,56 @@ def test_pass_equals_sequential_oracle_steps(lib, host_input):
         P, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, lr, float(sp.alpha0), 0.0)
         assert abs(losses[b] - g["loss"]) <= 1e-5 * abs(g["loss"]), b
     assert C.rel(Phi.cpu().numpy(), P) < TOL32
+
+
+# ----------------------------------------------------------------------------- BF16 tensor-core form
+@pytest.mark.parametrize("name,n", [("small_v500_k10", 1000), ("small_v500_k10", 37),
+                                    ("tweet_v5k_k50", 2048), ("stream_v20k_k100", 4099),
+                                    ("stream_v20k_k100", 8192)])
+def test_data_term_bf16(lib, name, n):
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name, precision="bf16")
+    c = C.corpus(name, n)
+    Phi = _phi0(sp)
+    G, S3 = t.cp_data_term(lib.DeviceCSR.from_corpus(c), torch.tensor(Phi, dtype=torch.float32, device="cuda"))
+    g = _oracle_grad(c, sp, W, m1, Phi)
+    assert S3 == g["S3"]
+    assert C.rel(G.cpu().numpy(), g["G_data"]) < TOL16
+
+
+@pytest.mark.parametrize("same_token", [True, False])
+def test_cp_step_bf16(lib, same_token):
+    name = "tweet_v5k_k50"
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name, precision="bf16", same_token=same_token)
+    c = C.corpus(name, 3000)
+    Phi0 = _phi0(sp)
+    Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(Phi)
+    lr = 0.002
+    loss = t.cp_step(lib.DeviceCSR.from_corpus(c), Phi, lr, grad=grad, want_loss=True)
+    g = _oracle_grad(c, sp, W, m1, Phi0, 0.0, same_token)
+    assert C.rel(grad.cpu().numpy(), g["grad"]) < TOL16
+    assert C.rel(Phi.cpu().numpy(), Phi0 - lr * g["grad"]) < TOL16
+    assert abs(loss - g["loss"]) <= TOL16 * abs(g["loss"])
+
+
+def test_pass_bf16_ragged(lib):
+    name = "stream_v20k_k100"
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name, precision="bf16")
+    c = C.corpus(name, 12000)
+    offs = [0, 513, 8192 + 513, 9000, 9001, 12000]
+    Phi0 = _phi0(sp)
+    Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+    lr = 0.002
+    losses = t.cp_pass(lib.DeviceCSR.from_corpus(c), offs, Phi, lr, losses=True)
+    P = Phi0.copy()
+    for b in range(len(offs) - 1):
+        r = c.rows(offs[b], offs[b + 1])
+        P, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, lr, float(sp.alpha0), 0.0)
+        assert abs(losses[b] - g["loss"]) <= TOL16 * abs(g["loss"]), b
+    assert C.rel(Phi.cpu().numpy(), P) < TOL16
 
 
 # ----------------------------------------------------------------------------- moments
