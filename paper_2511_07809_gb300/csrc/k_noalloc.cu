@@ -143,7 +143,6 @@ extern "C" tlda_status tlda_cp_step_noalloc(const tlda_csr *batch, const float *
   launch_phi_terms(a, s);
   if (B > 0) {
     launch_whiten(a, s, nullptr, true);
-    launch_compact(a, s);
     launch_qy_f32(a, s);
     launch_rz(a, s);
     launch_zh_f32(a, s);

@@ -4,9 +4,9 @@
 // touched-word compaction, the Phi-only terms and the final reduction/update.
 //
 // Per step, with U = W - 1 m1^T (V x D), X = F U, Y = X Phi, Q = U Phi:
-//   a1  L_d, S3, c_m = sum_d f_dm, CSR validation         k_scan_whiten
+//   a1  L_d, S3, c_m = sum_d f_dm, CSR validation,
+//       touched words {m : c_m > 0}                        k_scan_whiten
 //   a2  X = F U (= F W - L m1^T)                           k_scan_whiten
-//       touched words {m : c_m > 0}                        k_compact
 //   a3  Y = X Phi;  a4 Q = U Phi (touched rows)            k_qy_f32
 //   a4  R_d = sum_m f_dm Q_m^2,  Z = Y*Y - R;  H = F^T Y   k_rz
 //   a6  Zc_m = Q_m * (2 c_m Q_m - 2 H_m)                   k_zh_f32
@@ -61,15 +61,66 @@ void launch_make_u(const float *W, const float *m1, int V, int D, int Dp, float 
 }
 
 // ------------------------------------------------------------ a1 + a2: scan and whiten
+// Nonzeros of one document, 32 at a time: lane j holds nonzero base + j (word,
+// count), checked in place; invalid entries get weight 0 on row 0.
+struct NzChunk {
+  int m, f;      // word (0 if invalid) and count (0 if invalid)
+  bool in;       // lane holds a nonzero of this chunk
+  bool bad;      // lane's nonzero breaks the CSR rules
+  int n;         // nonzeros in this chunk (same in all lanes)
+};
+
+__device__ __forceinline__ NzChunk load_chunk(const BatchDesc &b, int V, int base, int hi, int lane, int prev) {
+  NzChunk c;
+  const int j = base + lane;
+  c.in = j < hi;
+  c.n = min(32, hi - base);
+  int m = -1, f = 0;
+  if (c.in) {
+    m = __ldg(b.indices + ((long long)j - b.nz_base));
+    f = __ldg(b.counts + ((long long)j - b.nz_base));
+  }
+  int mp = __shfl_up_sync(0xffffffffu, m, 1);
+  if (lane == 0) mp = prev;
+  const bool valid = c.in && m >= 0 && m < V && f > 0;
+  c.bad = c.in && (!valid || m <= mp);
+  c.m = valid ? m : 0;
+  c.f = valid ? f : 0;
+  return c;
+}
+
 // One warp per document: validates the row, accumulates L_d and
-// x_d = sum_m f_dm u_m (FP32) with float4 loads of the U rows, adds c_m and
-// the block's share of S3.  TC=true also writes X in BF16 row-major (X16)
-// and transposed (AT16 columns, via shared memory) for the tensor-core chain.
+// x_d = sum_m f_dm u_m (FP32) four U rows in flight at a time, and (stats)
+// adds c_m, appends first-seen words to the touched list, adds the block's
+// share of S3.  TC=true also writes X in BF16 row-major (X16) and transposed
+// (AT16 columns, via shared memory); its last block builds the shared-memory
+// image of the B operand Phi^T (BF16, 128-byte swizzle) for the Q/Y product.
 template <int NV, bool TC>
 __global__ void __launch_bounds__(32 * kDocsPerBlock)
     k_scan_whiten(StepArgs a, float *X_out, int stats) {
   const BatchDesc b = a.st->cur;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if constexpr (TC) {
+    if (X_out == nullptr && blockIdx.x == gridDim.x - 1) {
+      // Phi^T image: (Dp/64) sub-tiles of [Kp rows x 64] BF16, row n at n*128
+      // bytes, 16-byte chunk c of row n stored at chunk c ^ (n & 7).
+      const int groups = a.Kp * (a.Dp / 8);
+      for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+        const int n = g % a.Kp, kc = g / a.Kp;
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int k = kc * 8 + q;
+          v[q] = __float2bfloat16_rn((k < a.D && n < a.K) ? a.Phi[(long long)k * a.K + n] : 0.f);
+        }
+        const int sub = kc >> 3, ch = kc & 7;
+        unsigned char *dst = reinterpret_cast<unsigned char *>(a.PhiImg) + (size_t)sub * a.Kp * 128 +
+                             n * 128 + (((ch ^ (n & 7)) & 7) << 4);
+        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(v);
+      }
+      return;
+    }
+  }
   const int d0 = blockIdx.x * kDocsPerBlock;
   if (d0 >= (TC ? round_up(b.n_docs, 64) : b.n_docs)) return;
   const int d = d0 + warp;
@@ -83,29 +134,51 @@ __global__ void __launch_bounds__(32 * kDocsPerBlock)
   if (d < b.n_docs) {
     const int lo = b.indptr[d], hi = b.indptr[d + 1];
     bool bad = (lo < b.nz_base) || (hi < lo);
-    long long L = 0;
+    long long lsum = 0;
     int prev = -1;
     if (!bad) {
-      for (int j = lo; j < hi; ++j) {
-        const long long o = (long long)j - b.nz_base;
-        const int m = __ldg(b.indices + o), f = __ldg(b.counts + o);
-        if (m < 0 || m >= a.V || f <= 0) {
-          bad = true;
-          continue;
+      for (int base = lo; base < hi; base += 32) {
+        const NzChunk c = load_chunk(b, a.V, base, hi, lane, prev);
+        if (__any_sync(0xffffffffu, c.bad)) bad = true;
+        prev = __shfl_sync(0xffffffffu, c.in ? c.m : -1, c.n - 1);
+        lsum += c.f;
+        if (stats && a.same_token) {
+          bool fresh = false;
+          if (c.f > 0) fresh = atomicAdd(a.cnt + c.m, c.f) == 0;
+          const unsigned nm = __ballot_sync(0xffffffffu, fresh);
+          if (nm) {
+            int t0 = 0;
+            if (lane == 0) t0 = atomicAdd(&a.st->n_touched, __popc(nm));
+            t0 = __shfl_sync(0xffffffffu, t0, 0);
+            if (fresh) a.widx[t0 + __popc(nm & ((1u << lane) - 1u))] = c.m;
+          }
         }
-        if (m <= prev) bad = true;
-        prev = m;
-        L += f;
-        if (stats && a.same_token && lane == 0) atomicAdd(a.cnt + m, f);
-        const float ff = (float)f;
-        const float *urow = a.U32 + (long long)m * a.Dp;
+        for (int q = 0; q < c.n; q += 4) {
+          int mm[4];
+          float ff[4];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const int col = v * 128 + lane * 4;
-          if (col < a.Dp) acc[v] = fma4(ff, __ldg(reinterpret_cast<const float4 *>(urow + col)), acc[v]);
+          for (int u = 0; u < 4; ++u) {
+            mm[u] = __shfl_sync(0xffffffffu, c.m, (q + u) & 31);
+            ff[u] = (float)__shfl_sync(0xffffffffu, c.f, (q + u) & 31);
+            if (q + u >= c.n) ff[u] = 0.f;
+          }
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const int col = v * 128 + lane * 4;
+            if (col < a.Dp) {
+              float4 r[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                r[u] = __ldg(reinterpret_cast<const float4 *>(a.U32 + (long long)mm[u] * a.Dp + col));
+#pragma unroll
+              for (int u = 0; u < 4; ++u) acc[v] = fma4(ff[u], r[u], acc[v]);
+            }
+          }
         }
       }
     }
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    const long long L = lsum;
     if (bad && lane == 0) atomicOr(&a.st->err, kErrCsr);
     if (stats && lane == 0 && L >= 3) atomicAdd(&s3, (unsigned long long)(L * (L - 1) * (L - 2)));
     if (X_out) {
@@ -163,9 +236,9 @@ __global__ void __launch_bounds__(32 * kDocsPerBlock)
 }
 
 void launch_whiten(const StepArgs &a, cudaStream_t s, float *X_out, bool stats) {
-  const int grid = round_up(a.Bmax, 64) / kDocsPerBlock;
-  const int nv = (a.Dp + 127) / 128;
   const bool tc = a.precision == TLDA_BF16 && X_out == nullptr;
+  const int grid = round_up(a.Bmax, 64) / kDocsPerBlock + (tc ? 1 : 0);
+  const int nv = (a.Dp + 127) / 128;
 #define TLDA_WHITEN(NVv)                                                                        \
   if (nv == NVv) {                                                                              \
     if (tc) k_scan_whiten<NVv, true><<<grid, 32 * kDocsPerBlock, 0, s>>>(a, X_out, stats);     \
@@ -176,85 +249,109 @@ void launch_whiten(const StepArgs &a, cudaStream_t s, float *X_out, bool stats) 
 #undef TLDA_WHITEN
 }
 
-// ------------------------------------------------------------ touched words
-// Compact list of the batch's distinct words (c_m > 0), warp-aggregated.
-__global__ void k_compact(StepArgs a) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  const bool hit = m < a.V && a.cnt[m] > 0;
-  const unsigned mask = __ballot_sync(0xffffffffu, hit);
-  int base = 0;
-  if (lane == 0 && mask) base = atomicAdd(&a.st->n_touched, __popc(mask));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (hit) a.widx[base + __popc(mask & ((1u << lane) - 1u))] = m;
-}
-
 // ------------------------------------------------------------ a7/a8: Phi-only terms
-// Gram = Phi^T Phi (K x K, padded Kp) and a = m1^T Phi (extra block row).
-__global__ void k_phi_gram(StepArgs a) {
-  const int j = blockIdx.x * 16 + threadIdx.x;
-  const int i = blockIdx.y * 16 + threadIdx.y;
-  if ((int)blockIdx.y == (int)gridDim.y - 1) {
-    if (threadIdx.y == 0 && j < a.Kp) {
+// Gram = Phi^T Phi (Kp x Kp, zero padded) in 32 x 32 tiles over 64-row slabs
+// of Phi held in shared memory; the extra block row forms a = m1^T Phi.
+__global__ void __launch_bounds__(256) k_phi_gram(StepArgs a) {
+  const int bx = blockIdx.x, by = blockIdx.y, tid = threadIdx.x;
+  if (by == (int)gridDim.y - 1) {
+    if (tid < 32) {
+      const int j = bx * 32 + tid;
       float s = 0.f;
       if (j < a.K)
         for (int r = 0; r < a.D; ++r) s = fmaf(a.m1[r], a.Phi[(long long)r * a.K + j], s);
-      a.avec[j] = s;
+      if (j < a.Kp) a.avec[j] = s;
     }
     return;
   }
-  if (i >= a.Kp || j >= a.Kp) return;
-  float s = 0.f;
-  if (i < a.K && j < a.K)
-    for (int r = 0; r < a.D; ++r)
-      s = fmaf(a.Phi[(long long)r * a.K + i], a.Phi[(long long)r * a.K + j], s);
-  a.Gram[i * a.Kp + j] = s;
+  __shared__ float Pi[64][33], Pj[64][33];
+  const int ii = tid >> 3, jj = (tid & 7) * 4;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int r0 = 0; r0 < a.D; r0 += 64) {
+    for (int e = tid; e < 64 * 32; e += 256) {
+      const int r = e >> 5, c = e & 31, gr = r0 + r;
+      const int ci = by * 32 + c, cj = bx * 32 + c;
+      Pi[r][c] = (gr < a.D && ci < a.K) ? a.Phi[(long long)gr * a.K + ci] : 0.f;
+      Pj[r][c] = (gr < a.D && cj < a.K) ? a.Phi[(long long)gr * a.K + cj] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < 64; ++r) {
+      const float x = Pi[r][ii];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(x, Pj[r][jj + q], acc[q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) a.Gram[(by * 32 + ii) * a.Kp + bx * 32 + jj + q] = acc[q];
 }
 
-// E = 3(1+theta) P - 3 G3 and G3 per entry (r, i); block 0 also forms the
-// Phi-only part of the loss.
-__global__ void k_phi_terms(StepArgs a) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < a.D * a.K) {
-    const int r = e / a.K, i = e % a.K;
-    float p = 0.f;
-    for (int j = 0; j < a.K; ++j) {
-      const float g = a.Gram[j * a.Kp + i];
-      p = fmaf(a.Phi[(long long)r * a.K + j], g * g, p);
+// P = Phi (Gram * Gram) in 32 x 32 tiles (rows r of Phi, columns i), then per
+// entry G3 = 2 phi_ri a_i + m1_r |phi_i|^2 - 2 m1_r a_i^2 and
+// E = 3(1+theta) P - 3 G3.  Block (0, 0) also forms the Phi-only loss part.
+__global__ void __launch_bounds__(256) k_phi_terms(StepArgs a) {
+  const int bx = blockIdx.x, by = blockIdx.y, tid = threadIdx.x;
+  __shared__ float Pr[32][65], G2[64][33];
+  const int rr = tid >> 3, ic = (tid & 7) * 4;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int j0 = 0; j0 < a.K; j0 += 64) {
+    for (int e = tid; e < 32 * 64; e += 256) {
+      const int r = e >> 6, j = e & 63, gr = by * 32 + r, gj = j0 + j;
+      Pr[r][j] = (gr < a.D && gj < a.K) ? a.Phi[(long long)gr * a.K + gj] : 0.f;
+      const int jb = e >> 5, c = e & 31, gjb = j0 + jb, gi = bx * 32 + c;
+      const float g = (gjb < a.K && gi < a.K) ? a.Gram[gjb * a.Kp + gi] : 0.f;
+      G2[jb][c] = g * g;
     }
-    const float ai = a.avec[i], n2 = a.Gram[i * a.Kp + i], mr = a.m1[r];
-    const float g3 = 2.f * a.Phi[(long long)r * a.K + i] * ai + mr * n2 - 2.f * mr * ai * ai;
-    a.G3[r * a.Kp + i] = g3;
-    a.E[r * a.Kp + i] = 3.f * (1.f + a.theta) * p - 3.f * g3;
+    __syncthreads();
+#pragma unroll 8
+    for (int j = 0; j < 64; ++j) {
+      const float x = Pr[rr][j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(x, G2[j][ic + q], acc[q]);
+    }
+    __syncthreads();
   }
-  if (blockIdx.x == 0 && a.want_loss) {
+  const int r = by * 32 + rr;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = bx * 32 + ic + q;
+    if (r < a.D && i < a.K) {
+      const float ai = a.avec[i], n2 = a.Gram[i * a.Kp + i], mr = a.m1[r];
+      const float g3 = 2.f * a.Phi[(long long)r * a.K + i] * ai + mr * n2 - 2.f * mr * ai * ai;
+      a.G3[r * a.Kp + i] = g3;
+      a.E[r * a.Kp + i] = 3.f * (1.f + a.theta) * acc[q] - 3.f * g3;
+    }
+  }
+  if (bx == 0 && by == 0 && a.want_loss) {
     __shared__ double red[256];
     double s = 0.0;
-    for (int q = threadIdx.x; q < a.K * a.K; q += blockDim.x) {
+    for (int q = tid; q < a.K * a.K; q += blockDim.x) {
       const double g = a.Gram[(q / a.K) * a.Kp + (q % a.K)];
       s += 0.5 * (1.0 + a.theta) * g * g * g;
     }
-    for (int i = threadIdx.x; i < a.K; i += blockDim.x) {
+    for (int i = tid; i < a.K; i += blockDim.x) {
       const double ai = a.avec[i], n2 = a.Gram[i * a.Kp + i];
       s -= 3.0 * ai * n2 - 2.0 * ai * ai * ai;
     }
-    red[threadIdx.x] = s;
+    red[tid] = s;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      if (tid < w) red[tid] += red[tid + w];
       __syncthreads();
     }
-    if (threadIdx.x == 0) a.st->loss_phi = red[0];
+    if (tid == 0) a.st->loss_phi = red[0];
   }
 }
 
 void launch_phi_gram(const StepArgs &a, cudaStream_t s) {
-  dim3 g1(a.Kp / 16, a.Kp / 16 + 1), b1(16, 16);
-  k_phi_gram<<<g1, b1, 0, s>>>(a);
+  dim3 g(a.Kp / 32, a.Kp / 32 + 1);
+  k_phi_gram<<<g, 256, 0, s>>>(a);
 }
 
 void launch_phi_terms(const StepArgs &a, cudaStream_t s) {
-  k_phi_terms<<<(a.D * a.K + 255) / 256, 256, 0, s>>>(a);
+  dim3 g(a.Kp / 32, a.Dp / 32);
+  k_phi_terms<<<g, 256, 0, s>>>(a);
 }
 
 // ------------------------------------------------------------ a3/a4: Q and Y (FP32)
@@ -332,49 +429,63 @@ __global__ void __launch_bounds__(256) k_qy_f32(StepArgs a) {
 }
 
 // ------------------------------------------------------------ a4 + a6 scatter: R, Z, H
-// One warp per document: r_d = sum_m f_dm q_m^2 (gathered Q rows), z_d = y_d^2 - r_d,
-// H_m += f_dm y_d (vector atomics), and the document part of the loss.
+// One warp per document (16 per block): r_d = sum_m f_dm q_m^2 over gathered
+// Q rows (four in flight), z_d = y_d^2 - r_d, H_m += f_dm y_d (vector atomics),
+// and the document part of the loss.  TC=true writes Z^T (BF16) through shared
+// memory, 32 bytes per topic row, zero-filling up to the 64-column chunk.
 template <int NK, bool TC>
-__global__ void __launch_bounds__(256) k_rz(StepArgs a) {
+__global__ void __launch_bounds__(512) k_rz(StepArgs a) {
   const BatchDesc b = a.st->cur;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int d = blockIdx.x * 8 + warp;
-  if (d >= b.n_docs) {
-    if constexpr (TC) {  // zero Z^T columns up to the 64-column reduction chunk
-      if (d < round_up(b.n_docs, 64))
-        for (int i = lane; i < a.Kp; i += 32) a.BT16[(long long)i * a.ldT + d] = __float2bfloat16_rn(0.f);
-    }
-    return;
-  }
+  const int d0 = blockIdx.x * 16, d = d0 + warp;
+  if (d0 >= (TC ? round_up(b.n_docs, 64) : b.n_docs)) return;
+  __shared__ __nv_bfloat16 zs[TC ? 16 * kMaxDim : 1];
   float4 y[NK], r[NK];
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
     const int col = v * 128 + lane * 4;
-    y[v] = col < a.Kp ? *reinterpret_cast<const float4 *>(a.Y32 + (long long)d * a.Kp + col) : f4(0.f);
+    y[v] = (d < b.n_docs && col < a.Kp) ? *reinterpret_cast<const float4 *>(a.Y32 + (long long)d * a.Kp + col)
+                                         : f4(0.f);
     r[v] = f4(0.f);
   }
-  if (a.same_token) {
+  if (a.same_token && d < b.n_docs) {
     const int lo = b.indptr[d], hi = b.indptr[d + 1];
-    if (lo >= b.nz_base)
-      for (int j = lo; j < hi; ++j) {
-        const long long o = (long long)j - b.nz_base;
-        const int m = __ldg(b.indices + o), f = __ldg(b.counts + o);
-        if (m < 0 || m >= a.V || f <= 0) continue;
-        const float ff = (float)f;
+    if (lo >= b.nz_base) {
+      for (int base = lo; base < hi; base += 32) {
+        const NzChunk c = load_chunk(b, a.V, base, hi, lane, -1);
+        for (int q = 0; q < c.n; q += 4) {
+          int mm[4];
+          float ff[4];
 #pragma unroll
-        for (int v = 0; v < NK; ++v) {
-          const int col = v * 128 + lane * 4;
-          if (col < a.Kp) {
-            const float4 q = *reinterpret_cast<const float4 *>(a.Q32 + (long long)m * a.Kp + col);
-            r[v].x = fmaf(ff * q.x, q.x, r[v].x);
-            r[v].y = fmaf(ff * q.y, q.y, r[v].y);
-            r[v].z = fmaf(ff * q.z, q.z, r[v].z);
-            r[v].w = fmaf(ff * q.w, q.w, r[v].w);
-            atomicAdd(reinterpret_cast<float4 *>(a.H32 + (long long)m * a.Kp + col),
-                      make_float4(ff * y[v].x, ff * y[v].y, ff * y[v].z, ff * y[v].w));
+          for (int u = 0; u < 4; ++u) {
+            mm[u] = __shfl_sync(0xffffffffu, c.m, (q + u) & 31);
+            ff[u] = (float)__shfl_sync(0xffffffffu, c.f, (q + u) & 31);
+            if (q + u >= c.n) ff[u] = 0.f;
+          }
+#pragma unroll
+          for (int v = 0; v < NK; ++v) {
+            const int col = v * 128 + lane * 4;
+            if (col < a.Kp) {
+              float4 qv[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                qv[u] = *reinterpret_cast<const float4 *>(a.Q32 + (long long)mm[u] * a.Kp + col);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const float ff2 = ff[u];
+                r[v].x = fmaf(ff2 * qv[u].x, qv[u].x, r[v].x);
+                r[v].y = fmaf(ff2 * qv[u].y, qv[u].y, r[v].y);
+                r[v].z = fmaf(ff2 * qv[u].z, qv[u].z, r[v].z);
+                r[v].w = fmaf(ff2 * qv[u].w, qv[u].w, r[v].w);
+                if (ff2 != 0.f)
+                  atomicAdd(reinterpret_cast<float4 *>(a.H32 + (long long)mm[u] * a.Kp + col),
+                            make_float4(ff2 * y[v].x, ff2 * y[v].y, ff2 * y[v].z, ff2 * y[v].w));
+              }
+            }
           }
         }
       }
+    }
   }
   float ls = 0.f;
 #pragma unroll
@@ -384,10 +495,11 @@ __global__ void __launch_bounds__(256) k_rz(StepArgs a) {
       const float4 z = make_float4(y[v].x * y[v].x - r[v].x, y[v].y * y[v].y - r[v].y,
                                    y[v].z * y[v].z - r[v].z, y[v].w * y[v].w - r[v].w);
       if constexpr (TC) {
-        const float zz[4] = {z.x, z.y, z.z, z.w};
-        for (int q = 0; q < 4; ++q) a.BT16[(long long)(col + q) * a.ldT + d] = __float2bfloat16_rn(zz[q]);
+        __nv_bfloat162 *sz = reinterpret_cast<__nv_bfloat162 *>(zs + warp * a.Kp + col);
+        sz[0] = __floats2bfloat162_rn(z.x, z.y);
+        sz[1] = __floats2bfloat162_rn(z.z, z.w);
       } else {
-        *reinterpret_cast<float4 *>(a.Z32 + (long long)d * a.Kp + col) = z;
+        if (d < b.n_docs) *reinterpret_cast<float4 *>(a.Z32 + (long long)d * a.Kp + col) = z;
       }
       if (a.want_loss)
         ls += y[v].x * (y[v].x * y[v].x - 3.f * r[v].x) + y[v].y * (y[v].y * y[v].y - 3.f * r[v].y) +
@@ -396,7 +508,18 @@ __global__ void __launch_bounds__(256) k_rz(StepArgs a) {
   }
   if (a.want_loss) {
     for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
-    if (lane == 0) atomicAdd(&a.st->loss_data, (double)ls);
+    if (lane == 0 && ls != 0.f) atomicAdd(&a.st->loss_data, (double)ls);
+  }
+  if constexpr (TC) {
+    __syncthreads();
+    for (int n = threadIdx.x; n < a.Kp; n += blockDim.x) {
+      __align__(16) __nv_bfloat16 col[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) col[q] = zs[q * a.Kp + n];
+      uint4 *dst = reinterpret_cast<uint4 *>(a.BT16 + (long long)n * a.ldT + d0);
+      dst[0] = reinterpret_cast<const uint4 *>(col)[0];
+      dst[1] = reinterpret_cast<const uint4 *>(col)[1];
+    }
   }
 }
 
@@ -494,8 +617,6 @@ __global__ void __launch_bounds__(256) k_g_f32(StepArgs a) {
         make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
 }
 
-void launch_compact(const StepArgs &a, cudaStream_t s) { k_compact<<<(a.V + 255) / 256, 256, 0, s>>>(a); }
-
 void launch_qy_f32(const StepArgs &a, cudaStream_t s) {
   dim3 g((a.V + a.Bmax + 63) / 64, a.Kp / 64);
   k_qy_f32<<<g, 256, 0, s>>>(a);
@@ -506,8 +627,8 @@ void launch_rz(const StepArgs &a, cudaStream_t s) {
   const bool tc = a.precision == TLDA_BF16;
 #define TLDA_RZ(NKv)                                                                      \
   if (nk == NKv) {                                                                        \
-    if (tc) k_rz<NKv, true><<<(a.Bmax + 7) / 8, 256, 0, s>>>(a);                          \
-    else k_rz<NKv, false><<<(a.Bmax + 7) / 8, 256, 0, s>>>(a);                            \
+    if (tc) k_rz<NKv, true><<<round_up(a.Bmax, 64) / 16, 512, 0, s>>>(a);                 \
+    else k_rz<NKv, false><<<round_up(a.Bmax, 64) / 16, 512, 0, s>>>(a);                   \
     return;                                                                               \
   }
   TLDA_RZ(1) TLDA_RZ(2) TLDA_RZ(3) TLDA_RZ(4)
@@ -528,20 +649,30 @@ void launch_g_f32(const StepArgs &a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ a9: reduce + update
-// Entry (i, n): g = sum over partials; grad = E - 3 c3/S3 g; Phi -= lr grad
-// (skipped on a sticky error or S3 = 0).  The last block (ticket) writes the
-// loss, clears the per-step sums and advances the pass descriptor.
+// 32 entries (i, n) per block, the partial sums split over 8 warps:
+// g = sum over partials; grad = E - 3 c3/S3 g; Phi -= lr grad (skipped on a
+// sticky error or S3 = 0).  The last block (ticket) writes the loss, clears
+// the per-step sums and advances the pass descriptor.
 __global__ void __launch_bounds__(256) k_reduce_update(StepArgs a) {
   DevState *st = a.st;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
   const unsigned long long S3 = st->S3;
   const int err = st->err;
   const double scale = S3 ? a.c3 / (double)S3 : 0.0;
-  if (e < a.D * a.K) {
-    const int i = e / a.K, n = e % a.K;
-    const long long off = (long long)i * a.Kp + n, stride = (long long)a.Dp * a.Kp;
+  const bool live = e < a.D * a.K;
+  const int i = live ? e / a.K : 0, n = live ? e % a.K : 0;
+  const long long off = (long long)i * a.Kp + n, stride = (long long)a.Dp * a.Kp;
+  float part = 0.f;
+  if (live)
+    for (int s = w; s < a.nsplit; s += 8) part += a.Gpart[s * stride + off];
+  __shared__ float red[8][32];
+  red[w][lane] = part;
+  __syncthreads();
+  if (w == 0 && live) {
     float g = 0.f;
-    for (int s = 0; s < a.nsplit; ++s) g += a.Gpart[s * stride + off];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) g += red[q][lane];
     if (a.mode == 1) {
       a.gdata_out[e] = S3 ? (float)(scale * (double)g) + a.G3[off] : 0.f;
     } else {
@@ -552,6 +683,7 @@ __global__ void __launch_bounds__(256) k_reduce_update(StepArgs a) {
   }
   __threadfence();
   __shared__ bool last;
+  __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
   __syncthreads();
   if (last && threadIdx.x == 0) {
@@ -568,7 +700,7 @@ __global__ void __launch_bounds__(256) k_reduce_update(StepArgs a) {
 }
 
 void launch_reduce_update(const StepArgs &a, cudaStream_t s) {
-  k_reduce_update<<<(a.D * a.K + 255) / 256, 256, 0, s>>>(a);
+  k_reduce_update<<<(a.D * a.K + 31) / 32, 256, 0, s>>>(a);
 }
 
 }  // namespace tlda

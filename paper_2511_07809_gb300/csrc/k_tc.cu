@@ -70,6 +70,14 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
+// Non-tensor bulk copy global -> shared (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -131,12 +139,6 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 
 __host__ __device__ constexpr int tmem_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : 256; }
 
-// Byte offset of element (row, k) inside a [rows x 64] BF16 sub-tile stored in
-// the 128-byte swizzle layout (16-byte chunk index XOR row mod 8).
-__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
-  return static_cast<uint32_t>(row * 128 + ((((k >> 3) ^ (row & 7)) & 7) << 4) + ((k & 7) << 1));
-}
-
 __device__ __forceinline__ unsigned char *align1024(unsigned char *p) {
   return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
@@ -161,19 +163,7 @@ __global__ void __launch_bounds__(128) k_qy_tc(StepArgs a, const __grid_constant
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(tslot, tmem_cols(KP));
-  // B = Phi^T (KP x Dp, K-major), built from the FP32 factors (zero padded)
-  for (int g = tid; g < KP * KA * 8; g += 128) {
-    const int n = g % KP, kc = g / KP;  // kc: 8-element chunk along Dp
-    __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int k = kc * 8 + j;
-      v[j] = __float2bfloat16_rn((k < a.D && n < a.K) ? a.Phi[(long long)k * a.K + n] : 0.f);
-    }
-    const int sub = kc >> 3;
-    *reinterpret_cast<uint4 *>(sB + sub * KP * 128 + sw128_offset(n, (kc & 7) * 8)) =
-        *reinterpret_cast<const uint4 *>(v);
-  }
+  // B = Phi^T (KP x Dp, K-major): the swizzled image the scan kernel built
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
@@ -183,9 +173,10 @@ __global__ void __launch_bounds__(128) k_qy_tc(StepArgs a, const __grid_constant
   if (tid == 0) failed = 0;
   __syncthreads();
   if (tid == 0) {
-    mbar_arrive_expect_tx(&bars[0], KA * 16384);
+    mbar_arrive_expect_tx(&bars[0], KA * 16384 + KA * KP * 128);
 #pragma unroll
     for (int kb = 0; kb < KA; ++kb) tma_load_2d(sA + kb * 16384, &tmA, &bars[0], kb * 64, r0);
+    bulk_load(sB, a.PhiImg, KA * KP * 128, &bars[0]);
     if (mbar_wait(&bars[0], 0)) {
       tc_fence_after();
       const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
@@ -324,46 +315,70 @@ __global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant_
 }
 
 // ------------------------------------------------------------------ Zc (BF16, transposed)
-// One warp per compact slot t: Zc_t = q (2 c q - 2 H_m) into BT16 column
-// Bmax + t and U_m into AT16 column Bmax + t; H_m, c_m cleared.  Slots in
-// [n_touched, round_up(n_touched, 64)) write zero columns (reduction padding).
+// One warp per compact slot t (16 per block): Zc_t = q (2 c q - 2 H_m) and the
+// word's U row are staged in shared memory, then written as 32-byte runs into
+// columns Bmax + t0 .. t0+16 of BT16 and AT16; H_m and c_m are cleared.  Slots
+// in [n_touched, round_up(n_touched, 64)) write zero columns (chunk padding).
 template <int NK>
-__global__ void __launch_bounds__(256) k_zh_tc(StepArgs a) {
+__global__ void __launch_bounds__(512) k_zh_tc(StepArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * 8 + warp;
+  const int t0 = blockIdx.x * 16, t = t0 + warp;
   const int nt = a.st->n_touched;
-  if (t >= round_up(nt, 64)) return;
-  const long long colT = (long long)a.Bmax + t;
-  if (t >= nt) {
-    for (int i = lane; i < a.Dp; i += 32) a.AT16[(long long)i * a.ldT + colT] = __float2bfloat16_rn(0.f);
-    for (int i = lane; i < a.Kp; i += 32) a.BT16[(long long)i * a.ldT + colT] = __float2bfloat16_rn(0.f);
-    return;
+  if (t0 >= round_up(nt, 64)) return;
+  __shared__ __align__(16) __nv_bfloat16 zs[16 * kMaxDim];
+  __shared__ __align__(16) __nv_bfloat16 us[16 * kMaxDim];
+  float ls = 0.f, c = 0.f;
+  int m = -1;
+  if (t < nt) {
+    m = a.widx[t];
+    c = (float)a.cnt[m];
   }
-  const int m = a.widx[t];
-  const float c = (float)a.cnt[m];
-  float ls = 0.f;
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
     const int col = v * 128 + lane * 4;
     if (col < a.Kp) {
-      float4 *hp = reinterpret_cast<float4 *>(a.H32 + (long long)m * a.Kp + col);
-      const float4 q = *reinterpret_cast<const float4 *>(a.Q32 + (long long)m * a.Kp + col);
-      const float4 h = *hp;
-      const float z[4] = {q.x * (2.f * c * q.x - 2.f * h.x), q.y * (2.f * c * q.y - 2.f * h.y),
-                          q.z * (2.f * c * q.z - 2.f * h.z), q.w * (2.f * c * q.w - 2.f * h.w)};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) a.BT16[(long long)(col + j) * a.ldT + colT] = __float2bfloat16_rn(z[j]);
-      *hp = make_float4(0.f, 0.f, 0.f, 0.f);
-      ls += q.x * q.x * q.x + q.y * q.y * q.y + q.z * q.z * q.z + q.w * q.w * q.w;
+      float z[4] = {0.f, 0.f, 0.f, 0.f};
+      if (m >= 0) {
+        float4 *hp = reinterpret_cast<float4 *>(a.H32 + (long long)m * a.Kp + col);
+        const float4 q = *reinterpret_cast<const float4 *>(a.Q32 + (long long)m * a.Kp + col);
+        const float4 h = *hp;
+        z[0] = q.x * (2.f * c * q.x - 2.f * h.x);
+        z[1] = q.y * (2.f * c * q.y - 2.f * h.y);
+        z[2] = q.z * (2.f * c * q.z - 2.f * h.z);
+        z[3] = q.w * (2.f * c * q.w - 2.f * h.w);
+        *hp = make_float4(0.f, 0.f, 0.f, 0.f);
+        ls += q.x * q.x * q.x + q.y * q.y * q.y + q.z * q.z * q.z + q.w * q.w * q.w;
+      }
+      __nv_bfloat162 *sz = reinterpret_cast<__nv_bfloat162 *>(zs + warp * a.Kp + col);
+      sz[0] = __floats2bfloat162_rn(z[0], z[1]);
+      sz[1] = __floats2bfloat162_rn(z[2], z[3]);
     }
   }
-  for (int i = lane; i < a.Dp; i += 32) a.AT16[(long long)i * a.ldT + colT] = a.U16[(long long)m * a.Dp + i];
-  if (a.want_loss) {
+  for (int i = lane * 8; i < a.Dp; i += 256) {
+    uint4 u = make_uint4(0u, 0u, 0u, 0u);
+    if (m >= 0) u = *reinterpret_cast<const uint4 *>(a.U16 + (long long)m * a.Dp + i);
+    *reinterpret_cast<uint4 *>(us + warp * a.Dp + i) = u;
+  }
+  if (a.want_loss && m >= 0) {
     for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
     if (lane == 0) atomicAdd(&a.st->loss_data, 2.0 * (double)c * (double)ls);
   }
   __syncwarp();
-  if (lane == 0) a.cnt[m] = 0;
+  if (lane == 0 && m >= 0) a.cnt[m] = 0;
+  __syncthreads();
+  const long long colT = (long long)a.Bmax + t0;
+  for (int r = threadIdx.x; r < a.Kp + a.Dp; r += blockDim.x) {
+    const bool isB = r < a.Kp;
+    const int row = isB ? r : r - a.Kp;
+    const __nv_bfloat16 *src = isB ? zs : us;
+    const int ld = isB ? a.Kp : a.Dp;
+    __align__(16) __nv_bfloat16 colv[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) colv[q] = src[q * ld + row];
+    uint4 *dst = reinterpret_cast<uint4 *>((isB ? a.BT16 : a.AT16) + (long long)row * a.ldT + colT);
+    dst[0] = reinterpret_cast<const uint4 *>(colv)[0];
+    dst[1] = reinterpret_cast<const uint4 *>(colv)[1];
+  }
 }
 
 // ------------------------------------------------------------------ host side
@@ -465,9 +480,9 @@ void launch_g_tc(const StepArgs &a, cudaStream_t s) {
 
 void launch_zh_tc(const StepArgs &a, cudaStream_t s) {
   const int nk = (a.Kp + 127) / 128;
-  const int grid = round_up(a.V, 64) / 8;
-  if (nk == 1) k_zh_tc<1><<<grid, 256, 0, s>>>(a);
-  else k_zh_tc<2><<<grid, 256, 0, s>>>(a);
+  const int grid = round_up(a.V, 64) / 16;
+  if (nk == 1) k_zh_tc<1><<<grid, 512, 0, s>>>(a);
+  else k_zh_tc<2><<<grid, 512, 0, s>>>(a);
 }
 
 }  // namespace tlda

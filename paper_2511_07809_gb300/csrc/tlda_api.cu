@@ -12,8 +12,8 @@
 using namespace tlda;
 
 namespace tlda {
-const char *const kKernelNames[kNumKernels] = {"scan_whiten", "compact", "qy", "rz", "zh",
-                                                "g_reduce", "reduce_update", "phi_gram", "phi_terms"};
+const char *const kKernelNames[kNumKernels] = {"scan_whiten", "qy", "rz", "zh", "g_reduce",
+                                                "reduce_update", "phi_gram", "phi_terms"};
 }
 
 namespace {
@@ -97,6 +97,7 @@ StepArgs make_args(tlda_ctx *c) {
   a.ldT = c->ldT;
   a.precision = c->p.precision;
   a.tc_maps = c->tc_maps;
+  a.PhiImg = c->PhiImg;
   if (a.precision == TLDA_BF16) a.nsplit = c->nsplit_tc;
   return a;
 }
@@ -148,23 +149,22 @@ struct Prof {
 // Enqueues one CP step on ctx->stream for the batch in st->cur: the Phi-only
 // terms on the side stream, the data-term chain on the main stream, then the
 // reduction and update once both are done.
-tlda_status enqueue_step(tlda_ctx *ctx, const StepArgs &a) {
+tlda_status enqueue_step(tlda_ctx *ctx, const StepArgs &a, cudaStream_t main) {
   const bool tc = a.precision == TLDA_BF16;
-  CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+  CK(cudaEventRecord(ctx->ev_fork, main));
   CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
   { Prof p(ctx, kPhiGram, ctx->side); launch_phi_gram(a, ctx->side); }
   { Prof p(ctx, kPhiTerms, ctx->side); launch_phi_terms(a, ctx->side); }
   CKL();
   CK(cudaEventRecord(ctx->ev_join, ctx->side));
-  { Prof p(ctx, kWhiten, ctx->stream); launch_whiten(a, ctx->stream, nullptr, true); }
-  if (a.same_token) { Prof p(ctx, kCompact, ctx->stream); launch_compact(a, ctx->stream); }
-  { Prof p(ctx, kQY, ctx->stream); if (tc) launch_qy_tc(a, ctx->stream); else launch_qy_f32(a, ctx->stream); }
-  { Prof p(ctx, kRZ, ctx->stream); launch_rz(a, ctx->stream); }
-  if (a.same_token) { Prof p(ctx, kZH, ctx->stream); if (tc) launch_zh_tc(a, ctx->stream); else launch_zh_f32(a, ctx->stream); }
-  { Prof p(ctx, kG, ctx->stream); if (tc) launch_g_tc(a, ctx->stream); else launch_g_f32(a, ctx->stream); }
+  { Prof p(ctx, kWhiten, main); launch_whiten(a, main, nullptr, true); }
+  { Prof p(ctx, kQY, main); if (tc) launch_qy_tc(a, main); else launch_qy_f32(a, main); }
+  { Prof p(ctx, kRZ, main); launch_rz(a, main); }
+  if (a.same_token) { Prof p(ctx, kZH, main); if (tc) launch_zh_tc(a, main); else launch_zh_f32(a, main); }
+  { Prof p(ctx, kG, main); if (tc) launch_g_tc(a, main); else launch_g_f32(a, main); }
   CKL();
-  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-  { Prof p(ctx, kReduceUpdate, ctx->stream); launch_reduce_update(a, ctx->stream); }
+  CK(cudaStreamWaitEvent(main, ctx->ev_join, 0));
+  { Prof p(ctx, kReduceUpdate, main); launch_reduce_update(a, main); }
   CKL();
   return TLDA_OK;
 }
@@ -273,6 +273,9 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
   CA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
   CA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
   CA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  CA(cudaStreamCreateWithFlags(&ctx->pstream, cudaStreamNonBlocking));
+  CA(cudaEventCreateWithFlags(&ctx->ev_pass0, cudaEventDisableTiming));
+  CA(cudaEventCreateWithFlags(&ctx->ev_pass1, cudaEventDisableTiming));
   const size_t V = vocab, Dp = ctx->Dp, Kp = ctx->Kp, Bm = ctx->Bmax;
   const int tiles = (ctx->Dp / 64) * (ctx->Kp / 64);
   ctx->nsplit = std::max(8, std::min(256, 2 * ctx->num_sms / tiles));
@@ -303,6 +306,7 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
     ctx->X16 = ctx->UX16 + V * Dp;
     CA(dalloc(&ctx->AT16, Dp * (size_t)ctx->ldT, true));
     CA(dalloc(&ctx->BT16, Kp * (size_t)ctx->ldT, true));
+    CA(dalloc(&ctx->PhiImg, Dp * Kp, true));
     ctx->tc_maps = tc_make_maps(ctx->UX16, ctx->AT16, ctx->BT16, vocab, ctx->Bmax, ctx->Dp, ctx->Kp, ctx->ldT);
     if (!ctx->tc_maps) return bail(TLDA_ERR_CUDA, "cuTensorMapEncodeTiled", cudaErrorUnknown);
   }
@@ -320,7 +324,7 @@ tlda_status tlda_destroy(tlda_ctx *ctx) {
   if (ctx->tc_maps) tc_free_maps(ctx->tc_maps);
   dfree(ctx->X32); dfree(ctx->Q32); dfree(ctx->Y32); dfree(ctx->Z32); dfree(ctx->Zc32);
   dfree(ctx->H32); dfree(ctx->cnt); dfree(ctx->widx); dfree(ctx->Gpart); dfree(ctx->Gram);
-  dfree(ctx->avec); dfree(ctx->E); dfree(ctx->G3); dfree(ctx->AT16);
+  dfree(ctx->avec); dfree(ctx->E); dfree(ctx->G3); dfree(ctx->AT16); dfree(ctx->PhiImg);
   dfree(ctx->BT16); dfree(ctx->st); dfree(ctx->descs); dfree(ctx->P64); dfree(ctx->Ccnt);
   dfree(ctx->TS); dfree(ctx->fit_err); dfree(ctx->stage[0]); dfree(ctx->stage[1]);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
@@ -332,6 +336,10 @@ tlda_status tlda_destroy(tlda_ctx *ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->pstream) cudaStreamDestroy(ctx->pstream);
+  if (ctx->ev_pass0) cudaEventDestroy(ctx->ev_pass0);
+  if (ctx->ev_pass1) cudaEventDestroy(ctx->ev_pass1);
   delete ctx;
   return TLDA_OK;
 }
@@ -400,7 +408,7 @@ static tlda_status step_common(tlda_ctx *ctx, const tlda_csr *batch, float *Phi,
   a.want_loss = loss_out ? 1 : 0;
   launch_set_desc(ctx->st, desc_of(batch), ctx->stream);
   CKL();
-  s = enqueue_step(ctx, a);
+  s = enqueue_step(ctx, a, ctx->stream);
   if (s) return s;
   if (loss_out || mode == 1) {
     s = read_state(ctx);
@@ -479,35 +487,67 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
     }
     hd[b] = d;
   }
-  CK(cudaMemcpyAsync(ctx->descs, hd.data(), sizeof(BatchDesc) * n_batches, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));  // hd is pageable: keep it alive until copied
+  // the pass runs on the context's own non-blocking stream, ordered after
+  // and before the caller's stream by events (graph capture needs a stream
+  // other than the legacy default one)
+  cudaStream_t ps = ctx->pstream;
+  CK(cudaEventRecord(ctx->ev_pass0, ctx->stream));
+  CK(cudaStreamWaitEvent(ps, ctx->ev_pass0, 0));
+  CK(cudaMemcpyAsync(ctx->descs, hd.data(), sizeof(BatchDesc) * n_batches, cudaMemcpyHostToDevice, ps));
+  CK(cudaStreamSynchronize(ps));  // hd is pageable: keep it alive until copied
   StepArgs a = make_args(ctx);
   a.lr = lr;
   a.Phi = Phi;
   a.want_loss = loss_out ? 1 : 0;
   double *losses = nullptr;
   if (loss_out) CK(cudaMallocHost(reinterpret_cast<void **>(&losses), sizeof(double) * n_batches));
-  launch_begin_pass(ctx->st, ctx->descs, n_batches, ctx->stream);
+  launch_begin_pass(ctx->st, ctx->descs, n_batches, ps);
   CKL();
+  // one captured step, replayed per batch (not while the event profiler is on)
+  const bool use_graph = ctx->prof_mask == 0;
+  if (use_graph && !(ctx->step_exec && ctx->g_lr == lr && ctx->g_phi == Phi && ctx->g_loss == a.want_loss)) {
+    if (ctx->step_exec) {
+      cudaGraphExecDestroy(ctx->step_exec);
+      ctx->step_exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal));
+    tlda_status cs = enqueue_step(ctx, a, ps);
+    cudaError_t ce = cudaStreamEndCapture(ps, &g);
+    if (cs) {
+      if (g) cudaGraphDestroy(g);
+      return cs;
+    }
+    CK(ce);
+    ce = cudaGraphInstantiate(&ctx->step_exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(ce);
+    ctx->g_lr = lr;
+    ctx->g_phi = Phi;
+    ctx->g_loss = a.want_loss;
+  }
   for (int b = 0; b < n_batches && s == TLDA_OK; ++b) {
     if (host) {
-      // the slot was last read by step b-2; the stream orders the copy after it
+      // the slot was last read by step b-2, earlier on the same stream
       const int64_t d0 = batch_offsets[b], d1 = batch_offsets[b + 1];
       const long long lo = corpus->indptr[d0], hi = corpus->indptr[d1];
       const BatchDesc &d = hd[b];
       CK(cudaMemcpyAsync(const_cast<int32_t *>(d.indptr), corpus->indptr + d0, sizeof(int32_t) * (d1 - d0 + 1),
-                         cudaMemcpyHostToDevice, ctx->stream));
+                         cudaMemcpyHostToDevice, ps));
       if (hi > lo) {
         CK(cudaMemcpyAsync(const_cast<int32_t *>(d.indices), corpus->indices + lo, sizeof(int32_t) * (hi - lo),
-                           cudaMemcpyHostToDevice, ctx->stream));
+                           cudaMemcpyHostToDevice, ps));
         CK(cudaMemcpyAsync(const_cast<int32_t *>(d.counts), corpus->counts + lo, sizeof(int32_t) * (hi - lo),
-                           cudaMemcpyHostToDevice, ctx->stream));
+                           cudaMemcpyHostToDevice, ps));
       }
     }
-    s = enqueue_step(ctx, a);
+    if (use_graph) CK(cudaGraphLaunch(ctx->step_exec, ps));
+    else s = enqueue_step(ctx, a, ps);
     if (loss_out && s == TLDA_OK)
-      CK(cudaMemcpyAsync(losses + b, &ctx->st->loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(losses + b, &ctx->st->loss, sizeof(double), cudaMemcpyDeviceToHost, ps));
   }
+  CK(cudaEventRecord(ctx->ev_pass1, ps));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_pass1, 0));
   if (s) {
     if (losses) cudaFreeHost(losses);
     return s;

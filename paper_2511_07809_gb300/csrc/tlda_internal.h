@@ -84,6 +84,7 @@ struct StepArgs {
   int ldT;                       // Bmax + V rounded up
   int precision;
   const void *tc_maps;           // host pointer to the TMA tensor maps (BF16 form)
+  __nv_bfloat16 *PhiImg;         // shared-memory image of Phi^T (BF16 form, Kp x Dp, swizzled)
   // caller buffers
   float *Phi;                    // D x K (user layout), updated in place
   float *grad_out;               // D x K or null
@@ -114,6 +115,7 @@ struct tlda_ctx {
   int nsplit = 0, nsplit_tc = 0;
   __nv_bfloat16 *UX16 = nullptr, *X16 = nullptr, *AT16 = nullptr, *BT16 = nullptr;
   void *tc_maps = nullptr;
+  __nv_bfloat16 *PhiImg = nullptr;
   tlda::DevState *st = nullptr;
   tlda::DevState *st_host = nullptr;   // pinned mirror for reads
   tlda::BatchDesc *descs = nullptr;    // pass descriptors (device)
@@ -127,6 +129,13 @@ struct tlda_ctx {
   // pass staging (host input)
   int32_t *stage[2] = {nullptr, nullptr};
   long long stage_cap = 0;
+  // pass stream and the cached graph of one step (keyed by the baked arguments)
+  cudaStream_t pstream = nullptr;
+  cudaEvent_t ev_pass0 = nullptr, ev_pass1 = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  float g_lr = 0.f;
+  const float *g_phi = nullptr;
+  int g_loss = -1;
   // event profiler: kernels whose bit is set in prof_mask are bracketed by events
   uint32_t prof_mask = 0;
   struct ProfRec { int id; cudaEvent_t a, b; };
@@ -139,7 +148,7 @@ struct tlda_ctx {
 namespace tlda {
 // Kernels of one CP step, in launch order (ids used by the event profiler).
 enum KernelId {
-  kWhiten = 0, kCompact, kQY, kRZ, kZH, kG, kReduceUpdate, kPhiGram, kPhiTerms, kNumKernels
+  kWhiten = 0, kQY, kRZ, kZH, kG, kReduceUpdate, kPhiGram, kPhiTerms, kNumKernels
 };
 extern const char *const kKernelNames[kNumKernels];
 
@@ -147,7 +156,6 @@ extern const char *const kKernelNames[kNumKernels];
 void launch_set_desc(DevState *st, const BatchDesc &b, cudaStream_t s);
 void launch_begin_pass(DevState *st, const BatchDesc *descs, int n, cudaStream_t s);
 void launch_whiten(const StepArgs &a, cudaStream_t s, float *X_out, bool stats);
-void launch_compact(const StepArgs &a, cudaStream_t s);
 void launch_qy_f32(const StepArgs &a, cudaStream_t s);
 void launch_rz(const StepArgs &a, cudaStream_t s);
 void launch_zh_f32(const StepArgs &a, cudaStream_t s);

@@ -258,8 +258,8 @@ class TLDA:
         self._check(self.lib.tlda_sync(self.h))
 
     # ------------------------------------------------------------ profiling
-    KERNELS = ("scan_whiten", "compact", "qy", "rz", "zh", "g_reduce", "reduce_update",
-               "phi_gram", "phi_terms")
+    KERNELS = ("scan_whiten", "qy", "rz", "zh", "g_reduce", "reduce_update", "phi_gram",
+               "phi_terms")
 
     def profile(self, kernels=()):
         """Bracket the named kernels with CUDA events from now on (empty: off)."""
