@@ -354,15 +354,23 @@ def main():
     nnz_all = np.concatenate([np.diff(corpus.indptr[np.array(s)]) for s in timed_segs])
     D = K = sp.K
     roof = None
-    if dominant in ("qy", "g_reduce") and launches:
+    if dominant in ("qy", "g_reduce", "fused") and launches:
         nt = np.concatenate([distinct_words(corpus, s) for s in timed_segs])
-        flops = 2.0 * float((B_all + nt).sum()) * D * K / len(B_all)
+        if dominant == "fused":
+            # the method's contractions this kernel performs (factored count,
+            # unpadded D, K): X = F U, Y = X Phi, Q = U_t Phi, R = F (Q*Q),
+            # G1 = X^T Z, H = F^T Y, G2 = U_t^T Zc
+            flops = float((2.0 * nnz_all * D + 4.0 * B_all * D * K + 4.0 * nt * D * K
+                           + 4.0 * nnz_all * K).sum()) / len(B_all)
+        else:
+            flops = 2.0 * float((B_all + nt).sum()) * D * K / len(B_all)
         ach = flops / (kms / launches / 1e3) / 1e12
         if primary == "bf16":
             pk, unit, bound = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]), "TFLOP/s", "tensor"
         else:
             pk, unit, bound = FP32_ALU_PEAK_TFLOPS, "TFLOP/s", "alu"
-        roof = {"bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk}
+        roof = {"bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk,
+                "algorithmic_flop_per_launch": flops}
     elif launches:
         # HBM-bound kernels: algorithmic bytes = the batch's CSR stream + X written
         xbytes = D * 4 if primary == "fp32" else D * 2 * 2

@@ -249,7 +249,8 @@ tlda_status tlda_cp_step_noalloc(const tlda_csr *batch, const float *W, const fl
 /* Per-kernel device time, from CUDA events recorded around each launch on
  * the stream it is launched on.  Kernels of one CP step, in launch order:
  *   0 scan_whiten  1 qy  2 rz  3 zh  4 g_reduce  5 reduce_update
- *   6 phi_gram  7 phi_terms (6 and 7 run on the context's side stream).
+ *   6 phi_gram  7 phi_terms (6 and 7 run on the context's side stream)
+ *   8 fused (BF16 form with D, K <= 128: replaces kernels 0-4).
  * tlda_profile sets the mask of bracketed kernels (bit i = kernel i; 0 turns
  * profiling off) and clears the totals.  tlda_profile_read synchronises and
  * returns the kernel's name (static string), launch count and summed

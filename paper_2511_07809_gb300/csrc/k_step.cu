@@ -93,34 +93,12 @@ __device__ __forceinline__ NzChunk load_chunk(const BatchDesc &b, int V, int bas
 // x_d = sum_m f_dm u_m (FP32) four U rows in flight at a time, and (stats)
 // adds c_m, appends first-seen words to the touched list, adds the block's
 // share of S3.  TC=true also writes X in BF16 row-major (X16) and transposed
-// (AT16 columns, via shared memory); its last block builds the shared-memory
-// image of the B operand Phi^T (BF16, 128-byte swizzle) for the Q/Y product.
+// (AT16 columns, via shared memory).
 template <int NV, bool TC>
 __global__ void __launch_bounds__(32 * kDocsPerBlock)
     k_scan_whiten(StepArgs a, float *X_out, int stats) {
   const BatchDesc b = a.st->cur;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if constexpr (TC) {
-    if (X_out == nullptr && blockIdx.x == gridDim.x - 1) {
-      // Phi^T image: (Dp/64) sub-tiles of [Kp rows x 64] BF16, row n at n*128
-      // bytes, 16-byte chunk c of row n stored at chunk c ^ (n & 7).
-      const int groups = a.Kp * (a.Dp / 8);
-      for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-        const int n = g % a.Kp, kc = g / a.Kp;
-        __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int k = kc * 8 + q;
-          v[q] = __float2bfloat16_rn((k < a.D && n < a.K) ? a.Phi[(long long)k * a.K + n] : 0.f);
-        }
-        const int sub = kc >> 3, ch = kc & 7;
-        unsigned char *dst = reinterpret_cast<unsigned char *>(a.PhiImg) + (size_t)sub * a.Kp * 128 +
-                             n * 128 + (((ch ^ (n & 7)) & 7) << 4);
-        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(v);
-      }
-      return;
-    }
-  }
   const int d0 = blockIdx.x * kDocsPerBlock;
   if (d0 >= (TC ? round_up(b.n_docs, 64) : b.n_docs)) return;
   const int d = d0 + warp;
@@ -237,7 +215,7 @@ __global__ void __launch_bounds__(32 * kDocsPerBlock)
 
 void launch_whiten(const StepArgs &a, cudaStream_t s, float *X_out, bool stats) {
   const bool tc = a.precision == TLDA_BF16 && X_out == nullptr;
-  const int grid = round_up(a.Bmax, 64) / kDocsPerBlock + (tc ? 1 : 0);
+  const int grid = round_up(a.Bmax, 64) / kDocsPerBlock;
   const int nv = (a.Dp + 127) / 128;
 #define TLDA_WHITEN(NVv)                                                                        \
   if (nv == NVv) {                                                                              \
@@ -353,6 +331,31 @@ void launch_phi_terms(const StepArgs &a, cudaStream_t s) {
   dim3 g(a.Kp / 32, a.Dp / 32);
   k_phi_terms<<<g, 256, 0, s>>>(a);
 }
+
+// ------------------------------------------------------------ Phi^T image (BF16 forms)
+// Element (topic n, feature k) of the B operand Phi^T in the shared-memory
+// layout of the tensor-core kernels: (Dp/64) sub-tiles of [Kp rows x 64]
+// BF16, 16-byte chunk c of row n stored at chunk c ^ (n mod 8).
+__device__ __forceinline__ long long phi_img_index(int n, int k, int Kp) {
+  const int sub = k >> 6, kc = k & 63;
+  return (long long)sub * Kp * 64 + n * 64 + ((((kc >> 3) ^ (n & 7)) & 7) << 3) + (kc & 7);
+}
+
+__global__ void k_phi_img(StepArgs a) {
+  const int groups = a.Kp * (a.Dp / 8);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
+    const int n = g % a.Kp, kc = g / a.Kp;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = kc * 8 + q;
+      v[q] = __float2bfloat16_rn((k < a.D && n < a.K) ? a.Phi[(long long)k * a.K + n] : 0.f);
+    }
+    *reinterpret_cast<uint4 *>(a.PhiImg + phi_img_index(n, kc * 8, a.Kp)) = *reinterpret_cast<const uint4 *>(v);
+  }
+}
+
+void launch_phi_img(const StepArgs &a, cudaStream_t s) { k_phi_img<<<16, 256, 0, s>>>(a); }
 
 // ------------------------------------------------------------ a3/a4: Q and Y (FP32)
 // Rows t < n_touched: Q[widx[t]] = U[widx[t]] Phi; then Y[d] = X[d] Phi.
@@ -678,7 +681,12 @@ __global__ void __launch_bounds__(256) k_reduce_update(StepArgs a) {
     } else {
       const float grad = S3 ? a.E[off] - (float)(3.0 * scale * (double)g) : 0.f;
       if (a.grad_out) a.grad_out[e] = grad;
-      if (!err && S3) a.Phi[e] -= a.lr * grad;
+      float phi = a.Phi[e];
+      if (!err && S3) {
+        phi -= a.lr * grad;
+        a.Phi[e] = phi;
+      }
+      if (a.PhiImg) a.PhiImg[phi_img_index(n, i, a.Kp)] = __float2bfloat16_rn(phi);
     }
   }
   __threadfence();

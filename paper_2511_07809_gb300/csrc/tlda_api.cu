@@ -3,6 +3,7 @@
 // chain on the context's stream.
 #include <algorithm>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -13,7 +14,7 @@ using namespace tlda;
 
 namespace tlda {
 const char *const kKernelNames[kNumKernels] = {"scan_whiten", "qy", "rz", "zh", "g_reduce",
-                                                "reduce_update", "phi_gram", "phi_terms"};
+                                                "reduce_update", "phi_gram", "phi_terms", "fused"};
 }
 
 namespace {
@@ -98,7 +99,7 @@ StepArgs make_args(tlda_ctx *c) {
   a.precision = c->p.precision;
   a.tc_maps = c->tc_maps;
   a.PhiImg = c->PhiImg;
-  if (a.precision == TLDA_BF16) a.nsplit = c->nsplit_tc;
+  if (a.precision == TLDA_BF16) a.nsplit = c->fused ? c->fused_grid : c->nsplit_tc;
   return a;
 }
 
@@ -157,11 +158,18 @@ tlda_status enqueue_step(tlda_ctx *ctx, const StepArgs &a, cudaStream_t main) {
   { Prof p(ctx, kPhiTerms, ctx->side); launch_phi_terms(a, ctx->side); }
   CKL();
   CK(cudaEventRecord(ctx->ev_join, ctx->side));
-  { Prof p(ctx, kWhiten, main); launch_whiten(a, main, nullptr, true); }
-  { Prof p(ctx, kQY, main); if (tc) launch_qy_tc(a, main); else launch_qy_f32(a, main); }
-  { Prof p(ctx, kRZ, main); launch_rz(a, main); }
-  if (a.same_token) { Prof p(ctx, kZH, main); if (tc) launch_zh_tc(a, main); else launch_zh_f32(a, main); }
-  { Prof p(ctx, kG, main); if (tc) launch_g_tc(a, main); else launch_g_f32(a, main); }
+  if (tc && ctx->fused) {
+    // the fused kernel fills its SMs' shared memory: it leaves kPhiSMs SMs
+    // free so the side stream's Phi-only kernels run beside it
+    Prof p(ctx, kFused, main);
+    launch_fused(a, main, ctx->fused_grid);
+  } else {
+    { Prof p(ctx, kWhiten, main); launch_whiten(a, main, nullptr, true); }
+    { Prof p(ctx, kQY, main); if (tc) launch_qy_tc(a, main); else launch_qy_f32(a, main); }
+    { Prof p(ctx, kRZ, main); launch_rz(a, main); }
+    if (a.same_token) { Prof p(ctx, kZH, main); if (tc) launch_zh_tc(a, main); else launch_zh_f32(a, main); }
+    { Prof p(ctx, kG, main); if (tc) launch_g_tc(a, main); else launch_g_f32(a, main); }
+  }
   CKL();
   CK(cudaStreamWaitEvent(main, ctx->ev_join, 0));
   { Prof p(ctx, kReduceUpdate, main); launch_reduce_update(a, main); }
@@ -280,6 +288,8 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
   const int tiles = (ctx->Dp / 64) * (ctx->Kp / 64);
   ctx->nsplit = std::max(8, std::min(256, 2 * ctx->num_sms / tiles));
   ctx->nsplit_tc = 48;
+  ctx->fused = p->precision == TLDA_BF16 && fused_supported(ctx->Dp, ctx->Kp) && !getenv("TLDA_NO_FUSED");
+  ctx->fused_grid = std::max(1, ctx->num_sms - 8);
   CA(dalloc(&ctx->W32, V * D, true));
   CA(dalloc(&ctx->m1, Dp, true));
   CA(dalloc(&ctx->U32, V * Dp, true));
@@ -291,7 +301,7 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
   CA(dalloc(&ctx->H32, V * Kp, true));
   CA(dalloc(&ctx->cnt, V, true));
   CA(dalloc(&ctx->widx, V, true));
-  CA(dalloc(&ctx->Gpart, (size_t)std::max(ctx->nsplit, ctx->nsplit_tc) * Dp * Kp, true));
+  CA(dalloc(&ctx->Gpart, (size_t)std::max({ctx->nsplit, ctx->nsplit_tc, ctx->num_sms}) * Dp * Kp, true));
   CA(dalloc(&ctx->Gram, Kp * Kp, true));
   CA(dalloc(&ctx->avec, Kp, true));
   CA(dalloc(&ctx->E, Dp * Kp, true));
@@ -407,6 +417,7 @@ static tlda_status step_common(tlda_ctx *ctx, const tlda_csr *batch, float *Phi,
   a.mode = mode;
   a.want_loss = loss_out ? 1 : 0;
   launch_set_desc(ctx->st, desc_of(batch), ctx->stream);
+  if (a.PhiImg) launch_phi_img(a, ctx->stream);
   CKL();
   s = enqueue_step(ctx, a, ctx->stream);
   if (s) return s;
@@ -502,6 +513,7 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
   double *losses = nullptr;
   if (loss_out) CK(cudaMallocHost(reinterpret_cast<void **>(&losses), sizeof(double) * n_batches));
   launch_begin_pass(ctx->st, ctx->descs, n_batches, ps);
+  if (a.PhiImg) launch_phi_img(a, ps);
   CKL();
   // one captured step, replayed per batch (not while the event profiler is on)
   const bool use_graph = ctx->prof_mask == 0;

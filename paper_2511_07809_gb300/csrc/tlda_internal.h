@@ -113,6 +113,8 @@ struct tlda_ctx {
   int *cnt = nullptr, *widx = nullptr;
   float *Gpart = nullptr, *Gram = nullptr, *avec = nullptr, *E = nullptr, *G3 = nullptr;
   int nsplit = 0, nsplit_tc = 0;
+  bool fused = false;            // BF16 form through the fused kernel
+  int fused_grid = 0;            // its persistent CTAs (SMs minus those left to the side stream)
   __nv_bfloat16 *UX16 = nullptr, *X16 = nullptr, *AT16 = nullptr, *BT16 = nullptr;
   void *tc_maps = nullptr;
   __nv_bfloat16 *PhiImg = nullptr;
@@ -148,7 +150,7 @@ struct tlda_ctx {
 namespace tlda {
 // Kernels of one CP step, in launch order (ids used by the event profiler).
 enum KernelId {
-  kWhiten = 0, kQY, kRZ, kZH, kG, kReduceUpdate, kPhiGram, kPhiTerms, kNumKernels
+  kWhiten = 0, kQY, kRZ, kZH, kG, kReduceUpdate, kPhiGram, kPhiTerms, kFused, kNumKernels
 };
 extern const char *const kKernelNames[kNumKernels];
 
@@ -165,6 +167,10 @@ void launch_phi_terms(const StepArgs &a, cudaStream_t s);
 void launch_reduce_update(const StepArgs &a, cudaStream_t s);
 void launch_make_u(const float *W, const float *m1, int V, int D, int Dp, float *U32,
                    __nv_bfloat16 *U16, cudaStream_t s);
+void launch_phi_img(const StepArgs &a, cudaStream_t s);
+// k_fused.cu (BF16 fused tensor-core data term)
+bool fused_supported(int Dp, int Kp);
+void launch_fused(const StepArgs &a, cudaStream_t s, int grid);
 // k_tc.cu (BF16 tensor-core form)
 bool tc_supported(int Dp, int Kp);
 void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const __nv_bfloat16 *BT16, int V,

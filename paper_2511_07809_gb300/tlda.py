@@ -259,7 +259,7 @@ class TLDA:
 
     # ------------------------------------------------------------ profiling
     KERNELS = ("scan_whiten", "qy", "rz", "zh", "g_reduce", "reduce_update", "phi_gram",
-               "phi_terms")
+               "phi_terms", "fused")
 
     def profile(self, kernels=()):
         """Bracket the named kernels with CUDA events from now on (empty: off)."""

@@ -212,6 +212,30 @@ def test_cp_step_bf16(lib, same_token):
     assert abs(loss - g["loss"]) <= TOL16 * abs(g["loss"])
 
 
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("same_token", [True, False])
+def test_bf16_fused_and_unfused_forms(lib, monkeypatch, fused, same_token):
+    """D = K = 100 (padded 128) runs the fused tensor-core kernel; with
+    TLDA_NO_FUSED the same context size takes the multi-kernel BF16 path."""
+    if not fused:
+        monkeypatch.setenv("TLDA_NO_FUSED", "1")
+    name = "stream_v20k_k100"
+    sp = ts.WORKLOADS[name]
+    t, W, m1 = _ctx(lib, name, precision="bf16", same_token=same_token)
+    c = C.corpus(name, 6000)
+    b = c.rows(17, 5017)
+    Phi0 = _phi0(sp)
+    Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(Phi)
+    loss = t.cp_step(lib.DeviceCSR.from_corpus(b), Phi, 0.002, grad=grad, want_loss=True)
+    g = _oracle_grad(b, sp, W, m1, Phi0, 0.0, same_token)
+    assert C.rel(grad.cpu().numpy(), g["grad"]) < TOL16
+    assert abs(loss - g["loss"]) <= TOL16 * abs(g["loss"])
+    G, S3 = t.cp_data_term(lib.DeviceCSR.from_corpus(b), torch.tensor(Phi0, dtype=torch.float32, device="cuda"))
+    assert S3 == g["S3"]
+    assert C.rel(G.cpu().numpy(), g["G_data"]) < TOL16
+
+
 def test_pass_bf16_ragged(lib):
     name = "stream_v20k_k100"
     sp = ts.WORKLOADS[name]
