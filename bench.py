@@ -438,7 +438,11 @@ def main():
         cpu = cpu_baseline(ts, sp, cdf, mu, args.cpu_seconds)
 
     if rank == 0:
-        per_step_kernels = 8 if ctx.params.same_token_correction else 7
+        # kernels per step: fused BF16 form (D, K padded to 128): Phi-only x2,
+        # fused, reduction, step end; otherwise Phi-only x2, scan/whiten, Q/Y,
+        # R/Z/H, Zc, reduction over rows, reduction, step end
+        fused = primary == "bf16" and sp.K <= 128 and sp.K > 64
+        per_step_kernels = 5 if fused else 9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,

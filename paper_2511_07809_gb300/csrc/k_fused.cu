@@ -39,7 +39,7 @@ constexpr int kOffY = 180224;       // y tile FP32 32 x 128                     
 constexpr int kOffZ = 196608;       // z tile FP32 32 x 128                         16 KB
 constexpr int kWin = 1024;          // nonzeros whose metadata sit in shared memory
 constexpr int kOffMeta = 212992;    // window metadata m, f, d (12 KB), indptr slice, L
-constexpr int kOffBar = kOffMeta + 3 * kWin * 4 + 512;
+constexpr int kOffBar = kOffMeta + 3 * kWin * 4 + 512;  // 4 mbarriers + TMEM slot
 constexpr int kFusedSmem = 1024 + kOffBar + 64;
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
   int *s_d = reinterpret_cast<int *>(s_f + kWin);           // kWin local documents
   int *s_ptr = s_d + kWin;                                  // kT + 1 absolute offsets
   int *s_L = s_ptr + 64;                                    // kT token counts
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kOffBar);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kOffBar);  // 0: Phi, 1: Y/R and G, 2-3: Q buffers
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
   __shared__ int failed, s_bad, s_mlast;
   __shared__ float s_red[kFusedThreads / 32];
 
@@ -83,8 +83,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
   float *gp = a.Gpart + (long long)blockIdx.x * a.Dp * a.Kp;
 
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
     fence_mbar_init();
     failed = 0;
   }
@@ -95,7 +94,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t colQ = tmem, colYt = tmem + 128, colRt = tmem + 192, colG = tmem + 256;
+  // TMEM columns: Q (two buffers, chunk parity), Y^T, R^T, G
+  const uint32_t colQ0 = tmem, colYt = tmem + 256, colRt = tmem + 320, colG = tmem + 384;
   const bool has_work = ntiles > (int)blockIdx.x;
   if (has_work && tid == 0) {
     mbar_arrive_expect_tx(&bars[0], 32768);
@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
   }
   if (has_work && !mbar_wait(&bars[0], 0)) failed = 1;
   __syncthreads();
-  uint32_t mph = 0;        // completed phases of the MMA barrier
+  uint32_t mph = 0;        // completed phases of barrier 1 (Y/R and G products)
+  uint32_t qph[2] = {0, 0};  // completed phases of barriers 2, 3 (Q products)
   bool g_init = false;     // G accumulator holds data (uniform across the CTA)
   const uint32_t idQ = idesc_bf16(128, 128);
   const uint32_t idYR = idesc_bf16(128, 64) | (1u << 15) | (1u << 16);
@@ -112,6 +113,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
   auto mma_wait = [&]() {
     const bool ok = mbar_wait(&bars[1], mph & 1);
     ++mph;
+    if (!ok) failed = 1;
+    tc_fence_after();
+  };
+  auto q_wait = [&](int buf) {
+    const bool ok = mbar_wait(&bars[2 + buf], qph[buf] & 1);
+    ++qph[buf];
     if (!ok) failed = 1;
     tc_fence_after();
   };
@@ -135,14 +142,25 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
     // metadata of nonzeros [w0, w0 + kWin) of the tile; pass 1 also validates
     // the entries and adds the documents' token counts
     auto load_window = [&](int w0, bool check) {
-      for (int t = tid; t < kWin; t += kFusedThreads) {
-        const int j = w0 + t;
-        int m = -1, dd = 0;
+      constexpr int kPer = kWin / kFusedThreads;
+      int mr[kPer], fr[kPer];
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {  // all loads in flight first
+        const int j = w0 + tid + u * kFusedThreads;
+        mr[u] = -1;
+        fr[u] = 0;
+        if (j < nnz) {
+          mr[u] = __ldg(b.indices + ((long long)(nz0 + j) - b.nz_base));
+          fr[u] = __ldg(b.counts + ((long long)(nz0 + j) - b.nz_base));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int t = tid + u * kFusedThreads, j = w0 + t;
+        int dd = 0;
         float f = 0.f;
         if (j < nnz) {
           const int p = nz0 + j;
-          m = __ldg(b.indices + ((long long)p - b.nz_base));
-          const int fc = __ldg(b.counts + ((long long)p - b.nz_base));
           int lo = 0, hi = Te - 1;  // last document whose range starts at or before p
           while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -150,14 +168,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
             else hi = mid - 1;
           }
           dd = lo;
-          const bool valid = m >= 0 && m < a.V && fc > 0;
-          f = valid ? (float)fc : 0.f;
+          const bool valid = mr[u] >= 0 && mr[u] < a.V && fr[u] > 0;
+          f = valid ? (float)fr[u] : 0.f;
           if (check) {
             if (!valid) s_bad = 1;
-            else atomicAdd(s_L + dd, fc);
+            else atomicAdd(s_L + dd, fr[u]);
           }
         }
-        s_m[t] = m;
+        s_m[t] = mr[u];
         s_f[t] = f;
         s_d[t] = dd;
       }
@@ -186,56 +204,80 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
       }
       cp_async_commit();
     };
-    auto issue_q = [&](int buf) {  // Q chunk = U chunk Phi  (rows = nonzeros)
+    // Q chunk = U chunk Phi (rows = nonzeros) into TMEM buffer buf; committed
+    // to barrier 2 + buf
+    auto issue_q = [&](int buf) {
       if (tid == 0) {
         const uint32_t ub = smem_u32(sm + (buf ? kOffU1 : kOffU0)), pb = smem_u32(sPhi);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          mma_bf16(colQ, sdesc_sw128(ub + (kk >> 2) * 16384 + (kk & 3) * 32),
+          mma_bf16(colQ0 + buf * 128, sdesc_sw128(ub + (kk >> 2) * 16384 + (kk & 3) * 32),
                    sdesc_sw128(pb + (kk >> 2) * 16384 + (kk & 3) * 32), idQ, kk > 0 ? 1u : 0u);
-        mma_commit(&bars[1]);
+        mma_commit(&bars[2 + buf]);
       }
+    };
+    // 64 consecutive FP32 columns (4 loads in flight, one wait) of this warp's lanes
+    auto tmem_ld64 = [&](uint32_t taddr, float (&v)[64]) {
+      uint32_t r[64];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[p * 16 + 0]), "=r"(r[p * 16 + 1]), "=r"(r[p * 16 + 2]), "=r"(r[p * 16 + 3]),
+              "=r"(r[p * 16 + 4]), "=r"(r[p * 16 + 5]), "=r"(r[p * 16 + 6]), "=r"(r[p * 16 + 7]),
+              "=r"(r[p * 16 + 8]), "=r"(r[p * 16 + 9]), "=r"(r[p * 16 + 10]), "=r"(r[p * 16 + 11]),
+              "=r"(r[p * 16 + 12]), "=r"(r[p * 16 + 13]), "=r"(r[p * 16 + 14]), "=r"(r[p * 16 + 15])
+            : "r"(taddr + p * 16)
+            : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
     };
     float lacc = 0.f;
 
-    // ---------------- pass 1: y and r over all chunks (buffer of global chunk g = g & 1)
+    // ---------------- pass 1: y and r over all chunks (buffer of global chunk g = g & 1).
+    // The Q product of chunk c+1 runs while chunk c's Q rows are read out.
+    auto put_f = [&](int c, bool on) {  // F^T row r: f_r at the column of its document
+      if (tid < kChunk) {
+        const int t = c * kChunk + tid, dd = s_d[t];
+        *reinterpret_cast<__nv_bfloat16 *>(sF + sw_chunk(tid, dd >> 3) + ((dd & 7) << 1)) =
+            __float2bfloat16_rn(on ? s_f[t] : 0.f);
+      }
+    };
     for (int w = 0; w < nwin && !failed; ++w) {
-      const int w0 = w * kWin, wch = min(kWin, nnz - w0 + kChunk - 1) / kChunk;
+      const int w0 = w * kWin, wch = min(kWin, nnz - w0 + kChunk - 1) / kChunk, gb = w0 / kChunk;
       load_window(w0, true);
-      gather(0, ((w0 / kChunk) & 1));
+      gather(0, gb & 1);
+      if (wch > 1) gather(1, (gb + 1) & 1);
+      if (wch > 1) cp_async_wait_one();
+      else cp_async_wait_all();
+      put_f(0, true);
+      fence_proxy_async();
+      __syncthreads();
+      issue_q(gb & 1);
       for (int c = 0; c < wch; ++c) {
-        const int g = w0 / kChunk + c, buf = g & 1;
-        if (c + 1 < wch) {
-          gather(c + 1, buf ^ 1);  // its buffer was last read by chunk g-1's Q product
-          cp_async_wait_one();
-        } else {
+        const int g = gb + c, buf = g & 1;
+        if (c + 1 < wch) {  // chunk c+1's rows have landed: start its Q product now
           cp_async_wait_all();
+          fence_proxy_async();
+          tc_fence_before();
+          __syncthreads();
+          tc_fence_after();
+          issue_q(buf ^ 1);
         }
-        if (tid < kChunk) {  // F^T row r: f_r at the column of its document
-          const int t = c * kChunk + tid, dd = s_d[t];
-          *reinterpret_cast<__nv_bfloat16 *>(sF + sw_chunk(tid, dd >> 3) + ((dd & 7) << 1)) =
-              __float2bfloat16_rn(s_f[t]);
-        }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        issue_q(buf);
-        mma_wait();
+        q_wait(buf);
         if (__syncthreads_or(failed)) break;
+        if (c + 2 < wch) gather(c + 2, buf);  // this buffer's Q product is done
         {  // Q and Q*Q rows (BF16) for the MN-major reductions over nonzeros
           const int row = quad * 32 + lane;
-#pragma unroll 1
-          for (int p = 0; p < 4; ++p) {
-            const int c0 = half * 64 + p * 16;
-            float q[16];
-            tmem_ld16(colQ + (static_cast<uint32_t>(quad * 32) << 16) + c0, q);
+          float q[64];
+          tmem_ld64(colQ0 + buf * 128 + (static_cast<uint32_t>(quad * 32) << 16) + half * 64, q);
 #pragma unroll
-            for (int i = 0; i < 16; i += 4) {
-              st_bf16x4(sQ, 16384, row, c0 + i, q[i], q[i + 1], q[i + 2], q[i + 3]);
-              st_bf16x4(sQ2, 16384, row, c0 + i, q[i] * q[i], q[i + 1] * q[i + 1], q[i + 2] * q[i + 2],
-                        q[i + 3] * q[i + 3]);
-            }
+          for (int i = 0; i < 64; i += 4) {
+            const int c0 = half * 64 + i;
+            st_bf16x4(sQ, 16384, row, c0, q[i], q[i + 1], q[i + 2], q[i + 3]);
+            st_bf16x4(sQ2, 16384, row, c0, q[i] * q[i], q[i + 1] * q[i + 1], q[i + 2] * q[i + 2],
+                      q[i + 3] * q[i + 3]);
           }
         }
         fence_proxy_async();
@@ -254,11 +296,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
           mma_commit(&bars[1]);
         }
         mma_wait();
-        if (tid < kChunk) {  // clear this chunk's F^T entries (the products are done)
-          const int dd = s_d[c * kChunk + tid];
-          *reinterpret_cast<__nv_bfloat16 *>(sF + sw_chunk(tid, dd >> 3) + ((dd & 7) << 1)) =
-              __float2bfloat16_rn(0.f);
-        }
+        put_f(c, false);                     // these products are done: clear c's entries
+        if (c + 1 < wch) put_f(c + 1, true);  // and place c+1's
+        fence_proxy_async();
         if (__syncthreads_or(failed)) break;
       }
     }
@@ -285,58 +325,68 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
         lacc += y * (y * y - 3.f * r);
       }
     }
-    if (tid == 0) {
-      unsigned long long s3 = 0;
-      for (int dd = 0; dd < Te; ++dd) {
-        const long long L = s_L[dd];
-        if (L >= 3) s3 += (unsigned long long)(L * (L - 1) * (L - 2));
+    if (warp == 0) {
+      const long long L = lane < Te ? s_L[lane] : 0;
+      unsigned long long s3 = L >= 3 ? (unsigned long long)(L * (L - 1) * (L - 2)) : 0ull;
+      for (int o = 16; o > 0; o >>= 1) s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+      if (lane == 0) {
+        if (s3) atomicAdd(&a.st->S3, s3);
+        if (s_bad) atomicOr(&a.st->err, kErrCsr);
       }
-      if (s3) atomicAdd(&a.st->S3, s3);
-      if (s_bad) atomicOr(&a.st->err, kErrCsr);
     }
     __syncthreads();
     // ---------------- pass 2 in reverse chunk order: the last two chunks of
-    // pass 1 are still in their buffers; earlier ones are gathered again
+    // pass 1 are still in their buffers; earlier ones are gathered again.
+    // The Q product of the next (lower) chunk runs during this chunk's B''.
     for (int w = nwin - 1; w >= 0 && !failed; --w) {
-      const int w0 = w * kWin, wch = min(kWin, nnz - w0 + kChunk - 1) / kChunk;
+      const int w0 = w * kWin, wch = min(kWin, nnz - w0 + kChunk - 1) / kChunk, gb = w0 / kChunk;
       if (nwin > 1) load_window(w0, false);
       auto resident = [&](int c) { return nwin == 1 && c >= wch - 2; };
-      if (!resident(wch - 1)) gather(wch - 1, ((w0 / kChunk + wch - 1) & 1));
+      if (!resident(wch - 1)) gather(wch - 1, (gb + wch - 1) & 1);
+      if (wch > 1 && !resident(wch - 2)) gather(wch - 2, (gb + wch - 2) & 1);
+      if (wch > 1 && !resident(wch - 2) && !resident(wch - 1)) cp_async_wait_one();
+      else cp_async_wait_all();
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      issue_q((gb + wch - 1) & 1);
       for (int c = wch - 1; c >= 0; --c) {
-        const int g = w0 / kChunk + c, buf = g & 1;
-        if (c > 0 && !resident(c - 1)) {
-          gather(c - 1, buf ^ 1);  // its buffer held chunk g+1, whose G product is done
-          cp_async_wait_one();
-        } else {
+        const int g = gb + c, buf = g & 1;
+        if (c > 0) {  // chunk c-1's rows are in: start its Q product now
           cp_async_wait_all();
+          fence_proxy_async();
+          tc_fence_before();
+          __syncthreads();
+          tc_fence_after();
+          issue_q(buf ^ 1);
         }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        issue_q(buf);
-        mma_wait();
+        q_wait(buf);
         if (__syncthreads_or(failed)) break;
         {
           const int row = quad * 32 + lane, t = c * kChunk + row;
           const int dd = s_d[t];
           const float f = s_f[t];
-          const float *yr = sY + dd * 128, *zr = sZ + dd * 128;
-#pragma unroll 1
-          for (int p = 0; p < 4; ++p) {
-            const int c0 = half * 64 + p * 16;
-            float q[16];
-            tmem_ld16(colQ + (static_cast<uint32_t>(quad * 32) << 16) + c0, q);
-            float bb[16];
+          const float4 *yr = reinterpret_cast<const float4 *>(sY + dd * 128 + half * 64);
+          const float4 *zr = reinterpret_cast<const float4 *>(sZ + dd * 128 + half * 64);
+          float q[64];
+          tmem_ld64(colQ0 + buf * 128 + (static_cast<uint32_t>(quad * 32) << 16) + half * 64, q);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const float qi = q[i];
-              bb[i] = a.same_token ? f * (zr[c0 + i] + 2.f * qi * qi - 2.f * qi * yr[c0 + i]) : f * zr[c0 + i];
-              if (a.same_token) lacc += 2.f * f * qi * qi * qi;
+          for (int i4 = 0; i4 < 16; ++i4) {
+            const float4 y4 = yr[i4], z4 = zr[i4];
+            const float ys[4] = {y4.x, y4.y, y4.z, y4.w}, zs[4] = {z4.x, z4.y, z4.z, z4.w};
+            float bb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float qi = q[i4 * 4 + u];
+              if (a.same_token) {
+                bb[u] = f * (zs[u] + 2.f * qi * qi - 2.f * qi * ys[u]);
+                lacc += 2.f * f * qi * qi * qi;
+              } else {
+                bb[u] = f * zs[u];
+              }
             }
-#pragma unroll
-            for (int i = 0; i < 16; i += 4)
-              st_bf16x4(sQ, 16384, row, c0 + i, bb[i], bb[i + 1], bb[i + 2], bb[i + 3]);
+            st_bf16x4(sQ, 16384, row, half * 64 + i4 * 4, bb[0], bb[1], bb[2], bb[3]);
           }
         }
         fence_proxy_async();
@@ -354,6 +404,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
         g_init = true;
         mma_wait();
         if (__syncthreads_or(failed)) break;
+        if (c > 1 && !resident(c - 2)) gather(c - 2, buf);  // this buffer's products are done
       }
     }
     cp_async_wait_all();

@@ -236,8 +236,10 @@ __global__ void __launch_bounds__(256) k_phi_gram(StepArgs a) {
     if (tid < 32) {
       const int j = bx * 32 + tid;
       float s = 0.f;
-      if (j < a.K)
+      if (j < a.K) {
+#pragma unroll 8
         for (int r = 0; r < a.D; ++r) s = fmaf(a.m1[r], a.Phi[(long long)r * a.K + j], s);
+      }
       if (j < a.Kp) a.avec[j] = s;
     }
     return;
@@ -246,6 +248,7 @@ __global__ void __launch_bounds__(256) k_phi_gram(StepArgs a) {
   const int ii = tid >> 3, jj = (tid & 7) * 4;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   for (int r0 = 0; r0 < a.D; r0 += 64) {
+#pragma unroll
     for (int e = tid; e < 64 * 32; e += 256) {
       const int r = e >> 5, c = e & 31, gr = r0 + r;
       const int ci = by * 32 + c, cj = bx * 32 + c;
@@ -274,6 +277,7 @@ __global__ void __launch_bounds__(256) k_phi_terms(StepArgs a) {
   const int rr = tid >> 3, ic = (tid & 7) * 4;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   for (int j0 = 0; j0 < a.K; j0 += 64) {
+#pragma unroll
     for (int e = tid; e < 32 * 64; e += 256) {
       const int r = e >> 6, j = e & 63, gr = by * 32 + r, gj = j0 + j;
       Pr[r][j] = (gr < a.D && gj < a.K) ? a.Phi[(long long)gr * a.K + gj] : 0.f;
@@ -654,8 +658,7 @@ void launch_g_f32(const StepArgs &a, cudaStream_t s) {
 // ------------------------------------------------------------ a9: reduce + update
 // 32 entries (i, n) per block, the partial sums split over 8 warps:
 // g = sum over partials; grad = E - 3 c3/S3 g; Phi -= lr grad (skipped on a
-// sticky error or S3 = 0).  The last block (ticket) writes the loss, clears
-// the per-step sums and advances the pass descriptor.
+// sticky error or S3 = 0); the BF16 Phi^T image follows Phi.
 __global__ void __launch_bounds__(256) k_reduce_update(StepArgs a) {
   DevState *st = a.st;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -667,8 +670,17 @@ __global__ void __launch_bounds__(256) k_reduce_update(StepArgs a) {
   const int i = live ? e / a.K : 0, n = live ? e % a.K : 0;
   const long long off = (long long)i * a.Kp + n, stride = (long long)a.Dp * a.Kp;
   float part = 0.f;
-  if (live)
-    for (int s = w; s < a.nsplit; s += 8) part += a.Gpart[s * stride + off];
+  if (live) {  // eight partials in flight per iteration
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int s = w;
+    for (; s + 56 < a.nsplit; s += 64) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] += a.Gpart[(s + 8 * u) * stride + off];
+    }
+    for (; s < a.nsplit; s += 8) acc[0] += a.Gpart[s * stride + off];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) part += acc[u];
+  }
   __shared__ float red[8][32];
   red[w][lane] = part;
   __syncthreads();
@@ -689,26 +701,28 @@ __global__ void __launch_bounds__(256) k_reduce_update(StepArgs a) {
       if (a.PhiImg) a.PhiImg[phi_img_index(n, i, a.Kp)] = __float2bfloat16_rn(phi);
     }
   }
-  __threadfence();
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    st->loss = S3 ? st->loss_phi - scale * st->loss_data : 0.0;
-    st->last_S3 = S3;
-    st->S3 = 0;
-    st->loss_data = 0.0;
-    st->n_touched = 0;
-    st->ticket = 0;
-    st->step += 1;
-    if (st->descs && st->pass_pos < st->n_descs) st->cur = st->descs[st->pass_pos++];
-  }
+}
+
+// End of a step (one warp, after the reduction): the step's loss, the
+// per-step sums cleared for the next batch, the step counter, and the next
+// batch descriptor of a pass.
+__global__ void k_step_end(StepArgs a) {
+  DevState *st = a.st;
+  if (threadIdx.x != 0) return;
+  const unsigned long long S3 = st->S3;
+  const double scale = S3 ? a.c3 / (double)S3 : 0.0;
+  st->loss = S3 ? st->loss_phi - scale * st->loss_data : 0.0;
+  st->last_S3 = S3;
+  st->S3 = 0;
+  st->loss_data = 0.0;
+  st->n_touched = 0;
+  st->step += 1;
+  if (st->descs && st->pass_pos < st->n_descs) st->cur = st->descs[st->pass_pos++];
 }
 
 void launch_reduce_update(const StepArgs &a, cudaStream_t s) {
   k_reduce_update<<<(a.D * a.K + 31) / 32, 256, 0, s>>>(a);
+  k_step_end<<<1, 32, 0, s>>>(a);
 }
 
 }  // namespace tlda

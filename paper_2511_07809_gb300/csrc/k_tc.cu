@@ -279,7 +279,8 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2D BF16 tensor [outer x inner] (row pitch in bytes), box [box_outer x 64], 128-byte swizzle.
+// 2D BF16 tensor [outer x inner] (row pitch in bytes), box [box_outer x 64],
+// 128-byte swizzle (box_outer = 1 for tile::gather4 row gathers).
 bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
               uint32_t box_outer) {
   EncodeTiledFn fn = encode_fn();
@@ -294,6 +295,7 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, 
 }
 
 struct TcMaps {
+  CUtensorMap ug;  // U16: V x Dp, box 1 row x 64 (row gathers)
   CUtensorMap ux;  // UX16: (V + Bmax) x Dp, box 128 rows x 64
   CUtensorMap at;  // AT16: Dp x ldT, box 128 rows x 64 (rows >= Dp read as zero)
   CUtensorMap bt;  // BT16: Kp x ldT, box Kp rows x 64
@@ -328,7 +330,8 @@ bool tc_supported(int Dp, int Kp) { return Dp <= 128 && Kp <= 256; }
 void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const __nv_bfloat16 *BT16, int V,
                    int Bmax, int Dp, int Kp, int ldT) {
   TcMaps *m = new TcMaps();
-  bool ok = make_map(&m->ux, UX16, Dp, (uint64_t)V + Bmax, (uint64_t)Dp * 2, 128) &&
+  bool ok = make_map(&m->ug, UX16, Dp, (uint64_t)V, (uint64_t)Dp * 2, 1) &&
+            make_map(&m->ux, UX16, Dp, (uint64_t)V + Bmax, (uint64_t)Dp * 2, 128) &&
             make_map(&m->at, AT16, ldT, Dp, (uint64_t)ldT * 2, 128) &&
             make_map(&m->bt, BT16, ldT, Kp, (uint64_t)ldT * 2, Kp);
   if (!ok) {
@@ -339,6 +342,8 @@ void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const _
 }
 
 void tc_free_maps(void *p) { delete static_cast<TcMaps *>(p); }
+
+const void *tc_gather_map(const void *maps) { return &static_cast<const TcMaps *>(maps)->ug; }
 
 void launch_qy_tc(const StepArgs &a, cudaStream_t s) {
   const TcMaps &m = *static_cast<const TcMaps *>(a.tc_maps);

@@ -42,7 +42,6 @@ struct DevState {
   int32_t pass_pos;              // next descriptor of the pass
   int32_t step;                  // steps completed on this context
   int32_t err;                   // sticky error bits (kErr*)
-  unsigned int ticket;           // last-block ticket of the reduction kernel
   int32_t n_touched;             // distinct words of the current batch
   unsigned long long S3;         // sum_d L(L-1)(L-2) of the current batch
   unsigned long long last_S3;    // S3 of the last completed step
@@ -176,6 +175,7 @@ bool tc_supported(int Dp, int Kp);
 void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const __nv_bfloat16 *BT16, int V,
                    int Bmax, int Dp, int Kp, int ldT);
 void tc_free_maps(void *maps);
+const void *tc_gather_map(const void *maps);  // the U16 row-gather map (CUtensorMap)
 void launch_qy_tc(const StepArgs &a, cudaStream_t s);
 void launch_zh_tc(const StepArgs &a, cudaStream_t s);
 void launch_g_tc(const StepArgs &a, cudaStream_t s);
