@@ -113,6 +113,32 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def shard_first_doc(rank: int, sp) -> int:
+    """First document of a rank's replica shard: rank r generates documents
+    [r n_docs, r n_docs + n) of the workload's seeded stream, so shards are
+    disjoint and each is the same whichever world size runs it."""
+    return int(rank) * int(sp.n_docs)
+
+
+def reduce_over_ranks(x: float, op: str, world: int, device: str = "cuda") -> float:
+    """One float reduced over the process group ("max" or "sum")."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_throughput(ms: float, docs: float, world: int, device: str = "cuda"):
+    """Whole-job docs/s of N independent replicas: the documents of every
+    rank over the slowest rank's time.  Returns (value, ms_max, docs_all)."""
+    ms_max = reduce_over_ranks(ms, "max", world, device)
+    docs_all = reduce_over_ranks(docs, "sum", world, device)
+    return docs_all / (ms_max / 1e3), ms_max, docs_all
+
+
 def batch_plan(ts, sp, n_steps):
     """Seeded minibatch sizes (uniform 512..8192) for n_steps, and the document
     count they cover within one pass of the corpus."""
@@ -255,19 +281,13 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def allreduce(x, op):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=op)
-        return float(t.item())
 
     sp = ts.WORKLOADS[WORKLOAD]
     cdf, mu = ts.topics(sp)
     seq = batch_plan(ts, sp, args.warmup + args.steps)
     n_docs = int(min(seq.sum(), sp.n_docs))
     n_docs = max(n_docs, min(args.fit_docs, sp.n_docs))
-    shard0 = rank * sp.n_docs
+    shard0 = shard_first_doc(rank, sp)
     t_gen = time.perf_counter()
     corpus = ts.corpus(sp.with_docs(shard0 + n_docs), doc0=shard0, n_docs=n_docs, cdf=cdf)
     t_gen = time.perf_counter() - t_gen
@@ -327,14 +347,24 @@ def main():
 
     dev_or_host = dev
     host_corpus = None
-    # 1) which kernel dominates the step: a short bracketed run of every kernel
+    # 1) which kernel dominates: the persistent pass kernel where the context
+    # runs passes in one (its first pass also tunes the tile size), else a
+    # short bracketed run of every kernel of the per-step chain
     probe_segs = segments(seq[args.warmup:args.warmup + min(200, args.steps)], n_docs, last_off)
     Phi = Phi0.clone()
-    ctx.profile(tlda.TLDA.KERNELS)
+    ctx.profile(("pass",))
     for s in probe_segs:
         ctx.cp_pass(dev, s, Phi, LR)
     shares = ctx.profile_read()
     ctx.profile(())
+    persistent = shares["pass"][0] > 0
+    if not persistent:
+        Phi = Phi0.clone()
+        ctx.profile(tlda.TLDA.KERNELS)
+        for s in probe_segs:
+            ctx.cp_pass(dev, s, Phi, LR)
+        shares = ctx.profile_read()
+        ctx.profile(())
     dominant = max((k for k in shares if shares[k][0] > 0), key=lambda k: shares[k][1])
 
     # 2) the timed region (device-resident corpus), dominant kernel bracketed by events
@@ -342,9 +372,7 @@ def main():
     Phi = Phi0.clone()
     ms, prof = timed(ctx, Phi, profile=(dominant,))
     clocks = sampler.stop()
-    ms_max = allreduce(ms, dist.ReduceOp.MAX if world > 1 else None)
-    docs_all = allreduce(float(n_timed_docs), dist.ReduceOp.SUM if world > 1 else None)
-    value = docs_all / (ms_max / 1e3)
+    value, ms_max, docs_all = replica_throughput(ms, float(n_timed_docs), world)
     Phi_final = Phi.clone()
 
     # roofline of the dominant kernel
@@ -354,9 +382,15 @@ def main():
     nnz_all = np.concatenate([np.diff(corpus.indptr[np.array(s)]) for s in timed_segs])
     D = K = sp.K
     roof = None
-    if dominant in ("qy", "g_reduce", "fused") and launches:
+    if dominant in ("qy", "g_reduce", "fused", "pass") and launches:
         nt = np.concatenate([distinct_words(corpus, s) for s in timed_segs])
-        if dominant == "fused":
+        if dominant == "pass":
+            # every step of the launches: the data-term contractions as for
+            # "fused" below plus the Phi-only products Phi^T Phi and
+            # Phi (G * G), over all timed steps, per launch
+            flops = float((2.0 * nnz_all * D + 4.0 * B_all * D * K + 4.0 * nt * D * K
+                           + 4.0 * nnz_all * K + 4.0 * D * K * K).sum()) / launches
+        elif dominant == "fused":
             # the method's contractions this kernel performs (factored count,
             # unpadded D, K): X = F U, Y = X Phi, Q = U_t Phi, R = F (Q*Q),
             # G1 = X^T Z, H = F^T Y, G2 = U_t^T Zc
@@ -397,7 +431,7 @@ def main():
         host_corpus = tlda.DeviceCSR.from_corpus(corpus, device="cpu", pin=True)
         Phi = Phi0.clone()
         ms_e, _ = timed(ctx, Phi, host=True, losses=True)
-        ms_e = allreduce(ms_e, dist.ReduceOp.MAX if world > 1 else None)
+        ms_e = reduce_over_ranks(ms_e, "max", world)
         h2d = float(((B_all + 1) * 4 + nnz_all * 8).mean())
         e2e = {"value": docs_all / (ms_e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 8}
@@ -416,7 +450,7 @@ def main():
             c2.set_whitening(W, m1)
             Phi = Phi0.clone()
             ms2, _ = timed(c2, Phi)
-            ms2 = allreduce(ms2, dist.ReduceOp.MAX if world > 1 else None)
+            ms2 = reduce_over_ranks(ms2, "max", world)
             compare = {"precision": other[0], "value": docs_all / (ms2 / 1e3),
                        "ms_per_step": ms2 / args.steps}
             c2.close()
@@ -443,6 +477,10 @@ def main():
         # R/Z/H, Zc, reduction over rows, reduction, step end
         fused = primary == "bf16" and sp.K <= 128 and sp.K > 64
         per_step_kernels = 5 if fused else 9
+        # persistent form: per cp_pass call, the Phi^T image kernel and one
+        # pass kernel for all of its steps
+        launches_timed = (2 * len(timed_segs) if persistent
+                          else per_step_kernels * args.steps + len(timed_segs))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -457,7 +495,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "fit_docs": n_fit, "fit_s": round(t_fit, 2), "gen_s": round(t_gen, 2)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": per_step_kernels * args.steps + len(timed_segs),
+            "gpu_launches": launches_timed,
             "clocks": clocks, "compare": compare, "recovery": recovery,
             "kernel_shares": {k: round(v[1] / max(sum(x[1] for x in shares.values()), 1e-12), 4)
                               for k, v in shares.items() if v[0]},

@@ -185,15 +185,35 @@ tlda_status tlda_cp_data_term(tlda_ctx *ctx, const tlda_csr *batch, const float 
  * batch b is documents [batch_offsets[b], batch_offsets[b+1]) of `corpus`;
  * one CP step per batch, in order, on Phi (D x K FP32, device).
  * batch_offsets: host, n_batches + 1 non-decreasing document offsets.
- * With TLDA_HOST_INPUT the corpus CSR is in host memory and each batch is
- * copied to the device inside the call (double-buffered, overlapped with the
- * previous batch's compute); otherwise it is in device memory.
- * loss_out (host, n_batches doubles) may be NULL; if given, each step's loss
- * is copied back as the pass runs.  Synchronises at the end and returns any
- * sticky status. */
+ * With TLDA_HOST_INPUT the corpus CSR is in host memory and is copied to
+ * the device inside the call (double-buffered, each copy overlapped with the
+ * compute of the batches before it); otherwise it is in device memory.
+ * loss_out (host, n_batches doubles) may be NULL; if given, it receives each
+ * step's loss.  Synchronises at the end and returns any sticky status.
+ *
+ * In the BF16 form with D, K in (64, 128] the whole pass runs in one
+ * persistent cooperative kernel (host input: one launch per staged
+ * segment), with the tile size of tlda_autotune; a first device-input pass
+ * on a context with no tile size runs the tuner on its first batches.
+ * Otherwise each step is one replay of a captured CUDA graph. */
 tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets,
                          int32_t n_batches, float *Phi, float lr, uint32_t flags,
                          double *loss_out);
+
+/* Tile size of the persistent pass kernel: the most documents per tile,
+ * 1..32 (each batch is split into ceil(n_docs / SMs) document tiles up to
+ * this size).  With fixed_cap > 0 the size is set to fixed_cap and nothing
+ * runs (corpus may be NULL).  With fixed_cap = 0 the candidates 8, 16, 24
+ * and 32 are timed on up to the first 64 batches of `corpus` (device CSR,
+ * batches as in tlda_cp_pass), stepping a scratch copy of Phi (D x K FP32,
+ * device; Phi itself and the context's step and error state are left
+ * unchanged: a corrupt batch among them is reported by the pass that steps
+ * it), and the fastest is kept.  *tile_cap_out (may be NULL) receives the size in
+ * use.  Synchronises.  TLDA_ERR_UNIMPLEMENTED on a context without the
+ * persistent pass kernel; TLDA_ERR_STATE without a whitening. */
+tlda_status tlda_autotune(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets,
+                          int32_t n_batches, const float *Phi, int32_t fixed_cap,
+                          int32_t *tile_cap_out);
 
 /* --------------------------------------------------------------- recovery */
 #define TLDA_HOST_OUTPUT 1u    /* mu_out / alpha_out are host pointers */
@@ -250,7 +270,9 @@ tlda_status tlda_cp_step_noalloc(const tlda_csr *batch, const float *W, const fl
  * the stream it is launched on.  Kernels of one CP step, in launch order:
  *   0 scan_whiten  1 qy  2 rz  3 zh  4 g_reduce  5 reduce_update
  *   6 phi_gram  7 phi_terms (6 and 7 run on the context's side stream)
- *   8 fused (BF16 form with D, K <= 128: replaces kernels 0-4).
+ *   8 fused (BF16 form with D, K in (64, 128]: replaces kernels 0-4)
+ *   9 pass (the persistent kernel of tlda_cp_pass in that form: one launch
+ *     runs every step of the pass, kernels 0-8 do not run).
  * tlda_profile sets the mask of bracketed kernels (bit i = kernel i; 0 turns
  * profiling off) and clears the totals.  tlda_profile_read synchronises and
  * returns the kernel's name (static string), launch count and summed

@@ -1,13 +1,12 @@
 // Fused BF16 tensor-core CP-step data term for D, K in (64, 128] (padded to
-// 128).  One persistent CTA per SM walks 32-document tiles of the batch and
-// accumulates G1 + G2 (eq. vec_deriv's data term with the same-token terms of
-// distinct-token triples) in TMEM, without any V-sized intermediate.
+// 128), and the persistent kernel that runs a whole online pass with it.
 //
-// With q_j = u_{m_j} Phi for the tile's nonzeros j (word m_j, count f_j,
-// document d_j), the per-document quantities are sums over nonzeros:
+// Data term.  With q_j = u_{m_j} Phi for the nonzeros j of a tile of
+// documents (word m_j, count f_j, document d_j), the per-document sums
 //   y_d = sum_{j in d} f_j q_j          (= x_d Phi, x_d = sum f u)
 //   r_d = sum_{j in d} f_j q_j^2
-// and the data term is one reduction over nonzeros:
+// give G1 + G2 of eq. vec_deriv (with the same-token terms of distinct-token
+// triples) as one reduction over nonzeros:
 //   G1 + G2 = sum_d x_d z_d^T + sum_m u_m [q_m (2 c_m q_m - 2 H_m)]^T
 //           = sum_j u_{m_j} [f_j (z_{d_j} + 2 q_j^2 - 2 q_j y_{d_j})]^T,
 //   z_d = y_d^2 - r_d.
@@ -17,16 +16,31 @@
 //   then    y, z = y^2 - r into shared memory (FP32)
 //   pass 2: Q = U Phi again; B''_j = f_j (z + 2 q^2 - 2 q y); G += U^T B''
 //           (tcgen05, both MN-major: the gathered U tile read the other way)
-// Each CTA writes its 128 x 128 partial; the reduction kernel sums them.
+// G stays in TMEM across a block's tiles; each block then writes its
+// 128 x 128 partial.
+//
+// k_fused runs the data term of one step (the reduction and the update are
+// separate kernels).  k_pass runs steps [s0, s1) of a pass in one cooperative
+// launch, each step in two phases separated by grid barriers:
+//   A  the last K blocks: one column each of the Phi-only terms
+//      E = 3(1+theta) P - 3 G3 (P = Phi (Phi^T Phi * Phi^T Phi)) and its loss
+//      part; the first blocks: the data term of the step's batch, in tiles
+//      of ceil(n_docs / blocks) documents (at most tile_cap);
+//   B  block b: its slice of the entries of Phi: the partials summed,
+//      grad = E - 3 c3/S3 (G1 + G2), Phi -= lr grad, and the BF16 Phi^T
+//      image the next step's MMAs read.
+// Every wait (mbarrier or grid barrier) is bounded; an expired wait sets an
+// abort flag that ends every block's loop and is reported as a timeout.
 #include "tc_ptx.cuh"
 
 namespace tlda {
 namespace {
 using namespace tc;
 
-constexpr int kT = 32;        // documents per tile
+constexpr int kT = 32;        // documents per tile, at most
 constexpr int kChunk = 128;   // nonzeros per chunk
 constexpr int kFusedThreads = 256;
+constexpr int kMinPassGrid = 128;  // at least one block per Phi column (K <= 128)
 
 // shared-memory map (bytes from the 1024-aligned base)
 constexpr int kOffPhi = 0;          // Phi^T image 2 x [128 x 64] BF16               32 KB
@@ -39,7 +53,7 @@ constexpr int kOffY = 180224;       // y tile FP32 32 x 128                     
 constexpr int kOffZ = 196608;       // z tile FP32 32 x 128                         16 KB
 constexpr int kWin = 1024;          // nonzeros whose metadata sit in shared memory
 constexpr int kOffMeta = 212992;    // window metadata m, f, d (12 KB), indptr slice, L
-constexpr int kOffBar = kOffMeta + 3 * kWin * 4 + 512;  // 4 mbarriers + TMEM slot
+constexpr int kOffBar = kOffMeta + 3 * kWin * 4 + 512;  // 4 mbarriers, TMEM slot, flags
 constexpr int kFusedSmem = 1024 + kOffBar + 64;
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -60,372 +74,118 @@ __device__ __forceinline__ void st_bf16x4(unsigned char *tile, int sub_bytes, in
   *reinterpret_cast<uint2 *>(tile + (col >> 6) * sub_bytes + sw_chunk(row, (col & 63) >> 3) + ((col & 7) << 1)) = pk;
 }
 
-__global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char *sm = align1024(smem_raw);
-  unsigned char *sPhi = sm + kOffPhi, *sQ = sm + kOffQ, *sQ2 = sm + kOffQ2, *sF = sm + kOffF;
-  float *sY = reinterpret_cast<float *>(sm + kOffY), *sZ = reinterpret_cast<float *>(sm + kOffZ);
-  int *s_m = reinterpret_cast<int *>(sm + kOffMeta);        // kWin raw word indices (-1 past the end)
-  float *s_f = reinterpret_cast<float *>(s_m + kWin);       // kWin weights (0 if invalid)
-  int *s_d = reinterpret_cast<int *>(s_f + kWin);           // kWin local documents
-  int *s_ptr = s_d + kWin;                                  // kT + 1 absolute offsets
-  int *s_L = s_ptr + 64;                                    // kT token counts
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kOffBar);  // 0: Phi, 1: Y/R and G, 2-3: Q buffers
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
-  __shared__ int failed, s_bad, s_mlast;
-  __shared__ float s_red[kFusedThreads / 32];
+// 64 consecutive FP32 TMEM columns of this warp's lanes (4 loads in flight, one wait).
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[p * 16 + 0]), "=r"(r[p * 16 + 1]), "=r"(r[p * 16 + 2]), "=r"(r[p * 16 + 3]), "=r"(r[p * 16 + 4]),
+          "=r"(r[p * 16 + 5]), "=r"(r[p * 16 + 6]), "=r"(r[p * 16 + 7]), "=r"(r[p * 16 + 8]), "=r"(r[p * 16 + 9]),
+          "=r"(r[p * 16 + 10]), "=r"(r[p * 16 + 11]), "=r"(r[p * 16 + 12]), "=r"(r[p * 16 + 13]),
+          "=r"(r[p * 16 + 14]), "=r"(r[p * 16 + 15])
+        : "r"(taddr + p * 16)
+        : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, half = warp >> 2;
-  const BatchDesc b = a.st->cur;
-  const int nd = b.n_docs;
-  const int ntiles = (nd + kT - 1) / kT;
-  float *gp = a.Gpart + (long long)blockIdx.x * a.Dp * a.Kp;
-
-  if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
-    fence_mbar_init();
-    failed = 0;
-  }
-  if (warp == 0) tmem_alloc(tslot, 512);
-  // F^T tile starts (and is kept) at zero; entries are written and cleared per chunk
-  for (int e = tid; e < 16384 / 16; e += kFusedThreads) reinterpret_cast<uint4 *>(sF)[e] = make_uint4(0u, 0u, 0u, 0u);
-  tc_fence_before();
+// Block sum of one float per thread (every thread calls; the result is valid
+// in thread 0).
+__device__ __forceinline__ float block_sum(float v, float *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tslot;
-  // TMEM columns: Q (two buffers, chunk parity), Y^T, R^T, G
-  const uint32_t colQ0 = tmem, colYt = tmem + 256, colRt = tmem + 320, colG = tmem + 384;
-  const bool has_work = ntiles > (int)blockIdx.x;
-  if (has_work && tid == 0) {
-    mbar_arrive_expect_tx(&bars[0], 32768);
-    bulk_load(sPhi, a.PhiImg, 32768, &bars[0]);
-  }
-  if (has_work && !mbar_wait(&bars[0], 0)) failed = 1;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  uint32_t mph = 0;        // completed phases of barrier 1 (Y/R and G products)
-  uint32_t qph[2] = {0, 0};  // completed phases of barriers 2, 3 (Q products)
-  bool g_init = false;     // G accumulator holds data (uniform across the CTA)
-  const uint32_t idQ = idesc_bf16(128, 128);
-  const uint32_t idYR = idesc_bf16(128, 64) | (1u << 15) | (1u << 16);
-  const uint32_t idG = idesc_bf16(128, 128) | (1u << 15) | (1u << 16);
+  float t = 0.f;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kFusedThreads / 32; ++w) t += red[w];
+  return t;
+}
 
-  auto mma_wait = [&]() {
-    const bool ok = mbar_wait(&bars[1], mph & 1);
-    ++mph;
-    if (!ok) failed = 1;
-    tc_fence_after();
-  };
-  auto q_wait = [&](int buf) {
-    const bool ok = mbar_wait(&bars[2 + buf], qph[buf] & 1);
-    ++qph[buf];
-    if (!ok) failed = 1;
-    tc_fence_after();
-  };
+// One block's tile engine: shared-memory views, TMEM columns and the phases
+// of its mbarriers (0: Phi image, 1: Y/R and G products, 2-3: Q buffers).
+struct Fused {
+  unsigned char *sm, *sPhi, *sQ, *sQ2, *sF;
+  float *sY, *sZ;
+  int *s_m, *s_d, *s_ptr, *s_L;
+  float *s_f;
+  uint64_t *bars;
+  int *sh;                       // [0] failed, [1] bad tile, [2] last word of the previous window
+  uint32_t tmem, colQ0, colYt, colRt, colG;
+  uint32_t mph, qph0, qph1, pph;
+  int tid, warp, lane, quad, half;
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    if (failed) break;
-    const int d0 = tile * kT, Te = min(kT, nd - d0);
-    if (tid <= Te) s_ptr[tid] = b.indptr[d0 + tid];
-    if (tid < kT) s_L[tid] = 0;
+  __device__ bool failed() const { return *reinterpret_cast<volatile int *>(sh) != 0; }
+  __device__ void fail() { *reinterpret_cast<volatile int *>(sh) = 1; }
+
+  __device__ void init(unsigned char *raw) {
+    sm = align1024(raw);
+    sPhi = sm + kOffPhi;
+    sQ = sm + kOffQ;
+    sQ2 = sm + kOffQ2;
+    sF = sm + kOffF;
+    sY = reinterpret_cast<float *>(sm + kOffY);
+    sZ = reinterpret_cast<float *>(sm + kOffZ);
+    s_m = reinterpret_cast<int *>(sm + kOffMeta);   // kWin raw word indices (-1 past the end)
+    s_f = reinterpret_cast<float *>(s_m + kWin);    // kWin weights (0 if invalid)
+    s_d = reinterpret_cast<int *>(s_f + kWin);      // kWin local documents
+    s_ptr = s_d + kWin;                             // kT + 1 absolute offsets
+    s_L = s_ptr + 64;                               // kT token counts
+    bars = reinterpret_cast<uint64_t *>(sm + kOffBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
+    sh = reinterpret_cast<int *>(bars + 5);
+    tid = threadIdx.x;
+    warp = tid >> 5;
+    lane = tid & 31;
+    quad = warp & 3;
+    half = warp >> 2;
+    mph = qph0 = qph1 = pph = 0;
     if (tid == 0) {
-      s_bad = 0;
-      s_mlast = -1;
+      for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+      fence_mbar_init();
+      sh[0] = sh[1] = 0;
+      sh[2] = -1;
     }
+    if (warp == 0) tmem_alloc(tslot, 512);
+    // the F^T tile starts (and is kept) at zero; entries are written and cleared per chunk
+    for (int e = tid; e < 16384 / 16; e += kFusedThreads)
+      reinterpret_cast<uint4 *>(sF)[e] = make_uint4(0u, 0u, 0u, 0u);
+    tc_fence_before();
     __syncthreads();
-    if (tid < Te && (s_ptr[tid + 1] < s_ptr[tid] || s_ptr[tid] < b.nz_base)) s_bad = 1;
-    const int nz0 = s_ptr[0];
-    const int nnz = max(0, s_ptr[Te] - nz0);
-    const int nch = (nnz + kChunk - 1) / kChunk;
-    const int nwin = (nnz + kWin - 1) / kWin;
-
-    // metadata of nonzeros [w0, w0 + kWin) of the tile; pass 1 also validates
-    // the entries and adds the documents' token counts
-    auto load_window = [&](int w0, bool check) {
-      constexpr int kPer = kWin / kFusedThreads;
-      int mr[kPer], fr[kPer];
-#pragma unroll
-      for (int u = 0; u < kPer; ++u) {  // all loads in flight first
-        const int j = w0 + tid + u * kFusedThreads;
-        mr[u] = -1;
-        fr[u] = 0;
-        if (j < nnz) {
-          mr[u] = __ldg(b.indices + ((long long)(nz0 + j) - b.nz_base));
-          fr[u] = __ldg(b.counts + ((long long)(nz0 + j) - b.nz_base));
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kPer; ++u) {
-        const int t = tid + u * kFusedThreads, j = w0 + t;
-        int dd = 0;
-        float f = 0.f;
-        if (j < nnz) {
-          const int p = nz0 + j;
-          int lo = 0, hi = Te - 1;  // last document whose range starts at or before p
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_ptr[mid] <= p) lo = mid;
-            else hi = mid - 1;
-          }
-          dd = lo;
-          const bool valid = mr[u] >= 0 && mr[u] < a.V && fr[u] > 0;
-          f = valid ? (float)fr[u] : 0.f;
-          if (check) {
-            if (!valid) s_bad = 1;
-            else atomicAdd(s_L + dd, fr[u]);
-          }
-        }
-        s_m[t] = mr[u];
-        s_f[t] = f;
-        s_d[t] = dd;
-      }
-      __syncthreads();
-      if (check) {  // words strictly ascending within a document
-        for (int t = tid; t < kWin; t += kFusedThreads) {
-          const int j = w0 + t;
-          if (j < nnz && nz0 + j > s_ptr[s_d[t]]) {
-            const int mp = t > 0 ? s_m[t - 1] : s_mlast;
-            if (s_m[t] <= mp) s_bad = 1;
-          }
-        }
-        __syncthreads();
-        if (tid == 0) s_mlast = s_m[kWin - 1];
-      }
-    };
-    // cp.async gather of the BF16 U rows of window chunk c into buffer buf
-    auto gather = [&](int c, int buf) {
-      unsigned char *sU = sm + (buf ? kOffU1 : kOffU0);
-      for (int pce = tid; pce < kChunk * 16; pce += kFusedThreads) {
-        const int r = pce >> 4, pc = pce & 15;
-        const int m = s_m[c * kChunk + r];
-        unsigned char *dst = sU + (pc >> 3) * 16384 + sw_chunk(r, pc & 7);
-        if (m >= 0 && m < a.V) cp_async16(dst, a.U16 + (long long)m * a.Dp + pc * 8);
-        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
-      }
-      cp_async_commit();
-    };
-    // Q chunk = U chunk Phi (rows = nonzeros) into TMEM buffer buf; committed
-    // to barrier 2 + buf
-    auto issue_q = [&](int buf) {
-      if (tid == 0) {
-        const uint32_t ub = smem_u32(sm + (buf ? kOffU1 : kOffU0)), pb = smem_u32(sPhi);
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-          mma_bf16(colQ0 + buf * 128, sdesc_sw128(ub + (kk >> 2) * 16384 + (kk & 3) * 32),
-                   sdesc_sw128(pb + (kk >> 2) * 16384 + (kk & 3) * 32), idQ, kk > 0 ? 1u : 0u);
-        mma_commit(&bars[2 + buf]);
-      }
-    };
-    // 64 consecutive FP32 columns (4 loads in flight, one wait) of this warp's lanes
-    auto tmem_ld64 = [&](uint32_t taddr, float (&v)[64]) {
-      uint32_t r[64];
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[p * 16 + 0]), "=r"(r[p * 16 + 1]), "=r"(r[p * 16 + 2]), "=r"(r[p * 16 + 3]),
-              "=r"(r[p * 16 + 4]), "=r"(r[p * 16 + 5]), "=r"(r[p * 16 + 6]), "=r"(r[p * 16 + 7]),
-              "=r"(r[p * 16 + 8]), "=r"(r[p * 16 + 9]), "=r"(r[p * 16 + 10]), "=r"(r[p * 16 + 11]),
-              "=r"(r[p * 16 + 12]), "=r"(r[p * 16 + 13]), "=r"(r[p * 16 + 14]), "=r"(r[p * 16 + 15])
-            : "r"(taddr + p * 16)
-            : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
-    };
-    float lacc = 0.f;
-
-    // ---------------- pass 1: y and r over all chunks (buffer of global chunk g = g & 1).
-    // The Q product of chunk c+1 runs while chunk c's Q rows are read out.
-    auto put_f = [&](int c, bool on) {  // F^T row r: f_r at the column of its document
-      if (tid < kChunk) {
-        const int t = c * kChunk + tid, dd = s_d[t];
-        *reinterpret_cast<__nv_bfloat16 *>(sF + sw_chunk(tid, dd >> 3) + ((dd & 7) << 1)) =
-            __float2bfloat16_rn(on ? s_f[t] : 0.f);
-      }
-    };
-    for (int w = 0; w < nwin && !failed; ++w) {
-      const int w0 = w * kWin, wch = min(kWin, nnz - w0 + kChunk - 1) / kChunk, gb = w0 / kChunk;
-      load_window(w0, true);
-      gather(0, gb & 1);
-      if (wch > 1) gather(1, (gb + 1) & 1);
-      if (wch > 1) cp_async_wait_one();
-      else cp_async_wait_all();
-      put_f(0, true);
-      fence_proxy_async();
-      __syncthreads();
-      issue_q(gb & 1);
-      for (int c = 0; c < wch; ++c) {
-        const int g = gb + c, buf = g & 1;
-        if (c + 1 < wch) {  // chunk c+1's rows have landed: start its Q product now
-          cp_async_wait_all();
-          fence_proxy_async();
-          tc_fence_before();
-          __syncthreads();
-          tc_fence_after();
-          issue_q(buf ^ 1);
-        }
-        q_wait(buf);
-        if (__syncthreads_or(failed)) break;
-        if (c + 2 < wch) gather(c + 2, buf);  // this buffer's Q product is done
-        {  // Q and Q*Q rows (BF16) for the MN-major reductions over nonzeros
-          const int row = quad * 32 + lane;
-          float q[64];
-          tmem_ld64(colQ0 + buf * 128 + (static_cast<uint32_t>(quad * 32) << 16) + half * 64, q);
-#pragma unroll
-          for (int i = 0; i < 64; i += 4) {
-            const int c0 = half * 64 + i;
-            st_bf16x4(sQ, 16384, row, c0, q[i], q[i + 1], q[i + 2], q[i + 3]);
-            st_bf16x4(sQ2, 16384, row, c0, q[i] * q[i], q[i + 1] * q[i + 1], q[i + 2] * q[i + 2],
-                      q[i + 3] * q[i + 3]);
-          }
-        }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) {  // Y^T += Q^T F^T, R^T += (Q*Q)^T F^T  (M = topics, N = 64 documents)
-          const uint32_t qb = smem_u32(sQ), q2b = smem_u32(sQ2), fb = smem_u32(sF);
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            mma_bf16(colYt, sdesc_mn_sw128(qb + kk * 2048, 16384), sdesc_mn_sw128(fb + kk * 2048, 16384), idYR,
-                     (g > 0 || kk > 0) ? 1u : 0u);
-            mma_bf16(colRt, sdesc_mn_sw128(q2b + kk * 2048, 16384), sdesc_mn_sw128(fb + kk * 2048, 16384), idYR,
-                     (g > 0 || kk > 0) ? 1u : 0u);
-          }
-          mma_commit(&bars[1]);
-        }
-        mma_wait();
-        put_f(c, false);                     // these products are done: clear c's entries
-        if (c + 1 < wch) put_f(c + 1, true);  // and place c+1's
-        fence_proxy_async();
-        if (__syncthreads_or(failed)) break;
-      }
-    }
-    cp_async_wait_all();
-    if (__syncthreads_or(failed)) break;
-    // ---------------- y, z = y^2 - r (FP32, [document][topic]); S3 and validation
-    {
-      const int topic = quad * 32 + lane;
-      float yv[16], rv[16];
-      if (nch > 0) {
-        tmem_ld16(colYt + (static_cast<uint32_t>(quad * 32) << 16) + half * 16, yv);
-        tmem_ld16(colRt + (static_cast<uint32_t>(quad * 32) << 16) + half * 16, rv);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) yv[i] = rv[i] = 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int dd = half * 16 + i;
-        const float y = dd < Te ? yv[i] : 0.f;
-        const float r = (dd < Te && a.same_token) ? rv[i] : 0.f;
-        sY[dd * 128 + topic] = y;
-        sZ[dd * 128 + topic] = y * y - r;
-        lacc += y * (y * y - 3.f * r);
-      }
-    }
-    if (warp == 0) {
-      const long long L = lane < Te ? s_L[lane] : 0;
-      unsigned long long s3 = L >= 3 ? (unsigned long long)(L * (L - 1) * (L - 2)) : 0ull;
-      for (int o = 16; o > 0; o >>= 1) s3 += __shfl_xor_sync(0xffffffffu, s3, o);
-      if (lane == 0) {
-        if (s3) atomicAdd(&a.st->S3, s3);
-        if (s_bad) atomicOr(&a.st->err, kErrCsr);
-      }
-    }
-    __syncthreads();
-    // ---------------- pass 2 in reverse chunk order: the last two chunks of
-    // pass 1 are still in their buffers; earlier ones are gathered again.
-    // The Q product of the next (lower) chunk runs during this chunk's B''.
-    for (int w = nwin - 1; w >= 0 && !failed; --w) {
-      const int w0 = w * kWin, wch = min(kWin, nnz - w0 + kChunk - 1) / kChunk, gb = w0 / kChunk;
-      if (nwin > 1) load_window(w0, false);
-      auto resident = [&](int c) { return nwin == 1 && c >= wch - 2; };
-      if (!resident(wch - 1)) gather(wch - 1, (gb + wch - 1) & 1);
-      if (wch > 1 && !resident(wch - 2)) gather(wch - 2, (gb + wch - 2) & 1);
-      if (wch > 1 && !resident(wch - 2) && !resident(wch - 1)) cp_async_wait_one();
-      else cp_async_wait_all();
-      fence_proxy_async();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      issue_q((gb + wch - 1) & 1);
-      for (int c = wch - 1; c >= 0; --c) {
-        const int g = gb + c, buf = g & 1;
-        if (c > 0) {  // chunk c-1's rows are in: start its Q product now
-          cp_async_wait_all();
-          fence_proxy_async();
-          tc_fence_before();
-          __syncthreads();
-          tc_fence_after();
-          issue_q(buf ^ 1);
-        }
-        q_wait(buf);
-        if (__syncthreads_or(failed)) break;
-        {
-          const int row = quad * 32 + lane, t = c * kChunk + row;
-          const int dd = s_d[t];
-          const float f = s_f[t];
-          const float4 *yr = reinterpret_cast<const float4 *>(sY + dd * 128 + half * 64);
-          const float4 *zr = reinterpret_cast<const float4 *>(sZ + dd * 128 + half * 64);
-          float q[64];
-          tmem_ld64(colQ0 + buf * 128 + (static_cast<uint32_t>(quad * 32) << 16) + half * 64, q);
-#pragma unroll
-          for (int i4 = 0; i4 < 16; ++i4) {
-            const float4 y4 = yr[i4], z4 = zr[i4];
-            const float ys[4] = {y4.x, y4.y, y4.z, y4.w}, zs[4] = {z4.x, z4.y, z4.z, z4.w};
-            float bb[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float qi = q[i4 * 4 + u];
-              if (a.same_token) {
-                bb[u] = f * (zs[u] + 2.f * qi * qi - 2.f * qi * ys[u]);
-                lacc += 2.f * f * qi * qi * qi;
-              } else {
-                bb[u] = f * zs[u];
-              }
-            }
-            st_bf16x4(sQ, 16384, row, half * 64 + i4 * 4, bb[0], bb[1], bb[2], bb[3]);
-          }
-        }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) {  // G += U_chunk^T B''_chunk (M = features, N = topics)
-          const uint32_t ub = smem_u32(sm + (buf ? kOffU1 : kOffU0)), bq = smem_u32(sQ);
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk)
-            mma_bf16(colG, sdesc_mn_sw128(ub + kk * 2048, 16384), sdesc_mn_sw128(bq + kk * 2048, 16384), idG,
-                     (g_init || kk > 0) ? 1u : 0u);
-          mma_commit(&bars[1]);
-        }
-        g_init = true;
-        mma_wait();
-        if (__syncthreads_or(failed)) break;
-        if (c > 1 && !resident(c - 2)) gather(c - 2, buf);  // this buffer's products are done
-      }
-    }
-    cp_async_wait_all();
-    if (a.want_loss) {
-      for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, o);
-      if (lane == 0) s_red[warp] = lacc;
-      __syncthreads();
-      if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kFusedThreads / 32; ++w) t += s_red[w];
-        atomicAdd(&a.st->loss_data, t);
-      }
-    }
-    if (__syncthreads_or(failed)) break;
+    tc_fence_after();
+    tmem = *tslot;
+    // TMEM columns: Q (two buffers, chunk parity), Y^T, R^T, G
+    colQ0 = tmem;
+    colYt = tmem + 256;
+    colRt = tmem + 320;
+    colG = tmem + 384;
   }
-  cp_async_wait_all();
-  // ---------------- partial G of this CTA -> Gpart[blockIdx.x] (rows = features)
-  if (failed) {
-    if (tid == 0) atomicOr(&a.st->err, kErrTimeout);
-  } else {
+
+  __device__ void finish() {
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+  }
+
+  // Phi^T image into shared memory by bulk copy (image written by an earlier kernel).
+  __device__ void phi_bulk(const __nv_bfloat16 *img) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&bars[0], 32768);
+      bulk_load(sPhi, img, 32768, &bars[0]);
+    }
+  }
+  __device__ void phi_wait() {
+    if (!mbar_wait(&bars[0], pph & 1)) fail();
+    ++pph;
+  }
+
+  // Partial G (rows = features) -> dst (128 x Kp FP32); zeros if no tile added to it.
+  __device__ void write_g(float *dst, int Kp, bool g_init) {
     const int row = quad * 32 + lane;
+    tc_fence_after();
 #pragma unroll 1
     for (int p = 0; p < 4; ++p) {
       const int c0 = half * 64 + p * 16;
@@ -435,12 +195,587 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
         for (int i = 0; i < 16; ++i) v[i] = 0.f;
 #pragma unroll
       for (int q = 0; q < 16; q += 4)
-        *reinterpret_cast<float4 *>(gp + (long long)row * a.Kp + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        *reinterpret_cast<float4 *>(dst + (long long)row * Kp + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+    }
+    tc_fence_before();
+  }
+
+  // The data term of tiles tile0, tile0 + tstride, ... of batch b (td <= kT
+  // documents each), added to the G columns.  S3 and validation bits go to
+  // S3_dst and err_dst, the per-document loss parts to lacc.  Expects the Phi
+  // image in shared memory.  Returns false on an expired wait.
+  __device__ bool tiles(const StepArgs &a, const BatchDesc &b, int tile0, int tstride, int td, float &lacc,
+                        bool &g_init, unsigned long long *S3_dst, int *err_dst) {
+    const int nd = b.n_docs;
+    const int ntiles = nd > 0 ? (nd + td - 1) / td : 0;
+    const uint32_t idQ = idesc_bf16(128, 128);
+    const uint32_t idYR = idesc_bf16(128, 64) | (1u << 15) | (1u << 16);
+    const uint32_t idG = idesc_bf16(128, 128) | (1u << 15) | (1u << 16);
+    const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+
+    auto mma_wait = [&]() {
+      if (!mbar_wait(&bars[1], mph & 1)) fail();
+      ++mph;
+      tc_fence_after();
+    };
+    auto q_wait = [&](int buf) {
+      uint32_t &ph = buf ? qph1 : qph0;
+      if (!mbar_wait(&bars[2 + buf], ph & 1)) fail();
+      ++ph;
+      tc_fence_after();
+    };
+
+    for (int tile = tile0; tile < ntiles; tile += tstride) {
+      if (failed()) break;
+      const int d0 = tile * td, Te = min(td, nd - d0);
+      if (tid <= Te) s_ptr[tid] = b.indptr[d0 + tid];
+      if (tid < kT) s_L[tid] = 0;
+      if (tid == 0) {
+        sh[1] = 0;
+        sh[2] = -1;
+      }
+      __syncthreads();
+      if (tid < Te && (s_ptr[tid + 1] < s_ptr[tid] || s_ptr[tid] < b.nz_base)) sh[1] = 1;
+      const int nz0 = s_ptr[0];
+      const int nnz = max(0, s_ptr[Te] - nz0);
+      const int nch = (nnz + kChunk - 1) / kChunk;
+      const int nwin = (nnz + kWin - 1) / kWin;
+
+      // metadata of nonzeros [w0, w0 + kWin) of the tile; pass 1 also validates
+      // the entries and adds the documents' token counts
+      auto load_window = [&](int w0, bool check) {
+        constexpr int kPer = kWin / kFusedThreads;
+        int mr[kPer], fr[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {  // all loads in flight first
+          const int j = w0 + tid + u * kFusedThreads;
+          mr[u] = -1;
+          fr[u] = 0;
+          if (j < nnz) {
+            mr[u] = __ldg(b.indices + ((long long)(nz0 + j) - b.nz_base));
+            fr[u] = __ldg(b.counts + ((long long)(nz0 + j) - b.nz_base));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+          const int t = tid + u * kFusedThreads, j = w0 + t;
+          int dd = 0;
+          float f = 0.f;
+          if (j < nnz) {
+            const int p = nz0 + j;
+            int lo = 0, hi = Te - 1;  // last document whose range starts at or before p
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (s_ptr[mid] <= p) lo = mid;
+              else hi = mid - 1;
+            }
+            dd = lo;
+            const bool valid = mr[u] >= 0 && mr[u] < a.V && fr[u] > 0;
+            f = valid ? (float)fr[u] : 0.f;
+            if (check) {
+              if (!valid) sh[1] = 1;
+              else atomicAdd(s_L + dd, fr[u]);
+            }
+          }
+          s_m[t] = mr[u];
+          s_f[t] = f;
+          s_d[t] = dd;
+        }
+        __syncthreads();
+        if (check) {  // words strictly ascending within a document
+          for (int t = tid; t < kWin; t += kFusedThreads) {
+            const int j = w0 + t;
+            if (j < nnz && nz0 + j > s_ptr[s_d[t]]) {
+              const int mp = t > 0 ? s_m[t - 1] : sh[2];
+              if (s_m[t] <= mp) sh[1] = 1;
+            }
+          }
+          __syncthreads();
+          if (tid == 0) sh[2] = s_m[kWin - 1];
+        }
+      };
+      // cp.async gather of the BF16 U rows of window chunk c into buffer buf
+      auto gather = [&](int c, int buf) {
+        unsigned char *sU = sm + (buf ? kOffU1 : kOffU0);
+        for (int pce = tid; pce < kChunk * 16; pce += kFusedThreads) {
+          const int r = pce >> 4, pc = pce & 15;
+          const int m = s_m[c * kChunk + r];
+          unsigned char *dst = sU + (pc >> 3) * 16384 + sw_chunk(r, pc & 7);
+          if (m >= 0 && m < a.V) cp_async16(dst, a.U16 + (long long)m * a.Dp + pc * 8);
+          else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        cp_async_commit();
+      };
+      // Q chunk = U chunk Phi (rows = nonzeros) into TMEM buffer buf; committed
+      // to barrier 2 + buf
+      auto issue_q = [&](int buf) {
+        if (tid == 0) {
+          const uint32_t ub = smem_u32(sm + (buf ? kOffU1 : kOffU0)), pb = smem_u32(sPhi);
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk)
+            mma_bf16(colQ0 + buf * 128, sdesc_sw128(ub + (kk >> 2) * 16384 + (kk & 3) * 32),
+                     sdesc_sw128(pb + (kk >> 2) * 16384 + (kk & 3) * 32), idQ, kk > 0 ? 1u : 0u);
+          mma_commit(&bars[2 + buf]);
+        }
+      };
+      auto put_f = [&](int c, bool on) {  // F^T row r: f_r at the column of its document
+        if (tid < kChunk) {
+          const int t = c * kChunk + tid, dd = s_d[t];
+          *reinterpret_cast<__nv_bfloat16 *>(sF + sw_chunk(tid, dd >> 3) + ((dd & 7) << 1)) =
+              __float2bfloat16_rn(on ? s_f[t] : 0.f);
+        }
+      };
+
+      // ---------------- pass 1: y and r over all chunks (buffer of global chunk g = g & 1).
+      // The Q product of chunk c+1 runs while chunk c's Q rows are read out.
+      for (int w = 0; w < nwin && !failed(); ++w) {
+        const int w0 = w * kWin, wch = min(kWin, nnz - w0 + kChunk - 1) / kChunk, gb = w0 / kChunk;
+        load_window(w0, true);
+        gather(0, gb & 1);
+        if (wch > 1) gather(1, (gb + 1) & 1);
+        if (wch > 1) cp_async_wait_one();
+        else cp_async_wait_all();
+        put_f(0, true);
+        fence_proxy_async();
+        __syncthreads();
+        issue_q(gb & 1);
+        for (int c = 0; c < wch; ++c) {
+          const int g = gb + c, buf = g & 1;
+          if (c + 1 < wch) {  // chunk c+1's rows have landed: start its Q product now
+            cp_async_wait_all();
+            fence_proxy_async();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            issue_q(buf ^ 1);
+          }
+          q_wait(buf);
+          if (__syncthreads_or(failed())) break;
+          if (c + 2 < wch) gather(c + 2, buf);  // this buffer's Q product is done
+          {  // Q and Q*Q rows (BF16) for the MN-major reductions over nonzeros
+            const int row = quad * 32 + lane;
+            float q[64];
+            tmem_ld64(colQ0 + buf * 128 + lane_off + half * 64, q);
+#pragma unroll
+            for (int i = 0; i < 64; i += 4) {
+              const int c0 = half * 64 + i;
+              st_bf16x4(sQ, 16384, row, c0, q[i], q[i + 1], q[i + 2], q[i + 3]);
+              st_bf16x4(sQ2, 16384, row, c0, q[i] * q[i], q[i + 1] * q[i + 1], q[i + 2] * q[i + 2],
+                        q[i + 3] * q[i + 3]);
+            }
+          }
+          fence_proxy_async();
+          tc_fence_before();
+          __syncthreads();
+          tc_fence_after();
+          if (tid == 0) {  // Y^T += Q^T F^T, R^T += (Q*Q)^T F^T  (M = topics, N = 64 documents)
+            const uint32_t qb = smem_u32(sQ), q2b = smem_u32(sQ2), fb = smem_u32(sF);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+              mma_bf16(colYt, sdesc_mn_sw128(qb + kk * 2048, 16384), sdesc_mn_sw128(fb + kk * 2048, 16384), idYR,
+                       (g > 0 || kk > 0) ? 1u : 0u);
+              mma_bf16(colRt, sdesc_mn_sw128(q2b + kk * 2048, 16384), sdesc_mn_sw128(fb + kk * 2048, 16384), idYR,
+                       (g > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(&bars[1]);
+          }
+          mma_wait();
+          put_f(c, false);                     // these products are done: clear c's entries
+          if (c + 1 < wch) put_f(c + 1, true);  // and place c+1's
+          fence_proxy_async();
+          if (__syncthreads_or(failed())) break;
+        }
+      }
+      cp_async_wait_all();
+      if (__syncthreads_or(failed())) break;
+      // ---------------- y, z = y^2 - r (FP32, [document][topic]); S3 and validation
+      {
+        const int topic = quad * 32 + lane;
+        float yv[16], rv[16];
+        if (nch > 0) {
+          tmem_ld16(colYt + lane_off + half * 16, yv);
+          tmem_ld16(colRt + lane_off + half * 16, rv);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) yv[i] = rv[i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int dd = half * 16 + i;
+          const float y = dd < Te ? yv[i] : 0.f;
+          const float r = (dd < Te && a.same_token) ? rv[i] : 0.f;
+          sY[dd * 128 + topic] = y;
+          sZ[dd * 128 + topic] = y * y - r;
+          lacc += y * (y * y - 3.f * r);
+        }
+      }
+      if (warp == 0) {
+        const long long L = lane < Te ? s_L[lane] : 0;
+        unsigned long long s3 = L >= 3 ? (unsigned long long)(L * (L - 1) * (L - 2)) : 0ull;
+        for (int o = 16; o > 0; o >>= 1) s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+        if (lane == 0) {
+          if (s3) atomicAdd(S3_dst, s3);
+          if (sh[1]) atomicOr(err_dst, kErrCsr);
+        }
+      }
+      __syncthreads();
+      // ---------------- pass 2 in reverse chunk order: the last two chunks of
+      // pass 1 are still in their buffers; earlier ones are gathered again.
+      // The Q product of the next (lower) chunk runs during this chunk's B''.
+      for (int w = nwin - 1; w >= 0 && !failed(); --w) {
+        const int w0 = w * kWin, wch = min(kWin, nnz - w0 + kChunk - 1) / kChunk, gb = w0 / kChunk;
+        if (nwin > 1) load_window(w0, false);
+        auto resident = [&](int c) { return nwin == 1 && c >= wch - 2; };
+        if (!resident(wch - 1)) gather(wch - 1, (gb + wch - 1) & 1);
+        if (wch > 1 && !resident(wch - 2)) gather(wch - 2, (gb + wch - 2) & 1);
+        if (wch > 1 && !resident(wch - 2) && !resident(wch - 1)) cp_async_wait_one();
+        else cp_async_wait_all();
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        issue_q((gb + wch - 1) & 1);
+        for (int c = wch - 1; c >= 0; --c) {
+          const int g = gb + c, buf = g & 1;
+          if (c > 0) {  // chunk c-1's rows are in: start its Q product now
+            cp_async_wait_all();
+            fence_proxy_async();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            issue_q(buf ^ 1);
+          }
+          q_wait(buf);
+          if (__syncthreads_or(failed())) break;
+          {
+            const int row = quad * 32 + lane, t = c * kChunk + row;
+            const int dd = s_d[t];
+            const float f = s_f[t];
+            const float4 *yr = reinterpret_cast<const float4 *>(sY + dd * 128 + half * 64);
+            const float4 *zr = reinterpret_cast<const float4 *>(sZ + dd * 128 + half * 64);
+            float q[64];
+            tmem_ld64(colQ0 + buf * 128 + lane_off + half * 64, q);
+#pragma unroll
+            for (int i4 = 0; i4 < 16; ++i4) {
+              const float4 y4 = yr[i4], z4 = zr[i4];
+              const float ys[4] = {y4.x, y4.y, y4.z, y4.w}, zs[4] = {z4.x, z4.y, z4.z, z4.w};
+              float bb[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const float qi = q[i4 * 4 + u];
+                if (a.same_token) {
+                  bb[u] = f * (zs[u] + 2.f * qi * qi - 2.f * qi * ys[u]);
+                  lacc += 2.f * f * qi * qi * qi;
+                } else {
+                  bb[u] = f * zs[u];
+                }
+              }
+              st_bf16x4(sQ, 16384, row, half * 64 + i4 * 4, bb[0], bb[1], bb[2], bb[3]);
+            }
+          }
+          fence_proxy_async();
+          tc_fence_before();
+          __syncthreads();
+          tc_fence_after();
+          if (tid == 0) {  // G += U_chunk^T B''_chunk (M = features, N = topics)
+            const uint32_t ub = smem_u32(sm + (buf ? kOffU1 : kOffU0)), bq = smem_u32(sQ);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+              mma_bf16(colG, sdesc_mn_sw128(ub + kk * 2048, 16384), sdesc_mn_sw128(bq + kk * 2048, 16384), idG,
+                       (g_init || kk > 0) ? 1u : 0u);
+            mma_commit(&bars[1]);
+          }
+          g_init = true;
+          mma_wait();
+          if (__syncthreads_or(failed())) break;
+          if (c > 1 && !resident(c - 2)) gather(c - 2, buf);  // this buffer's products are done
+        }
+      }
+      cp_async_wait_all();
+      if (__syncthreads_or(failed())) break;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    return !failed();
+  }
+};
+
+__global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ float s_red[kFusedThreads / 32];
+  Fused f;
+  f.init(smem_raw);
+  const BatchDesc b = a.st->cur;
+  const int ntiles = (b.n_docs + kT - 1) / kT;
+  const bool has_work = b.n_docs > 0 && ntiles > (int)blockIdx.x;
+  if (has_work) {
+    f.phi_bulk(a.PhiImg);
+    f.phi_wait();
+  }
+  __syncthreads();
+  float lacc = 0.f;
+  bool g_init = false;
+  if (has_work) f.tiles(a, b, blockIdx.x, gridDim.x, kT, lacc, g_init, &a.st->S3, &a.st->err);
+  if (a.want_loss) {
+    const float t = block_sum(lacc, s_red);
+    if (f.tid == 0 && t != 0.f) atomicAdd(&a.st->loss_data, (double)t);
+  }
+  if (f.failed()) {
+    if (f.tid == 0) atomicOr(&a.st->err, kErrTimeout);
+  } else {
+    f.write_g(a.Gpart + (long long)blockIdx.x * a.Dp * a.Kp, a.Kp, g_init);
+  }
+  f.finish();
+}
+
+// ------------------------------------------------------------ persistent pass
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier (every block is resident: cooperative launch): waits until the
+// launch's monotone arrival counter reaches `target`.  Bounded; false if it
+// expired here, or if any block flagged an abort.
+__device__ bool grid_sync(PassCtl *ctl, unsigned target, int *s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(&ctl->bar, 1u);
+    const long long t0 = clock64();
+    while (ld_acquire(&ctl->bar) < target) {
+      if (*reinterpret_cast<volatile int *>(&ctl->abort)) {
+        ok = 0;
+        break;
+      }
+      if (clock64() - t0 > kWaitCycles) {
+        atomicExch(&ctl->abort, 1);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    *reinterpret_cast<volatile int *>(s_ok) = ok;
+  }
+  __syncthreads();
+  return *reinterpret_cast<volatile int *>(s_ok) != 0;
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs p) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ float s_red[kFusedThreads / 32];
+  __shared__ float s_am;
+  __shared__ int s_ok;
+  Fused f;
+  f.init(smem_raw);
+  PassCtl *ctl = p.ctl;
+  DevState *st = a.st;
+  const int G = gridDim.x, blk = blockIdx.x, tid = f.tid;
+  const int D = a.D, K = a.K, Kp = a.Kp, DK = a.D * a.K;
+  const long long DpKp = (long long)a.Dp * a.Kp;
+  // phase B: this block's entries of Phi (row-major D x K)
+  const int per = (DK + G - 1) / G;
+  const int e0 = min(DK, blk * per), e1 = min(DK, e0 + per);
+  // phase A: the Phi-only column of this block (columns go to the last K blocks,
+  // tiles to the first ones, so small batches keep the two apart)
+  const int col = blk - (G - K);
+  float *gp = a.Gpart + (long long)blk * DpKp;
+  // phase A: Phi (D x K FP32, rows padded to K + 1 floats against bank
+  // conflicts) in the U-buffer and Q region, free until the tiles start
+  float *sPh = reinterpret_cast<float *>(f.sm + kOffU0);
+  const int ldp = K + 1;
+  unsigned nbar = 0;
+  bool alive = true;
+  double last_loss = 0.0;
+  unsigned long long last_S3 = 0;
+
+  for (int s = p.s0; s < p.s1 && alive; ++s) {
+    const int slot = s & 1;
+    const BatchDesc b = p.descs[s];
+    const int nd = b.n_docs;
+    const int td = nd > 0 ? max(1, min(p.tile_cap, (nd + G - 1) / G)) : 1;
+    const int ntiles = nd > 0 ? (nd + td - 1) / td : 0;
+    const int nwork = min(G, ntiles);
+    const bool has = blk < ntiles;
+
+    // ---------------- phase A: the Phi^T image and Phi into shared memory
+    // (L2 loads: both were written by other blocks during this launch)
+    {
+      constexpr int kImgPer = 32768 / 16 / kFusedThreads;  // 8 x 16 B
+      constexpr int kPhiPer = 128 * 128 / kFusedThreads;   // 64
+      uint4 img[kImgPer];
+      float ph[kPhiPer];
+      if (has) {
+#pragma unroll
+        for (int u = 0; u < kImgPer; ++u)
+          img[u] = __ldcg(reinterpret_cast<const uint4 *>(a.PhiImg) + tid + u * kFusedThreads);
+      }
+      if (col >= 0) {
+#pragma unroll
+        for (int u = 0; u < kPhiPer; ++u) {
+          const int e = tid + u * kFusedThreads;
+          ph[u] = e < DK ? __ldcg(a.Phi + e) : 0.f;
+        }
+      }
+      if (has) {
+#pragma unroll
+        for (int u = 0; u < kImgPer; ++u) reinterpret_cast<uint4 *>(f.sPhi)[tid + u * kFusedThreads] = img[u];
+      }
+      if (col >= 0) {
+#pragma unroll
+        for (int u = 0; u < kPhiPer; ++u) {
+          const int e = tid + u * kFusedThreads;
+          if (e < DK) sPh[(e / K) * ldp + e % K] = ph[u];
+        }
+      }
+      fence_proxy_async();
+      __syncthreads();
+    }
+    // column `col` of the Phi-only terms: G_{b,col} = phi_b . phi_col for all
+    // b (Phi^T Phi is symmetric), a = m1 . phi_col, then for every row r
+    //   P_r = sum_b Phi_rb G_{b,col}^2,
+    //   G3_r = 2 Phi_r,col a + m1_r |phi_col|^2 - 2 m1_r a^2,
+    //   E_r = 3(1+theta) P_r - 3 G3_r,
+    // and the column's loss part (1+theta)/2 sum_b G^3 - (3 a |phi|^2 - 2 a^3)
+    if (col >= 0) {
+      float *sg = f.sZ;  // [0, 256): two halves of the Gram column; [256, 384): the column
+      {
+        const int n = tid & 127, rh = tid >> 7;
+        float g = 0.f;
+        if (n < K) {
+          const int r0 = rh ? (D + 1) / 2 : 0, r1 = rh ? D : (D + 1) / 2;
+#pragma unroll 4
+          for (int r = r0; r < r1; ++r) g = fmaf(sPh[r * ldp + col], sPh[r * ldp + n], g);
+        }
+        sg[rh * 128 + n] = g;
+        if (f.warp == 0) {
+          float am = 0.f;
+          for (int r = f.lane; r < D; r += 32) am = fmaf(a.m1[r], sPh[r * ldp + col], am);
+          for (int o = 16; o > 0; o >>= 1) am += __shfl_xor_sync(0xffffffffu, am, o);
+          if (f.lane == 0) s_am = am;
+        }
+        __syncthreads();
+        if (tid < 128) sg[256 + tid] = tid < K ? sg[tid] + sg[128 + tid] : 0.f;
+        __syncthreads();
+      }
+      const float am = s_am, n2 = sg[256 + col];
+      {
+        const int r = tid & 127, bh = tid >> 7;
+        float pv = 0.f;
+        if (r < D) {
+          const int b0 = bh ? (K + 1) / 2 : 0, b1 = bh ? K : (K + 1) / 2;
+#pragma unroll 4
+          for (int bb = b0; bb < b1; ++bb) {
+            const float g = sg[256 + bb];
+            pv = fmaf(sPh[r * ldp + bb], g * g, pv);
+          }
+        }
+        sg[bh * 128 + r] = pv;  // the first two halves are free again
+        __syncthreads();
+        if (tid < D) {
+          const float P = sg[tid] + sg[128 + tid];
+          const float mr = a.m1[tid];
+          const float g3 = 2.f * sPh[tid * ldp + col] * am + mr * n2 - 2.f * mr * am * am;
+          a.E[tid * Kp + col] = 3.f * (1.f + a.theta) * P - 3.f * g3;
+        }
+      }
+      if (a.want_loss) {
+        const float gg = tid < K ? sg[256 + tid] : 0.f;
+        float v = tid < K ? 0.5f * (1.f + a.theta) * gg * gg * gg : 0.f;
+        if (tid == 0) v -= 3.f * am * n2 - 2.f * am * am * am;
+        const float t = block_sum(v, s_red);
+        if (tid == 0) atomicAdd(&ctl->loss_phi[slot], (double)t);
+      }
+      __syncthreads();
+    }
+    // the data term of this block's tiles
+    if (has) {
+      float lacc = 0.f;
+      bool g_init = false;
+      f.tiles(a, b, blk, G, td, lacc, g_init, &ctl->S3[slot], &st->err);
+      if (a.want_loss) {
+        const float t = block_sum(lacc, s_red);
+        if (tid == 0 && t != 0.f) atomicAdd(&ctl->loss_data[slot], (double)t);
+      }
+      if (!f.failed()) f.write_g(gp, Kp, g_init);
+      __syncthreads();
+    }
+    if (f.failed() && tid == 0) atomicExch(&ctl->abort, 1);
+    if (!grid_sync(ctl, ++nbar * G, &s_ok)) break;
+
+    // ---------------- phase B: sum the partials of this block's entries,
+    // grad = E - 3 c3/S3 (G1 + G2), Phi -= lr grad, the Phi^T image
+    const unsigned long long S3 = *reinterpret_cast<volatile unsigned long long *>(&ctl->S3[slot]);
+    const int err = *reinterpret_cast<volatile int *>(&st->err);
+    const double scale = S3 ? a.c3 / (double)S3 : 0.0;
+    for (int base = e0; base < e1; base += 128) {
+      const int cnt = min(128, e1 - base);
+      // warp w sums partials w, w + 8, ... (all of its loads in flight at once);
+      // lane l takes entries l, l + 32, l + 64, l + 96 of the group
+      constexpr int kPW = 20;  // partials per warp in the unrolled part (G <= 160)
+      float acc[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int q = f.lane + 32 * j, e = base + q;
+        const bool ok = q < cnt;
+        const long long off = ok ? (long long)(e / K) * Kp + e % K : 0;
+        float v[kPW];
+#pragma unroll
+        for (int u = 0; u < kPW; ++u) {
+          const int c = f.warp + 8 * u;
+          v[u] = (ok && c < nwork) ? __ldcg(a.Gpart + c * DpKp + off) : 0.f;
+        }
+        float t = 0.f;
+#pragma unroll
+        for (int u = 0; u < kPW; ++u) t += v[u];
+        for (int c = f.warp + 8 * kPW; ok && c < nwork; c += 8) t += __ldcg(a.Gpart + c * DpKp + off);
+        acc[j] = t;
+      }
+      float *red = f.sY;  // 8 x 128
+#pragma unroll
+      for (int j = 0; j < 4; ++j) red[f.warp * 128 + f.lane + 32 * j] = acc[j];
+      __syncthreads();
+      if (tid < cnt) {
+        const int e = base + tid, i = e / K, n = e % K;
+        float g = 0.f;
+#pragma unroll
+        for (int w = 0; w < kFusedThreads / 32; ++w) g += red[w * 128 + tid];
+        const float E = __ldcg(a.E + i * Kp + n);
+        const float grad = S3 ? E - (float)(3.0 * scale * (double)g) : 0.f;
+        float phi = __ldcg(a.Phi + e);
+        if (!err && S3) {
+          phi -= a.lr * grad;
+          a.Phi[e] = phi;
+        }
+        a.PhiImg[phi_img_index(n, i, Kp)] = __float2bfloat16_rn(phi);
+      }
+      __syncthreads();
+    }
+    if (blk == 0 && tid == 0) {
+      last_S3 = S3;
+      last_loss = 0.0;
+      if (S3) {
+        const double lp = *reinterpret_cast<volatile double *>(&ctl->loss_phi[slot]);
+        const double ld = *reinterpret_cast<volatile double *>(&ctl->loss_data[slot]);
+        last_loss = lp - scale * ld;
+      }
+      if (p.losses) p.losses[s] = last_loss;
+      ctl->S3[slot ^ 1] = 0;
+      ctl->loss_data[slot ^ 1] = 0.0;
+      ctl->loss_phi[slot ^ 1] = 0.0;
+    }
+    if (s + 1 < p.s1) {
+      if (!grid_sync(ctl, ++nbar * G, &s_ok)) alive = false;
+    } else if (p.record && blk == 0 && tid == 0) {
+      st->step += p.s1 - p.s0;
+      st->last_S3 = last_S3;
+      st->loss = last_loss;
     }
   }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 512);
+  if (tid == 0 && (f.failed() || *reinterpret_cast<volatile int *>(&ctl->abort))) atomicOr(&st->err, kErrTimeout);
+  f.finish();
 }
 
 }  // namespace
@@ -454,6 +789,25 @@ void launch_fused(const StepArgs &a, cudaStream_t s, int grid) {
     attr = true;
   }
   k_fused<<<grid, kFusedThreads, kFusedSmem, s>>>(a);
+}
+
+int pass_grid() {
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaFuncSetAttribute(k_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass, kFusedThreads, kFusedSmem) != cudaSuccess)
+    return 0;
+  return (per_sm >= 1 && sms >= kMinPassGrid) ? sms : 0;
+}
+
+cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, int grid) {
+  StepArgs aa = a;
+  PassArgs pp = p;
+  void *args[] = {&aa, &pp};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_pass), dim3(grid), dim3(kFusedThreads), args,
+                                     kFusedSmem, s);
 }
 
 }  // namespace tlda

@@ -337,14 +337,6 @@ void launch_phi_terms(const StepArgs &a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ Phi^T image (BF16 forms)
-// Element (topic n, feature k) of the B operand Phi^T in the shared-memory
-// layout of the tensor-core kernels: (Dp/64) sub-tiles of [Kp rows x 64]
-// BF16, 16-byte chunk c of row n stored at chunk c ^ (n mod 8).
-__device__ __forceinline__ long long phi_img_index(int n, int k, int Kp) {
-  const int sub = k >> 6, kc = k & 63;
-  return (long long)sub * Kp * 64 + n * 64 + ((((kc >> 3) ^ (n & 7)) & 7) << 3) + (kc & 7);
-}
-
 __global__ void k_phi_img(StepArgs a) {
   const int groups = a.Kp * (a.Dp / 8);
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {

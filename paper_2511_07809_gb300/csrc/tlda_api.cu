@@ -14,7 +14,8 @@ using namespace tlda;
 
 namespace tlda {
 const char *const kKernelNames[kNumKernels] = {"scan_whiten", "qy", "rz", "zh", "g_reduce",
-                                                "reduce_update", "phi_gram", "phi_terms", "fused"};
+                                                "reduce_update", "phi_gram", "phi_terms", "fused",
+                                                "pass"};
 }
 
 namespace {
@@ -211,6 +212,190 @@ tlda_status take_sticky(tlda_ctx *ctx) {
   return TLDA_OK;
 }
 
+// ------------------------------------------------------------ persistent pass
+constexpr long long kStageWords = 1ll << 23;  // int32 words per host-input staging buffer (32 MB)
+constexpr int kTuneBatches = 64;
+
+tlda_status ensure_descs(tlda_ctx *ctx, int n) {
+  if (ctx->descs_cap < n) {
+    dfree(ctx->descs);
+    CK(dalloc(&ctx->descs, (size_t)n));
+    ctx->descs_cap = n;
+  }
+  return TLDA_OK;
+}
+
+// One cooperative launch: steps [s0, s1) of the descriptors in ctx->descs.
+tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int cap, double *dl, int record,
+                        cudaStream_t ps) {
+  PassArgs pa{};
+  pa.descs = ctx->descs;
+  pa.s0 = s0;
+  pa.s1 = s1;
+  pa.tile_cap = cap;
+  pa.losses = dl;
+  pa.ctl = ctx->ctl;
+  pa.record = record;
+  CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(PassCtl), ps));
+  Prof pr(ctx, kPass, ps);
+  CK(launch_pass(a, pa, ps, ctx->pass_grid));
+  return TLDA_OK;
+}
+
+// Times each candidate tile size over steps [0, n) of ctx->descs on a
+// scratch copy of Phi (lr = 0) and a scratch device state (a corrupt batch
+// is left for the real pass to report), and keeps the fastest.
+tlda_status tune_tiles(tlda_ctx *ctx, const float *Phi, int n, cudaStream_t ps) {
+  StepArgs a = make_args(ctx);
+  a.Phi = ctx->phi_scratch;
+  a.st = ctx->st_tune;
+  CK(cudaMemsetAsync(ctx->st_tune, 0, sizeof(DevState), ps));
+  CK(cudaMemcpyAsync(ctx->phi_scratch, Phi, sizeof(float) * ctx->D * ctx->K, cudaMemcpyDeviceToDevice, ps));
+  launch_phi_img(a, ps);
+  CKL();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int cands[] = {8, 16, 24, 32};
+  int best = ctx->tile_cap;
+  float best_ms = 0.f;
+  tlda_status s = TLDA_OK;
+  for (int c : cands) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && s == TLDA_OK; ++rep) {  // the first run is a warm-up
+      cudaEventRecord(e0, ps);
+      s = pass_launch(ctx, a, 0, n, c, nullptr, 0, ps);
+      cudaEventRecord(e1, ps);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        s = fail(ctx, TLDA_ERR_CUDA, "tile tuning: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    if (s) break;
+    if (best_ms == 0.f || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s) return s;
+  ctx->tile_cap = best;
+  ctx->tuned = true;
+  return TLDA_OK;
+}
+
+// The whole pass through the persistent kernel on the pass stream.  Device
+// input: one launch.  Host input: the batches are cut into segments that fit
+// a staging buffer; segment g is copied on the copy stream into buffer g & 1
+// (after the kernel of segment g - 2 is done with it) while the kernel of
+// segment g - 1 runs.
+tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *off, int nb, float *Phi,
+                               float lr, bool host, double *loss_out) {
+  std::vector<int> seg{0};
+  std::vector<BatchDesc> hd(nb);
+  if (host) {
+    const int32_t *ip = corpus->indptr;
+    auto need = [&](int b0, int b1) {
+      return (long long)(off[b1] - off[b0] + 1) + 2ll * ((long long)ip[off[b1]] - ip[off[b0]]);
+    };
+    long long max_need = 0;
+    for (int b = 0; b < nb; ++b) {
+      if (ip[off[b + 1]] < ip[off[b]] || ip[off[b]] < 0)
+        return fail(ctx, TLDA_ERR_INVALID, "host indptr not monotone at batch %d", b);
+      max_need = std::max(max_need, need(b, b + 1));
+    }
+    const long long cap = std::max(max_need, std::min(need(0, nb), kStageWords));
+    if (ctx->stage_cap < cap) {
+      dfree(ctx->stage[0]);
+      dfree(ctx->stage[1]);
+      ctx->stage_cap = 0;
+      CK(dalloc(&ctx->stage[0], (size_t)cap));
+      CK(dalloc(&ctx->stage[1], (size_t)cap));
+      ctx->stage_cap = cap;
+    }
+    for (int b0 = 0; b0 < nb;) {
+      int b1 = b0 + 1;
+      while (b1 < nb && need(b0, b1 + 1) <= ctx->stage_cap) ++b1;
+      seg.push_back(b1);
+      b0 = b1;
+    }
+    for (size_t g = 0; g + 1 < seg.size(); ++g) {
+      const int b0 = seg[g], b1 = seg[g + 1];
+      const long long d0 = off[b0], nds = off[b1] - d0, lo = ip[d0], nnz = ip[off[b1]] - lo;
+      int32_t *sg = ctx->stage[g & 1];
+      for (int b = b0; b < b1; ++b) {
+        BatchDesc &d = hd[b];
+        d.indptr = sg + (off[b] - d0);
+        d.indices = sg + nds + 1;
+        d.counts = sg + nds + 1 + nnz;
+        d.nz_base = lo;
+        d.n_docs = (int32_t)(off[b + 1] - off[b]);
+      }
+    }
+  } else {
+    seg.push_back(nb);
+    for (int b = 0; b < nb; ++b) {
+      BatchDesc &d = hd[b];
+      d.indptr = corpus->indptr + off[b];
+      d.indices = corpus->indices;
+      d.counts = corpus->counts;
+      d.nz_base = 0;
+      d.n_docs = (int32_t)(off[b + 1] - off[b]);
+    }
+  }
+  tlda_status s = ensure_descs(ctx, nb);
+  if (s) return s;
+  if (loss_out && ctx->dlosses_cap < nb) {
+    dfree(ctx->dlosses);
+    ctx->dlosses_cap = 0;
+    CK(dalloc(&ctx->dlosses, (size_t)nb));
+    ctx->dlosses_cap = nb;
+  }
+  cudaStream_t ps = ctx->pstream;
+  CK(cudaEventRecord(ctx->ev_pass0, ctx->stream));
+  CK(cudaStreamWaitEvent(ps, ctx->ev_pass0, 0));
+  CK(cudaMemcpyAsync(ctx->descs, hd.data(), sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, ps));
+  CK(cudaStreamSynchronize(ps));  // hd is pageable: keep it alive until copied
+  if (!ctx->tuned && !host) {
+    s = tune_tiles(ctx, Phi, std::min(nb, kTuneBatches), ps);
+    if (s) return s;
+  }
+  StepArgs a = make_args(ctx);
+  a.lr = lr;
+  a.Phi = Phi;
+  a.want_loss = loss_out ? 1 : 0;
+  launch_phi_img(a, ps);
+  CKL();
+  for (size_t g = 0; g + 1 < seg.size() && s == TLDA_OK; ++g) {
+    const int b0 = seg[g], b1 = seg[g + 1];
+    if (host) {
+      cudaStream_t cs = ctx->cstream;
+      const int32_t *ip = corpus->indptr;
+      const long long d0 = off[b0], d1 = off[b1], lo = ip[d0], hi = ip[d1];
+      const long long nds = d1 - d0;
+      int32_t *sg = ctx->stage[g & 1];
+      if (g >= 2) CK(cudaStreamWaitEvent(cs, ctx->ev_seg[2 + (g & 1)], 0));
+      CK(cudaMemcpyAsync(sg, ip + d0, sizeof(int32_t) * (nds + 1), cudaMemcpyHostToDevice, cs));
+      if (hi > lo) {
+        CK(cudaMemcpyAsync(sg + nds + 1, corpus->indices + lo, sizeof(int32_t) * (hi - lo), cudaMemcpyHostToDevice, cs));
+        CK(cudaMemcpyAsync(sg + nds + 1 + (hi - lo), corpus->counts + lo, sizeof(int32_t) * (hi - lo),
+                           cudaMemcpyHostToDevice, cs));
+      }
+      CK(cudaEventRecord(ctx->ev_seg[g & 1], cs));
+      CK(cudaStreamWaitEvent(ps, ctx->ev_seg[g & 1], 0));
+    }
+    s = pass_launch(ctx, a, b0, b1, ctx->tile_cap, loss_out ? ctx->dlosses : nullptr, 1, ps);
+    if (host && s == TLDA_OK) CK(cudaEventRecord(ctx->ev_seg[2 + (g & 1)], ps));
+  }
+  if (s == TLDA_OK && loss_out)
+    CK(cudaMemcpyAsync(loss_out, ctx->dlosses, sizeof(double) * nb, cudaMemcpyDeviceToHost, ps));
+  CK(cudaEventRecord(ctx->ev_pass1, ps));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_pass1, 0));
+  if (s) return s;
+  s = read_state(ctx);
+  if (s == TLDA_OK) s = take_sticky(ctx);
+  return s;
+}
+
 const uint32_t kStateMagic = 0x41444C54u;  // "TLDA"
 const uint32_t kStateVersion = 1;
 
@@ -320,6 +505,14 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
     ctx->tc_maps = tc_make_maps(ctx->UX16, ctx->AT16, ctx->BT16, vocab, ctx->Bmax, ctx->Dp, ctx->Kp, ctx->ldT);
     if (!ctx->tc_maps) return bail(TLDA_ERR_CUDA, "cuTensorMapEncodeTiled", cudaErrorUnknown);
   }
+  if (ctx->fused && !getenv("TLDA_NO_PASS")) ctx->pass_grid = pass_grid();
+  if (ctx->pass_grid > 0) {
+    CA(dalloc(&ctx->ctl, 1, true));
+    CA(dalloc(&ctx->st_tune, 1, true));
+    CA(dalloc(&ctx->phi_scratch, (size_t)D * K, true));
+    CA(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
+    for (cudaEvent_t &ev : ctx->ev_seg) CA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
 #undef CA
   CK(cudaDeviceSynchronize());
   *out = ctx;
@@ -337,6 +530,10 @@ tlda_status tlda_destroy(tlda_ctx *ctx) {
   dfree(ctx->avec); dfree(ctx->E); dfree(ctx->G3); dfree(ctx->AT16); dfree(ctx->PhiImg);
   dfree(ctx->BT16); dfree(ctx->st); dfree(ctx->descs); dfree(ctx->P64); dfree(ctx->Ccnt);
   dfree(ctx->TS); dfree(ctx->fit_err); dfree(ctx->stage[0]); dfree(ctx->stage[1]);
+  dfree(ctx->ctl); dfree(ctx->st_tune); dfree(ctx->dlosses); dfree(ctx->phi_scratch);
+  if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
+  for (cudaEvent_t ev : ctx->ev_seg)
+    if (ev) cudaEventDestroy(ev);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
   for (auto &r : ctx->prof_pending) {
     cudaEventDestroy(r.a);
@@ -456,6 +653,8 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
     if (d0 < 0 || d1 < d0 || d1 > corpus->n_docs) return fail(ctx, TLDA_ERR_INVALID, "batch_offsets[%d] out of range", b);
     if (d1 - d0 > ctx->Bmax) return fail(ctx, TLDA_ERR_INVALID, "batch %d has %lld docs > max_batch", b, (long long)(d1 - d0));
   }
+  if (ctx->pass_grid > 0 && (ctx->prof_mask & ~(1u << kPass)) == 0)
+    return cp_pass_persistent(ctx, corpus, batch_offsets, n_batches, Phi, lr, host, loss_out);
   // descriptors
   if (ctx->descs_cap < n_batches) {
     dfree(ctx->descs);
@@ -571,6 +770,42 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
   }
   if (losses) cudaFreeHost(losses);
   return s;
+}
+
+tlda_status tlda_autotune(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets, int32_t n_batches,
+                          const float *Phi, int32_t fixed_cap, int32_t *tile_cap_out) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  if (ctx->pass_grid <= 0) return fail(ctx, TLDA_ERR_UNIMPLEMENTED, "no persistent pass kernel on this context");
+  if (fixed_cap < 0 || fixed_cap > 32) return fail(ctx, TLDA_ERR_INVALID, "tile size %d not in 1..32", fixed_cap);
+  if (fixed_cap > 0) {
+    ctx->tile_cap = fixed_cap;
+    ctx->tuned = true;
+  } else {
+    if (!ctx->whitened) return fail(ctx, TLDA_ERR_STATE, "no whitening: fit or set one first");
+    tlda_status s = check_csr(ctx, corpus);
+    if (s) return s;
+    if (!Phi || !batch_offsets || n_batches < 1) return fail(ctx, TLDA_ERR_INVALID, "bad tuning arguments");
+    const int n = std::min<int>(n_batches, kTuneBatches);
+    std::vector<BatchDesc> hd(n);
+    for (int b = 0; b < n; ++b) {
+      const int64_t d0 = batch_offsets[b], d1 = batch_offsets[b + 1];
+      if (d0 < 0 || d1 < d0 || d1 > corpus->n_docs) return fail(ctx, TLDA_ERR_INVALID, "batch_offsets[%d] out of range", b);
+      if (d1 - d0 > ctx->Bmax) return fail(ctx, TLDA_ERR_INVALID, "batch %d has %lld docs > max_batch", b, (long long)(d1 - d0));
+      hd[b] = BatchDesc{corpus->indptr + d0, corpus->indices, corpus->counts, 0, (int32_t)(d1 - d0), 0};
+    }
+    s = ensure_descs(ctx, n);
+    if (s) return s;
+    cudaStream_t ps = ctx->pstream;
+    CK(cudaEventRecord(ctx->ev_pass0, ctx->stream));
+    CK(cudaStreamWaitEvent(ps, ctx->ev_pass0, 0));
+    CK(cudaMemcpyAsync(ctx->descs, hd.data(), sizeof(BatchDesc) * n, cudaMemcpyHostToDevice, ps));
+    s = tune_tiles(ctx, Phi, n, ps);
+    CK(cudaEventRecord(ctx->ev_pass1, ps));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_pass1, 0));
+    if (s) return s;
+  }
+  if (tile_cap_out) *tile_cap_out = ctx->tile_cap;
+  return TLDA_OK;
 }
 
 tlda_status tlda_profile(tlda_ctx *ctx, uint32_t mask) {

@@ -50,6 +50,35 @@ struct DevState {
   double loss;                   // loss of the last completed step
 };
 
+// Control block of one persistent-pass launch (zeroed before the launch).
+// Per-step sums live in slot (step & 1): a slot is cleared during the
+// update phase of the step before its next use.
+struct PassCtl {
+  unsigned int bar;              // grid-barrier arrivals
+  int abort;                     // set by a block whose bounded wait expired
+  unsigned long long S3[2];
+  double loss_data[2];
+  double loss_phi[2];
+};
+
+// Steps [s0, s1) of a pass of the persistent kernel.
+struct PassArgs {
+  const BatchDesc *descs;        // all batches of the pass (device)
+  int s0, s1;
+  int tile_cap;                  // most documents per tile
+  double *losses;                // per-step loss (device, indexed by step) or null
+  PassCtl *ctl;
+  int record;                    // 1: advance the context's step state (0 for tuning runs)
+};
+
+// Element (topic n, feature k) of the B operand Phi^T in the shared-memory
+// layout of the tensor-core kernels: (Dp/64) sub-tiles of [Kp rows x 64]
+// BF16, 16-byte chunk c of row n stored at chunk c ^ (n mod 8).
+__host__ __device__ inline long long phi_img_index(int n, int k, int Kp) {
+  const int sub = k >> 6, kc = k & 63;
+  return (long long)sub * Kp * 64 + n * 64 + ((((kc >> 3) ^ (n & 7)) & 7) << 3) + (kc & 7);
+}
+
 // Kernel-side view of the workspace for one CP step.
 struct StepArgs {
   int V, D, K, Dp, Kp, Bmax;
@@ -134,6 +163,17 @@ struct tlda_ctx {
   cudaStream_t pstream = nullptr;
   cudaEvent_t ev_pass0 = nullptr, ev_pass1 = nullptr;
   cudaGraphExec_t step_exec = nullptr;
+  // persistent pass kernel (BF16 fused form)
+  int pass_grid = 0;                   // its blocks (0: not available)
+  int tile_cap = 32;                   // most documents per tile (tuned on the first pass)
+  bool tuned = false;
+  tlda::PassCtl *ctl = nullptr;
+  tlda::DevState *st_tune = nullptr;   // device state of tuning runs (kept apart from st)
+  double *dlosses = nullptr;           // per-step losses of a pass (device)
+  int dlosses_cap = 0;
+  float *phi_scratch = nullptr;        // D x K: tuning runs on a copy of Phi
+  cudaStream_t cstream = nullptr;      // host-input copies of the pass
+  cudaEvent_t ev_seg[4] = {nullptr, nullptr, nullptr, nullptr};
   float g_lr = 0.f;
   const float *g_phi = nullptr;
   int g_loss = -1;
@@ -149,7 +189,7 @@ struct tlda_ctx {
 namespace tlda {
 // Kernels of one CP step, in launch order (ids used by the event profiler).
 enum KernelId {
-  kWhiten = 0, kQY, kRZ, kZH, kG, kReduceUpdate, kPhiGram, kPhiTerms, kFused, kNumKernels
+  kWhiten = 0, kQY, kRZ, kZH, kG, kReduceUpdate, kPhiGram, kPhiTerms, kFused, kPass, kNumKernels
 };
 extern const char *const kKernelNames[kNumKernels];
 
@@ -170,6 +210,8 @@ void launch_phi_img(const StepArgs &a, cudaStream_t s);
 // k_fused.cu (BF16 fused tensor-core data term)
 bool fused_supported(int Dp, int Kp);
 void launch_fused(const StepArgs &a, cudaStream_t s, int grid);
+int pass_grid();                                  // co-resident blocks of the pass kernel (0: none)
+cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, int grid);
 // k_tc.cu (BF16 tensor-core form)
 bool tc_supported(int Dp, int Kp);
 void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const __nv_bfloat16 *BT16, int V,

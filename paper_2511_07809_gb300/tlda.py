@@ -36,7 +36,7 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_set_whitening", "tlda_whiten_batch", "tlda_cp_step",
                 "tlda_cp_data_term", "tlda_cp_pass", "tlda_unwhiten_topics",
                 "tlda_profile", "tlda_profile_read", "tlda_save_state", "tlda_load_state",
-                "tlda_cp_step_noalloc")
+                "tlda_cp_step_noalloc", "tlda_autotune")
 
 
 class Params(ctypes.Structure):
@@ -82,6 +82,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "tlda_cp_step": (i32, [vp, P(CSR), vp, f32, vp, vp]),
         "tlda_cp_data_term": (i32, [vp, P(CSR), vp, vp, vp]),
         "tlda_cp_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, u32, vp]),
+        "tlda_autotune": (i32, [vp, P(CSR), vp, i32, vp, i32, P(i32)]),
         "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
         "tlda_cp_step_noalloc": (i32, [P(CSR), vp, vp, i32, i32, f64, f32, vp, f32, vp, vp, vp]),
         "tlda_profile": (i32, [vp, u32]),
@@ -254,12 +255,28 @@ class TLDA:
                                           out.ctypes.data if losses else None))
         return out[:nb] if losses else None
 
+    def autotune(self, corpus: DeviceCSR | None = None, batch_offsets=None,
+                 Phi: torch.Tensor | None = None, fixed: int = 0) -> int:
+        """Tile size of the persistent pass kernel: set it (fixed > 0) or time
+        the candidates on the first batches of `corpus` (Phi unchanged).
+        Returns the size in use."""
+        out = ctypes.c_int32()
+        if fixed:
+            self._check(self.lib.tlda_autotune(self.h, None, None, 0, None, int(fixed),
+                                               ctypes.byref(out)))
+            return out.value
+        off = np.ascontiguousarray(np.asarray(batch_offsets, dtype=np.int64))
+        s = corpus.struct()
+        self._check(self.lib.tlda_autotune(self.h, ctypes.byref(s), off.ctypes.data, len(off) - 1,
+                                           Phi.data_ptr(), 0, ctypes.byref(out)))
+        return out.value
+
     def sync(self):
         self._check(self.lib.tlda_sync(self.h))
 
     # ------------------------------------------------------------ profiling
     KERNELS = ("scan_whiten", "qy", "rz", "zh", "g_reduce", "reduce_update", "phi_gram",
-               "phi_terms", "fused")
+               "phi_terms", "fused", "pass")
 
     def profile(self, kernels=()):
         """Bracket the named kernels with CUDA events from now on (empty: off)."""
@@ -291,3 +308,39 @@ class TLDA:
 
     def load_state(self, path: str):
         self._check(self.lib.tlda_load_state(self.h, str(path).encode()))
+
+
+# ---------------------------------------------------------------------------- autograd
+class TLDALoss(torch.autograd.Function):
+    """The CP objective of one minibatch as a differentiable function of Phi.
+
+    forward(Phi, model, batch) returns, as a 0-dim float64 tensor on Phi's
+    device, the loss of tlda_cp_step at Phi (section "Stochastic Tensor
+    Gradient Descent": (1+theta)/2 sum_ij (phi_i.phi_j)^3 minus
+    sum_i T_B(phi_i, phi_i, phi_i)); backward returns grad_output times the
+    gradient of eq. vec_deriv that the same call wrote.  Both come from one
+    tlda_cp_step with lr = 0, which leaves Phi unchanged; the call
+    synchronises because the loss is read on the host.
+    """
+
+    @staticmethod
+    def forward(ctx, Phi: torch.Tensor, model: "TLDA", batch: DeviceCSR):
+        P = Phi.detach()
+        if P.dtype != torch.float32 or not P.is_cuda or not P.is_contiguous():
+            raise TypeError("TLDALoss: Phi must be a contiguous float32 CUDA tensor")
+        if tuple(P.shape) != (model.D, model.K):
+            raise ValueError(f"TLDALoss: Phi must be {model.D} x {model.K}")
+        G = torch.empty_like(P)
+        loss = model.cp_step(batch, P, 0.0, grad=G, want_loss=True)
+        ctx.save_for_backward(G)
+        return torch.tensor(loss, dtype=torch.float64, device=P.device)
+
+    @staticmethod
+    def backward(ctx, grad_output):
+        (G,) = ctx.saved_tensors
+        return grad_output.to(G.dtype) * G, None, None
+
+
+def tlda_loss(Phi: torch.Tensor, model: "TLDA", batch: DeviceCSR) -> torch.Tensor:
+    """TLDALoss.apply(Phi, model, batch)."""
+    return TLDALoss.apply(Phi, model, batch)

@@ -1,0 +1,147 @@
+"""The persistent pass kernel of tlda_cp_pass (BF16 form, D = K in (64, 128]):
+every step of a pass in one cooperative launch, against the FP64 oracle's
+sequential CP steps (section "Fully Online Implementation", eq. vec_deriv),
+for several tile sizes; host-input staging in several segments against the
+device-input pass; the tile tuner; a corrupt batch in the middle of a pass."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import tlda_synth as ts
+from oracle import tlda_oracle as O
+
+from . import _cases as C
+
+pytestmark = pytest.mark.gpu
+TOL16 = 2e-2
+NAME = "stream_v20k_k100"
+
+
+def _ctx(lib, max_batch=8192):
+    sp = ts.WORKLOADS[NAME]
+    W, m1 = C.population_whitening(NAME)
+    t = lib.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="bf16", max_batch=max_batch)
+    t.set_whitening(torch.tensor(W, dtype=torch.float32), torch.tensor(m1, dtype=torch.float32))
+    return t, W, m1
+
+
+def _phi0(sp):
+    return ts.initial_factors(sp.seed, sp.K, sp.K).astype(np.float64)
+
+
+def _oracle_pass(c, offs, sp, W, m1, Phi0, lr):
+    P, losses = Phi0.copy(), []
+    for b in range(len(offs) - 1):
+        r = c.rows(offs[b], offs[b + 1])
+        P, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, lr, float(sp.alpha0), 0.0)
+        losses.append(g["loss"])
+    return P, np.array(losses)
+
+
+@pytest.mark.parametrize("cap", [1, 8, 32])
+def test_pass_tile_sizes_match_oracle(lib, cap):
+    sp = ts.WORKLOADS[NAME]
+    t, W, m1 = _ctx(lib)
+    assert t.autotune(fixed=cap) == cap
+    c = C.corpus(NAME, 14000)
+    # ragged sizes: below and above one tile per SM, one document, an exact 8192
+    offs = [0, 700, 701, 700 + 4099, 700 + 4099 + 8192, 14000]
+    Phi0 = _phi0(sp)
+    Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+    lr = 0.002
+    losses = t.cp_pass(lib.DeviceCSR.from_corpus(c), offs, Phi, lr, losses=True)
+    P, lo = _oracle_pass(c, offs, sp, W, m1, Phi0, lr)
+    assert np.all(np.abs(losses - lo) <= TOL16 * np.abs(lo))
+    assert C.rel(Phi.cpu().numpy(), P) < TOL16
+    t.close()
+
+
+def test_pass_host_segments_equal_device_pass(lib):
+    """A host-input pass large enough to be staged in several segments gives
+    the device-input pass's Phi bit for bit (same kernel, same tiles)."""
+    sp = ts.WORKLOADS[NAME]
+    t, W, m1 = _ctx(lib)
+    t.autotune(fixed=32)
+    n = 1_500_000  # ~18M nonzeros: ~37M staged words, more than four 8M-word segments
+    c = C.corpus(NAME, n)
+    sizes = ts.batch_sizes(sp.with_docs(n))
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    offs = offs[offs <= n]
+    if offs[-1] != n:
+        offs = np.append(offs, n)
+    Phi0 = torch.tensor(_phi0(sp), dtype=torch.float32, device="cuda")
+    Pd, Ph = Phi0.clone(), Phi0.clone()
+    ld = t.cp_pass(lib.DeviceCSR.from_corpus(c), offs, Pd, 1e-3, losses=True)
+    lh = t.cp_pass(lib.DeviceCSR.from_corpus(c, device="cpu", pin=True), offs, Ph, 1e-3,
+                   host_input=True, losses=True)
+    assert torch.equal(Pd, Ph)
+    assert np.allclose(ld, lh, rtol=1e-9, atol=0)
+    assert np.isfinite(Pd.cpu().numpy()).all()
+    t.close()
+
+
+def test_pass_and_graph_path_agree(lib, monkeypatch):
+    """The persistent kernel and the per-step graph path of the same form."""
+    sp = ts.WORKLOADS[NAME]
+    c = C.corpus(NAME, 20000)
+    offs = [0, 512, 4000, 12192, 20000]
+    Phi0 = _phi0(sp)
+    out = []
+    for no_pass in (False, True):
+        if no_pass:
+            monkeypatch.setenv("TLDA_NO_PASS", "1")
+        t, W, m1 = _ctx(lib)
+        Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+        t.cp_pass(lib.DeviceCSR.from_corpus(c), offs, Phi, 0.002)
+        out.append(Phi.cpu().numpy())
+        t.close()
+    P, _ = _oracle_pass(c, offs, sp, W, m1, Phi0, 0.002)
+    assert C.rel(out[0], P) < TOL16 and C.rel(out[1], P) < TOL16
+    assert C.rel(out[0], out[1]) < TOL16
+
+
+def test_autotune_leaves_phi_and_state(lib, tmp_path):
+    sp = ts.WORKLOADS[NAME]
+    t, W, m1 = _ctx(lib)
+    c = C.corpus(NAME, 30000)
+    offs = np.arange(0, 30001, 3000)
+    dev = lib.DeviceCSR.from_corpus(c)
+    Phi = torch.tensor(_phi0(sp), dtype=torch.float32, device="cuda")
+    before = Phi.clone()
+    t.save_state(tmp_path / "a.tlda")
+    cap = t.autotune(dev, offs, Phi)
+    assert cap in (8, 16, 24, 32)
+    assert torch.equal(Phi, before)
+    t.save_state(tmp_path / "b.tlda")
+    assert (tmp_path / "a.tlda").read_bytes() == (tmp_path / "b.tlda").read_bytes()
+    # the pass then runs with that size: equal to a context fixed to it
+    t.cp_pass(dev, offs, Phi, 0.002)
+    t2, _, _ = _ctx(lib)
+    t2.autotune(fixed=cap)
+    P2 = before.clone()
+    t2.cp_pass(dev, offs, P2, 0.002)
+    assert torch.equal(Phi, P2)
+    t.close()
+    t2.close()
+
+
+def test_corrupt_batch_stops_updates_from_that_step(lib):
+    sp = ts.WORKLOADS[NAME]
+    t, W, m1 = _ctx(lib)
+    c = C.corpus(NAME, 12000)
+    offs = [0, 3000, 6000, 9000, 12000]
+    counts = c.counts.copy()
+    counts[c.indptr[7000] + 1] = 0  # inside batch 2
+    dev = lib.DeviceCSR.from_arrays(c.indptr, c.indices, counts, sp.V)
+    Phi0 = _phi0(sp)
+    Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+    with pytest.raises(lib.TLDAError) as e:
+        t.cp_pass(dev, offs, Phi, 0.002)
+    assert e.value.status == lib.ERR_INVALID
+    P, _ = _oracle_pass(c, offs[:3], sp, W, m1, Phi0, 0.002)
+    assert C.rel(Phi.cpu().numpy(), P) < TOL16
+    # the error was taken: the next pass on valid data runs
+    t.cp_pass(lib.DeviceCSR.from_corpus(c), offs[:2], Phi, 0.002)
+    t.close()
