@@ -182,21 +182,64 @@ struct Fused {
     ++pph;
   }
 
-  // Partial G (rows = features) -> dst (128 x Kp FP32); zeros if no tile added to it.
-  __device__ void write_g(float *dst, int Kp, bool g_init) {
+  // Partial G (rows = features) -> dst (rows < D, columns < K rounded up to
+  // 16, row pitch Kp, FP32); zeros if no tile added to it.
+  __device__ void write_g(float *dst, int D, int K, int Kp, bool g_init) {
     const int row = quad * 32 + lane;
     tc_fence_after();
 #pragma unroll 1
     for (int p = 0; p < 4; ++p) {
       const int c0 = half * 64 + p * 16;
+      if (c0 >= K) break;  // warp-uniform
       float v[16];
       if (g_init) tmem_ld16(colG + (static_cast<uint32_t>(quad * 32) << 16) + c0, v);
       else
         for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      if (row < D) {
 #pragma unroll
-      for (int q = 0; q < 16; q += 4)
-        *reinterpret_cast<float4 *>(dst + (long long)row * Kp + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        for (int q = 0; q < 16; q += 4)
+          *reinterpret_cast<float4 *>(dst + (long long)row * Kp + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      }
     }
+    tc_fence_before();
+  }
+
+  // Partial G in the slice-blocked layout of the pass kernel: entry e = i K + n
+  // of this block's partial goes to dst[(e / per) G + blk][e % per], so the
+  // partials of one slice of entries are contiguous across blocks.
+  __device__ void write_g_sliced(float *dst, int D, int K, int G, int blk, int per, bool g_init) {
+    const int row = quad * 32 + lane;
+    tc_fence_after();
+#pragma unroll 1
+    for (int p = 0; p < 4; ++p) {
+      const int c0 = half * 64 + p * 16;
+      if (c0 >= K) break;  // warp-uniform
+      float v[16];
+      if (g_init) tmem_ld16(colG + (static_cast<uint32_t>(quad * 32) << 16) + c0, v);
+      else
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      if (row < D) {
+        if ((K & 3) == 0) {  // 4 entries never straddle a slice (per is a multiple of 4)
+#pragma unroll
+          for (int q = 0; q < 16; q += 4) {
+            if (c0 + q < K) {
+              const int e = row * K + c0 + q, sl = e / per;
+              *reinterpret_cast<float4 *>(dst + ((long long)sl * G + blk) * per + (e - sl * per)) =
+                  make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            if (c0 + q < K) {
+              const int e = row * K + c0 + q, sl = e / per;
+              dst[((long long)sl * G + blk) * per + (e - sl * per)] = v[q];
+            }
+          }
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");  // the slices are read by bulk copies
     tc_fence_before();
   }
 
@@ -523,7 +566,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(StepArgs a) {
   if (f.failed()) {
     if (f.tid == 0) atomicOr(&a.st->err, kErrTimeout);
   } else {
-    f.write_g(a.Gpart + (long long)blockIdx.x * a.Dp * a.Kp, a.Kp, g_init);
+    f.write_g(a.Gpart + (long long)blockIdx.x * a.Dp * a.Kp, a.D, a.K, a.Kp, g_init);
   }
   f.finish();
 }
@@ -574,18 +617,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
   DevState *st = a.st;
   const int G = gridDim.x, blk = blockIdx.x, tid = f.tid;
   const int D = a.D, K = a.K, Kp = a.Kp, DK = a.D * a.K;
-  const long long DpKp = (long long)a.Dp * a.Kp;
-  // phase B: this block's entries of Phi (row-major D x K)
-  const int per = (DK + G - 1) / G;
+  // phase B: this block's entries of Phi (row-major D x K), a multiple of 4
+  // per block (16-byte slices for the bulk copies)
+  const int per = ((DK + G - 1) / G + 3) & ~3;
   const int e0 = min(DK, blk * per), e1 = min(DK, e0 + per);
   // phase A: the Phi-only column of this block (columns go to the last K blocks,
   // tiles to the first ones, so small batches keep the two apart)
   const int col = blk - (G - K);
-  float *gp = a.Gpart + (long long)blk * DpKp;
   // phase A: Phi (D x K FP32, rows padded to K + 1 floats against bank
   // conflicts) in the U-buffer and Q region, free until the tiles start
   float *sPh = reinterpret_cast<float *>(f.sm + kOffU0);
   const int ldp = K + 1;
+  __shared__ float s_m1[128];
+  if (tid < 128) s_m1[tid] = tid < D ? a.m1[tid] : 0.f;
+  __syncthreads();
   unsigned nbar = 0;
   bool alive = true;
   double last_loss = 0.0;
@@ -601,12 +646,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const bool has = blk < ntiles;
 
     // ---------------- phase A: the Phi^T image and Phi into shared memory
-    // (L2 loads: both were written by other blocks during this launch)
+    // (L2 loads: both were written by other blocks during this launch; every
+    // load is issued before the first store)
     {
       constexpr int kImgPer = 32768 / 16 / kFusedThreads;  // 8 x 16 B
-      constexpr int kPhiPer = 128 * 128 / kFusedThreads;   // 64
+      constexpr int kRows = 128 / (kFusedThreads / 32);     // rows of Phi per warp (16)
       uint4 img[kImgPer];
-      float ph[kPhiPer];
+      float ph[kRows][4];
       if (has) {
 #pragma unroll
         for (int u = 0; u < kImgPer; ++u)
@@ -614,10 +660,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       }
       if (col >= 0) {
 #pragma unroll
-        for (int u = 0; u < kPhiPer; ++u) {
-          const int e = tid + u * kFusedThreads;
-          ph[u] = e < DK ? __ldcg(a.Phi + e) : 0.f;
-        }
+        for (int i = 0; i < kRows; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int r = f.warp + 8 * i, n = f.lane + 32 * j;
+            ph[i][j] = (r < D && n < K) ? __ldcg(a.Phi + r * K + n) : 0.f;
+          }
       }
       if (has) {
 #pragma unroll
@@ -625,10 +673,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       }
       if (col >= 0) {
 #pragma unroll
-        for (int u = 0; u < kPhiPer; ++u) {
-          const int e = tid + u * kFusedThreads;
-          if (e < DK) sPh[(e / K) * ldp + e % K] = ph[u];
-        }
+        for (int i = 0; i < kRows; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int r = f.warp + 8 * i, n = f.lane + 32 * j;
+            if (r < D && n < K) sPh[r * ldp + n] = ph[i][j];
+          }
       }
       fence_proxy_async();
       __syncthreads();
@@ -643,16 +693,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       float *sg = f.sZ;  // [0, 256): two halves of the Gram column; [256, 384): the column
       {
         const int n = tid & 127, rh = tid >> 7;
-        float g = 0.f;
+        float g4[4] = {0.f, 0.f, 0.f, 0.f};
         if (n < K) {
           const int r0 = rh ? (D + 1) / 2 : 0, r1 = rh ? D : (D + 1) / 2;
-#pragma unroll 4
-          for (int r = r0; r < r1; ++r) g = fmaf(sPh[r * ldp + col], sPh[r * ldp + n], g);
+          int r = r0;
+          for (; r + 4 <= r1; r += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) g4[u] = fmaf(sPh[(r + u) * ldp + col], sPh[(r + u) * ldp + n], g4[u]);
+          }
+          for (; r < r1; ++r) g4[0] = fmaf(sPh[r * ldp + col], sPh[r * ldp + n], g4[0]);
         }
-        sg[rh * 128 + n] = g;
+        sg[rh * 128 + n] = (g4[0] + g4[1]) + (g4[2] + g4[3]);
         if (f.warp == 0) {
           float am = 0.f;
-          for (int r = f.lane; r < D; r += 32) am = fmaf(a.m1[r], sPh[r * ldp + col], am);
+          for (int r = f.lane; r < D; r += 32) am = fmaf(s_m1[r], sPh[r * ldp + col], am);
           for (int o = 16; o > 0; o >>= 1) am += __shfl_xor_sync(0xffffffffu, am, o);
           if (f.lane == 0) s_am = am;
         }
@@ -663,20 +717,27 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       const float am = s_am, n2 = sg[256 + col];
       {
         const int r = tid & 127, bh = tid >> 7;
-        float pv = 0.f;
+        float p4[4] = {0.f, 0.f, 0.f, 0.f};
         if (r < D) {
           const int b0 = bh ? (K + 1) / 2 : 0, b1 = bh ? K : (K + 1) / 2;
-#pragma unroll 4
-          for (int bb = b0; bb < b1; ++bb) {
+          int bb = b0;
+          for (; bb + 4 <= b1; bb += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float g = sg[256 + bb + u];
+              p4[u] = fmaf(sPh[r * ldp + bb + u], g * g, p4[u]);
+            }
+          }
+          for (; bb < b1; ++bb) {
             const float g = sg[256 + bb];
-            pv = fmaf(sPh[r * ldp + bb], g * g, pv);
+            p4[0] = fmaf(sPh[r * ldp + bb], g * g, p4[0]);
           }
         }
-        sg[bh * 128 + r] = pv;  // the first two halves are free again
+        sg[bh * 128 + r] = (p4[0] + p4[1]) + (p4[2] + p4[3]);  // the first two halves are free again
         __syncthreads();
         if (tid < D) {
           const float P = sg[tid] + sg[128 + tid];
-          const float mr = a.m1[tid];
+          const float mr = s_m1[tid];
           const float g3 = 2.f * sPh[tid * ldp + col] * am + mr * n2 - 2.f * mr * am * am;
           a.E[tid * Kp + col] = 3.f * (1.f + a.theta) * P - 3.f * g3;
         }
@@ -699,7 +760,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
         const float t = block_sum(lacc, s_red);
         if (tid == 0 && t != 0.f) atomicAdd(&ctl->loss_data[slot], (double)t);
       }
-      if (!f.failed()) f.write_g(gp, Kp, g_init);
+      if (!f.failed()) f.write_g_sliced(a.Gpart, D, K, G, blk, per, g_init);
       __syncthreads();
     }
     if (f.failed() && tid == 0) atomicExch(&ctl->abort, 1);
@@ -710,38 +771,38 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const unsigned long long S3 = *reinterpret_cast<volatile unsigned long long *>(&ctl->S3[slot]);
     const int err = *reinterpret_cast<volatile int *>(&st->err);
     const double scale = S3 ? a.c3 / (double)S3 : 0.0;
-    for (int base = e0; base < e1; base += 128) {
-      const int cnt = min(128, e1 - base);
-      // warp w sums partials w, w + 8, ... (all of its loads in flight at once);
-      // lane l takes entries l, l + 32, l + 64, l + 96 of the group
-      constexpr int kPW = 20;  // partials per warp in the unrolled part (G <= 160)
-      float acc[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int q = f.lane + 32 * j, e = base + q;
-        const bool ok = q < cnt;
-        const long long off = ok ? (long long)(e / K) * Kp + e % K : 0;
-        float v[kPW];
-#pragma unroll
-        for (int u = 0; u < kPW; ++u) {
-          const int c = f.warp + 8 * u;
-          v[u] = (ok && c < nwork) ? __ldcg(a.Gpart + c * DpKp + off) : 0.f;
-        }
-        float t = 0.f;
-#pragma unroll
-        for (int u = 0; u < kPW; ++u) t += v[u];
-        for (int c = f.warp + 8 * kPW; ok && c < nwork; c += 8) t += __ldcg(a.Gpart + c * DpKp + off);
-        acc[j] = t;
+    if (e1 > e0 && nwork > 0) {  // this slice of every partial: one bulk copy
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const uint32_t bytes = (uint32_t)(nwork * per * 4);
+        mbar_arrive_expect_tx(&f.bars[0], bytes);
+        bulk_load(f.sm + kOffU0, a.Gpart + (long long)blk * G * per, bytes, &f.bars[0]);
       }
-      float *red = f.sY;  // 8 x 128
+      f.phi_wait();  // bounded wait on barrier 0
+    }
+    if (__syncthreads_or(f.failed())) {
+      if (tid == 0) atomicExch(&ctl->abort, 1);
+      break;
+    }
+    if (e1 > e0) {
+      const int cnt = e1 - e0;  // <= per <= 128
+      const float *sG = reinterpret_cast<const float *>(f.sm + kOffU0);
+      const int q = tid & 127, part = tid >> 7;
+      float g4[4] = {0.f, 0.f, 0.f, 0.f};
+      if (q < cnt) {
+        int c = part;
+        for (; c + 6 < nwork; c += 8) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) red[f.warp * 128 + f.lane + 32 * j] = acc[j];
+          for (int u = 0; u < 4; ++u) g4[u] += sG[(c + 2 * u) * per + q];
+        }
+        for (; c < nwork; c += 2) g4[0] += sG[c * per + q];
+      }
+      float *red = f.sY;
+      red[part * 128 + q] = (g4[0] + g4[1]) + (g4[2] + g4[3]);
       __syncthreads();
       if (tid < cnt) {
-        const int e = base + tid, i = e / K, n = e % K;
-        float g = 0.f;
-#pragma unroll
-        for (int w = 0; w < kFusedThreads / 32; ++w) g += red[w * 128 + tid];
+        const int e = e0 + tid, i = e / K, n = e % K;
+        const float g = red[tid] + red[128 + tid];
         const float E = __ldcg(a.E + i * Kp + n);
         const float grad = S3 ? E - (float)(3.0 * scale * (double)g) : 0.f;
         float phi = __ldcg(a.Phi + e);

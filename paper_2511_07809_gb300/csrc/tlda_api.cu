@@ -486,7 +486,10 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
   CA(dalloc(&ctx->H32, V * Kp, true));
   CA(dalloc(&ctx->cnt, V, true));
   CA(dalloc(&ctx->widx, V, true));
-  CA(dalloc(&ctx->Gpart, (size_t)std::max({ctx->nsplit, ctx->nsplit_tc, ctx->num_sms}) * Dp * Kp, true));
+  // partial sums; the pass kernel's slice-blocked layout needs up to
+  // blocks x (D K + 4 blocks) floats
+  CA(dalloc(&ctx->Gpart, (size_t)std::max({ctx->nsplit, ctx->nsplit_tc, ctx->num_sms}) * Dp * Kp +
+                             4 * (size_t)ctx->num_sms * ctx->num_sms, true));
   CA(dalloc(&ctx->Gram, Kp * Kp, true));
   CA(dalloc(&ctx->avec, Kp, true));
   CA(dalloc(&ctx->E, Dp * Kp, true));
