@@ -423,7 +423,14 @@ def main():
                 tr = json.load(f)
             key = f"{primary}:{dominant}"
             if key in tr and tr[key].get("src_sha") == src_sha(os.path.join(ROOT, tr[key]["src"])):
-                roof["traffic"] = tr[key]["bytes_per_launch"]
+                if "bytes_per_doc" in tr[key]:
+                    # DRAM bytes fitted on smaller captured launches (a fixed
+                    # part per launch plus a part per document), evaluated at
+                    # the documents one timed launch processes
+                    roof["traffic"] = (tr[key].get("bytes_fixed_per_launch", 0.0)
+                                       + tr[key]["bytes_per_doc"] * n_timed_docs / max(launches, 1))
+                else:
+                    roof["traffic"] = tr[key]["bytes_per_launch"]
 
     # 3) end to end through the public API: host CSR -> device inside the call, loss read back
     e2e = None
