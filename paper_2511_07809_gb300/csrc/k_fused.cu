@@ -22,10 +22,11 @@
 // k_fused runs the data term of one step (the reduction and the update are
 // separate kernels).  k_pass runs steps [s0, s1) of a pass in one cooperative
 // launch, each step in two phases separated by grid barriers:
-//   A  the last K blocks: one column each of the Phi-only terms
-//      E = 3(1+theta) P - 3 G3 (P = Phi (Phi^T Phi * Phi^T Phi)) and its loss
-//      part; the first blocks: the data term of the step's batch, in tiles
-//      of ceil(n_docs / blocks) documents (at most tile_cap);
+//   A  the first blocks: the data term of the step's batch, in tiles of
+//      ceil(n_docs / blocks) documents (at most tile_cap); then every block
+//      takes columns of the Phi-only terms E = 3(1+theta) P - 3 G3
+//      (P = Phi (Phi^T Phi * Phi^T Phi)) and their loss parts from a counter
+//      until all K are done;
 //   B  block b: its slice of the entries of Phi: the partials summed,
 //      grad = E - 3 c3/S3 (G1 + G2), Phi -= lr grad, and the BF16 Phi^T
 //      image the next step's MMAs read.
@@ -610,7 +611,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
   extern __shared__ unsigned char smem_raw[];
   __shared__ float s_red[kFusedThreads / 32];
   __shared__ float s_am;
-  __shared__ int s_ok;
+  __shared__ int s_ok, s_col;
   Fused f;
   f.init(smem_raw);
   PassCtl *ctl = p.ctl;
@@ -621,9 +622,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
   // per block (16-byte slices for the bulk copies)
   const int per = ((DK + G - 1) / G + 3) & ~3;
   const int e0 = min(DK, blk * per), e1 = min(DK, e0 + per);
-  // phase A: the Phi-only column of this block (columns go to the last K blocks,
-  // tiles to the first ones, so small batches keep the two apart)
-  const int col = blk - (G - K);
   // phase A: Phi (D x K FP32, rows padded to K + 1 floats against bank
   // conflicts) in the U-buffer and Q region, free until the tiles start
   float *sPh = reinterpret_cast<float *>(f.sm + kOffU0);
@@ -645,20 +643,43 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const int nwork = min(G, ntiles);
     const bool has = blk < ntiles;
 
-    // ---------------- phase A: the Phi^T image and Phi into shared memory
-    // (L2 loads: both were written by other blocks during this launch; every
-    // load is issued before the first store)
-    {
+    // ---------------- phase A: the Phi^T image into shared memory (L2 loads:
+    // it was written by other blocks during this launch)
+    if (has) {
       constexpr int kImgPer = 32768 / 16 / kFusedThreads;  // 8 x 16 B
-      constexpr int kRows = 128 / (kFusedThreads / 32);     // rows of Phi per warp (16)
       uint4 img[kImgPer];
-      float ph[kRows][4];
-      if (has) {
 #pragma unroll
-        for (int u = 0; u < kImgPer; ++u)
-          img[u] = __ldcg(reinterpret_cast<const uint4 *>(a.PhiImg) + tid + u * kFusedThreads);
+      for (int u = 0; u < kImgPer; ++u)
+        img[u] = __ldcg(reinterpret_cast<const uint4 *>(a.PhiImg) + tid + u * kFusedThreads);
+#pragma unroll
+      for (int u = 0; u < kImgPer; ++u) reinterpret_cast<uint4 *>(f.sPhi)[tid + u * kFusedThreads] = img[u];
+      fence_proxy_async();
+      __syncthreads();
+    }
+    // the data term of this block's tiles
+    if (has) {
+      float lacc = 0.f;
+      bool g_init = false;
+      f.tiles(a, b, blk, G, td, lacc, g_init, &ctl->S3[slot], &st->err);
+      if (a.want_loss) {
+        const float t = block_sum(lacc, s_red);
+        if (tid == 0 && t != 0.f) atomicAdd(&ctl->loss_data[slot], (double)t);
       }
-      if (col >= 0) {
+      if (!f.failed()) f.write_g_sliced(a.Gpart, D, K, G, blk, per, g_init);
+      __syncthreads();
+    }
+    // the Phi-only terms, one column at a time, handed out by a counter: the
+    // blocks that finish their tiles first (or have none) take them.  Phi is
+    // staged once per block (in the U slots, free after the tiles; rows
+    // padded to K + 1 floats against bank conflicts).
+    for (bool staged = false;;) {
+      if (tid == 0) s_col = (int)atomicAdd(&ctl->col_next[slot], 1u);
+      __syncthreads();
+      const int col = s_col;
+      if (col >= K) break;
+      if (!staged) {
+        constexpr int kRows = 128 / (kFusedThreads / 32);  // rows of Phi per warp (16)
+        float ph[kRows][4];
 #pragma unroll
         for (int i = 0; i < kRows; ++i)
 #pragma unroll
@@ -666,12 +687,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
             const int r = f.warp + 8 * i, n = f.lane + 32 * j;
             ph[i][j] = (r < D && n < K) ? __ldcg(a.Phi + r * K + n) : 0.f;
           }
-      }
-      if (has) {
-#pragma unroll
-        for (int u = 0; u < kImgPer; ++u) reinterpret_cast<uint4 *>(f.sPhi)[tid + u * kFusedThreads] = img[u];
-      }
-      if (col >= 0) {
 #pragma unroll
         for (int i = 0; i < kRows; ++i)
 #pragma unroll
@@ -679,17 +694,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
             const int r = f.warp + 8 * i, n = f.lane + 32 * j;
             if (r < D && n < K) sPh[r * ldp + n] = ph[i][j];
           }
+        __syncthreads();
+        staged = true;
       }
-      fence_proxy_async();
-      __syncthreads();
-    }
-    // column `col` of the Phi-only terms: G_{b,col} = phi_b . phi_col for all
-    // b (Phi^T Phi is symmetric), a = m1 . phi_col, then for every row r
-    //   P_r = sum_b Phi_rb G_{b,col}^2,
-    //   G3_r = 2 Phi_r,col a + m1_r |phi_col|^2 - 2 m1_r a^2,
-    //   E_r = 3(1+theta) P_r - 3 G3_r,
-    // and the column's loss part (1+theta)/2 sum_b G^3 - (3 a |phi|^2 - 2 a^3)
-    if (col >= 0) {
+      // column `col`: G_{b,col} = phi_b . phi_col for all b (Phi^T Phi is
+      // symmetric), a = m1 . phi_col, then for every row r
+      //   P_r = sum_b Phi_rb G_{b,col}^2,
+      //   G3_r = 2 Phi_r,col a + m1_r |phi_col|^2 - 2 m1_r a^2,
+      //   E_r = 3(1+theta) P_r - 3 G3_r,
+      // and the column's loss part (1+theta)/2 sum_b G^3 - (3 a |phi|^2 - 2 a^3)
       float *sg = f.sZ;  // [0, 256): two halves of the Gram column; [256, 384): the column
       {
         const int n = tid & 127, rh = tid >> 7;
@@ -749,18 +762,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
         const float t = block_sum(v, s_red);
         if (tid == 0) atomicAdd(&ctl->loss_phi[slot], (double)t);
       }
-      __syncthreads();
-    }
-    // the data term of this block's tiles
-    if (has) {
-      float lacc = 0.f;
-      bool g_init = false;
-      f.tiles(a, b, blk, G, td, lacc, g_init, &ctl->S3[slot], &st->err);
-      if (a.want_loss) {
-        const float t = block_sum(lacc, s_red);
-        if (tid == 0 && t != 0.f) atomicAdd(&ctl->loss_data[slot], (double)t);
-      }
-      if (!f.failed()) f.write_g_sliced(a.Gpart, D, K, G, blk, per, g_init);
       __syncthreads();
     }
     if (f.failed() && tid == 0) atomicExch(&ctl->abort, 1);
@@ -826,6 +827,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       ctl->S3[slot ^ 1] = 0;
       ctl->loss_data[slot ^ 1] = 0.0;
       ctl->loss_phi[slot ^ 1] = 0.0;
+      ctl->col_next[slot ^ 1] = 0;
     }
     if (s + 1 < p.s1) {
       if (!grid_sync(ctl, ++nbar * G, &s_ok)) alive = false;

@@ -59,6 +59,7 @@ struct PassCtl {
   unsigned long long S3[2];
   double loss_data[2];
   double loss_phi[2];
+  unsigned int col_next[2];      // next column of the Phi-only terms to hand out
 };
 
 // Steps [s0, s1) of a pass of the persistent kernel.
