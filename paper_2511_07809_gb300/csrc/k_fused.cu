@@ -247,9 +247,10 @@ struct Fused {
   // The data term of tiles tile0, tile0 + tstride, ... of batch b (td <= kT
   // documents each), added to the G columns.  S3 and validation bits go to
   // S3_dst and err_dst, the per-document loss parts to lacc.  Expects the Phi
-  // image in shared memory.  Returns false on an expired wait.
+  // image in shared memory, or (phi_pending) its bulk copy on barrier 0 in
+  // flight, waited for before the first MMA.  Returns false on an expired wait.
   __device__ bool tiles(const StepArgs &a, const BatchDesc &b, int tile0, int tstride, int td, float &lacc,
-                        bool &g_init, unsigned long long *S3_dst, int *err_dst) {
+                        bool &g_init, unsigned long long *S3_dst, int *err_dst, bool phi_pending = false) {
     const int nd = b.n_docs;
     const int ntiles = nd > 0 ? (nd + td - 1) / td : 0;
     const uint32_t idQ = idesc_bf16(128, 128);
@@ -381,6 +382,10 @@ struct Fused {
         else cp_async_wait_all();
         put_f(0, true);
         fence_proxy_async();
+        if (phi_pending) {  // the Phi^T image (bulk copy issued with the tile set-up)
+          phi_wait();
+          phi_pending = false;
+        }
         __syncthreads();
         issue_q(gb & 1);
         for (int c = 0; c < wch; ++c) {
@@ -539,6 +544,7 @@ struct Fused {
       if (__syncthreads_or(failed())) break;
     }
     cp_async_wait_all();
+    if (phi_pending) phi_wait();  // no tile reached an MMA: still consume the copy's phase
     __syncthreads();
     return !failed();
   }
@@ -643,24 +649,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const int nwork = min(G, ntiles);
     const bool has = blk < ntiles;
 
-    // ---------------- phase A: the Phi^T image into shared memory (L2 loads:
-    // it was written by other blocks during this launch)
+    // ---------------- phase A: the data term of this block's tiles.  The
+    // Phi^T image (written by every block in the previous phase B) comes by
+    // one bulk copy that runs while the first tile's CSR slice is read.
     if (has) {
-      constexpr int kImgPer = 32768 / 16 / kFusedThreads;  // 8 x 16 B
-      uint4 img[kImgPer];
-#pragma unroll
-      for (int u = 0; u < kImgPer; ++u)
-        img[u] = __ldcg(reinterpret_cast<const uint4 *>(a.PhiImg) + tid + u * kFusedThreads);
-#pragma unroll
-      for (int u = 0; u < kImgPer; ++u) reinterpret_cast<uint4 *>(f.sPhi)[tid + u * kFusedThreads] = img[u];
-      fence_proxy_async();
-      __syncthreads();
-    }
-    // the data term of this block's tiles
-    if (has) {
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        mbar_arrive_expect_tx(&f.bars[0], 32768);
+        bulk_load(f.sPhi, a.PhiImg, 32768, &f.bars[0]);
+      }
       float lacc = 0.f;
       bool g_init = false;
-      f.tiles(a, b, blk, G, td, lacc, g_init, &ctl->S3[slot], &st->err);
+      f.tiles(a, b, blk, G, td, lacc, g_init, &ctl->S3[slot], &st->err, true);
       if (a.want_loss) {
         const float t = block_sum(lacc, s_red);
         if (tid == 0 && t != 0.f) atomicAdd(&ctl->loss_data[slot], (double)t);
@@ -812,6 +812,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
           a.Phi[e] = phi;
         }
         a.PhiImg[phi_img_index(n, i, Kp)] = __float2bfloat16_rn(phi);
+        asm volatile("fence.proxy.async.global;" ::: "memory");  // read by bulk copies next step
       }
       __syncthreads();
     }
