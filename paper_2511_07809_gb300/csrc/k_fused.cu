@@ -616,7 +616,7 @@ __device__ bool grid_sync(PassCtl *ctl, unsigned target, int *s_ok) {
 __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ float s_red[kFusedThreads / 32];
-  __shared__ float s_am;
+  __shared__ float s_am4[4];
   __shared__ int s_ok, s_col;
   Fused f;
   f.init(smem_raw);
@@ -668,15 +668,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       if (!f.failed()) f.write_g_sliced(a.Gpart, D, K, G, blk, per, g_init);
       __syncthreads();
     }
-    // the Phi-only terms, one column at a time, handed out by a counter: the
-    // blocks that finish their tiles first (or have none) take them.  Phi is
-    // staged once per block (in the U slots, free after the tiles; rows
+    // the Phi-only terms, four columns at a time, handed out by a counter:
+    // the blocks that finish their tiles first (or have none) take them.  Phi
+    // is staged once per block (in the U slots, free after the tiles; rows
     // padded to K + 1 floats against bank conflicts).
     for (bool staged = false;;) {
-      if (tid == 0) s_col = (int)atomicAdd(&ctl->col_next[slot], 1u);
+      if (tid == 0) s_col = (int)atomicAdd(&ctl->col_next[slot], 4u);
       __syncthreads();
-      const int col = s_col;
-      if (col >= K) break;
+      const int n0 = s_col;
+      if (n0 >= K) break;
       if (!staged) {
         constexpr int kRows = 128 / (kFusedThreads / 32);  // rows of Phi per warp (16)
         float ph[kRows][4];
@@ -697,68 +697,95 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
         __syncthreads();
         staged = true;
       }
-      // column `col`: G_{b,col} = phi_b . phi_col for all b (Phi^T Phi is
-      // symmetric), a = m1 . phi_col, then for every row r
-      //   P_r = sum_b Phi_rb G_{b,col}^2,
-      //   G3_r = 2 Phi_r,col a + m1_r |phi_col|^2 - 2 m1_r a^2,
-      //   E_r = 3(1+theta) P_r - 3 G3_r,
-      // and the column's loss part (1+theta)/2 sum_b G^3 - (3 a |phi|^2 - 2 a^3)
-      float *sg = f.sZ;  // [0, 256): two halves of the Gram column; [256, 384): the column
-      {
-        const int n = tid & 127, rh = tid >> 7;
-        float g4[4] = {0.f, 0.f, 0.f, 0.f};
-        if (n < K) {
-          const int r0 = rh ? (D + 1) / 2 : 0, r1 = rh ? D : (D + 1) / 2;
-          int r = r0;
-          for (; r + 4 <= r1; r += 4) {
+      // columns n = n0 .. n0+3 (those < K): G_{b,n} = phi_b . phi_n for all b
+      // (Phi^T Phi is symmetric), a_n = m1 . phi_n, then for every row r
+      //   P_rn = sum_b Phi_rb G_{b,n}^2,
+      //   G3_rn = 2 Phi_rn a_n + m1_r |phi_n|^2 - 2 m1_r a_n^2,
+      //   E_rn = 3(1+theta) P_rn - 3 G3_rn,
+      // and the columns' loss part (1+theta)/2 sum_b G^3 - (3 a |phi|^2 - 2 a^3)
+      float4 *sg4 = reinterpret_cast<float4 *>(f.sZ);  // [0, 256): half sums; [256, 384): the columns
+      int nn[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) g4[u] = fmaf(sPh[(r + u) * ldp + col], sPh[(r + u) * ldp + n], g4[u]);
+      for (int k = 0; k < 4; ++k) nn[k] = min(n0 + k, K - 1);  // past K: repeat column K-1, not stored
+      {
+        const int b = tid & 127, rh = tid >> 7;
+        float g[4] = {0.f, 0.f, 0.f, 0.f};
+        if (b < K) {
+          const int r0 = rh ? (D + 1) / 2 : 0, r1 = rh ? D : (D + 1) / 2;
+#pragma unroll 2
+          for (int r = r0; r < r1; ++r) {
+            const float x = sPh[r * ldp + b];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) g[k] = fmaf(x, sPh[r * ldp + nn[k]], g[k]);
           }
-          for (; r < r1; ++r) g4[0] = fmaf(sPh[r * ldp + col], sPh[r * ldp + n], g4[0]);
         }
-        sg[rh * 128 + n] = (g4[0] + g4[1]) + (g4[2] + g4[3]);
-        if (f.warp == 0) {
+        sg4[rh * 128 + b] = make_float4(g[0], g[1], g[2], g[3]);
+        if (f.warp < 4) {  // warp k: a for column k
           float am = 0.f;
-          for (int r = f.lane; r < D; r += 32) am = fmaf(s_m1[r], sPh[r * ldp + col], am);
+          const int nw = min(n0 + f.warp, K - 1);
+          for (int r = f.lane; r < D; r += 32) am = fmaf(s_m1[r], sPh[r * ldp + nw], am);
           for (int o = 16; o > 0; o >>= 1) am += __shfl_xor_sync(0xffffffffu, am, o);
-          if (f.lane == 0) s_am = am;
+          if (f.lane == 0) s_am4[f.warp] = am;
         }
         __syncthreads();
-        if (tid < 128) sg[256 + tid] = tid < K ? sg[tid] + sg[128 + tid] : 0.f;
+        if (tid < 128) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (tid < K) {
+            const float4 x = sg4[tid], y = sg4[128 + tid];
+            v = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+          }
+          sg4[256 + tid] = v;
+        }
         __syncthreads();
       }
-      const float am = s_am, n2 = sg[256 + col];
       {
         const int r = tid & 127, bh = tid >> 7;
-        float p4[4] = {0.f, 0.f, 0.f, 0.f};
+        float pv[4] = {0.f, 0.f, 0.f, 0.f};
         if (r < D) {
           const int b0 = bh ? (K + 1) / 2 : 0, b1 = bh ? K : (K + 1) / 2;
-          int bb = b0;
-          for (; bb + 4 <= b1; bb += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float g = sg[256 + bb + u];
-              p4[u] = fmaf(sPh[r * ldp + bb + u], g * g, p4[u]);
-            }
-          }
-          for (; bb < b1; ++bb) {
-            const float g = sg[256 + bb];
-            p4[0] = fmaf(sPh[r * ldp + bb], g * g, p4[0]);
+#pragma unroll 2
+          for (int bb = b0; bb < b1; ++bb) {
+            const float x = sPh[r * ldp + bb];
+            const float4 gv = sg4[256 + bb];
+            pv[0] = fmaf(x, gv.x * gv.x, pv[0]);
+            pv[1] = fmaf(x, gv.y * gv.y, pv[1]);
+            pv[2] = fmaf(x, gv.z * gv.z, pv[2]);
+            pv[3] = fmaf(x, gv.w * gv.w, pv[3]);
           }
         }
-        sg[bh * 128 + r] = (p4[0] + p4[1]) + (p4[2] + p4[3]);  // the first two halves are free again
+        sg4[bh * 128 + r] = make_float4(pv[0], pv[1], pv[2], pv[3]);  // the half sums are free again
         __syncthreads();
         if (tid < D) {
-          const float P = sg[tid] + sg[128 + tid];
+          const float4 x = sg4[tid], y = sg4[128 + tid];
+          const float P[4] = {x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w};
           const float mr = s_m1[tid];
-          const float g3 = 2.f * sPh[tid * ldp + col] * am + mr * n2 - 2.f * mr * am * am;
-          a.E[tid * Kp + col] = 3.f * (1.f + a.theta) * P - 3.f * g3;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (n0 + k < K) {
+              const float am = s_am4[k];
+              const float4 gc = sg4[256 + nn[k]];
+              const float n2 = k == 0 ? gc.x : k == 1 ? gc.y : k == 2 ? gc.z : gc.w;
+              const float g3 = 2.f * sPh[tid * ldp + nn[k]] * am + mr * n2 - 2.f * mr * am * am;
+              a.E[tid * Kp + nn[k]] = 3.f * (1.f + a.theta) * P[k] - 3.f * g3;
+            }
+          }
         }
       }
       if (a.want_loss) {
-        const float gg = tid < K ? sg[256 + tid] : 0.f;
-        float v = tid < K ? 0.5f * (1.f + a.theta) * gg * gg * gg : 0.f;
-        if (tid == 0) v -= 3.f * am * n2 - 2.f * am * am * am;
+        float v = 0.f;
+        if (tid < K) {
+          const float4 gv = sg4[256 + tid];
+          const float gs[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (n0 + k < K) v += 0.5f * (1.f + a.theta) * gs[k] * gs[k] * gs[k];
+        }
+        if (tid < 4 && n0 + tid < K) {
+          const float am = s_am4[tid];
+          const float4 gc = sg4[256 + n0 + tid];
+          const float n2 = tid == 0 ? gc.x : tid == 1 ? gc.y : tid == 2 ? gc.z : gc.w;
+          v -= 3.f * am * n2 - 2.f * am * am * am;
+        }
         const float t = block_sum(v, s_red);
         if (tid == 0) atomicAdd(&ctl->loss_phi[slot], (double)t);
       }
@@ -772,6 +799,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const unsigned long long S3 = *reinterpret_cast<volatile unsigned long long *>(&ctl->S3[slot]);
     const int err = *reinterpret_cast<volatile int *>(&st->err);
     const double scale = S3 ? a.c3 / (double)S3 : 0.0;
+    float E_own = 0.f, phi_own = 0.f;  // this thread's entry: loads in flight during the copy
+    if (tid < e1 - e0) {
+      const int e = e0 + tid;
+      E_own = __ldcg(a.E + (e / K) * Kp + e % K);
+      phi_own = __ldcg(a.Phi + e);
+    }
     if (e1 > e0 && nwork > 0) {  // this slice of every partial: one bulk copy
       if (tid == 0) {
         asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -804,9 +837,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       if (tid < cnt) {
         const int e = e0 + tid, i = e / K, n = e % K;
         const float g = red[tid] + red[128 + tid];
-        const float E = __ldcg(a.E + i * Kp + n);
-        const float grad = S3 ? E - (float)(3.0 * scale * (double)g) : 0.f;
-        float phi = __ldcg(a.Phi + e);
+        const float grad = S3 ? E_own - (float)(3.0 * scale * (double)g) : 0.f;
+        float phi = phi_own;
         if (!err && S3) {
           phi -= a.lr * grad;
           a.Phi[e] = phi;
