@@ -139,6 +139,20 @@ def replica_throughput(ms: float, docs: float, world: int, device: str = "cuda")
     return docs_all / (ms_max / 1e3), ms_max, docs_all
 
 
+def recovery_l1(ctx, Phi, mu, steps):
+    """Per-topic l1 distance of the recovered topics to the generator's, after
+    Hungarian matching (a sanity figure: one SGD pass is far from converged)."""
+    try:
+        from scipy.optimize import linear_sum_assignment
+        mu_e, _ = ctx.unwhiten_topics(Phi)
+        Dm = np.abs(mu[:, :, None] - mu_e[None, :, :]).sum(axis=1)
+        r_, c_ = linear_sum_assignment(Dm)
+        l1 = Dm[r_, c_]
+        return {"l1_mean": float(l1.mean()), "l1_max": float(l1.max()), "after_steps": steps}
+    except Exception as e:  # noqa: BLE001
+        return {"error": str(e)[:80]}
+
+
 def batch_plan(ts, sp, n_steps):
     """Seeded minibatch sizes (uniform 512..8192) for n_steps, and the document
     count they cover within one pass of the corpus."""
@@ -459,20 +473,12 @@ def main():
             ms2, _ = timed(c2, Phi)
             ms2 = reduce_over_ranks(ms2, "max", world)
             compare = {"precision": other[0], "value": docs_all / (ms2 / 1e3),
-                       "ms_per_step": ms2 / args.steps}
+                       "ms_per_step": ms2 / args.steps,
+                       "recovery": recovery_l1(c2, Phi, mu, args.warmup + args.steps)}
             c2.close()
 
     # recovery of the pass (per-topic l1 after Hungarian matching), as a sanity figure
-    recovery = None
-    try:
-        from scipy.optimize import linear_sum_assignment
-        mu_e, _ = ctx.unwhiten_topics(Phi_final)
-        Dm = np.abs(mu[:, :, None] - mu_e[None, :, :]).sum(axis=1)
-        r_, c_ = linear_sum_assignment(Dm)
-        l1 = Dm[r_, c_]
-        recovery = {"l1_mean": float(l1.mean()), "l1_max": float(l1.max()), "after_steps": args.warmup + args.steps}
-    except Exception as e:  # noqa: BLE001
-        recovery = {"error": str(e)[:80]}
+    recovery = recovery_l1(ctx, Phi_final, mu, args.warmup + args.steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
