@@ -469,8 +469,9 @@ struct Fused {
       }
       __syncthreads();
       // ---------------- pass 2 in reverse chunk order: the last two chunks of
-      // pass 1 are still in their buffers; earlier ones are gathered again.
-      // The Q product of the next (lower) chunk runs during this chunk's B''.
+      // pass 1 are still in their buffers (rows in shared memory, Q in TMEM);
+      // earlier ones are gathered again.  The Q product of the next (lower)
+      // chunk runs during this chunk's B''.
       for (int w = nwin - 1; w >= 0 && !failed(); --w) {
         const int w0 = w * kWin, wch = min(kWin, nnz - w0 + kChunk - 1) / kChunk, gb = w0 / kChunk;
         if (nwin > 1) load_window(w0, false);
@@ -483,7 +484,8 @@ struct Fused {
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        issue_q((gb + wch - 1) & 1);
+        // a resident chunk's Q is also still in its TMEM buffer from pass 1
+        if (!resident(wch - 1)) issue_q((gb + wch - 1) & 1);
         for (int c = wch - 1; c >= 0; --c) {
           const int g = gb + c, buf = g & 1;
           if (c > 0) {  // chunk c-1's rows are in: start its Q product now
@@ -492,9 +494,10 @@ struct Fused {
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
-            issue_q(buf ^ 1);
+            if (!resident(c - 1)) issue_q(buf ^ 1);
           }
-          q_wait(buf);
+          if (!resident(c)) q_wait(buf);
+          else tc_fence_after();
           if (__syncthreads_or(failed())) break;
           {
             const int row = quad * 32 + lane, t = c * kChunk + row;
