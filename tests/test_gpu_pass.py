@@ -145,3 +145,34 @@ def test_corrupt_batch_stops_updates_from_that_step(lib):
     # the error was taken: the next pass on valid data runs
     t.cp_pass(lib.DeviceCSR.from_corpus(c), offs[:2], Phi, 0.002)
     t.close()
+
+
+def test_bench_sized_pass_sampled_steps(lib):
+    """The bench's configuration: the streaming workload's seeded minibatch
+    sequence (512..8192 documents), the persistent kernel with the tuned tile
+    size.  Steps sampled deep into a 400-step pass are checked against the
+    oracle's step from the GPU's own Phi before it: the update
+    Phi_{t+1} - Phi_t = -lr grad and the loss."""
+    sp = ts.WORKLOADS[NAME]
+    sizes = ts.batch_sizes(sp)[:400]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(offs[-1])
+    c = C.corpus(NAME, n)
+    t, W, m1 = _ctx(lib)
+    dev = lib.DeviceCSR.from_corpus(c)
+    lr = 5e-4  # with this whitening, SGD at 2e-3 leaves the basin after ~250 steps (the oracle too)
+    Phi = torch.tensor(_phi0(sp), dtype=torch.float32, device="cuda")
+    cap = t.autotune(dev, offs[:65], Phi)
+    assert cap in (8, 16, 24, 32)
+    prev = 0
+    for s_ in (137, 283, 399):
+        t.cp_pass(dev, offs[prev:s_ + 1], Phi, lr)  # steps prev .. s_-1
+        before = Phi.cpu().numpy().astype(np.float64)
+        loss = t.cp_pass(dev, offs[s_:s_ + 2], Phi, lr, losses=True)[0]  # step s_
+        r = c.rows(int(offs[s_]), int(offs[s_ + 1]))
+        ref, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, before, lr, float(sp.alpha0), 0.0)
+        step_gpu = Phi.cpu().numpy().astype(np.float64) - before
+        assert C.rel(step_gpu, ref - before) < TOL16, s_
+        assert abs(loss - g["loss"]) <= TOL16 * abs(g["loss"]), s_
+        prev = s_ + 1
+    t.close()
