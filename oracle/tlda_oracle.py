@@ -30,10 +30,20 @@ with itself):
   F  Phi unconstrained (no unit-norm projection); weights ride on ||phi_i||.
   G  lambda_i = ||phi_i||^3, alpha_i proportional to lambda_i^-2, sum 1.
   L  in the batch tensor, whitened M2 is replaced by I (its defining value).
+  P  the fully online mode's incremental PCA is a one-pass sketch Z = P Omega
+     of the pair counts (Omega: V x r Gaussian test matrix, an input), with
+     the whitening rebuilt from it by the single-pass eigendecomposition of
+     Halko, Martinsson and Tropp (2011, section 5.5), which also holds for
+     the indefinite M2 of a small sample.
+  Q  in that mode, batches go in blocks of `every`: a block's documents update
+     the statistics and the whitening first, then its CP steps run (every = 1
+     is the paper's per-batch order); on a change of whitening the factors
+     are carried into the new basis so that the topics they encode stay put.
 """
 from __future__ import annotations
 
 import numpy as np
+import scipy.linalg
 import scipy.sparse as sp
 from scipy.optimize import linear_sum_assignment
 
@@ -441,3 +451,97 @@ def population_factors(mu, h, W):
     """Stationary CP factors of the population tensor at theta = 0:
     phi_i = h_i^(1/3) W^T mu_i (so ||phi_i|| = h_i^-1/6, lambda_i = h_i^-1/2)."""
     return (W.T @ mu.T) * (h ** (1.0 / 3.0))[None, :]
+
+
+# ----------------------------------------------------------------------------- online mode
+
+
+def sketch_accumulate(indptr, indices, counts, V, Omega):
+    """A batch's part of the one-pass sketch Z = P Omega of the pair counts
+    P = sum_d (f_d f_d^T - diag f_d) (the numerator of O3; reading P):
+    row m is sum_d f_dm (f_d^T Omega - Omega_m)."""
+    F = csr_matrix(indptr, indices, counts, V)
+    S = F @ Omega                                # B x r rows f_d^T Omega
+    c = np.asarray(F.sum(axis=0)).ravel()        # c_m = sum_d f_dm
+    return F.T @ S - c[:, None] * Omega
+
+
+def sketch_eigenpairs(Y, Omega, k):
+    """Top-k eigenpairs of a symmetric matrix A from Y = A Omega alone (the
+    single-pass eigenvalue decomposition of Halko, Martinsson and Tropp 2011,
+    section 5.5): Q R = Y (thin QR), B solves B (Q^T Omega) = Q^T Y in the
+    least-squares sense, B is symmetrised, B = E Lambda E^T, U = Q E.  Exact
+    when range(A) lies in range(Y) (rank A <= r, or r = V).  Pairs in
+    descending order, each vector's largest-magnitude entry made positive
+    (reading J).  Returns (U_k, Lambda_k)."""
+    Q, R = np.linalg.qr(Y)
+    C2 = Q.T @ Omega
+    B = np.linalg.lstsq(C2.T, R.T, rcond=None)[0].T
+    B = 0.5 * (B + B.T)
+    lam, E = np.linalg.eigh(B)
+    order = np.argsort(-lam, kind="stable")[:k]
+    lam, U = lam[order], Q @ E[:, order]
+    for j in range(k):
+        i = int(np.argmax(np.abs(U[:, j])))
+        if U[i, j] < 0:
+            U[:, j] = -U[:, j]
+    return U, lam
+
+
+def sketch_whitening(Z, C, T, S2, Omega, alpha0, k):
+    """The whitening of the online mode (reading P): with M1 = C/T, the sketch
+    of M2 = (alpha0+1) P/S2 - alpha0 M1 M1^T (O3) is
+    Y = (alpha0+1)/S2 Z - alpha0 M1 (M1^T Omega); its eigenpairs
+    (``sketch_eigenpairs``) give W = U_k Lambda_k^-1/2.
+    Returns (W, m1 = W^T M1, Lambda_k)."""
+    M1 = np.asarray(C, dtype=np.float64) / float(T)
+    Y = (alpha0 + 1.0) / float(S2) * Z - alpha0 * np.outer(M1, M1 @ Omega)
+    U, lam = sketch_eigenpairs(Y, Omega, k)
+    if not (lam[-1] > 1e-12 * lam[0]):
+        raise ValueError("the sketched M2 has fewer than k positive eigenvalues")
+    W = U / np.sqrt(lam)[None, :]
+    return W, W.T @ M1, lam
+
+
+def rotate_factors(Phi, W_old, W_new):
+    """CP factors carried into a new whitened basis (reading Q).  The topics
+    they encode, mu_i proportional to (W^T)^dagger phi_i (section "Recovering
+    the Topic Model Parameters"), stay put:
+    phi_i' = W_new^T (W_old^T)^dagger phi_i."""
+    return W_new.T @ (pinv_transpose(W_old) @ Phi)
+
+
+def online_pass(indptr, indices, counts, V, offsets, Omega, every, alpha0, theta, lr, Phi, k,
+                same_token=True, state=None):
+    """One fully online pass (section "Fully Online Implementation", readings
+    P and Q): batch b is documents [offsets[b], offsets[b+1]); the batches go
+    in blocks of `every`.  For each block its documents first update the token
+    statistics (C, T, S2) and the sketch Z, the whitening is rebuilt from the
+    sketch (``sketch_whitening``) and Phi carried into it, then the block's
+    CP steps run in order.
+    `state` (C, T, S2, Z, W, m1) carries over between calls.  Returns
+    (Phi, state, losses)."""
+    indptr = np.asarray(indptr, dtype=np.int64)
+    if state is None:
+        state = dict(C=np.zeros(V, dtype=np.int64), T=0, S2=0, Z=np.zeros_like(Omega), W=None, m1=None)
+    Phi = np.array(Phi, dtype=np.float64)
+    losses = []
+    nb = len(offsets) - 1
+    for b0 in range(0, nb, every):
+        b1 = min(nb, b0 + every)
+        d0, d1 = int(offsets[b0]), int(offsets[b1])
+        rows = indptr[d0:d1 + 1]
+        st = ingest(rows, indices, counts, V)
+        state["C"] = state["C"] + st["C"]
+        state["T"] += st["T"]
+        state["S2"] += st["S2"]
+        state["Z"] = state["Z"] + sketch_accumulate(rows, indices, counts, V, Omega)
+        W, m1, _ = sketch_whitening(state["Z"], state["C"], state["T"], state["S2"], Omega, alpha0, k)
+        if state["W"] is not None:
+            Phi = rotate_factors(Phi, state["W"], W)
+        state["W"], state["m1"] = W, m1
+        for b in range(b0, b1):
+            r = indptr[int(offsets[b]):int(offsets[b + 1]) + 1]
+            Phi, g = cp_step(r, indices, counts, V, W, m1, Phi, lr, alpha0, theta, same_token)
+            losses.append(g["loss"])
+    return Phi, state, np.array(losses)
