@@ -215,6 +215,38 @@ tlda_status tlda_autotune(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *
                           int32_t n_batches, const float *Phi, int32_t fixed_cap,
                           int32_t *tile_cap_out);
 
+/* ------------------------------------------------------- fully online mode */
+
+/* Starts the fully online mode (section "Fully Online Implementation"): the
+ * context keeps exact token statistics (C, T, S2, S3) and a one-pass sketch
+ * Z = P Omega of the pair counts P = sum_d (f_d f_d^T - diag f_d), with the
+ * caller's test matrix Omega (V x r FP64, device, row-major, typically
+ * Gaussian; r even, D <= r <= min(V, 512)).  Omega is copied and the
+ * statistics are cleared; the context's whitening, if any, is kept.
+ * Synchronises.  TLDA_ERR_INVALID for bad sizes. */
+tlda_status tlda_online_begin(tlda_ctx *ctx, const double *Omega, int32_t r);
+
+/* One fully online pass: batch b is documents [batch_offsets[b],
+ * batch_offsets[b+1]) of `corpus` (device CSR, indptr absolute), taken in
+ * blocks of `rewhiten_every` batches.  For each block, its documents first
+ * update the statistics and the sketch; then the whitening is rebuilt from
+ * them: M1 = C/T, Y = (alpha0+1)/S2 Z - alpha0 M1 (M1^T Omega) (the sketch
+ * of M2), Q = orth(Y), B solves B (Q^T Omega) = Q^T Y, B = E Lambda E^T
+ * (symmetrised), U = Q E, W = U_D Lambda_D^-1/2 with the sign convention of
+ * tlda_fit_moments (Halko, Martinsson and Tropp 2011, section 5.5).  If the
+ * context already had a whitening W_old, Phi (D x K FP32, device) is carried
+ * into the new basis, Phi <- W^T W_old (W_old^T W_old)^-1 Phi, so that the
+ * topics it encodes stay put.  Then the block's CP steps run as in
+ * tlda_cp_pass.  rewhiten_every = 1 is the paper's per-batch order: update
+ * M1, update the PCA, then take the gradient step.  loss_out (host,
+ * n_batches doubles) may be NULL.  Synchronises.  TLDA_ERR_STATE before
+ * tlda_online_begin; TLDA_ERR_INVALID for a corrupt batch (the statistics
+ * then hold part of it: begin again); TLDA_ERR_NUMERIC if the sketched M2
+ * has fewer than D positive eigenvalues. */
+tlda_status tlda_online_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets,
+                             int32_t n_batches, float *Phi, float lr, int32_t rewhiten_every,
+                             double *loss_out);
+
 /* --------------------------------------------------------------- recovery */
 #define TLDA_HOST_OUTPUT 1u    /* mu_out / alpha_out are host pointers */
 

@@ -577,6 +577,245 @@ tlda_status finalize(tlda_ctx *ctx) {
   return TLDA_OK;
 }
 
+// ------------------------------------------------------------------ fully online mode
+// One warp per document of a block of batches (absolute offsets into the
+// corpus CSR): validation, L, and the exact counts C_m, T, S2, S3; then the
+// document's part of the sketch Z = P Omega of the pair counts,
+// Z_m += f_m (f^T Omega - Omega_m) for each of its words (FP64 atomics).  A
+// document that fails validation adds nothing and sets *err.
+__global__ void __launch_bounds__(256) k_online_acc(const int32_t *indptr, const int32_t *indices,
+                                                     const int32_t *counts, int n_docs, int V, int r,
+                                                     const double *Om, double *Z, unsigned long long *C,
+                                                     unsigned long long *TS, int *err) {
+  constexpr int kCols = kMaxDim / 32;
+  const int doc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (doc >= n_docs) return;
+  const long long p0 = indptr[doc], p1 = indptr[doc + 1];
+  if (p0 < 0 || p1 < p0) {
+    if (lane == 0) atomicOr(err, 1);
+    return;
+  }
+  double sv[kCols];
+#pragma unroll
+  for (int i = 0; i < kCols; ++i) sv[i] = 0.0;
+  long long L = 0;
+  int prev = -1;
+  bool bad = false;
+  for (long long p = p0; p < p1; ++p) {  // warp-uniform loop
+    const int m = indices[p], f = counts[p];
+    if (m < 0 || m >= V || f <= 0 || m <= prev) {
+      bad = true;
+      break;
+    }
+    prev = m;
+    L += f;
+    const double *om = Om + (long long)m * r;
+#pragma unroll
+    for (int i = 0; i < kCols; ++i) {
+      const int col = lane + 32 * i;
+      if (col < r) sv[i] += (double)f * om[col];
+    }
+  }
+  if (bad) {
+    if (lane == 0) atomicOr(err, 1);
+    return;
+  }
+  for (long long p = p0; p < p1; ++p) {
+    const int m = indices[p], f = counts[p];
+    const double *om = Om + (long long)m * r;
+    double *z = Z + (long long)m * r;
+#pragma unroll
+    for (int i = 0; i < kCols; ++i) {
+      const int col = lane + 32 * i;
+      if (col < r) atomicAdd(z + col, (double)f * (sv[i] - om[col]));
+    }
+    if (lane == 0) atomicAdd(C + m, (unsigned long long)f);
+  }
+  if (lane == 0 && L > 0) {
+    atomicAdd(TS + 0, (unsigned long long)L);
+    atomicAdd(TS + 1, (unsigned long long)(L * (L - 1)));
+    atomicAdd(TS + 2, (unsigned long long)(L * (L - 1) * (L - 2)));
+  }
+}
+
+// In-place inverse of an n x n FP64 matrix (row-major) by Gauss-Jordan
+// elimination with partial pivoting; false if it is singular.
+bool host_inverse(std::vector<double> &A, int n) {
+  std::vector<double> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < n; ++i)
+      if (std::fabs(A[(size_t)i * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = i;
+    if (!(std::fabs(A[(size_t)piv * n + c]) > 0.0)) return false;
+    if (piv != c)
+      for (int j = 0; j < n; ++j) {
+        std::swap(A[(size_t)c * n + j], A[(size_t)piv * n + j]);
+        std::swap(I[(size_t)c * n + j], I[(size_t)piv * n + j]);
+      }
+    const double d = A[(size_t)c * n + c];
+    for (int j = 0; j < n; ++j) {
+      A[(size_t)c * n + j] /= d;
+      I[(size_t)c * n + j] /= d;
+    }
+    for (int i = 0; i < n; ++i) {
+      if (i == c) continue;
+      const double f = A[(size_t)i * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        A[(size_t)i * n + j] -= f * A[(size_t)c * n + j];
+        I[(size_t)i * n + j] -= f * I[(size_t)c * n + j];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+// Rebuilds the whitening from the online statistics (section "Fully Online
+// Implementation", the PCA update): with M1 = C/T, the sketch of
+// M2 = (alpha0+1) P/S2 - alpha0 M1 M1^T is Y = (alpha0+1)/S2 Z - alpha0 M1 (M1^T Omega);
+// then the single-pass eigendecomposition of Halko, Martinsson and Tropp
+// (2011, section 5.5): Q = orth(Y) (FP64 CholeskyQR2), B solves
+// B (Q^T Omega) = Q^T Y, B symmetrised, B = E Lambda E^T (Jacobi), U = Q E,
+// and W = U_D Lambda_D^-1/2 with the signs of fit_moments, m1 = W^T M1, U.
+// The previous W is kept in on_Wold.
+tlda_status online_rewhiten(tlda_ctx *ctx) {
+  cudaStream_t s = ctx->stream;
+  const int V = ctx->V, D = ctx->D, r = ctx->on_r;
+  unsigned long long TS[3];
+  int ferr = 0;
+  CKF(cudaMemcpyAsync(TS, ctx->on_TS, sizeof TS, cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(&ferr, ctx->on_err, sizeof ferr, cudaMemcpyDeviceToHost, s));
+  CKF(cudaStreamSynchronize(s));
+  if (ferr) return fail(ctx, TLDA_ERR_INVALID, "corrupt CSR batch in the online pass");
+  if (TS[0] == 0 || TS[1] == 0) return fail(ctx, TLDA_ERR_NUMERIC, "no token pairs accumulated");
+  const double a0 = ctx->p.alpha0, sP = (a0 + 1.0) / (double)TS[1];
+  Scratch sc;
+  double *M1 = nullptr, *m1q = nullptr, *Y = nullptr, *Q1 = nullptr, *Q2 = nullptr, *G = nullptr;
+  double *Linv = nullptr, *LinvT = nullptr, *C1 = nullptr, *C2 = nullptr, *Bm = nullptr, *Ev = nullptr;
+  double *ev = nullptr, *Ek = nullptr, *U64 = nullptr, *lam = nullptr;
+  int *status = nullptr;
+  CKF(sc.get(&M1, V));
+  CKF(sc.get(&m1q, r));
+  CKF(sc.get(&Y, (size_t)V * r));
+  CKF(sc.get(&Q1, (size_t)V * r));
+  CKF(sc.get(&Q2, (size_t)V * r));
+  CKF(sc.get(&G, (size_t)r * r));
+  CKF(sc.get(&Linv, (size_t)r * r));
+  CKF(sc.get(&LinvT, (size_t)r * r));
+  CKF(sc.get(&C1, (size_t)r * r));
+  CKF(sc.get(&C2, (size_t)r * r));
+  CKF(sc.get(&Bm, (size_t)r * r));
+  CKF(sc.get(&Ev, (size_t)r * r));
+  CKF(sc.get(&ev, r));
+  CKF(sc.get(&Ek, (size_t)r * D));
+  CKF(sc.get(&U64, (size_t)V * D));
+  CKF(sc.get(&lam, D));
+  CKF(sc.get(&status, 2, true));
+  k_m1<<<(V + 255) / 256, 256, 0, s>>>(ctx->on_C, ctx->on_TS, V, M1);
+  gemm_tn64<double, double>(M1, 1, ctx->on_Om, r, m1q, r, 1, r, V, s);
+  CKF(cudaMemcpyAsync(Y, ctx->on_Z, sizeof(double) * (size_t)V * r, cudaMemcpyDeviceToDevice, s));
+  k_rank1_fix<<<(unsigned)(((long long)V * r + 255) / 256), 256, 0, s>>>(Y, M1, m1q, V, r, sP, a0);
+  // CholeskyQR2: out = in L^-T with L L^T = in^T in, twice
+  auto cholqr_pass = [&](const double *in, double *out) {
+    gemm_tn64<double, double>(in, r, in, r, G, r, r, r, V, s);
+    k_chol_inv<<<1, 256, 0, s>>>(G, r, Linv, status);
+    k_transpose_rr<<<(r * r + 255) / 256, 256, 0, s>>>(Linv, r, nullptr, LinvT);
+    gemm_nn<double>(in, r, LinvT, r, out, r, V, r, r, s);
+  };
+  cholqr_pass(Y, Q1);
+  cholqr_pass(Q1, Q2);
+  gemm_tn64<double, double>(Q2, r, Y, r, C1, r, r, r, V, s);           // Q^T Y
+  gemm_tn64<double, double>(Q2, r, ctx->on_Om, r, C2, r, r, r, V, s);  // Q^T Omega
+  CKF(cudaGetLastError());
+  std::vector<double> hC1((size_t)r * r), hC2((size_t)r * r);
+  int hstat[2];
+  CKF(cudaMemcpyAsync(hC1.data(), C1, sizeof(double) * r * r, cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(hC2.data(), C2, sizeof(double) * r * r, cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(hstat, status, sizeof hstat, cudaMemcpyDeviceToHost, s));
+  CKF(cudaStreamSynchronize(s));
+  if (hstat[0]) return fail(ctx, TLDA_ERR_NUMERIC, "sketch basis lost rank (CholeskyQR breakdown)");
+  if (!host_inverse(hC2, r)) return fail(ctx, TLDA_ERR_NUMERIC, "Q^T Omega is singular");
+  std::vector<double> hB((size_t)r * r, 0.0);
+  for (int i = 0; i < r; ++i)
+    for (int k = 0; k < r; ++k) {
+      const double c = hC1[(size_t)i * r + k];
+      for (int j = 0; j < r; ++j) hB[(size_t)i * r + j] += c * hC2[(size_t)k * r + j];
+    }
+  for (int i = 0; i < r; ++i)
+    for (int j = i + 1; j < r; ++j) {
+      const double v = 0.5 * (hB[(size_t)i * r + j] + hB[(size_t)j * r + i]);
+      hB[(size_t)i * r + j] = hB[(size_t)j * r + i] = v;
+    }
+  CKF(cudaMemcpyAsync(Bm, hB.data(), sizeof(double) * r * r, cudaMemcpyHostToDevice, s));
+  k_jacobi<<<1, 512, 0, s>>>(Bm, r, Ev, ev, 40, status + 1);
+  CKF(cudaGetLastError());
+  std::vector<double> hev(r), hEv((size_t)r * r);
+  CKF(cudaMemcpyAsync(hev.data(), ev, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(hEv.data(), Ev, sizeof(double) * r * r, cudaMemcpyDeviceToHost, s));
+  CKF(cudaStreamSynchronize(s));
+  std::vector<int> ord(r);
+  for (int i = 0; i < r; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return hev[x] > hev[y]; });
+  std::vector<double> hEk((size_t)r * D), hlam(D);
+  for (int j = 0; j < D; ++j) {
+    hlam[j] = hev[ord[j]];
+    for (int i = 0; i < r; ++i) hEk[(size_t)i * D + j] = hEv[(size_t)i * r + ord[j]];
+  }
+  if (!(hlam[D - 1] > 1e-12 * hlam[0]))
+    return fail(ctx, TLDA_ERR_NUMERIC, "the sketched M2 has fewer than D positive eigenvalues");
+  CKF(cudaMemcpyAsync(Ek, hEk.data(), sizeof(double) * r * D, cudaMemcpyHostToDevice, s));
+  CKF(cudaMemcpyAsync(lam, hlam.data(), sizeof(double) * D, cudaMemcpyHostToDevice, s));
+  gemm_nn<double>(Q2, r, Ek, D, U64, D, V, D, r, s);
+  if (ctx->whitened)
+    CKF(cudaMemcpyAsync(ctx->on_Wold, ctx->W32, sizeof(float) * (size_t)V * D, cudaMemcpyDeviceToDevice, s));
+  k_make_w<<<D, 256, 0, s>>>(U64, V, D, lam, ctx->W32, nullptr, nullptr);
+  CKF(cudaMemsetAsync(ctx->m1, 0, sizeof(float) * ctx->Dp, s));
+  k_wtm1<<<D, 256, 0, s>>>(ctx->W32, M1, V, D, ctx->m1);
+  launch_make_u(ctx->W32, ctx->m1, V, D, ctx->Dp, ctx->U32, ctx->U16, s);
+  CKF(cudaGetLastError());
+  CKF(cudaStreamSynchronize(s));
+  ctx->eig = hlam;
+  return TLDA_OK;
+}
+
+// Phi (D x K, device) <- W^T W_old (W_old^T W_old)^-1 Phi: the factors carried
+// from the previous whitening (on_Wold) into the current one (W32).
+tlda_status online_rotate(tlda_ctx *ctx, float *Phi) {
+  cudaStream_t s = ctx->stream;
+  const int V = ctx->V, D = ctx->D, K = ctx->K;
+  Scratch sc;
+  double *A = nullptr, *G = nullptr;
+  CKF(sc.get(&A, (size_t)D * D));
+  CKF(sc.get(&G, (size_t)D * D));
+  gemm_tn64<float, float>(ctx->W32, D, ctx->on_Wold, D, A, D, D, D, V, s);
+  gemm_tn64<float, float>(ctx->on_Wold, D, ctx->on_Wold, D, G, D, D, D, V, s);
+  CKF(cudaGetLastError());
+  std::vector<double> hA((size_t)D * D), hG((size_t)D * D);
+  std::vector<float> hP((size_t)D * K);
+  CKF(cudaMemcpyAsync(hA.data(), A, sizeof(double) * D * D, cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(hG.data(), G, sizeof(double) * D * D, cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(hP.data(), Phi, sizeof(float) * D * K, cudaMemcpyDeviceToHost, s));
+  CKF(cudaStreamSynchronize(s));
+  if (!host_inverse(hG, D)) return fail(ctx, TLDA_ERR_NUMERIC, "W^T W of the previous whitening is singular");
+  std::vector<double> R((size_t)D * D, 0.0), hN((size_t)D * K, 0.0);
+  for (int i = 0; i < D; ++i)
+    for (int k = 0; k < D; ++k) {
+      const double a = hA[(size_t)i * D + k];
+      for (int j = 0; j < D; ++j) R[(size_t)i * D + j] += a * hG[(size_t)k * D + j];
+    }
+  for (int i = 0; i < D; ++i)
+    for (int k = 0; k < D; ++k) {
+      const double rr = R[(size_t)i * D + k];
+      for (int j = 0; j < K; ++j) hN[(size_t)i * K + j] += rr * hP[(size_t)k * K + j];
+    }
+  for (size_t e = 0; e < hP.size(); ++e) hP[e] = (float)hN[e];
+  CKF(cudaMemcpyAsync(Phi, hP.data(), sizeof(float) * D * K, cudaMemcpyHostToDevice, s));
+  CKF(cudaStreamSynchronize(s));
+  return TLDA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -674,6 +913,75 @@ tlda_status tlda_unwhiten_topics(tlda_ctx *ctx, const float *Phi, double *mu_out
   }
   CKF(cudaStreamSynchronize(s));
   if (hst) return fail(ctx, TLDA_ERR_NUMERIC, "W^T W is not positive definite");
+  return TLDA_OK;
+}
+
+tlda_status tlda_online_begin(tlda_ctx *ctx, const double *Omega, int32_t r) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  if (!Omega || r < ctx->D || r > kMaxDim || (r & 1) || r > ctx->V)
+    return fail(ctx, TLDA_ERR_INVALID, "the sketch needs an even r with D <= r <= min(V, 512)");
+  const size_t V = ctx->V;
+  if (ctx->on_r != r) {
+    if (ctx->on_Om) cudaFree(ctx->on_Om);
+    if (ctx->on_Z) cudaFree(ctx->on_Z);
+    ctx->on_Om = ctx->on_Z = nullptr;
+    ctx->on_r = 0;
+    CKF(dalloc(&ctx->on_Om, V * r));
+    CKF(dalloc(&ctx->on_Z, V * r));
+    ctx->on_r = r;
+  }
+  if (!ctx->on_C) CKF(dalloc(&ctx->on_C, V));
+  if (!ctx->on_TS) CKF(dalloc(&ctx->on_TS, 3));
+  if (!ctx->on_err) CKF(dalloc(&ctx->on_err, 1));
+  if (!ctx->on_Wold) CKF(dalloc(&ctx->on_Wold, V * ctx->D));
+  cudaStream_t s = ctx->stream;
+  CKF(cudaMemcpyAsync(ctx->on_Om, Omega, sizeof(double) * V * r, cudaMemcpyDeviceToDevice, s));
+  CKF(cudaMemsetAsync(ctx->on_Z, 0, sizeof(double) * V * r, s));
+  CKF(cudaMemsetAsync(ctx->on_C, 0, sizeof(unsigned long long) * V, s));
+  CKF(cudaMemsetAsync(ctx->on_TS, 0, sizeof(unsigned long long) * 3, s));
+  CKF(cudaMemsetAsync(ctx->on_err, 0, sizeof(int), s));
+  CKF(cudaStreamSynchronize(s));
+  ctx->on_active = true;
+  return TLDA_OK;
+}
+
+tlda_status tlda_online_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets, int32_t n_batches,
+                             float *Phi, float lr, int32_t rewhiten_every, double *loss_out) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  if (!ctx->on_active) return fail(ctx, TLDA_ERR_STATE, "tlda_online_begin has not been called");
+  if (!corpus || corpus->vocab != ctx->V || corpus->n_docs < 0 || !corpus->indptr ||
+      (corpus->n_docs > 0 && (!corpus->indices || !corpus->counts)))
+    return fail(ctx, TLDA_ERR_INVALID, "bad corpus");
+  if (!Phi || !batch_offsets || n_batches < 0 || rewhiten_every < 1)
+    return fail(ctx, TLDA_ERR_INVALID, "bad online pass arguments");
+  for (int b = 0; b < n_batches; ++b) {
+    const int64_t d0 = batch_offsets[b], d1 = batch_offsets[b + 1];
+    if (d0 < 0 || d1 < d0 || d1 > corpus->n_docs) return fail(ctx, TLDA_ERR_INVALID, "batch offsets out of range");
+  }
+  cudaStream_t s = ctx->stream;
+  for (int b0 = 0; b0 < n_batches; b0 += rewhiten_every) {
+    const int b1 = std::min(n_batches, b0 + rewhiten_every);
+    const int64_t d0 = batch_offsets[b0], d1 = batch_offsets[b1];
+    const int nd = (int)(d1 - d0);
+    if (nd > 0) {
+      const long long threads = (long long)nd * 32;
+      k_online_acc<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(corpus->indptr + d0, corpus->indices,
+                                                                     corpus->counts, nd, ctx->V, ctx->on_r,
+                                                                     ctx->on_Om, ctx->on_Z, ctx->on_C,
+                                                                     ctx->on_TS, ctx->on_err);
+      CKF(cudaGetLastError());
+    }
+    const bool had = ctx->whitened;  // Phi is carried over from the context's current whitening
+    tlda_status st = online_rewhiten(ctx);
+    if (st) return st;
+    if (had) {
+      st = online_rotate(ctx, Phi);
+      if (st) return st;
+    }
+    ctx->whitened = true;
+    st = tlda_cp_pass(ctx, corpus, batch_offsets + b0, b1 - b0, Phi, lr, 0, loss_out ? loss_out + b0 : nullptr);
+    if (st) return st;
+  }
   return TLDA_OK;
 }
 

@@ -157,6 +157,13 @@ struct tlda_ctx {
   unsigned long long *TS = nullptr;    // T, S2, S3 of the fit
   int *fit_err = nullptr;
   bool fit_open = false, fitted = false;
+  // fully online mode: exact counts and the sketch Z = P Omega of the pair counts
+  int on_r = 0;
+  bool on_active = false;
+  double *on_Om = nullptr, *on_Z = nullptr;           // V x r
+  unsigned long long *on_C = nullptr, *on_TS = nullptr;  // V; T, S2, S3
+  int *on_err = nullptr;
+  float *on_Wold = nullptr;            // V x D: the whitening before the last rebuild
   // pass staging (host input)
   int32_t *stage[2] = {nullptr, nullptr};
   long long stage_cap = 0;

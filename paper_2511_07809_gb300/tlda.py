@@ -36,7 +36,8 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_set_whitening", "tlda_whiten_batch", "tlda_cp_step",
                 "tlda_cp_data_term", "tlda_cp_pass", "tlda_unwhiten_topics",
                 "tlda_profile", "tlda_profile_read", "tlda_save_state", "tlda_load_state",
-                "tlda_cp_step_noalloc", "tlda_autotune")
+                "tlda_cp_step_noalloc", "tlda_autotune", "tlda_online_begin",
+                "tlda_online_pass")
 
 
 class Params(ctypes.Structure):
@@ -83,6 +84,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "tlda_cp_data_term": (i32, [vp, P(CSR), vp, vp, vp]),
         "tlda_cp_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, u32, vp]),
         "tlda_autotune": (i32, [vp, P(CSR), vp, i32, vp, i32, P(i32)]),
+        "tlda_online_begin": (i32, [vp, vp, i32]),
+        "tlda_online_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, i32, vp]),
         "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
         "tlda_cp_step_noalloc": (i32, [P(CSR), vp, vp, i32, i32, f64, f32, vp, f32, vp, vp, vp]),
         "tlda_profile": (i32, [vp, u32]),
@@ -270,6 +273,28 @@ class TLDA:
         self._check(self.lib.tlda_autotune(self.h, ctypes.byref(s), off.ctypes.data, len(off) - 1,
                                            Phi.data_ptr(), 0, ctypes.byref(out)))
         return out.value
+
+    # ------------------------------------------------------------ fully online mode
+    def online_begin(self, Omega: torch.Tensor):
+        """Start the fully online mode with the sketch test matrix Omega
+        (V x r float64, any device; copied)."""
+        Om = Omega.to(device="cuda", dtype=torch.float64).contiguous()
+        assert Om.dim() == 2 and Om.shape[0] == self.V
+        self._check(self.lib.tlda_online_begin(self.h, Om.data_ptr(), int(Om.shape[1])))
+
+    def online_pass(self, corpus: DeviceCSR, batch_offsets, Phi: torch.Tensor, lr: float,
+                    rewhiten_every: int = 1, losses: bool = False):
+        """One fully online pass (blocks of `rewhiten_every` batches: statistics
+        and whitening first, then the block's CP steps); Phi updated in place."""
+        assert Phi.dtype == torch.float32 and Phi.is_cuda and Phi.is_contiguous()
+        off = np.ascontiguousarray(np.asarray(batch_offsets, dtype=np.int64))
+        nb = len(off) - 1
+        out = np.zeros(max(nb, 1), dtype=np.float64) if losses else None
+        s = corpus.struct()
+        self._check(self.lib.tlda_online_pass(self.h, ctypes.byref(s), off.ctypes.data, nb,
+                                              Phi.data_ptr(), float(lr), int(rewhiten_every),
+                                              out.ctypes.data if losses else None))
+        return out[:nb] if losses else None
 
     def sync(self):
         self._check(self.lib.tlda_sync(self.h))
