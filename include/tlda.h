@@ -103,6 +103,12 @@ tlda_status tlda_destroy(tlda_ctx *ctx);
 /* Message of the last failure on ctx ("" if none).  Owned by ctx. */
 const char *tlda_last_error(const tlda_ctx *ctx);
 
+/* Sweeps the symmetric eigensolver (cyclic Jacobi, stopped once off-diagonal
+ * entries are near 1e-13 of the matrix scale, at most 40) took in the last
+ * whitening built on ctx (tlda_fit_moments' finalisation or an online
+ * re-whitening); 0 before any, -1 for a NULL context.  Diagnostic. */
+int32_t tlda_eig_sweeps(const tlda_ctx *ctx);
+
 /* Synchronises the context's stream and returns (then clears) any sticky
  * device-side status: TLDA_ERR_INVALID for a corrupt batch, TLDA_ERR_TIMEOUT
  * for an expired bounded wait. */

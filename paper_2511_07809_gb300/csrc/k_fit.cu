@@ -186,43 +186,7 @@ __global__ void k_f2d(const float *x, double *y, long long n) {
   if (e < n) y[e] = x[e];
 }
 
-// ------------------------------------------------------------------ small dense FP64 (one block)
-// In-place Cholesky G = L L^T (lower triangle of G, global memory), then
-// Linv = L^-1.  status[0] = 1 on breakdown (non-positive pivot).
-__global__ void k_chol_inv(double *L, int r, double *Linv, int *status) {
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  for (int j = 0; j < r; ++j) {
-    if (threadIdx.x == 0) {
-      double d = L[j * r + j];
-      for (int k = 0; k < j; ++k) d -= L[j * r + k] * L[j * r + k];
-      if (!(d > 0.0)) {
-        bad = 1;
-        d = 1.0;
-      }
-      L[j * r + j] = sqrt(d);
-    }
-    __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) {
-      double v = L[i * r + j];
-      for (int k = 0; k < j; ++k) v -= L[i * r + k] * L[j * r + k];
-      L[i * r + j] = v / L[j * r + j];
-    }
-    __syncthreads();
-  }
-  // column c of L^-1 by forward substitution of L x = e_c (x_i = 0 for i < c)
-  for (int c = threadIdx.x; c < r; c += blockDim.x) {
-    for (int i = 0; i < r; ++i) {
-      double v = (i == c) ? 1.0 : 0.0;
-      if (i >= c)
-        for (int k = c; k < i; ++k) v -= L[i * r + k] * Linv[k * r + c];
-      Linv[i * r + c] = (i < c) ? 0.0 : v / L[i * r + i];
-    }
-  }
-  if (threadIdx.x == 0 && bad) *status = 1;
-}
-
+// ------------------------------------------------------------------ small dense FP64
 // Transpose r x r (FP64 -> FP32 for the Y Linv^T product).
 __global__ void k_transpose_rr(const double *A, int r, float *AT32, double *AT64) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -232,52 +196,125 @@ __global__ void k_transpose_rr(const double *A, int r, float *AT32, double *AT64
   if (AT64) AT64[j * r + i] = A[e];
 }
 
+// Control block of the grid-wide Jacobi: the grid barrier's arrival counter,
+// an abort flag, the sweep count, and each block's partial sums of the squared
+// off-diagonal and total entries (two slots, by sweep parity).
+constexpr int kJacThreads = 256, kJacMaxGrid = 256;
+struct JacCtl {
+  unsigned bar;
+  int abort;
+  int sweeps;
+  int pad;
+  double part[2][2][kJacMaxGrid];
+};
+
+__device__ __forceinline__ unsigned jac_ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier of a cooperative launch (every block resident): bounded to
+// about a second; false if it expired here or any block flagged an abort.
+__device__ bool jac_sync(JacCtl *ctl, unsigned target, int *s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(&ctl->bar, 1u);
+    const long long t0 = clock64();
+    while (jac_ld_acquire(&ctl->bar) < target) {
+      if (*reinterpret_cast<volatile int *>(&ctl->abort)) {
+        ok = 0;
+        break;
+      }
+      if (clock64() - t0 > 2000000000ll) {
+        atomicExch(&ctl->abort, 1);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    *reinterpret_cast<volatile int *>(s_ok) = ok;
+  }
+  __syncthreads();
+  return *reinterpret_cast<volatile int *>(s_ok) != 0;
+}
+
 // Cyclic Jacobi for a symmetric r x r FP64 matrix A (r even, global memory,
 // overwritten), round-robin ordering so each round applies r/2 disjoint
 // rotations in parallel (Golub & Van Loan, "Matrix Computations", sec. 8.5,
 // parallel ordering).  Rotation of pair (p, q): tau = (a_qq - a_pp)/(2 a_pq),
-// t = sign(tau)/(|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c, and
-// A <- J^T A J, E <- E J.  On return eval[i] = A_ii, columns of Evec are the
-// eigenvectors; sweeps stop when the off-diagonal mass is below 1e-30 of the
-// total (or after max_sweeps).
-__global__ void k_jacobi(double *A, int r, double *Evec, double *eval, int max_sweeps, int *sweeps_out) {
-  __shared__ double cs[kMaxDim], sn[kMaxDim];
-  __shared__ int pp[kMaxDim], qq[kMaxDim];
-  __shared__ double red_o[512], red_t[512];
-  const int h = r / 2;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+// t = sign(tau)/(|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c.
+// Because the rotations of one round are disjoint, A <- J^T A J is applied in
+// one pass over the 2 x 2 blocks (pair k rows, pair l columns), each block
+// rotated on the left by pair k and on the right by pair l; the eigenvectors
+// are kept as rows, Et <- J^T Et.  The rounds are spread over the whole grid
+// (FP64 arithmetic is scarce per SM), one grid barrier per round; every
+// block derives the round's rotations itself.  Et starts as I; on return
+// eval[i] = A_ii and row i of Et is its eigenvector.
+// Sweeps stop when the off-diagonal mass is below 1e-26 r^2 of the total,
+// i.e. entries near 1e-13 of the scale (or after max_sweeps).
+__global__ void __launch_bounds__(kJacThreads) k_jacobi(double *__restrict__ A, int r, double *__restrict__ Et,
+                                                       double *__restrict__ eval, int max_sweeps,
+                                                       JacCtl *ctl) {
+  __shared__ double cs[kMaxDim / 2], sn[kMaxDim / 2];
+  __shared__ int pp[kMaxDim / 2], qq[kMaxDim / 2];
+  __shared__ double red_o[kJacThreads / 32], red_t[kJacThreads / 32];
+  __shared__ int s_ok, s_done;
+  const int G = gridDim.x, tid = threadIdx.x, nt = blockDim.x;
+  const int gt = blockIdx.x * nt + tid, gn = G * nt;
+  const int h = r / 2, rr = r * r;
+  unsigned nbar = 0;
+  for (int e = gt; e < rr; e += gn) {
     const int i = e / r, j = e % r;
     if (i < j) {
       const double v = 0.5 * (A[i * r + j] + A[j * r + i]);
       A[i * r + j] = v;
       A[j * r + i] = v;
     }
-    Evec[e] = (i == j) ? 1.0 : 0.0;
+    Et[e] = (i == j) ? 1.0 : 0.0;
   }
-  __syncthreads();
+  if (!jac_sync(ctl, ++nbar * G, &s_ok)) return;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     double o = 0.0, t = 0.0;
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-      const double v = A[e] * A[e];
-      t += v;
-      if (e / r != e % r) o += v;
+    for (int e = gt; e < rr; e += gn) {
+      const double v = __ldcg(A + e);
+      t += v * v;
+      if (e / r != e % r) o += v * v;
     }
-    red_o[threadIdx.x] = o;
-    red_t[threadIdx.x] = t;
+    for (int m = 16; m > 0; m >>= 1) {
+      o += __shfl_xor_sync(0xffffffffu, o, m);
+      t += __shfl_xor_sync(0xffffffffu, t, m);
+    }
+    if ((tid & 31) == 0) {
+      red_o[tid >> 5] = o;
+      red_t[tid >> 5] = t;
+    }
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if ((int)threadIdx.x < w) {
-        red_o[threadIdx.x] += red_o[threadIdx.x + w];
-        red_t[threadIdx.x] += red_t[threadIdx.x + w];
+    if (tid == 0) {
+      double so = 0.0, st = 0.0;
+      for (int w = 0; w < nt / 32; ++w) {
+        so += red_o[w];
+        st += red_t[w];
       }
-      __syncthreads();
+      ctl->part[sweep & 1][0][blockIdx.x] = so;
+      ctl->part[sweep & 1][1][blockIdx.x] = st;
     }
-    const bool done = red_o[0] <= 1e-30 * red_t[0];
+    if (!jac_sync(ctl, ++nbar * G, &s_ok)) return;
+    if (tid == 0) {  // every block sums the partials in the same order
+      double so = 0.0, st = 0.0;
+      for (int g = 0; g < G; ++g) {
+        so += __ldcg(&ctl->part[sweep & 1][0][g]);
+        st += __ldcg(&ctl->part[sweep & 1][1][g]);
+      }
+      s_done = so <= 1e-26 * (double)r * r * st;
+    }
     __syncthreads();
-    if (done) break;
+    if (s_done) break;
     for (int round = 0; round < r - 1; ++round) {
-      for (int k = threadIdx.x; k < h; k += blockDim.x) {
+      for (int k = tid; k < h; k += nt) {
         // round-robin pairing: slot 0 holds index 0, the others rotate
         const int sa = k, sb = r - 1 - k;
         int p = sa == 0 ? 0 : 1 + (sa - 1 + round) % (r - 1);
@@ -287,10 +324,11 @@ __global__ void k_jacobi(double *A, int r, double *Evec, double *eval, int max_s
           p = q;
           q = tmp;
         }
-        const double apq = A[p * r + q];
+        const double apq = __ldcg(A + p * r + q);
+        const double app = __ldcg(A + p * r + p), aqq = __ldcg(A + q * r + q);
         double c = 1.0, sv = 0.0;
         if (apq != 0.0) {
-          const double tau = (A[q * r + q] - A[p * r + p]) / (2.0 * apq);
+          const double tau = (aqq - app) / (2.0 * apq);
           const double tt = tau >= 0.0 ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : -1.0 / (-tau + sqrt(1.0 + tau * tau));
           c = 1.0 / sqrt(1.0 + tt * tt);
           sv = tt * c;
@@ -301,28 +339,228 @@ __global__ void k_jacobi(double *A, int r, double *Evec, double *eval, int max_s
         qq[k] = q;
       }
       __syncthreads();
-      for (int w = threadIdx.x; w < h * r; w += blockDim.x) {  // rows: A <- J^T A
-        const int k = w / r, j = w % r, p = pp[k], q = qq[k];
-        const double c = cs[k], sv = sn[k], ap = A[p * r + j], aq = A[q * r + j];
-        A[p * r + j] = c * ap - sv * aq;
-        A[q * r + j] = sv * ap + c * aq;
+      // 2 x 2 blocks, two per thread per iteration (loads before stores)
+      const int nb = h * h;
+      for (int w0 = gt; w0 < nb; w0 += 2 * gn) {
+        double x[2][4];
+        int base[2][4];
+        bool ok[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int w = w0 + u * gn;
+          ok[u] = w < nb;
+          const int k = ok[u] ? w / h : 0, l = ok[u] ? w % h : 0;
+          const int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
+          base[u][0] = pk * r + pl;
+          base[u][1] = pk * r + ql;
+          base[u][2] = qk * r + pl;
+          base[u][3] = qk * r + ql;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) x[u][v] = ok[u] ? __ldcg(A + base[u][v]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (!ok[u]) continue;
+          const int w = w0 + u * gn, k = w / h, l = w % h;
+          const double ck = cs[k], sk = sn[k], cl = cs[l], sl = sn[l];
+          const double a1 = ck * x[u][0] - sk * x[u][2], b1 = ck * x[u][1] - sk * x[u][3];
+          const double c1 = sk * x[u][0] + ck * x[u][2], d1 = sk * x[u][1] + ck * x[u][3];
+          A[base[u][0]] = cl * a1 - sl * b1;
+          A[base[u][1]] = (k == l) ? 0.0 : sl * a1 + cl * b1;
+          A[base[u][2]] = (k == l) ? 0.0 : cl * c1 - sl * d1;
+          A[base[u][3]] = sl * c1 + cl * d1;
+        }
       }
-      __syncthreads();
-      for (int w = threadIdx.x; w < h * r; w += blockDim.x) {  // columns: A <- A J, E <- E J
-        const int k = w / r, i = w % r, p = pp[k], q = qq[k];
-        const double c = cs[k], sv = sn[k];
-        const double ap = A[i * r + p], aq = A[i * r + q];
-        A[i * r + p] = c * ap - sv * aq;
-        A[i * r + q] = sv * ap + c * aq;
-        const double ep = Evec[i * r + p], eq = Evec[i * r + q];
-        Evec[i * r + p] = c * ep - sv * eq;
-        Evec[i * r + q] = sv * ep + c * eq;
+      // eigenvector rows: Et[p] <- c Et[p] - s Et[q], Et[q] <- s Et[p] + c Et[q]
+      const int ne = h * r;
+      for (int w0 = gt; w0 < ne; w0 += 2 * gn) {
+        double ep[2], eq[2];
+        int ip[2], iq[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int w = w0 + u * gn;
+          const int k = w < ne ? w / r : 0, j = w < ne ? w % r : 0;
+          ip[u] = pp[k] * r + j;
+          iq[u] = qq[k] * r + j;
+          ep[u] = w < ne ? __ldcg(Et + ip[u]) : 0.0;
+          eq[u] = w < ne ? __ldcg(Et + iq[u]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int w = w0 + u * gn;
+          if (w >= ne) continue;
+          const int k = w / r;
+          const double c = cs[k], sv = sn[k];
+          Et[ip[u]] = c * ep[u] - sv * eq[u];
+          Et[iq[u]] = sv * ep[u] + c * eq[u];
+        }
       }
-      __syncthreads();
+      if (!jac_sync(ctl, ++nbar * G, &s_ok)) return;
     }
   }
-  for (int i = threadIdx.x; i < r; i += blockDim.x) eval[i] = A[i * r + i];
-  if (threadIdx.x == 0) *sweeps_out = sweep;
+  for (int i = gt; i < r; i += gn) eval[i] = __ldcg(A + i * r + i);
+  if (gt == 0) ctl->sweeps = sweep;
+}
+
+
+// Cholesky factor and inverse of a symmetric positive definite r x r FP64
+// matrix A (overwritten): A = L L^T by right-looking elimination (column j:
+// l_jj = sqrt(a_jj), l_ij = a_ij / l_jj, then a_ik -= l_ij l_kj for
+// j < k <= i), and X = L^-1 by right-looking forward substitution on
+// Z = diag(L) X (z_ic -= l_ik / l_kk z_kc for i > k, then x_ic = z_ic / l_ii).
+// Spread over the grid, one grid barrier per column of each phase.  L (lower,
+// zeros above) and the scratch Z are required; Linv, LinvT64 = L^-T and
+// LinvT32 (FP32) are written when given.  status: 1 if a pivot was not
+// positive (it is taken as 1), 2 if a grid barrier expired.
+__global__ void __launch_bounds__(kJacThreads) k_chol_inv(double *__restrict__ A, int r, double *__restrict__ L,
+                                                         double *__restrict__ Z, double *Linv, double *LinvT64,
+                                                         float *LinvT32, int *status, JacCtl *ctl) {
+  __shared__ int s_ok;
+  const int G = gridDim.x, gt = blockIdx.x * blockDim.x + threadIdx.x, gn = G * blockDim.x;
+  const int rr = r * r;
+  unsigned nbar = 0;
+  for (int e = gt; e < rr; e += gn) {
+    const int i = e / r, k = e % r;
+    Z[e] = (i == k) ? 1.0 : 0.0;
+    if (k > i) L[e] = 0.0;
+  }
+  for (int j = 0; j < r; ++j) {
+    double d = __ldcg(A + j * r + j);
+    if (!(d > 0.0)) {
+      if (gt == 0) atomicMax(status, 1);
+      d = 1.0;
+    }
+    d = sqrt(d);
+    const double inv = 1.0 / d;
+    const int m = r - j - 1;
+    for (int e = gt; e <= m; e += gn) L[(j + e) * r + j] = e == 0 ? d : __ldcg(A + (j + e) * r + j) * inv;
+    for (int e = gt; e < m * m; e += gn) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k <= i) A[i * r + k] = __ldcg(A + i * r + k) - (__ldcg(A + i * r + j) * inv) * (__ldcg(A + k * r + j) * inv);
+    }
+    if (!jac_sync(ctl, ++nbar * G, &s_ok)) {
+      if (threadIdx.x == 0) atomicMax(status, 2);
+      return;
+    }
+  }
+  for (int k = 0; k < r - 1; ++k) {
+    const double f = 1.0 / __ldcg(L + k * r + k);
+    const int m = r - k - 1, w = k + 1;  // rows k+1 .. r-1, columns 0 .. k
+    for (int e = gt; e < m * w; e += gn) {
+      const int i = k + 1 + e / w, c = e % w;
+      Z[i * r + c] = __ldcg(Z + i * r + c) - __ldcg(L + i * r + k) * f * __ldcg(Z + k * r + c);
+    }
+    if (!jac_sync(ctl, ++nbar * G, &s_ok)) {
+      if (threadIdx.x == 0) atomicMax(status, 2);
+      return;
+    }
+  }
+  for (int e = gt; e < rr; e += gn) {
+    const int i = e / r, c = e % r;
+    const double x = c <= i ? __ldcg(Z + e) / __ldcg(L + i * r + i) : 0.0;
+    if (Linv) Linv[e] = x;
+    if (LinvT64) LinvT64[c * r + i] = x;
+    if (LinvT32) LinvT32[c * r + i] = (float)x;
+  }
+}
+
+// B = C1 C2^-1 for r x r FP64 matrices (C2 general, row-major): Gauss-Jordan
+// elimination with partial pivoting (largest |pivot| among the rows not yet
+// used, lowest index on ties) of C2^T B^T = C1^T, spread over the grid, one
+// grid barrier per column.  M and R are r x r scratch (the system and its
+// right-hand sides, eliminated in place; column j of M is left as it was once
+// eliminated, being read no more).  status: 1 if a pivot is zero (C2
+// singular), 2 if a grid barrier expired.
+__global__ void __launch_bounds__(kJacThreads) k_solve_right(const double *__restrict__ C1,
+                                                            const double *__restrict__ C2, int r,
+                                                            double *__restrict__ M, double *__restrict__ R,
+                                                            double *__restrict__ B, int *status, JacCtl *ctl) {
+  __shared__ unsigned char used[kMaxDim];
+  __shared__ int piv[kMaxDim];
+  __shared__ double red_v[kJacThreads / 32];
+  __shared__ int red_i[kJacThreads / 32];
+  __shared__ int s_ok, s_p;
+  const int G = gridDim.x, tid = threadIdx.x, nt = blockDim.x;
+  const int gt = blockIdx.x * nt + tid, gn = G * nt, rr = r * r;
+  unsigned nbar = 0;
+  for (int e = gt; e < rr; e += gn) {
+    const int i = e / r, c = e % r;
+    M[e] = C2[c * r + i];
+    R[e] = C1[c * r + i];
+  }
+  for (int i = tid; i < r; i += nt) used[i] = 0;
+  if (!jac_sync(ctl, ++nbar * G, &s_ok)) {
+    if (tid == 0) atomicMax(status, 2);
+    return;
+  }
+  for (int j = 0; j < r; ++j) {
+    double bv = -1.0;
+    int bi = r;
+    for (int i = tid; i < r; i += nt)
+      if (!used[i]) {
+        const double v = fabs(__ldcg(M + i * r + j));
+        if (v > bv) {
+          bv = v;
+          bi = i;
+        }
+      }
+    for (int m = 16; m > 0; m >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, m);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, m);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if ((tid & 31) == 0) {
+      red_v[tid >> 5] = bv;
+      red_i[tid >> 5] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < nt / 32; ++w)
+        if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bi)) {
+          bv = red_v[w];
+          bi = red_i[w];
+        }
+      if (!(bv > 0.0)) {
+        if (blockIdx.x == 0) atomicMax(status, 1);
+        if (bi >= r)  // no finite candidate: take the first unused row
+          for (bi = 0; bi < r && used[bi]; ++bi) {
+          }
+      }
+      used[bi] = 1;
+      piv[j] = bi;
+      s_p = bi;
+    }
+    __syncthreads();
+    const int p = s_p;
+    const double mpj = __ldcg(M + p * r + j);
+    const double inv = mpj != 0.0 ? 1.0 / mpj : 0.0;
+    const int wm = r - j - 1, width = wm + r;  // columns j+1 .. r-1 of M, then every column of R
+    for (int e = gt; e < r * width; e += gn) {
+      const int i = e / width, c = e % width;
+      if (i == p) continue;
+      const double f = __ldcg(M + i * r + j) * inv;
+      if (c < wm) {
+        const int cc = j + 1 + c;
+        M[i * r + cc] = __ldcg(M + i * r + cc) - f * __ldcg(M + p * r + cc);
+      } else {
+        const int cc = c - wm;
+        R[i * r + cc] = __ldcg(R + i * r + cc) - f * __ldcg(R + p * r + cc);
+      }
+    }
+    if (!jac_sync(ctl, ++nbar * G, &s_ok)) {
+      if (tid == 0) atomicMax(status, 2);
+      return;
+    }
+  }
+  // row j of B^T is the pivot row of column j, divided by its pivot
+  for (int e = gt; e < rr; e += gn) {
+    const int j = e / r, c = e % r, p = piv[j];
+    const double d = __ldcg(M + p * r + j);
+    B[c * r + j] = d != 0.0 ? __ldcg(R + p * r + c) / d : 0.0;
+  }
 }
 
 // Z = sP * Z - a0 * M1 (M1^T Q)  (rank-one part of M2 applied to Q), r columns.
@@ -467,6 +705,77 @@ struct Scratch {
   }
 };
 
+// Blocks of the grid-wide Jacobi, Cholesky and solve kernels: one per SM, all
+// co-resident (cooperative launch).
+int coop_grid() {
+  static int g = -1;
+  if (g >= 0) return g;
+  int dev = 0, sms = 0, coop = 0, pj = 0, pc = 0, ps = 0;
+  g = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return g;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pj, k_jacobi, kJacThreads, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_chol_inv, kJacThreads, 0) != cudaSuccess || pj < 1 ||
+      pc < 1 || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_solve_right, kJacThreads, 0) != cudaSuccess ||
+      ps < 1)
+    return g;
+  g = std::min(sms, kJacMaxGrid);
+  return g;
+}
+
+// The context's control block for those kernels, zeroed on its stream.
+tlda_status coop_ctl(tlda_ctx *ctx, JacCtl **out, cudaStream_t s) {
+  if (coop_grid() < 1) return fail(ctx, TLDA_ERR_CUDA, "cooperative launch unavailable for the dense FP64 kernels");
+  if (!ctx->coop_ctl) CKF(cudaMalloc(&ctx->coop_ctl, sizeof(JacCtl)));
+  CKF(cudaMemsetAsync(ctx->coop_ctl, 0, sizeof(JacCtl), s));
+  *out = static_cast<JacCtl *>(ctx->coop_ctl);
+  return TLDA_OK;
+}
+
+// Diagonalises the symmetric r x r matrix A (device, overwritten): eigenvalues
+// to ev, eigenvector rows to Et.  Synchronises.
+tlda_status run_jacobi(tlda_ctx *ctx, double *A, int r, double *Et, double *ev, cudaStream_t s) {
+  JacCtl *ctl = nullptr;
+  if (tlda_status st = coop_ctl(ctx, &ctl, s)) return st;
+  int ms = 40;
+  void *args[] = {&A, &r, &Et, &ev, &ms, &ctl};
+  CKF(cudaLaunchCooperativeKernel((const void *)k_jacobi, dim3(coop_grid()), dim3(kJacThreads), args, 0, s));
+  int hs[3];
+  CKF(cudaMemcpyAsync(hs, &ctl->bar, sizeof hs, cudaMemcpyDeviceToHost, s));
+  CKF(cudaStreamSynchronize(s));
+  if (hs[1]) return fail(ctx, TLDA_ERR_TIMEOUT, "grid barrier of the Jacobi eigensolver expired");
+  ctx->jacobi_sweeps = hs[2];
+  return TLDA_OK;
+}
+
+// Enqueues k_chol_inv (asynchronous; failures land in *status).
+tlda_status run_chol_inv(tlda_ctx *ctx, double *A, int r, double *L, double *Z, double *Linv, double *LinvT64,
+                         float *LinvT32, int *status, cudaStream_t s) {
+  JacCtl *ctl = nullptr;
+  if (tlda_status st = coop_ctl(ctx, &ctl, s)) return st;
+  void *args[] = {&A, &r, &L, &Z, &Linv, &LinvT64, &LinvT32, &status, &ctl};
+  CKF(cudaLaunchCooperativeKernel((const void *)k_chol_inv, dim3(coop_grid()), dim3(kJacThreads), args, 0, s));
+  return TLDA_OK;
+}
+
+// Enqueues k_solve_right: B = C1 C2^-1 (asynchronous; failures land in *status).
+tlda_status run_solve_right(tlda_ctx *ctx, const double *C1, const double *C2, int r, double *M, double *R,
+                            double *B, int *status, cudaStream_t s) {
+  JacCtl *ctl = nullptr;
+  if (tlda_status st = coop_ctl(ctx, &ctl, s)) return st;
+  void *args[] = {&C1, &C2, &r, &M, &R, &B, &status, &ctl};
+  CKF(cudaLaunchCooperativeKernel((const void *)k_solve_right, dim3(coop_grid()), dim3(kJacThreads), args, 0, s));
+  return TLDA_OK;
+}
+
+// Maps the status word of k_chol_inv / k_solve_right to the call's result.
+tlda_status chol_status(tlda_ctx *ctx, int st, const char *breakdown) {
+  if (st >= 2) return fail(ctx, TLDA_ERR_TIMEOUT, "grid barrier of a dense FP64 kernel expired");
+  if (st == 1) return fail(ctx, TLDA_ERR_NUMERIC, breakdown);
+  return TLDA_OK;
+}
+
 tlda_status finalize(tlda_ctx *ctx) {
   cudaStream_t s = ctx->stream;
   const int V = ctx->V, D = ctx->D;
@@ -483,6 +792,7 @@ tlda_status finalize(tlda_ctx *ctx) {
   const double a0 = ctx->p.alpha0, sP = (a0 + 1.0) / (double)TS[1];
   Scratch sc;
   double *M1 = nullptr, *Q64 = nullptr, *Z64 = nullptr, *G = nullptr, *Linv = nullptr, *LinvT64 = nullptr;
+  double *Zr = nullptr;
   double *Bm = nullptr, *Ev = nullptr, *ev = nullptr, *m1q = nullptr, *U64 = nullptr, *lam = nullptr, *Ek = nullptr;
   float *M2 = nullptr, *Om = nullptr, *Y = nullptr, *Qf = nullptr, *LinvT32 = nullptr;
   int *status = nullptr;
@@ -498,6 +808,7 @@ tlda_status finalize(tlda_ctx *ctx) {
   CKF(sc.get(&Linv, (size_t)r * r));
   CKF(sc.get(&LinvT64, (size_t)r * r));
   CKF(sc.get(&LinvT32, (size_t)r * r));
+  CKF(sc.get(&Zr, (size_t)r * r));
   CKF(sc.get(&Bm, (size_t)r * r));
   CKF(sc.get(&Ev, (size_t)r * r));
   CKF(sc.get(&ev, (size_t)r));
@@ -510,47 +821,46 @@ tlda_status finalize(tlda_ctx *ctx) {
   k_m2_f32<<<(unsigned)((VV + 255) / 256), 256, 0, s>>>(ctx->P64, M1, V, sP, a0, M2);
   k_gauss<<<(unsigned)(((long long)V * r + 255) / 256), 256, 0, s>>>(Om, (long long)V * r, ctx->p.seed * 0x100000001B3ull + 17);
   // one CholeskyQR pass: out = in L^-T with L L^T = in^T in (FP64 Gram)
-  auto cholqr_pass = [&](const float *in, float *out) {
+  auto cholqr_pass = [&](const float *in, float *out) -> tlda_status {
     gemm_tn64<float, float>(in, r, in, r, G, r, r, r, V, s);
-    k_chol_inv<<<1, 256, 0, s>>>(G, r, Linv, status);
-    k_transpose_rr<<<(r * r + 255) / 256, 256, 0, s>>>(Linv, r, LinvT32, nullptr);
+    if (tlda_status st = run_chol_inv(ctx, G, r, Linv, Zr, nullptr, nullptr, LinvT32, status, s)) return st;
     gemm_nn<float>(in, r, LinvT32, r, out, r, V, r, r, s);
+    return TLDA_OK;
   };
   // CholeskyQR2 of Y into Qf (Y is clobbered)
-  auto cholqr2 = [&]() {
-    cholqr_pass(Y, Qf);
-    cholqr_pass(Qf, Y);
-    cudaMemcpyAsync(Qf, Y, sizeof(float) * (size_t)V * r, cudaMemcpyDeviceToDevice, s);
+  auto cholqr2 = [&]() -> tlda_status {
+    if (tlda_status st = cholqr_pass(Y, Qf)) return st;
+    if (tlda_status st = cholqr_pass(Qf, Y)) return st;
+    CKF(cudaMemcpyAsync(Qf, Y, sizeof(float) * (size_t)V * r, cudaMemcpyDeviceToDevice, s));
+    return TLDA_OK;
   };
   gemm_nn<float>(M2, V, Om, r, Y, r, V, r, V, s);
-  cholqr2();
+  if (tlda_status st = cholqr2()) return st;
   const int n_iter = 24;
   for (int it = 0; it < n_iter; ++it) {
     gemm_nn<float>(M2, V, Qf, r, Y, r, V, r, V, s);
-    cholqr2();
+    if (tlda_status st = cholqr2()) return st;
   }
   // FP64 Rayleigh-Ritz on the exact M2 = sP P - a0 M1 M1^T
   k_f2d<<<(unsigned)(((long long)V * r + 255) / 256), 256, 0, s>>>(Qf, Q64, (long long)V * r);
   // one FP64 CholeskyQR pass to make Q64 orthonormal to FP64 accuracy
   gemm_tn64<double, double>(Q64, r, Q64, r, G, r, r, r, V, s);
-  k_chol_inv<<<1, 256, 0, s>>>(G, r, Linv, status);
-  k_transpose_rr<<<(r * r + 255) / 256, 256, 0, s>>>(Linv, r, nullptr, LinvT64);
+  if (tlda_status st = run_chol_inv(ctx, G, r, Linv, Zr, nullptr, LinvT64, nullptr, status, s)) return st;
   gemm_nn<double>(Q64, r, LinvT64, r, Z64, r, V, r, r, s);
   cudaMemcpyAsync(Q64, Z64, sizeof(double) * (size_t)V * r, cudaMemcpyDeviceToDevice, s);
   gemm_nn<double>(ctx->P64, V, Q64, r, Z64, r, V, r, V, s);
   gemm_tn64<double, double>(M1, 1, Q64, r, m1q, r, 1, r, V, s);
   k_rank1_fix<<<(unsigned)(((long long)V * r + 255) / 256), 256, 0, s>>>(Z64, M1, m1q, V, r, sP, a0);
   gemm_tn64<double, double>(Q64, r, Z64, r, Bm, r, r, r, V, s);
-  int *sweeps = status + 1;
-  k_jacobi<<<1, 512, 0, s>>>(Bm, r, Ev, ev, 40, sweeps);
   CKF(cudaGetLastError());
+  if (tlda_status js = run_jacobi(ctx, Bm, r, Ev, ev, s)) return js;
   std::vector<double> hev(r), hEv((size_t)r * r);
   int hstat[2];
   CKF(cudaMemcpyAsync(hev.data(), ev, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
   CKF(cudaMemcpyAsync(hEv.data(), Ev, sizeof(double) * r * r, cudaMemcpyDeviceToHost, s));
   CKF(cudaMemcpyAsync(hstat, status, sizeof hstat, cudaMemcpyDeviceToHost, s));
   CKF(cudaStreamSynchronize(s));
-  if (hstat[0]) return fail(ctx, TLDA_ERR_NUMERIC, "subspace basis lost rank (CholeskyQR breakdown)");
+  if (tlda_status st = chol_status(ctx, hstat[0], "subspace basis lost rank (CholeskyQR breakdown)")) return st;
   // order the Ritz pairs by descending value and keep D of them
   std::vector<int> ord(r);
   for (int i = 0; i < r; ++i) ord[i] = i;
@@ -558,7 +868,7 @@ tlda_status finalize(tlda_ctx *ctx) {
   std::vector<double> hEk((size_t)r * D), hlam(D);
   for (int j = 0; j < D; ++j) {
     hlam[j] = hev[ord[j]];
-    for (int i = 0; i < r; ++i) hEk[(size_t)i * D + j] = hEv[(size_t)i * r + ord[j]];
+    for (int i = 0; i < r; ++i) hEk[(size_t)i * D + j] = hEv[(size_t)ord[j] * r + i];
   }
   if (!(hlam[D - 1] > 1e-12 * hlam[0]))
     return fail(ctx, TLDA_ERR_NUMERIC, "M2 has fewer than D positive eigenvalues");
@@ -638,40 +948,6 @@ __global__ void __launch_bounds__(256) k_online_acc(const int32_t *indptr, const
   }
 }
 
-// In-place inverse of an n x n FP64 matrix (row-major) by Gauss-Jordan
-// elimination with partial pivoting; false if it is singular.
-bool host_inverse(std::vector<double> &A, int n) {
-  std::vector<double> I((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
-  for (int c = 0; c < n; ++c) {
-    int piv = c;
-    for (int i = c + 1; i < n; ++i)
-      if (std::fabs(A[(size_t)i * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = i;
-    if (!(std::fabs(A[(size_t)piv * n + c]) > 0.0)) return false;
-    if (piv != c)
-      for (int j = 0; j < n; ++j) {
-        std::swap(A[(size_t)c * n + j], A[(size_t)piv * n + j]);
-        std::swap(I[(size_t)c * n + j], I[(size_t)piv * n + j]);
-      }
-    const double d = A[(size_t)c * n + c];
-    for (int j = 0; j < n; ++j) {
-      A[(size_t)c * n + j] /= d;
-      I[(size_t)c * n + j] /= d;
-    }
-    for (int i = 0; i < n; ++i) {
-      if (i == c) continue;
-      const double f = A[(size_t)i * n + c];
-      if (f == 0.0) continue;
-      for (int j = 0; j < n; ++j) {
-        A[(size_t)i * n + j] -= f * A[(size_t)c * n + j];
-        I[(size_t)i * n + j] -= f * I[(size_t)c * n + j];
-      }
-    }
-  }
-  A.swap(I);
-  return true;
-}
-
 // Rebuilds the whitening from the online statistics (section "Fully Online
 // Implementation", the PCA update): with M1 = C/T, the sketch of
 // M2 = (alpha0+1) P/S2 - alpha0 M1 M1^T is Y = (alpha0+1)/S2 Z - alpha0 M1 (M1^T Omega);
@@ -680,6 +956,24 @@ bool host_inverse(std::vector<double> &A, int n) {
 // B (Q^T Omega) = Q^T Y, B symmetrised, B = E Lambda E^T (Jacobi), U = Q E,
 // and W = U_D Lambda_D^-1/2 with the signs of fit_moments, m1 = W^T M1, U.
 // The previous W is kept in on_Wold.
+// Workspace of a re-whitening (one FP64 allocation, made by tlda_online_begin).
+struct OnlineWs {
+  double *Y, *Q1, *Q2, *M1, *U64;               // V x r (three), V, V x D
+  double *G, *Z, *LinvT, *L1, *L2, *L1T, *C1, *C2, *Bm, *Et, *Ms, *Rs;  // r x r
+  double *m1q, *ev, *Ek, *lam;                  // r, r, r x D, D
+  static size_t words(size_t V, size_t r, size_t D) { return 3 * V * r + V + V * D + 12 * r * r + 2 * r + r * D + D; }
+  OnlineWs(double *w, size_t V, size_t r, size_t D) {
+    double **rr_bufs[] = {&G, &Z, &LinvT, &L1, &L2, &L1T, &C1, &C2, &Bm, &Et, &Ms, &Rs};
+    Y = w, Q1 = Y + V * r, Q2 = Q1 + V * r, M1 = Q2 + V * r, U64 = M1 + V;
+    w = U64 + V * D;
+    for (double **b : rr_bufs) {
+      *b = w;
+      w += r * r;
+    }
+    m1q = w, ev = m1q + r, Ek = ev + r, lam = Ek + r * D;
+  }
+};
+
 tlda_status online_rewhiten(tlda_ctx *ctx) {
   cudaStream_t s = ctx->stream;
   const int V = ctx->V, D = ctx->D, r = ctx->on_r;
@@ -691,69 +985,38 @@ tlda_status online_rewhiten(tlda_ctx *ctx) {
   if (ferr) return fail(ctx, TLDA_ERR_INVALID, "corrupt CSR batch in the online pass");
   if (TS[0] == 0 || TS[1] == 0) return fail(ctx, TLDA_ERR_NUMERIC, "no token pairs accumulated");
   const double a0 = ctx->p.alpha0, sP = (a0 + 1.0) / (double)TS[1];
-  Scratch sc;
-  double *M1 = nullptr, *m1q = nullptr, *Y = nullptr, *Q1 = nullptr, *Q2 = nullptr, *G = nullptr;
-  double *Linv = nullptr, *LinvT = nullptr, *C1 = nullptr, *C2 = nullptr, *Bm = nullptr, *Ev = nullptr;
-  double *ev = nullptr, *Ek = nullptr, *U64 = nullptr, *lam = nullptr;
-  int *status = nullptr;
-  CKF(sc.get(&M1, V));
-  CKF(sc.get(&m1q, r));
-  CKF(sc.get(&Y, (size_t)V * r));
-  CKF(sc.get(&Q1, (size_t)V * r));
-  CKF(sc.get(&Q2, (size_t)V * r));
-  CKF(sc.get(&G, (size_t)r * r));
-  CKF(sc.get(&Linv, (size_t)r * r));
-  CKF(sc.get(&LinvT, (size_t)r * r));
-  CKF(sc.get(&C1, (size_t)r * r));
-  CKF(sc.get(&C2, (size_t)r * r));
-  CKF(sc.get(&Bm, (size_t)r * r));
-  CKF(sc.get(&Ev, (size_t)r * r));
-  CKF(sc.get(&ev, r));
-  CKF(sc.get(&Ek, (size_t)r * D));
-  CKF(sc.get(&U64, (size_t)V * D));
-  CKF(sc.get(&lam, D));
-  CKF(sc.get(&status, 2, true));
-  k_m1<<<(V + 255) / 256, 256, 0, s>>>(ctx->on_C, ctx->on_TS, V, M1);
-  gemm_tn64<double, double>(M1, 1, ctx->on_Om, r, m1q, r, 1, r, V, s);
-  CKF(cudaMemcpyAsync(Y, ctx->on_Z, sizeof(double) * (size_t)V * r, cudaMemcpyDeviceToDevice, s));
-  k_rank1_fix<<<(unsigned)(((long long)V * r + 255) / 256), 256, 0, s>>>(Y, M1, m1q, V, r, sP, a0);
-  // CholeskyQR2: out = in L^-T with L L^T = in^T in, twice
-  auto cholqr_pass = [&](const double *in, double *out) {
-    gemm_tn64<double, double>(in, r, in, r, G, r, r, r, V, s);
-    k_chol_inv<<<1, 256, 0, s>>>(G, r, Linv, status);
-    k_transpose_rr<<<(r * r + 255) / 256, 256, 0, s>>>(Linv, r, nullptr, LinvT);
-    gemm_nn<double>(in, r, LinvT, r, out, r, V, r, r, s);
+  OnlineWs w(ctx->on_ws, V, r, D);
+  int *status = ctx->on_status;
+  CKF(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));
+  k_m1<<<(V + 255) / 256, 256, 0, s>>>(ctx->on_C, ctx->on_TS, V, w.M1);
+  gemm_tn64<double, double>(w.M1, 1, ctx->on_Om, r, w.m1q, r, 1, r, V, s);
+  CKF(cudaMemcpyAsync(w.Y, ctx->on_Z, sizeof(double) * (size_t)V * r, cudaMemcpyDeviceToDevice, s));
+  k_rank1_fix<<<(unsigned)(((long long)V * r + 255) / 256), 256, 0, s>>>(w.Y, w.M1, w.m1q, V, r, sP, a0);
+  // CholeskyQR2: out = in L^-T with L L^T = in^T in, twice; Y = Q2 (L1 L2)^T
+  auto cholqr_pass = [&](const double *in, double *out, double *Lf) -> tlda_status {
+    gemm_tn64<double, double>(in, r, in, r, w.G, r, r, r, V, s);
+    if (tlda_status st = run_chol_inv(ctx, w.G, r, Lf, w.Z, nullptr, w.LinvT, nullptr, status, s)) return st;
+    gemm_nn<double>(in, r, w.LinvT, r, out, r, V, r, r, s);
+    return TLDA_OK;
   };
-  cholqr_pass(Y, Q1);
-  cholqr_pass(Q1, Q2);
-  gemm_tn64<double, double>(Q2, r, Y, r, C1, r, r, r, V, s);           // Q^T Y
-  gemm_tn64<double, double>(Q2, r, ctx->on_Om, r, C2, r, r, r, V, s);  // Q^T Omega
+  if (tlda_status st = cholqr_pass(w.Y, w.Q1, w.L1)) return st;
+  if (tlda_status st = cholqr_pass(w.Q1, w.Q2, w.L2)) return st;
+  gemm_tn64<double, double>(w.Q2, r, ctx->on_Om, r, w.C2, r, r, r, V, s);  // Q^T Omega
+  // Q^T Y = R = (L1 L2)^T = L2^T L1^T
+  k_transpose_rr<<<(r * r + 255) / 256, 256, 0, s>>>(w.L1, r, nullptr, w.L1T);
+  gemm_tn64<double, double>(w.L2, r, w.L1T, r, w.C1, r, r, r, r, s);
+  // B = (Q^T Y)(Q^T Omega)^-1, symmetrised by the eigensolver
+  if (tlda_status st = run_solve_right(ctx, w.C1, w.C2, r, w.Ms, w.Rs, w.Bm, status + 1, s)) return st;
   CKF(cudaGetLastError());
-  std::vector<double> hC1((size_t)r * r), hC2((size_t)r * r);
   int hstat[2];
-  CKF(cudaMemcpyAsync(hC1.data(), C1, sizeof(double) * r * r, cudaMemcpyDeviceToHost, s));
-  CKF(cudaMemcpyAsync(hC2.data(), C2, sizeof(double) * r * r, cudaMemcpyDeviceToHost, s));
   CKF(cudaMemcpyAsync(hstat, status, sizeof hstat, cudaMemcpyDeviceToHost, s));
   CKF(cudaStreamSynchronize(s));
-  if (hstat[0]) return fail(ctx, TLDA_ERR_NUMERIC, "sketch basis lost rank (CholeskyQR breakdown)");
-  if (!host_inverse(hC2, r)) return fail(ctx, TLDA_ERR_NUMERIC, "Q^T Omega is singular");
-  std::vector<double> hB((size_t)r * r, 0.0);
-  for (int i = 0; i < r; ++i)
-    for (int k = 0; k < r; ++k) {
-      const double c = hC1[(size_t)i * r + k];
-      for (int j = 0; j < r; ++j) hB[(size_t)i * r + j] += c * hC2[(size_t)k * r + j];
-    }
-  for (int i = 0; i < r; ++i)
-    for (int j = i + 1; j < r; ++j) {
-      const double v = 0.5 * (hB[(size_t)i * r + j] + hB[(size_t)j * r + i]);
-      hB[(size_t)i * r + j] = hB[(size_t)j * r + i] = v;
-    }
-  CKF(cudaMemcpyAsync(Bm, hB.data(), sizeof(double) * r * r, cudaMemcpyHostToDevice, s));
-  k_jacobi<<<1, 512, 0, s>>>(Bm, r, Ev, ev, 40, status + 1);
-  CKF(cudaGetLastError());
+  if (tlda_status st = chol_status(ctx, hstat[0], "sketch basis lost rank (CholeskyQR breakdown)")) return st;
+  if (tlda_status st = chol_status(ctx, hstat[1], "Q^T Omega is singular")) return st;
+  if (tlda_status js = run_jacobi(ctx, w.Bm, r, w.Et, w.ev, s)) return js;
   std::vector<double> hev(r), hEv((size_t)r * r);
-  CKF(cudaMemcpyAsync(hev.data(), ev, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
-  CKF(cudaMemcpyAsync(hEv.data(), Ev, sizeof(double) * r * r, cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(hev.data(), w.ev, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(hEv.data(), w.Et, sizeof(double) * r * r, cudaMemcpyDeviceToHost, s));
   CKF(cudaStreamSynchronize(s));
   std::vector<int> ord(r);
   for (int i = 0; i < r; ++i) ord[i] = i;
@@ -761,18 +1024,18 @@ tlda_status online_rewhiten(tlda_ctx *ctx) {
   std::vector<double> hEk((size_t)r * D), hlam(D);
   for (int j = 0; j < D; ++j) {
     hlam[j] = hev[ord[j]];
-    for (int i = 0; i < r; ++i) hEk[(size_t)i * D + j] = hEv[(size_t)i * r + ord[j]];
+    for (int i = 0; i < r; ++i) hEk[(size_t)i * D + j] = hEv[(size_t)ord[j] * r + i];
   }
   if (!(hlam[D - 1] > 1e-12 * hlam[0]))
     return fail(ctx, TLDA_ERR_NUMERIC, "the sketched M2 has fewer than D positive eigenvalues");
-  CKF(cudaMemcpyAsync(Ek, hEk.data(), sizeof(double) * r * D, cudaMemcpyHostToDevice, s));
-  CKF(cudaMemcpyAsync(lam, hlam.data(), sizeof(double) * D, cudaMemcpyHostToDevice, s));
-  gemm_nn<double>(Q2, r, Ek, D, U64, D, V, D, r, s);
+  CKF(cudaMemcpyAsync(w.Ek, hEk.data(), sizeof(double) * r * D, cudaMemcpyHostToDevice, s));
+  CKF(cudaMemcpyAsync(w.lam, hlam.data(), sizeof(double) * D, cudaMemcpyHostToDevice, s));
+  gemm_nn<double>(w.Q2, r, w.Ek, D, w.U64, D, V, D, r, s);
   if (ctx->whitened)
     CKF(cudaMemcpyAsync(ctx->on_Wold, ctx->W32, sizeof(float) * (size_t)V * D, cudaMemcpyDeviceToDevice, s));
-  k_make_w<<<D, 256, 0, s>>>(U64, V, D, lam, ctx->W32, nullptr, nullptr);
+  k_make_w<<<D, 256, 0, s>>>(w.U64, V, D, w.lam, ctx->W32, nullptr, nullptr);
   CKF(cudaMemsetAsync(ctx->m1, 0, sizeof(float) * ctx->Dp, s));
-  k_wtm1<<<D, 256, 0, s>>>(ctx->W32, M1, V, D, ctx->m1);
+  k_wtm1<<<D, 256, 0, s>>>(ctx->W32, w.M1, V, D, ctx->m1);
   launch_make_u(ctx->W32, ctx->m1, V, D, ctx->Dp, ctx->U32, ctx->U16, s);
   CKF(cudaGetLastError());
   CKF(cudaStreamSynchronize(s));
@@ -785,26 +1048,23 @@ tlda_status online_rewhiten(tlda_ctx *ctx) {
 tlda_status online_rotate(tlda_ctx *ctx, float *Phi) {
   cudaStream_t s = ctx->stream;
   const int V = ctx->V, D = ctx->D, K = ctx->K;
-  Scratch sc;
-  double *A = nullptr, *G = nullptr;
-  CKF(sc.get(&A, (size_t)D * D));
-  CKF(sc.get(&G, (size_t)D * D));
-  gemm_tn64<float, float>(ctx->W32, D, ctx->on_Wold, D, A, D, D, D, V, s);
-  gemm_tn64<float, float>(ctx->on_Wold, D, ctx->on_Wold, D, G, D, D, D, V, s);
+  OnlineWs w(ctx->on_ws, V, ctx->on_r, D);  // r x r buffers hold the D x D ones (D <= r)
+  int *status = ctx->on_status;
+  CKF(cudaMemsetAsync(status, 0, sizeof(int), s));
+  gemm_tn64<float, float>(ctx->W32, D, ctx->on_Wold, D, w.C1, D, D, D, V, s);
+  gemm_tn64<float, float>(ctx->on_Wold, D, ctx->on_Wold, D, w.C2, D, D, D, V, s);
+  // R = (W^T W_old)(W_old^T W_old)^-1
+  if (tlda_status st = run_solve_right(ctx, w.C1, w.C2, D, w.Ms, w.Rs, w.Bm, status, s)) return st;
   CKF(cudaGetLastError());
-  std::vector<double> hA((size_t)D * D), hG((size_t)D * D);
+  std::vector<double> R((size_t)D * D);
   std::vector<float> hP((size_t)D * K);
-  CKF(cudaMemcpyAsync(hA.data(), A, sizeof(double) * D * D, cudaMemcpyDeviceToHost, s));
-  CKF(cudaMemcpyAsync(hG.data(), G, sizeof(double) * D * D, cudaMemcpyDeviceToHost, s));
+  int hst = 0;
+  CKF(cudaMemcpyAsync(R.data(), w.Bm, sizeof(double) * D * D, cudaMemcpyDeviceToHost, s));
   CKF(cudaMemcpyAsync(hP.data(), Phi, sizeof(float) * D * K, cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(&hst, status, sizeof hst, cudaMemcpyDeviceToHost, s));
   CKF(cudaStreamSynchronize(s));
-  if (!host_inverse(hG, D)) return fail(ctx, TLDA_ERR_NUMERIC, "W^T W of the previous whitening is singular");
-  std::vector<double> R((size_t)D * D, 0.0), hN((size_t)D * K, 0.0);
-  for (int i = 0; i < D; ++i)
-    for (int k = 0; k < D; ++k) {
-      const double a = hA[(size_t)i * D + k];
-      for (int j = 0; j < D; ++j) R[(size_t)i * D + j] += a * hG[(size_t)k * D + j];
-    }
+  if (tlda_status st = chol_status(ctx, hst, "W^T W of the previous whitening is singular")) return st;
+  std::vector<double> hN((size_t)D * K, 0.0);
   for (int i = 0; i < D; ++i)
     for (int k = 0; k < D; ++k) {
       const double rr = R[(size_t)i * D + k];
@@ -879,6 +1139,7 @@ tlda_status tlda_unwhiten_topics(tlda_ctx *ctx, const float *Phi, double *mu_out
   const int V = ctx->V, D = ctx->D, K = ctx->K;
   Scratch sc;
   double *W64 = nullptr, *G = nullptr, *Linv = nullptr, *LinvT = nullptr, *Ginv = nullptr, *T = nullptr;
+  double *Lf = nullptr, *Zs = nullptr;
   double *mu = nullptr, *al = nullptr;
   int *status = nullptr;
   CKF(sc.get(&W64, (size_t)V * D));
@@ -886,6 +1147,8 @@ tlda_status tlda_unwhiten_topics(tlda_ctx *ctx, const float *Phi, double *mu_out
   CKF(sc.get(&Linv, (size_t)D * D));
   CKF(sc.get(&LinvT, (size_t)D * D));
   CKF(sc.get(&Ginv, (size_t)D * D));
+  CKF(sc.get(&Lf, (size_t)D * D));
+  CKF(sc.get(&Zs, (size_t)D * D));
   CKF(sc.get(&T, (size_t)D * K));
   CKF(sc.get(&status, 1, true));
   const bool host = flags & TLDA_HOST_OUTPUT;
@@ -898,8 +1161,7 @@ tlda_status tlda_unwhiten_topics(tlda_ctx *ctx, const float *Phi, double *mu_out
   }
   k_f2d<<<(unsigned)(((long long)V * D + 255) / 256), 256, 0, s>>>(ctx->W32, W64, (long long)V * D);
   gemm_tn64<double, double>(W64, D, W64, D, G, D, D, D, V, s);         // W^T W
-  k_chol_inv<<<1, 256, 0, s>>>(G, D, Linv, status);
-  k_transpose_rr<<<(D * D + 255) / 256, 256, 0, s>>>(Linv, D, nullptr, LinvT);
+  if (tlda_status st = run_chol_inv(ctx, G, D, Lf, Zs, Linv, LinvT, nullptr, status, s)) return st;
   gemm_nn<double>(LinvT, D, Linv, D, Ginv, D, D, D, D, s);              // (W^T W)^-1 = L^-T L^-1
   k_unwhiten_coef<<<1, 256, 0, s>>>(Phi, D, K, Ginv, T, al);
   gemm_nn<double>(W64, D, T, K, mu, K, V, K, D, s);                     // mu = W (W^T W)^-1 Phi diag(|phi|^2)
@@ -912,7 +1174,7 @@ tlda_status tlda_unwhiten_topics(tlda_ctx *ctx, const float *Phi, double *mu_out
     CKF(cudaMemcpyAsync(alpha_out, al, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
   }
   CKF(cudaStreamSynchronize(s));
-  if (hst) return fail(ctx, TLDA_ERR_NUMERIC, "W^T W is not positive definite");
+  if (tlda_status st = chol_status(ctx, hst, "W^T W is not positive definite")) return st;
   return TLDA_OK;
 }
 
@@ -924,15 +1186,18 @@ tlda_status tlda_online_begin(tlda_ctx *ctx, const double *Omega, int32_t r) {
   if (ctx->on_r != r) {
     if (ctx->on_Om) cudaFree(ctx->on_Om);
     if (ctx->on_Z) cudaFree(ctx->on_Z);
-    ctx->on_Om = ctx->on_Z = nullptr;
+    if (ctx->on_ws) cudaFree(ctx->on_ws);
+    ctx->on_Om = ctx->on_Z = ctx->on_ws = nullptr;
     ctx->on_r = 0;
     CKF(dalloc(&ctx->on_Om, V * r));
     CKF(dalloc(&ctx->on_Z, V * r));
+    CKF(dalloc(&ctx->on_ws, OnlineWs::words(V, r, ctx->D)));
     ctx->on_r = r;
   }
   if (!ctx->on_C) CKF(dalloc(&ctx->on_C, V));
   if (!ctx->on_TS) CKF(dalloc(&ctx->on_TS, 3));
   if (!ctx->on_err) CKF(dalloc(&ctx->on_err, 1));
+  if (!ctx->on_status) CKF(dalloc(&ctx->on_status, 2));
   if (!ctx->on_Wold) CKF(dalloc(&ctx->on_Wold, V * ctx->D));
   cudaStream_t s = ctx->stream;
   CKF(cudaMemcpyAsync(ctx->on_Om, Omega, sizeof(double) * V * r, cudaMemcpyDeviceToDevice, s));

@@ -430,6 +430,8 @@ void tlda_default_params(tlda_params *p, int32_t k) {
 
 const char *tlda_last_error(const tlda_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
 
+int32_t tlda_eig_sweeps(const tlda_ctx *ctx) { return ctx ? ctx->jacobi_sweeps : -1; }
+
 tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, void *cuda_stream) {
   if (!out || !p) return TLDA_ERR_INVALID;
   *out = nullptr;
@@ -535,7 +537,8 @@ tlda_status tlda_destroy(tlda_ctx *ctx) {
   dfree(ctx->TS); dfree(ctx->fit_err); dfree(ctx->stage[0]); dfree(ctx->stage[1]);
   dfree(ctx->ctl); dfree(ctx->st_tune); dfree(ctx->dlosses); dfree(ctx->phi_scratch);
   dfree(ctx->on_Om); dfree(ctx->on_Z); dfree(ctx->on_C); dfree(ctx->on_TS); dfree(ctx->on_err);
-  dfree(ctx->on_Wold);
+  dfree(ctx->on_Wold); dfree(ctx->on_ws); dfree(ctx->on_status);
+  if (ctx->coop_ctl) cudaFree(ctx->coop_ctl);
   if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
   for (cudaEvent_t ev : ctx->ev_seg)
     if (ev) cudaEventDestroy(ev);

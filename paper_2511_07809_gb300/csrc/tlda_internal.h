@@ -164,6 +164,10 @@ struct tlda_ctx {
   unsigned long long *on_C = nullptr, *on_TS = nullptr;  // V; T, S2, S3
   int *on_err = nullptr;
   float *on_Wold = nullptr;            // V x D: the whitening before the last rebuild
+  double *on_ws = nullptr;             // workspace of a re-whitening (V x r x 3 + r x r x 12 + ...)
+  int *on_status = nullptr;            // its device status words
+  int jacobi_sweeps = 0;               // sweeps of the last symmetric eigensolve
+  void *coop_ctl = nullptr;            // control block of the grid-wide FP64 kernels (k_fit.cu)
   // pass staging (host input)
   int32_t *stage[2] = {nullptr, nullptr};
   long long stage_cap = 0;

@@ -37,7 +37,7 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_cp_data_term", "tlda_cp_pass", "tlda_unwhiten_topics",
                 "tlda_profile", "tlda_profile_read", "tlda_save_state", "tlda_load_state",
                 "tlda_cp_step_noalloc", "tlda_autotune", "tlda_online_begin",
-                "tlda_online_pass")
+                "tlda_online_pass", "tlda_eig_sweeps")
 
 
 class Params(ctypes.Structure):
@@ -74,6 +74,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "tlda_create": (i32, [P(vp), i32, P(Params), vp]),
         "tlda_destroy": (i32, [vp]),
         "tlda_last_error": (ctypes.c_char_p, [vp]),
+        "tlda_eig_sweeps": (i32, [vp]),
         "tlda_sync": (i32, [vp]),
         "tlda_fit_moments": (i32, [vp, P(CSR), u32]),
         "tlda_get_whitening": (i32, [vp, vp, vp, vp]),
@@ -204,6 +205,10 @@ class TLDA:
         self._check(self.lib.tlda_get_whitening(self.h, W.data_ptr(), m1.data_ptr(),
                                                 ev.ctypes.data))
         return W, m1, ev
+
+    def eig_sweeps(self) -> int:
+        """Jacobi sweeps of the last whitening's eigensolve (diagnostic)."""
+        return int(self.lib.tlda_eig_sweeps(self.h))
 
     def get_counts(self):
         C = np.zeros(self.V, dtype=np.int64)

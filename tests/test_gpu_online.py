@@ -44,6 +44,7 @@ def test_online_whitening_matches_oracle_sketch(lib):
     assert C.rel(W.cpu().numpy(), Wo) < 1e-5
     assert C.rel(m1.cpu().numpy(), m1o) < 1e-5
     assert torch.equal(Phi.cpu(), torch.tensor(Phi0, dtype=torch.float32))  # one block: no rotation, lr = 0
+    assert 1 <= t.eig_sweeps() < 40
     t.close()
 
 
@@ -82,6 +83,7 @@ def test_online_pass_bf16_persistent_kernel(lib):
     Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
     lr = 5e-4
     losses = t.online_pass(lib.DeviceCSR.from_corpus(c), offs, Phi, lr, rewhiten_every=8, losses=True)
+    assert 1 <= t.eig_sweeps() < 40
     P, _, lo = O.online_pass(c.indptr, c.indices, c.counts, sp.V, offs, Om, 8, float(sp.alpha0), 0.0, lr,
                              Phi0.astype(np.float64), sp.K)
     assert C.rel(Phi.cpu().numpy(), P) < 2e-2
@@ -94,6 +96,7 @@ def test_online_arguments(lib):
     t = lib.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0))
     c = C.corpus("small_v500_k10", 1000)
     Phi = torch.zeros((sp.K, sp.K), dtype=torch.float32, device="cuda")
+    assert t.eig_sweeps() == 0
     with pytest.raises(lib.TLDAError) as e:
         t.online_pass(lib.DeviceCSR.from_corpus(c), [0, 1000], Phi, 0.01)
     assert e.value.status == lib.ERR_STATE

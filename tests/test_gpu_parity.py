@@ -276,6 +276,7 @@ def test_fit_moments_small(lib):
     # same subspace and same signed eigenvectors (eigengap here is well above 1e-6 lambda_1)
     assert C.rel(Wg, Wo) < 1e-4
     assert C.rel(m1g.cpu().numpy(), Wo.T @ M1) < 1e-4
+    assert 1 <= t.eig_sweeps() < 40  # the Jacobi eigensolve converged before its sweep cap
 
 
 def test_unwhiten_population_factors(lib):
