@@ -214,14 +214,15 @@ __device__ __forceinline__ unsigned jac_ld_acquire(const unsigned *p) {
   return v;
 }
 
-// Grid barrier of a cooperative launch (every block resident): bounded to
-// about a second; false if it expired here or any block flagged an abort.
+// Grid barrier of a cooperative launch (every block resident): a release
+// increment of the arrival counter, then acquire loads until it reaches
+// `target`; bounded to about a second; false if it expired here or any block
+// flagged an abort.
 __device__ bool jac_sync(JacCtl *ctl, unsigned target, int *s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    atomicAdd(&ctl->bar, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar) : "memory");
     const long long t0 = clock64();
     while (jac_ld_acquire(&ctl->bar) < target) {
       if (*reinterpret_cast<volatile int *>(&ctl->abort)) {
@@ -234,7 +235,6 @@ __device__ bool jac_sync(JacCtl *ctl, unsigned target, int *s_ok) {
         break;
       }
     }
-    __threadfence();
     *reinterpret_cast<volatile int *>(s_ok) = ok;
   }
   __syncthreads();

@@ -588,15 +588,16 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   return v;
 }
 
-// Grid barrier (every block is resident: cooperative launch): waits until the
-// launch's monotone arrival counter reaches `target`.  Bounded; false if it
-// expired here, or if any block flagged an abort.
+// Grid barrier (every block is resident: cooperative launch): a release
+// increment of the launch's monotone arrival counter, then acquire loads until
+// it reaches `target`.  Bounded; false if it expired here, or if any block
+// flagged an abort.
 __device__ bool grid_sync(PassCtl *ctl, unsigned target, int *s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    atomicAdd(&ctl->bar, 1u);
+    // release: this block's writes (ordered before by the block barrier)
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar) : "memory");
     const long long t0 = clock64();
     while (ld_acquire(&ctl->bar) < target) {
       if (*reinterpret_cast<volatile int *>(&ctl->abort)) {
@@ -609,7 +610,6 @@ __device__ bool grid_sync(PassCtl *ctl, unsigned target, int *s_ok) {
         break;
       }
     }
-    __threadfence();
     *reinterpret_cast<volatile int *>(s_ok) = ok;
   }
   __syncthreads();
