@@ -108,6 +108,10 @@ __device__ __forceinline__ float block_sum(float v, float *red) {
 
 // One block's tile engine: shared-memory views, TMEM columns and the phases
 // of its mbarriers (0: Phi image, 1: Y/R and G products, 2-3: Q buffers).
+struct NoPre {
+  __device__ bool operator()() const { return true; }
+};
+
 struct Fused {
   unsigned char *sm, *sPhi, *sQ, *sQ2, *sF;
   float *sY, *sZ;
@@ -247,10 +251,15 @@ struct Fused {
   // The data term of tiles tile0, tile0 + tstride, ... of batch b (td <= kT
   // documents each), added to the G columns.  S3 and validation bits go to
   // S3_dst and err_dst, the per-document loss parts to lacc.  Expects the Phi
-  // image in shared memory, or (phi_pending) its bulk copy on barrier 0 in
-  // flight, waited for before the first MMA.  Returns false on an expired wait.
+  // image in shared memory, or (phi_pending) its bulk copy on barrier 0: then
+  // pre() runs once, by every thread, after the first window's CSR slice and
+  // U rows are requested and before the first MMA (it starts the copy, after
+  // whatever the image waits for; false if that failed), and the copy is
+  // waited for.  Returns false on an expired wait.
+  template <class Pre = NoPre>
   __device__ bool tiles(const StepArgs &a, const BatchDesc &b, int tile0, int tstride, int td, float &lacc,
-                        bool &g_init, unsigned long long *S3_dst, int *err_dst, bool phi_pending = false) {
+                        bool &g_init, unsigned long long *S3_dst, int *err_dst, bool phi_pending = false,
+                        Pre pre = Pre()) {
     const int nd = b.n_docs;
     const int ntiles = nd > 0 ? (nd + td - 1) / td : 0;
     const uint32_t idQ = idesc_bf16(128, 128);
@@ -382,8 +391,9 @@ struct Fused {
         else cp_async_wait_all();
         put_f(0, true);
         fence_proxy_async();
-        if (phi_pending) {  // the Phi^T image (bulk copy issued with the tile set-up)
-          phi_wait();
+        if (phi_pending) {  // the Phi^T image: its bulk copy, started by pre()
+          if (pre()) phi_wait();
+          else fail();
           phi_pending = false;
         }
         __syncthreads();
@@ -547,7 +557,10 @@ struct Fused {
       if (__syncthreads_or(failed())) break;
     }
     cp_async_wait_all();
-    if (phi_pending) phi_wait();  // no tile reached an MMA: still consume the copy's phase
+    if (phi_pending) {  // no tile reached an MMA: still run pre() and consume the copy's phase
+      if (pre()) phi_wait();
+      else fail();
+    }
     __syncthreads();
     return !failed();
   }
@@ -588,16 +601,20 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   return v;
 }
 
-// Grid barrier (every block is resident: cooperative launch): a release
-// increment of the launch's monotone arrival counter, then acquire loads until
-// it reaches `target`.  Bounded; false if it expired here, or if any block
-// flagged an abort.
-__device__ bool grid_sync(PassCtl *ctl, unsigned target, int *s_ok) {
+// Grid barrier (every block is resident: cooperative launch) in two halves:
+// grid_arrive is a release increment of the launch's monotone arrival
+// counter, grid_wait polls it with acquire loads until it reaches `target`
+// (bounded; false if it expired here, or if any block flagged an abort).
+// Work that needs nothing from the other blocks can run between the two.
+__device__ void grid_arrive(PassCtl *ctl) {
   __syncthreads();
+  // release: this block's writes (ordered before by the block barrier)
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar) : "memory");
+}
+
+__device__ bool grid_wait(PassCtl *ctl, unsigned target, int *s_ok) {
   if (threadIdx.x == 0) {
     int ok = 1;
-    // release: this block's writes (ordered before by the block barrier)
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar) : "memory");
     const long long t0 = clock64();
     while (ld_acquire(&ctl->bar) < target) {
       if (*reinterpret_cast<volatile int *>(&ctl->abort)) {
@@ -614,6 +631,11 @@ __device__ bool grid_sync(PassCtl *ctl, unsigned target, int *s_ok) {
   }
   __syncthreads();
   return *reinterpret_cast<volatile int *>(s_ok) != 0;
+}
+
+__device__ bool grid_sync(PassCtl *ctl, unsigned target, int *s_ok) {
+  grid_arrive(ctl);
+  return grid_wait(ctl, target, s_ok);
 }
 
 __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs p) {
@@ -639,11 +661,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
   if (tid < 128) s_m1[tid] = tid < D ? a.m1[tid] : 0.f;
   __syncthreads();
   unsigned nbar = 0;
-  bool alive = true;
+  bool bar_pending = false;
   double last_loss = 0.0;
   unsigned long long last_S3 = 0;
 
-  for (int s = p.s0; s < p.s1 && alive; ++s) {
+  for (int s = p.s0; s < p.s1; ++s) {
     const int slot = s & 1;
     const BatchDesc b = p.descs[s];
     const int nd = b.n_docs;
@@ -653,23 +675,35 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const bool has = blk < ntiles;
 
     // ---------------- phase A: the data term of this block's tiles.  The
-    // Phi^T image (written by every block in the previous phase B) comes by
-    // one bulk copy that runs while the first tile's CSR slice is read.
-    if (has) {
+    // first tile's CSR slice and U rows are requested before the wait for the
+    // previous step's barrier (they need nothing from phase B); then the Phi^T
+    // image (written by every block in that phase B) comes by one bulk copy.
+    auto pre = [&]() -> bool {
+      if (bar_pending) {
+        bar_pending = false;
+        if (!grid_wait(ctl, nbar * G, &s_ok)) return false;
+      }
       if (tid == 0) {
         asm volatile("fence.proxy.async.global;" ::: "memory");
         mbar_arrive_expect_tx(&f.bars[0], 32768);
         bulk_load(f.sPhi, a.PhiImg, 32768, &f.bars[0]);
       }
+      return true;
+    };
+    if (has) {
       float lacc = 0.f;
       bool g_init = false;
-      f.tiles(a, b, blk, G, td, lacc, g_init, &ctl->S3[slot], &st->err, true);
+      f.tiles(a, b, blk, G, td, lacc, g_init, &ctl->S3[slot], &st->err, true, pre);
       if (a.want_loss) {
         const float t = block_sum(lacc, s_red);
         if (tid == 0 && t != 0.f) atomicAdd(&ctl->loss_data[slot], (double)t);
       }
       if (!f.failed()) f.write_g_sliced(a.Gpart, D, K, G, blk, per, g_init);
       __syncthreads();
+    }
+    if (bar_pending) {  // no tiles here: wait before the Phi-only columns
+      bar_pending = false;
+      if (!grid_wait(ctl, nbar * G, &s_ok)) break;
     }
     // the Phi-only terms, four columns at a time, handed out by a counter:
     // the blocks that finish their tiles first (or have none) take them.  Phi
@@ -865,8 +899,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       ctl->loss_phi[slot ^ 1] = 0.0;
       ctl->col_next[slot ^ 1] = 0;
     }
-    if (s + 1 < p.s1) {
-      if (!grid_sync(ctl, ++nbar * G, &s_ok)) alive = false;
+    if (s + 1 < p.s1) {  // waited for in the next step, once its first tile is requested
+      grid_arrive(ctl);
+      ++nbar;
+      bar_pending = true;
     } else if (p.record && blk == 0 && tid == 0) {
       st->step += p.s1 - p.s0;
       st->last_S3 = last_S3;
