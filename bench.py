@@ -13,6 +13,7 @@ already in HBM); `e2e` goes through the host-input pass of the public API
 loss read back).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --online [--online-every E] [--online-r R]   (fully online mode)
 
 With N > 1 (torchrun) each rank runs an independent replica on its own shard
 of documents (the pass has no exchange step in this build); value = docs of
@@ -57,6 +58,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--online", action="store_true",
+                    help="time the fully online mode (sketched whitening rebuilt every E minibatches)")
+    ap.add_argument("--online-every", type=int, default=256)
+    ap.add_argument("--online-r", type=int, default=216)
     return ap.parse_args()
 
 
@@ -276,10 +281,78 @@ def reference_arm(args):
 
 
 # ----------------------------------------------------------------------------- our arm
+def online_main(args):
+    """`--online`: docs/s of the fully online mode on the streaming workload
+    (BF16 form).  Per block of E minibatches: the block's statistics go into
+    the one-pass sketch, the whitening is rebuilt from it, Phi is carried into
+    the new basis, then the block's CP steps run.  The warm-up pass builds the
+    first whitening; the timed pass covers the next `steps` minibatches with
+    the corpus resident in HBM.  Also times a plain pass over the same batches
+    with the final whitening, so the rebuild cost per block follows."""
+    import torch
+    import tlda_synth as ts
+    from paper_2511_07809_gb300 import tlda
+
+    sp = ts.WORKLOADS[WORKLOAD]
+    cdf, _ = ts.topics(sp)
+    seq = batch_plan(ts, sp, args.warmup + args.steps)
+    n_docs = int(seq.sum())
+    corpus = ts.corpus(sp.with_docs(n_docs), n_docs=n_docs, cdf=cdf)
+    dev = tlda.DeviceCSR.from_corpus(corpus)
+    offs = np.concatenate([[0], np.cumsum(seq)]).astype(np.int64)
+    r, every, lr = args.online_r, args.online_every, 5e-4
+    Om = torch.tensor(ts.gaussian(sp.seed, 0x4F4D, sp.V * r).reshape(sp.V, r))
+    ctx = tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="bf16", max_batch=8192, seed=1)
+    ctx.online_begin(Om)
+    Phi = torch.tensor(ts.initial_factors(sp.seed + 1, sp.K, sp.K), dtype=torch.float32, device="cuda")
+    ctx.online_pass(dev, offs[:args.warmup + 1], Phi, lr, rewhiten_every=args.warmup)
+    torch.cuda.synchronize()
+    timed_offs = offs[args.warmup:]
+    n_timed = int(timed_offs[-1] - timed_offs[0])
+    sampler = ClockSampler(0).start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.online_pass(dev, timed_offs, Phi, lr, rewhiten_every=every)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    sweeps = ctx.eig_sweeps()
+    # the same minibatches as plain CP steps with the last whitening
+    Phi2 = Phi.clone()
+    e0.record()
+    ctx.cp_pass(dev, timed_offs, Phi2, lr)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_pass = e0.elapsed_time(e1)
+    n_blocks = (args.steps + every - 1) // every
+    line = {
+        "metric": "docs/sec of the fully online TLDA mode at k=100,V=20k (sketched whitening "
+                  f"rebuilt every {every} minibatches)",
+        "value": n_timed / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic: seeded LDA corpus (Dirichlet(0.1) topics, Poisson(12) lengths)",
+        "config": {"workload": WORKLOAD, "V": sp.V, "K": sp.K, "D": sp.K, "sketch_r": r,
+                   "rewhiten_every": every, "rebuilds": n_blocks, "docs": n_timed, "lr": lr,
+                   "l2": "inputs larger than L2: a "
+                         f"{(corpus.nnz * 8 + corpus.n_docs * 4) / 1e9:.2f} GB device-resident corpus"},
+        "plain_pass_docs_s": n_timed / (ms_pass / 1e3),
+        "ms_per_rebuild": (ms - ms_pass) / n_blocks,
+        "jacobi_sweeps_last": sweeps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.online:
+        return online_main(args)
     import torch
     import torch.distributed as dist
     import tlda_synth as ts

@@ -948,14 +948,6 @@ __global__ void __launch_bounds__(256) k_online_acc(const int32_t *indptr, const
   }
 }
 
-// Rebuilds the whitening from the online statistics (section "Fully Online
-// Implementation", the PCA update): with M1 = C/T, the sketch of
-// M2 = (alpha0+1) P/S2 - alpha0 M1 M1^T is Y = (alpha0+1)/S2 Z - alpha0 M1 (M1^T Omega);
-// then the single-pass eigendecomposition of Halko, Martinsson and Tropp
-// (2011, section 5.5): Q = orth(Y) (FP64 CholeskyQR2), B solves
-// B (Q^T Omega) = Q^T Y, B symmetrised, B = E Lambda E^T (Jacobi), U = Q E,
-// and W = U_D Lambda_D^-1/2 with the signs of fit_moments, m1 = W^T M1, U.
-// The previous W is kept in on_Wold.
 // Workspace of a re-whitening (one FP64 allocation, made by tlda_online_begin).
 struct OnlineWs {
   double *Y, *Q1, *Q2, *M1, *U64;               // V x r (three), V, V x D
@@ -974,6 +966,14 @@ struct OnlineWs {
   }
 };
 
+// Rebuilds the whitening from the online statistics (section "Fully Online
+// Implementation", the PCA update): with M1 = C/T, the sketch of
+// M2 = (alpha0+1) P/S2 - alpha0 M1 M1^T is Y = (alpha0+1)/S2 Z - alpha0 M1 (M1^T Omega);
+// then the single-pass eigendecomposition of Halko, Martinsson and Tropp
+// (2011, section 5.5): Q = orth(Y) (FP64 CholeskyQR2), B solves
+// B (Q^T Omega) = Q^T Y, B symmetrised, B = E Lambda E^T (Jacobi), U = Q E,
+// and W = U_D Lambda_D^-1/2 with the signs of fit_moments, m1 = W^T M1, U.
+// The previous W is kept in on_Wold.
 tlda_status online_rewhiten(tlda_ctx *ctx) {
   cudaStream_t s = ctx->stream;
   const int V = ctx->V, D = ctx->D, r = ctx->on_r;
