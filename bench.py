@@ -14,6 +14,7 @@ loss read back).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --online [--online-every E] [--online-r R]   (fully online mode)
+  python bench.py --e1 [--e1-reps N]   (the simulation study's shape check, batched mode)
 
 With N > 1 (torchrun) each rank runs an independent replica on its own shard
 of documents (the pass has no exchange step in this build); value = docs of
@@ -62,6 +63,11 @@ def parse():
                     help="time the fully online mode (sketched whitening rebuilt every E minibatches)")
     ap.add_argument("--online-every", type=int, default=256)
     ap.add_argument("--online-r", type=int, default=216)
+    ap.add_argument("--e1", action="store_true",
+                    help="the simulation study's recovery check with the batched mode")
+    ap.add_argument("--e1-reps", type=int, default=10)
+    ap.add_argument("--e1-epochs", type=int, default=30)
+    ap.add_argument("--e1-starts", type=int, default=8)
     return ap.parse_args()
 
 
@@ -347,12 +353,81 @@ def online_main(args):
     return 0
 
 
+def topic_correlation(mu_est, mu_true):
+    """Pearson correlation of each true topic (row of mu_true) with its
+    learned match (column of mu_est) under the matching of largest total
+    correlation: the simulation study's score."""
+    from scipy.optimize import linear_sum_assignment
+    K = mu_true.shape[0]
+    Cm = np.nan_to_num(np.corrcoef(np.vstack([mu_true, mu_est.T]))[:K, K:])
+    r_, c_ = linear_sum_assignment(-Cm)
+    return Cm[r_, c_]
+
+
+def e1_main(args):
+    """`--e1`: the simulation study as a shape check (section "Parameter
+    Recovery and Comparison to Previous TLDA Methods"): K = 2, alpha0 = 0.01,
+    whitening size 2, 20,000 documents, V in {500, 1000, 1500}, N seeded
+    corpora each.  Per corpus: the batched mode (moments and whitening, then
+    `epochs` passes of 1000-document batches from each Gaussian start, the
+    start with the lowest last-epoch loss kept), the topics, and their
+    correlation with the generator's.  Also the first start alone.  Device
+    time per fit by CUDA events; the paper's figures are context only."""
+    import torch
+    import tlda_synth as ts
+    from paper_2511_07809_gb300 import tlda
+
+    paper = {500: 0.943, 1000: 0.930, 1500: 0.873}
+    per_v = {}
+    for V in (500, 1000, 1500):
+        best, single, ms_fit = [], [], []
+        for rep in range(args.e1_reps):
+            sp = ts.e1_spec(V, rep)
+            cdf, mu = ts.topics(sp)
+            c = ts.corpus(sp, cdf=cdf)
+            dev = tlda.DeviceCSR.from_corpus(c)
+            offs = np.arange(0, sp.n_docs + 1, 1000, dtype=np.int64)
+            starts = np.stack([ts.initial_factors(sp.seed + s, sp.K, sp.K) for s in range(args.e1_starts)])
+            t = tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="fp32")
+            Ps = torch.tensor(starts, dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            t.fit_batched(dev, offs, Ps, 1e-2, epochs=args.e1_epochs)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_fit.append(e0.elapsed_time(e1))
+            best.append(float(topic_correlation(t.unwhiten_topics(Ps[0])[0], mu).mean()))
+            P1 = torch.tensor(starts[:1], dtype=torch.float32, device="cuda")
+            t.fit_batched(dev, offs, P1, 1e-2, epochs=args.e1_epochs, reuse_whitening=True)
+            single.append(float(topic_correlation(t.unwhiten_topics(P1[0])[0], mu).mean()))
+            t.close()
+        per_v[str(V)] = {"corr_mean": float(np.mean(best)), "corr_std": float(np.std(best)),
+                         "single_start_corr_mean": float(np.mean(single)),
+                         "single_start_corr_std": float(np.std(single)),
+                         "ms_per_fit_mean": float(np.mean(ms_fit)), "paper_corr_mean": paper[V]}
+    line = {
+        "metric": "simulation study shape check: mean topic correlation (K=2, alpha0=0.01, D=2, "
+                  "20k docs, batched mode)",
+        "value": float(np.mean([v["corr_mean"] for v in per_v.values()])), "unit": "pearson r",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic: seeded LDA corpora (Dirichlet(0.1) topics, Poisson(50) lengths)",
+        "config": {"workload": "e1_v{500,1000,1500}_k2", "reps": args.e1_reps, "epochs": args.e1_epochs,
+                   "starts": args.e1_starts, "batch": 1000, "lr": 1e-2},
+        "per_V": per_v,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.online:
         return online_main(args)
+    if args.e1:
+        return e1_main(args)
     import torch
     import torch.distributed as dist
     import tlda_synth as ts

@@ -206,6 +206,30 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
                          int32_t n_batches, float *Phi, float lr, uint32_t flags,
                          double *loss_out);
 
+#define TLDA_REUSE_WHITENING 2u /* tlda_fit_batched: keep the context's whitening */
+
+/* The batched mode (section "Batched Implementation Enables Arbitrary
+ * Scaling"): the corpus is read once for the moments, then looped over for
+ * the third-moment decomposition.
+ *  1. Unless flags hold TLDA_REUSE_WHITENING, tlda_fit_moments(ACCUMULATE |
+ *     FINALIZE) runs on the whole `corpus` (device CSR): M1, then M2 and its
+ *     whitening.
+ *  2. For each of n_starts initial factor matrices, `epochs` passes of
+ *     tlda_cp_pass over the batches (batch_offsets: host, n_batches + 1
+ *     document offsets).  Phi is device memory holding n_starts consecutive
+ *     D x K FP32 matrices, each updated in place.
+ *  3. The start whose last epoch has the lowest mean step loss is copied
+ *     into the first matrix of Phi.  NaN losses never win.  Several starts
+ *     guard against the spurious stationary points of the unconstrained CP
+ *     objective: one collapsed component, or two components sharing one
+ *     topic.
+ * loss_out (host, n_starts doubles) may be NULL; it receives each start's
+ * mean last-epoch loss.  Synchronises.  Errors as tlda_fit_moments and
+ * tlda_cp_pass; TLDA_ERR_STATE with TLDA_REUSE_WHITENING and no whitening. */
+tlda_status tlda_fit_batched(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets,
+                             int32_t n_batches, int32_t epochs, int32_t n_starts, float *Phi, float lr,
+                             uint32_t flags, double *loss_out);
+
 /* Tile size of the persistent pass kernel: the most documents per tile,
  * 1..32 (each batch is split into ceil(n_docs / SMs) document tiles up to
  * this size).  With fixed_cap > 0 the size is set to fixed_cap and nothing

@@ -39,6 +39,13 @@ with itself):
      the statistics and the whitening first, then its CP steps run (every = 1
      is the paper's per-batch order); on a change of whitening the factors
      are carried into the new basis so that the topics they encode stay put.
+  R  the batched mode's loop over the data for the third moment runs from
+     several initial factor matrices and keeps the one whose last epoch has
+     the lowest mean loss: the unconstrained objective (reading F) has
+     spurious stationary points (a collapsed component, two components on
+     one topic) that a single start may end in.  The simulations' score is
+     the Pearson correlation of each true topic with its learned match, under
+     the one-to-one matching of largest total correlation.
 """
 from __future__ import annotations
 
@@ -545,3 +552,59 @@ def online_pass(indptr, indices, counts, V, offsets, Omega, every, alpha0, theta
             Phi, g = cp_step(r, indices, counts, V, W, m1, Phi, lr, alpha0, theta, same_token)
             losses.append(g["loss"])
     return Phi, state, np.array(losses)
+
+
+# ----------------------------------------------------------------------------- batched mode
+
+
+def batched_fit(indptr, indices, counts, V, offsets, epochs, alpha0, theta, lr, Phi_starts, k,
+                same_token=True):
+    """The batched mode (section "Batched Implementation Enables Arbitrary
+    Scaling"; reading R): the moments and the whitening from the whole corpus
+    (O1-O4), then `epochs` passes of CP steps over the batches
+    [offsets[b], offsets[b+1]) from each initial factor matrix; the start
+    whose last epoch has the lowest mean loss is kept (NaN never wins).
+    Returns (kept Phi, W, m1, mean last-epoch loss per start, final Phi per start)."""
+    indptr = np.asarray(indptr, dtype=np.int64)
+    st = ingest(indptr, indices, counts, V)
+    M1 = first_moment(st["C"], st["T"])
+    M2 = second_moment(pair_counts(indptr, indices, counts, V), st["S2"], M1, alpha0)
+    W, _, _ = whitening(M2, k)
+    m1 = W.T @ M1
+    finals, means = [], []
+    for P0 in Phi_starts:
+        P = np.array(P0, dtype=np.float64)
+        for _ in range(epochs):
+            losses = []
+            for b in range(len(offsets) - 1):
+                r = indptr[int(offsets[b]):int(offsets[b + 1]) + 1]
+                P, g = cp_step(r, indices, counts, V, W, m1, P, lr, alpha0, theta, same_token)
+                losses.append(g["loss"])
+        means.append(float(np.mean(losses)))
+        finals.append(P)
+    means = np.array(means)
+    ok = np.flatnonzero(np.isfinite(means))
+    best = int(ok[np.argmin(means[ok])]) if len(ok) else 0
+    return finals[best], W, m1, means, finals
+
+
+def topic_correlation(mu_est, mu_true):
+    """Recovery score of the simulations (section "Parameter Recovery and
+    Comparison to Previous TLDA Methods"; reading R): the Pearson correlation
+    of each true topic-word distribution (row i of mu_true, K x V) with a
+    learned one (column j of mu_est, V x K), under the one-to-one matching
+    that maximises the total correlation (Hungarian assignment).  A constant
+    column correlates 0 with everything.  Returns (perm, correlation per true
+    topic), learned column perm[i] matched to true topic i."""
+    K = mu_true.shape[0]
+    Cm = np.zeros((K, K))
+    for i in range(K):
+        a = mu_true[i] - mu_true[i].mean()
+        for j in range(K):
+            b = mu_est[:, j] - mu_est[:, j].mean()
+            den = np.linalg.norm(a) * np.linalg.norm(b)
+            Cm[i, j] = float(a @ b) / den if den > 0 else 0.0
+    r, c = linear_sum_assignment(-Cm)
+    perm = np.empty(K, dtype=np.int64)
+    perm[r] = c
+    return perm, Cm[np.arange(K), perm]

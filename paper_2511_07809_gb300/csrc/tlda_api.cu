@@ -780,6 +780,44 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
   return s;
 }
 
+tlda_status tlda_fit_batched(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets,
+                             int32_t n_batches, int32_t epochs, int32_t n_starts, float *Phi, float lr,
+                             uint32_t flags, double *loss_out) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  if (!corpus || !batch_offsets || !Phi || n_batches < 1 || epochs < 1 || n_starts < 1)
+    return fail(ctx, TLDA_ERR_INVALID, "bad batched-fit arguments");
+  if (flags & TLDA_REUSE_WHITENING) {
+    if (!ctx->whitened) return fail(ctx, TLDA_ERR_STATE, "TLDA_REUSE_WHITENING without a whitening");
+  } else if (tlda_status s = tlda_fit_moments(ctx, corpus, TLDA_ACCUMULATE | TLDA_FINALIZE)) {
+    return s;
+  }
+  const size_t DK = (size_t)ctx->D * ctx->K;
+  std::vector<double> last(n_batches);
+  int best = -1;
+  double best_loss = 0.0;
+  for (int st = 0; st < n_starts; ++st) {
+    float *P = Phi + st * DK;
+    for (int e = 0; e < epochs; ++e) {
+      tlda_status s = tlda_cp_pass(ctx, corpus, batch_offsets, n_batches, P, lr, 0,
+                                   e + 1 == epochs ? last.data() : nullptr);
+      if (s) return s;
+    }
+    double m = 0.0;
+    for (double v : last) m += v;
+    m /= n_batches;
+    if (loss_out) loss_out[st] = m;
+    if (m == m && (best < 0 || m < best_loss)) {
+      best = st;
+      best_loss = m;
+    }
+  }
+  if (best > 0) {
+    CK(cudaMemcpyAsync(Phi, Phi + best * DK, sizeof(float) * DK, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return TLDA_OK;
+}
+
 tlda_status tlda_autotune(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets, int32_t n_batches,
                           const float *Phi, int32_t fixed_cap, int32_t *tile_cap_out) {
   if (!ctx) return TLDA_ERR_INVALID;

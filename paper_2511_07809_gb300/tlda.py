@@ -24,6 +24,7 @@ FP32, BF16 = 0, 1
 ACCUMULATE, FINALIZE = 1, 2
 HOST_INPUT = 1
 HOST_OUTPUT = 1
+REUSE_WHITENING = 2
 
 STATUS_NAMES = {OK: "TLDA_OK", ERR_INVALID: "TLDA_ERR_INVALID", ERR_CUDA: "TLDA_ERR_CUDA",
                 ERR_NUMERIC: "TLDA_ERR_NUMERIC", ERR_TIMEOUT: "TLDA_ERR_TIMEOUT",
@@ -37,7 +38,7 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_cp_data_term", "tlda_cp_pass", "tlda_unwhiten_topics",
                 "tlda_profile", "tlda_profile_read", "tlda_save_state", "tlda_load_state",
                 "tlda_cp_step_noalloc", "tlda_autotune", "tlda_online_begin",
-                "tlda_online_pass", "tlda_eig_sweeps")
+                "tlda_online_pass", "tlda_eig_sweeps", "tlda_fit_batched")
 
 
 class Params(ctypes.Structure):
@@ -85,6 +86,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "tlda_cp_data_term": (i32, [vp, P(CSR), vp, vp, vp]),
         "tlda_cp_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, u32, vp]),
         "tlda_autotune": (i32, [vp, P(CSR), vp, i32, vp, i32, P(i32)]),
+        "tlda_fit_batched": (i32, [vp, P(CSR), vp, i32, i32, i32, vp, f32, u32, vp]),
         "tlda_online_begin": (i32, [vp, vp, i32]),
         "tlda_online_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, i32, vp]),
         "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
@@ -262,6 +264,25 @@ class TLDA:
                                           HOST_INPUT if host_input else 0,
                                           out.ctypes.data if losses else None))
         return out[:nb] if losses else None
+
+    def fit_batched(self, corpus: DeviceCSR, batch_offsets, Phi_starts: torch.Tensor, lr: float,
+                    epochs: int, reuse_whitening: bool = False):
+        """The batched mode: moments and whitening from `corpus` (unless
+        reuse_whitening), then `epochs` passes from each start of Phi_starts
+        (n_starts x D x K float32, CUDA, updated in place); the start with the
+        lowest mean last-epoch loss ends up in Phi_starts[0].  Returns each
+        start's mean last-epoch loss."""
+        assert Phi_starts.dtype == torch.float32 and Phi_starts.is_cuda and Phi_starts.is_contiguous()
+        assert Phi_starts.dim() == 3 and tuple(Phi_starts.shape[1:]) == (self.D, self.K)
+        off = np.ascontiguousarray(np.asarray(batch_offsets, dtype=np.int64))
+        n = int(Phi_starts.shape[0])
+        out = np.zeros(n, dtype=np.float64)
+        s = corpus.struct()
+        self._check(self.lib.tlda_fit_batched(self.h, ctypes.byref(s), off.ctypes.data, len(off) - 1,
+                                              int(epochs), n, Phi_starts.data_ptr(), float(lr),
+                                              REUSE_WHITENING if reuse_whitening else 0,
+                                              out.ctypes.data))
+        return out
 
     def autotune(self, corpus: DeviceCSR | None = None, batch_offsets=None,
                  Phi: torch.Tensor | None = None, fixed: int = 0) -> int:

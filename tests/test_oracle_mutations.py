@@ -30,7 +30,15 @@ MUTATIONS = [
     ("pair normalisation", "return (alpha0 + 1.0) * (P.astype(np.float64) / float(S2))",
      "return (alpha0 + 1.0) * (P.astype(np.float64) / float(S2 + 1000))"),
     ("Y from uncentred W", "Y = X @ Phi  ", "Y = (F @ W) @ Phi  "),
+    ("sketch keeps the diagonal", "return F.T @ S - c[:, None] * Omega", "return F.T @ S"),
+    ("sketched M2 rank-one sign", "Y = (alpha0 + 1.0) / float(S2) * Z - alpha0 * np.outer(M1, M1 @ Omega)",
+     "Y = (alpha0 + 1.0) / float(S2) * Z + alpha0 * np.outer(M1, M1 @ Omega)"),
+    ("rotation without the old basis", "return W_new.T @ (pinv_transpose(W_old) @ Phi)", "return W_new.T @ (W_old @ Phi)"),
+    ("correlation not centred", "a = mu_true[i] - mu_true[i].mean()", "a = mu_true[i]"),
+    ("matching minimises", "r, c = linear_sum_assignment(-Cm)", "r, c = linear_sum_assignment(Cm)"),
+    ("batched keeps the highest loss", "best = int(ok[np.argmin(means[ok])])", "best = int(ok[np.argmax(means[ok])])"),
 ]
+PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_online.py", "tests/test_oracle_batched.py"]
 
 
 @pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
@@ -43,7 +51,7 @@ def test_pins_catch_planted_mistake(tmp_path, name, old, new):
     shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests",
                     ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
     env = dict(os.environ, PYTHONPATH=f"{tmp_path}{os.pathsep}{ROOT}")
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py"], cwd=tmp_path, env=env,
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", *PIN_FILES],
+                       cwd=tmp_path, env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"planted mistake {name!r} passed every pin:\n{r.stdout[-800:]}"

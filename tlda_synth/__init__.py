@@ -123,6 +123,16 @@ WORKLOADS = {
 }
 
 
+def e1_spec(V: int, rep: int) -> CorpusSpec:
+    """The simulation study's corpora (section "Parameter Recovery and
+    Comparison to Previous TLDA Methods"): K = 2 topics, alpha0 = 0.01,
+    20,000 documents, vocabulary V (500, 1000 or 1500 there), one seed per
+    repetition.  The topic prior and the lengths are not stated there: the
+    small workload's Dirichlet(0.1) and Poisson(50), at least 3 words."""
+    return CorpusSpec(f"e1_v{V}_k2_rep{rep}", int(V), 2, 0.1, 0.0, Fraction(1, 100), 50.0, 3, 20_000,
+                      _BASE_SEED + 0x100 + 16 * int(rep) + int(V) // 500, (1000, 1000))
+
+
 # --------------------------------------------------------------------------- draws
 def philox4x32_10(ctr, key) -> np.ndarray:
     """One Philox4x32-10 block (exposed for known-answer tests)."""
