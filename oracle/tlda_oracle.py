@@ -52,6 +52,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg
 import scipy.sparse as sp
+import scipy.special
 from scipy.optimize import linear_sum_assignment
 
 # ----------------------------------------------------------------------------- O1 ingest
@@ -608,3 +609,62 @@ def topic_correlation(mu_est, mu_true):
     perm = np.empty(K, dtype=np.int64)
     perm[r] = c
     return perm, Cm[np.arange(K), perm]
+
+
+# ----------------------------------------------------------------------------- document-topic VI
+
+
+def doc_topics(indptr, indices, counts, V, mu, alpha, n_iter):
+    """Document-level parameters from the recovered topics by standard
+    variational inference (section "Input and Output": topic-word matrix and
+    weights fed to VI), the per-document E-step of Blei, Ng and Jordan (2003,
+    section 5.2) with the topics fixed.  mu: V x K (column k = topic k),
+    alpha: the K Dirichlet parameters (alpha0 times the learned weights).
+    Per document, gamma = alpha + L/K, then n_iter rounds of
+        phi_jk proportional to mu_{m_j k} exp(digamma(gamma_k))  (over k),
+        gamma_k = alpha_k + sum_j f_j phi_jk;
+    a word whose mu row is all zero gets phi = 0.  Returns (theta = gamma /
+    sum gamma, gamma), both B x K."""
+    indptr = np.asarray(indptr, dtype=np.int64)
+    mu = np.asarray(mu, dtype=np.float64)
+    alpha = np.asarray(alpha, dtype=np.float64)
+    B, K = len(indptr) - 1, mu.shape[1]
+    gamma = np.zeros((B, K))
+    for d in range(B):
+        lo, hi = int(indptr[d]), int(indptr[d + 1])
+        m = np.asarray(indices[lo:hi], dtype=np.int64)
+        f = np.asarray(counts[lo:hi], dtype=np.float64)
+        g = alpha + f.sum() / K
+        rows = mu[m]                                          # nnz x K
+        for _ in range(n_iter):
+            _, g = vi_update(f, rows, alpha, g)
+        gamma[d] = g
+    return gamma / gamma.sum(axis=1, keepdims=True), gamma
+
+
+def vi_update(f, rows, alpha, gamma):
+    """One round of the E-step for one document (counts f of its words, their
+    topic rows nnz x K): phi_jk proportional to rows_jk exp(digamma(gamma_k)),
+    then gamma' = alpha + f^T phi.  Returns (phi, gamma')."""
+    p = rows * np.exp(scipy.special.digamma(gamma))[None, :]
+    s = p.sum(axis=1, keepdims=True)
+    phi = np.divide(p, s, out=np.zeros_like(p), where=s > 0)
+    return phi, alpha + f @ phi
+
+
+def doc_elbo(f, rows, alpha, gamma, phi):
+    """The per-document evidence lower bound of LDA with fixed topics (Blei,
+    Ng and Jordan 2003, appendix A.3), for counts f of words with topic rows
+    `rows` (nnz x K), variational Dirichlet gamma and multinomials phi
+    (nnz x K, one per distinct word, shared by its f tokens)."""
+    dg = scipy.special.digamma(gamma) - scipy.special.digamma(gamma.sum())
+    gl = scipy.special.gammaln
+    e_logtheta = (scipy.special.gammaln(alpha.sum()) - gl(alpha).sum() + ((alpha - 1.0) * dg).sum())
+    with np.errstate(divide="ignore", invalid="ignore"):
+        logrows = np.where(rows > 0, np.log(np.where(rows > 0, rows, 1.0)), 0.0)
+        logphi = np.where(phi > 0, np.log(np.where(phi > 0, phi, 1.0)), 0.0)
+    e_z = (f[:, None] * phi * dg[None, :]).sum()
+    e_w = (f[:, None] * phi * logrows).sum()
+    h_theta = -(gl(gamma.sum()) - gl(gamma).sum() + ((gamma - 1.0) * dg).sum())
+    h_z = -(f[:, None] * phi * logphi).sum()
+    return e_logtheta + e_z + e_w + h_theta + h_z

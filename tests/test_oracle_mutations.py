@@ -37,8 +37,12 @@ MUTATIONS = [
     ("correlation not centred", "a = mu_true[i] - mu_true[i].mean()", "a = mu_true[i]"),
     ("matching minimises", "r, c = linear_sum_assignment(-Cm)", "r, c = linear_sum_assignment(Cm)"),
     ("batched keeps the highest loss", "best = int(ok[np.argmin(means[ok])])", "best = int(ok[np.argmax(means[ok])])"),
+    ("VI without digamma", "p = rows * np.exp(scipy.special.digamma(gamma))[None, :]", "p = rows * gamma[None, :]"),
+    ("VI drops the prior", "return phi, alpha + f @ phi", "return phi, f @ phi"),
+    ("bound entropy sign", "h_z = -(f[:, None] * phi * logphi).sum()", "h_z = (f[:, None] * phi * logphi).sum()"),
 ]
-PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_online.py", "tests/test_oracle_batched.py"]
+PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_online.py", "tests/test_oracle_batched.py",
+             "tests/test_oracle_vi.py"]
 
 
 @pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
