@@ -326,6 +326,33 @@ tlda_status tlda_cp_step_noalloc(const tlda_csr *batch, const float *W, const fl
                                  int32_t dim, int32_t k, double alpha0, float theta, float *Phi,
                                  float lr, float *grad_out, int32_t *err_out, void *cuda_stream);
 
+/* ------------------------------------------------- document-topic VI */
+
+/* Document-topic proportions by standard variational inference (section
+ * "Input and Output": the recovered topic-word matrix and weights feed a VI
+ * that gives the document-topic matrix; the per-document E-step of Blei, Ng
+ * and Jordan 2003, section 5.2, with the topics fixed).  No context.
+ *   docs: host struct of device CSR pointers (indptr absolute, as batches of
+ *         tlda_cp_pass; V = docs->vocab);
+ *   mu:   V x K FP32 device, row-major, column k = topic k (for example the
+ *         output of tlda_unwhiten_topics in FP32);
+ *   alpha: K FP32 device, the Dirichlet parameters (alpha0 times the learned
+ *         weights).
+ * Per document with length L: gamma = alpha + L/K, then n_iter rounds of
+ *   phi_jk proportional to mu_{m_j k} exp(digamma(gamma_k)) over k,
+ *   gamma_k = alpha_k + sum_j f_j phi_jk,
+ * where a word whose mu row is all zero gets phi = 0.  theta_out (B x K FP32,
+ * device) receives gamma / sum_k gamma_k; gamma_out (B x K FP32, device) may
+ * be NULL.  FP32 arithmetic; digamma by its recurrence up to x >= 6 and its
+ * asymptotic series.  err_out (one int32, device) may be NULL; bit 0 is set
+ * for a document with a word outside [0, V), a count <= 0 or a decreasing
+ * indptr, and that document's outputs are NaN.  K in [1, 512], n_iter >= 0,
+ * else TLDA_ERR_INVALID.  Enqueued on cuda_stream (NULL: the default stream);
+ * returns without waiting; allocates nothing. */
+tlda_status tlda_doc_topics(const tlda_csr *docs, const float *mu, const float *alpha, int32_t K,
+                            int32_t n_iter, float *theta_out, float *gamma_out, int32_t *err_out,
+                            void *cuda_stream);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Per-kernel device time, from CUDA events recorded around each launch on

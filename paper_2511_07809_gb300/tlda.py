@@ -38,7 +38,7 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_cp_data_term", "tlda_cp_pass", "tlda_unwhiten_topics",
                 "tlda_profile", "tlda_profile_read", "tlda_save_state", "tlda_load_state",
                 "tlda_cp_step_noalloc", "tlda_autotune", "tlda_online_begin",
-                "tlda_online_pass", "tlda_eig_sweeps", "tlda_fit_batched")
+                "tlda_online_pass", "tlda_eig_sweeps", "tlda_fit_batched", "tlda_doc_topics")
 
 
 class Params(ctypes.Structure):
@@ -87,6 +87,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "tlda_cp_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, u32, vp]),
         "tlda_autotune": (i32, [vp, P(CSR), vp, i32, vp, i32, P(i32)]),
         "tlda_fit_batched": (i32, [vp, P(CSR), vp, i32, i32, i32, vp, f32, u32, vp]),
+        "tlda_doc_topics": (i32, [P(CSR), vp, vp, i32, i32, vp, vp, vp, vp]),
         "tlda_online_begin": (i32, [vp, vp, i32]),
         "tlda_online_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, i32, vp]),
         "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
@@ -359,6 +360,32 @@ class TLDA:
 
     def load_state(self, path: str):
         self._check(self.lib.tlda_load_state(self.h, str(path).encode()))
+
+
+# ---------------------------------------------------------------------------- document topics
+def doc_topics(docs: DeviceCSR, mu, alpha, n_iter: int = 20, want_gamma: bool = False, stream=None):
+    """Document-topic proportions by variational inference with the topics
+    fixed (tlda_doc_topics): mu V x K (column k = topic k), alpha the K
+    Dirichlet parameters; any device or dtype (copied to CUDA float32).
+    Returns theta (B x K CUDA float32), and gamma if want_gamma; raises on a
+    corrupt document."""
+    lib = load()
+    mu_d = torch.as_tensor(mu).to(device="cuda", dtype=torch.float32).contiguous()
+    al_d = torch.as_tensor(alpha).to(device="cuda", dtype=torch.float32).contiguous()
+    K = int(mu_d.shape[1])
+    assert mu_d.dim() == 2 and int(mu_d.shape[0]) == docs.vocab and tuple(al_d.shape) == (K,)
+    theta = torch.empty((docs.n_docs, K), dtype=torch.float32, device="cuda")
+    gamma = torch.empty_like(theta) if want_gamma else None
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = docs.struct()
+    st = lib.tlda_doc_topics(ctypes.byref(s), mu_d.data_ptr(), al_d.data_ptr(), K, int(n_iter),
+                             theta.data_ptr(), gamma.data_ptr() if want_gamma else None, err.data_ptr(),
+                             ctypes.c_void_p(stream.cuda_stream) if stream is not None else None)
+    if st != OK:
+        raise TLDAError(st, "tlda_doc_topics: bad arguments")
+    if int(err.item()):
+        raise TLDAError(ERR_INVALID, "tlda_doc_topics: corrupt document (outputs NaN)")
+    return (theta, gamma) if want_gamma else theta
 
 
 # ---------------------------------------------------------------------------- autograd
