@@ -15,6 +15,7 @@ loss read back).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --online [--online-every E] [--online-r R]   (fully online mode)
   python bench.py --e1 [--e1-reps N]   (the simulation study's shape check, batched mode)
+  python bench.py --vi [--vi-docs N] [--vi-iters I]   (document-topic VI)
 
 With N > 1 (torchrun) each rank runs an independent replica on its own shard
 of documents (the pass has no exchange step in this build); value = docs of
@@ -68,6 +69,10 @@ def parse():
     ap.add_argument("--e1-reps", type=int, default=10)
     ap.add_argument("--e1-epochs", type=int, default=30)
     ap.add_argument("--e1-starts", type=int, default=8)
+    ap.add_argument("--vi", action="store_true", help="time document-topic variational inference")
+    ap.add_argument("--vi-docs", type=int, default=2_000_000)
+    ap.add_argument("--vi-iters", type=int, default=20)
+    ap.add_argument("--vi-reps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -420,10 +425,90 @@ def e1_main(args):
     return 0
 
 
+def vi_main(args):
+    """`--vi`: docs/s of document-topic variational inference
+    (tlda_doc_topics) over the first N documents of the streaming workload,
+    with its ground-truth topics and alpha = alpha0/K, `vi_reps` timed
+    repetitions after two untimed ones (each repetition one call over all N
+    documents; the CSR and theta exceed L2).  The oracle's E-step on a
+    sample of the same documents is timed beside it; e2e adds the host->device
+    copy of the CSR and the device->host copy of theta."""
+    import torch
+    import tlda_synth as ts
+    from paper_2511_07809_gb300 import tlda
+
+    sp = ts.WORKLOADS[WORKLOAD]
+    cdf, mu = ts.topics(sp)
+    n = args.vi_docs
+    c = ts.corpus(sp.with_docs(n), n_docs=n, cdf=cdf)
+    dev = tlda.DeviceCSR.from_corpus(c)
+    mu_d = torch.tensor(mu.T.copy(), dtype=torch.float32, device="cuda")
+    al = np.full(sp.K, float(sp.alpha0) / sp.K)
+    al_d = torch.tensor(al, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        theta = tlda.doc_topics(dev, mu_d, al_d, args.vi_iters)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0).start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.vi_reps):
+        theta = tlda.doc_topics(dev, mu_d, al_d, args.vi_iters)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.vi_reps
+    # end to end: host CSR in, theta out
+    host = tlda.DeviceCSR.from_corpus(c, device="cpu", pin=True)
+    out = torch.empty((n, sp.K), dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2 = tlda.DeviceCSR(host.indptr.to("cuda", non_blocking=True), host.indices.to("cuda", non_blocking=True),
+                        host.counts.to("cuda", non_blocking=True), sp.V)
+    out.copy_(tlda.doc_topics(d2, mu_d, al_d, args.vi_iters), non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    nnz = c.nnz
+    byts = 8.0 * nnz + 4.0 * (n + 1) + 4.0 * n * sp.K           # CSR stream + theta written
+    flops = 4.0 * sp.K * nnz * args.vi_iters
+    peaks, src = measured_peaks()
+    hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    ach = byts / (ms / 1e3) / 1e9
+    # the oracle on a bounded sample
+    from oracle import tlda_oracle as O
+    ns = 1500
+    r = c.rows(0, ns)
+    t0 = time.perf_counter()
+    O.doc_topics(r.indptr, r.indices, r.counts, sp.V, mu.T, al, args.vi_iters)
+    cpu_s = time.perf_counter() - t0
+    line = {
+        "metric": "docs/sec of document-topic variational inference at k=100,V=20k "
+                  f"({args.vi_iters} E-step rounds per document)",
+        "value": n / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.vi_reps, "warmup": 2,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded LDA corpus (Dirichlet(0.1) topics, Poisson(12) lengths), true topics",
+        "config": {"workload": WORKLOAD, "V": sp.V, "K": sp.K, "docs": n, "nnz": nnz, "iters": args.vi_iters,
+                   "l2": f"inputs larger than L2: {(8 * nnz + 4 * n) / 1e9:.2f} GB CSR, "
+                         f"{4 * n * sp.K / 1e9:.2f} GB theta written per call"},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "algorithmic_bytes_per_call": byts, "peak_source": src,
+                     "fp32_tflops": flops / (ms / 1e3) / 1e12,
+                     "fp32_frac": flops / (ms / 1e3) / 1e12 / FP32_ALU_PEAK_TFLOPS, "traffic": None},
+        "cpu_baseline": {"value": ns / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {ns} documents, FP64 numpy/scipy E-step, {cpu_s:.1f} s"},
+        "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8.0 * nnz + 4.0 * (n + 1),
+                "d2h_bytes_per_step": 4.0 * n * sp.K},
+        "gpu_launches": args.vi_reps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.vi:
+        return vi_main(args)
     if args.online:
         return online_main(args)
     if args.e1:
