@@ -353,6 +353,40 @@ tlda_status tlda_doc_topics(const tlda_csr *docs, const float *mu, const float *
                             int32_t n_iter, float *theta_out, float *gamma_out, int32_t *err_out,
                             void *cuda_stream);
 
+/* ------------------------------------------------- synthetic corpora */
+
+/* On-device generation of documents doc0 .. doc0+n_docs-1 of a seeded
+ * synthetic corpus: the simulation data-generating process of the paper's
+ * appendix, defined exactly as the host generator of the test inputs, so the
+ * CSR arrays are identical to the host's for the same arguments.
+ *  - Philox4x32-10 (Salmon et al., SC'11): counter (document lo, document hi,
+ *    token, tag | refill << 8), key = seed.
+ *  - Document length: the first l with u < len_cdf[l] (u the first word of
+ *    tag 1), clipped below at min_len.
+ *  - Token topics: the Polya urn of Dirichlet(alpha0/K), alpha0 =
+ *    a_num / a_den, with Lemire integer draws (tag 2).
+ *  - Token words: the first w with u < topic_cdf[z][w].
+ *  - Tokens sorted and merged into strictly ascending words with counts.
+ * Arguments:
+ *  - topic_cdf: K x V uint64, device; each row a 2^32-scaled cumulative
+ *    table whose last entry is 2^32.
+ *  - len_cdf: n_len uint64, device; a cumulative table of the same kind,
+ *    n_len <= 1025, so documents have at most 1024 tokens.
+ *  - Output, device: indptr_out (n_docs + 1 int32, relative: indptr[0] = 0),
+ *    indices_out and counts_out (capacity nnz_cap int32 each).  With
+ *    nnz_cap = 0 only indptr and *nnz_out are produced.
+ *  - scratch: device, (n_docs + 1023) / 1024 + 2 int64 words.
+ *  - *nnz_out (host): the chunk's nonzeros.
+ * Synchronises the stream once, to learn the nonzeros.  Errors:
+ *  - TLDA_ERR_OOM if they exceed nnz_cap (indices not written) or 2^31 - 1;
+ *  - TLDA_ERR_INVALID for bad arguments, or if K (a_num + 1024 a_den)
+ *    reaches 2^32. */
+tlda_status tlda_generate_docs(uint64_t seed, int32_t V, int32_t K, const uint64_t *topic_cdf,
+                               uint32_t a_num, uint32_t a_den, const uint64_t *len_cdf, int32_t n_len,
+                               int32_t min_len, int64_t doc0, int32_t n_docs, int32_t *indptr_out,
+                               int32_t *indices_out, int32_t *counts_out, int64_t nnz_cap,
+                               int64_t *scratch, int64_t *nnz_out, void *cuda_stream);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Per-kernel device time, from CUDA events recorded around each launch on

@@ -38,7 +38,8 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_cp_data_term", "tlda_cp_pass", "tlda_unwhiten_topics",
                 "tlda_profile", "tlda_profile_read", "tlda_save_state", "tlda_load_state",
                 "tlda_cp_step_noalloc", "tlda_autotune", "tlda_online_begin",
-                "tlda_online_pass", "tlda_eig_sweeps", "tlda_fit_batched", "tlda_doc_topics")
+                "tlda_online_pass", "tlda_eig_sweeps", "tlda_fit_batched", "tlda_doc_topics",
+                "tlda_generate_docs")
 
 
 class Params(ctypes.Structure):
@@ -69,6 +70,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib = ctypes.CDLL(path)
     vp, i32, i64, f32, f64, u32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                                    ctypes.c_float, ctypes.c_double, ctypes.c_uint32)
+    u64 = ctypes.c_uint64
     P = ctypes.POINTER
     sig = {
         "tlda_default_params": (None, [P(Params), i32]),
@@ -88,6 +90,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "tlda_autotune": (i32, [vp, P(CSR), vp, i32, vp, i32, P(i32)]),
         "tlda_fit_batched": (i32, [vp, P(CSR), vp, i32, i32, i32, vp, f32, u32, vp]),
         "tlda_doc_topics": (i32, [P(CSR), vp, vp, i32, i32, vp, vp, vp, vp]),
+        "tlda_generate_docs": (i32, [u64, i32, i32, vp, u32, u32, vp, i32, i32, i64, i32, vp, vp, vp, i64,
+                                     vp, P(i64), vp]),
         "tlda_online_begin": (i32, [vp, vp, i32]),
         "tlda_online_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, i32, vp]),
         "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
@@ -360,6 +364,52 @@ class TLDA:
 
     def load_state(self, path: str):
         self._check(self.lib.tlda_load_state(self.h, str(path).encode()))
+
+
+# ---------------------------------------------------------------------------- synthetic corpora
+class DeviceGenerator:
+    """Documents of a seeded synthetic corpus generated on the device
+    (tlda_generate_docs): topic_cdf K x V and len_cdf as the host generator
+    builds them (uploaded once), alpha0 = a_num / a_den."""
+
+    def __init__(self, seed: int, V: int, K: int, topic_cdf, a_num: int, a_den: int, len_cdf, min_len: int):
+        self.lib = load()
+        self.seed, self.V, self.K = int(seed), int(V), int(K)
+        self.cdf = torch.as_tensor(np.ascontiguousarray(topic_cdf, dtype=np.uint64).view(np.int64)).to("cuda")
+        self.len_cdf = torch.as_tensor(np.ascontiguousarray(len_cdf, dtype=np.uint64).view(np.int64)).to("cuda")
+        self.a_num, self.a_den, self.min_len = int(a_num), int(a_den), int(min_len)
+
+    def _call(self, doc0, n_docs, indptr, indices, counts, cap, scratch):
+        nnz = ctypes.c_int64()
+        st = self.lib.tlda_generate_docs(self.seed, self.V, self.K, self.cdf.data_ptr(), self.a_num, self.a_den,
+                                         self.len_cdf.data_ptr(), int(self.len_cdf.numel()), self.min_len,
+                                         int(doc0), int(n_docs), indptr.data_ptr(),
+                                         indices.data_ptr() if indices is not None else None,
+                                         counts.data_ptr() if counts is not None else None, int(cap),
+                                         scratch.data_ptr(), ctypes.byref(nnz), None)
+        return st, nnz.value
+
+    def generate(self, doc0: int, n_docs: int, out: "DeviceCSR | None" = None) -> DeviceCSR:
+        """Documents doc0 .. doc0+n_docs-1 as a device CSR; `out` (with enough
+        capacity in indices/counts) is reused when given."""
+        scratch = torch.empty((n_docs + 1023) // 1024 + 2, dtype=torch.int64, device="cuda")
+        if out is not None and out.indptr.numel() >= n_docs + 1:
+            indptr, indices, counts = out.indptr[:n_docs + 1], out.indices, out.counts
+            st, nnz = self._call(doc0, n_docs, indptr, indices, counts, indices.numel(), scratch)
+            if st == OK:
+                return DeviceCSR(indptr, indices[:nnz], counts[:nnz], self.V)
+            if st != ERR_OOM:
+                raise TLDAError(st, "tlda_generate_docs failed")
+        indptr = torch.empty(n_docs + 1, dtype=torch.int32, device="cuda")
+        st, nnz = self._call(doc0, n_docs, indptr, None, None, 0, scratch)
+        if st != OK:
+            raise TLDAError(st, "tlda_generate_docs failed")
+        indices = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        counts = torch.empty_like(indices)
+        st, nnz = self._call(doc0, n_docs, indptr, indices, counts, indices.numel(), scratch)
+        if st != OK:
+            raise TLDAError(st, "tlda_generate_docs failed")
+        return DeviceCSR(indptr, indices[:nnz], counts[:nnz], self.V)
 
 
 # ---------------------------------------------------------------------------- document topics

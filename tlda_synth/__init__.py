@@ -76,6 +76,8 @@ def _load():
     lib.tsyn_batch_sizes.restype = ctypes.c_int64
     lib.tsyn_gaussian.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, c_f64p]
     lib.tsyn_philox_block.argtypes = [c_u32p, c_u32p, c_u32p]
+    lib.tsyn_len_table.argtypes = [ctypes.c_double, ctypes.c_int, c_u64p]
+    lib.tsyn_len_table.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -188,6 +190,17 @@ class Corpus:
         rows = np.repeat(np.arange(self.n_docs), np.diff(self.indptr))
         F[rows, self.indices] = self.counts
         return F
+
+
+def len_table(spec: CorpusSpec) -> np.ndarray:
+    """The Poisson length table the generator draws document lengths from
+    (uint64, 2^32-scaled CDF; the last entry is 2^32)."""
+    lib = _load()
+    out = np.zeros(4096, dtype=np.uint64)
+    n = lib.tsyn_len_table(float(spec.lam), 4096, _ptr(out, ctypes.c_uint64))
+    if n < 0:
+        raise ValueError("length table out of range")
+    return out[:n].copy()
 
 
 def corpus(spec: CorpusSpec, doc0: int = 0, n_docs: int | None = None, cdf=None,

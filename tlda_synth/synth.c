@@ -440,6 +440,16 @@ void tsyn_corpus_copy(const tsyn_corpus *h, int64_t *indptr, int32_t *indices, i
   if (lengths) memcpy(lengths, h->lengths, sizeof(int32_t) * (size_t)h->n_docs);
 }
 
+/* The length table of Poisson(lam) (2^32-scaled CDF, as drawn from by the
+ * corpus generator), for generators elsewhere that must draw the same
+ * lengths.  Writes up to cap entries; returns the table size, or -1. */
+int tsyn_len_table(double lam, int cap, uint64_t *out) {
+  len_table lt;
+  if (build_len_table(lam, &lt) || lt.n > cap) return -1;
+  memcpy(out, lt.cdf, sizeof(uint64_t) * (size_t)lt.n);
+  return lt.n;
+}
+
 /* Raw token stream of one document (topics and words in draw order), for
  * tests of the sampler itself. Returns the length, or -1. */
 int tsyn_doc_tokens(uint64_t seed, int V, int K, const uint64_t *cdf, uint32_t a_num, uint32_t a_den,
