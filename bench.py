@@ -16,6 +16,7 @@ loss read back).
   python bench.py --online [--online-every E] [--online-r R]   (fully online mode)
   python bench.py --e1 [--e1-reps N]   (the simulation study's shape check, batched mode)
   python bench.py --vi [--vi-docs N] [--vi-iters I]   (document-topic VI)
+  python bench.py --billion [--billion-docs N]   (V = 100k, K = 300, on-device generation)
 
 With N > 1 (torchrun) each rank runs an independent replica on its own shard
 of documents (the pass has no exchange step in this build); value = docs of
@@ -73,6 +74,11 @@ def parse():
     ap.add_argument("--vi-docs", type=int, default=2_000_000)
     ap.add_argument("--vi-iters", type=int, default=20)
     ap.add_argument("--vi-reps", type=int, default=5)
+    ap.add_argument("--billion", action="store_true",
+                    help="the billion-document workload: chunks generated on the device, one-pass sketch, CP pass")
+    ap.add_argument("--billion-docs", type=int, default=16_000_000)
+    ap.add_argument("--billion-chunk", type=int, default=1_000_000)
+    ap.add_argument("--billion-r", type=int, default=512)
     return ap.parse_args()
 
 
@@ -503,10 +509,105 @@ def vi_main(args):
     return 0
 
 
+def billion_main(args):
+    """`--billion`: the billion-document workload (V = 100,000, K = D = 300,
+    Zipf(1.07)-shaped topics, alpha0 = 5, Poisson(15) lengths, minibatches of
+    65,536) on the first N documents, in chunks generated on the device and
+    never stored whole.  Pass 1: each chunk is generated and added to the
+    one-pass sketch and the token statistics.  Then one whitening from the
+    sketch (r = 512).  Pass 2: each chunk is generated again and its
+    minibatches take CP steps (FP32 form).  Reported: docs/s of each pass
+    (generation included) and of the whole job, the per-chunk times (linear
+    scaling: flat), the whitening time."""
+    import torch
+    import tlda_synth as ts
+    from paper_2511_07809_gb300 import tlda
+
+    sp = ts.WORKLOADS["billion_v100k_k300"]
+    t0 = time.perf_counter()
+    cdf, mu = ts.topics(sp)
+    t_topics = time.perf_counter() - t0
+    r = args.billion_r
+    t0 = time.perf_counter()
+    Om = torch.tensor(ts.gaussian(sp.seed, 0x4F4D, sp.V * r).reshape(sp.V, r))
+    t_omega = time.perf_counter() - t0
+    a = sp.alpha0
+    gen = tlda.DeviceGenerator(sp.seed, sp.V, sp.K, cdf, a.numerator, a.denominator, ts.len_table(sp), sp.min_len)
+    B = sp.batch[0]
+    chunk = args.billion_chunk
+    n_chunks = (args.billion_docs + chunk - 1) // chunk
+    cap = chunk * 48
+    buf = tlda.DeviceCSR(torch.empty(chunk + 1, dtype=torch.int32, device="cuda"),
+                         torch.empty(cap, dtype=torch.int32, device="cuda"),
+                         torch.empty(cap, dtype=torch.int32, device="cuda"), sp.V)
+    ctx = tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="fp32", max_batch=B, seed=1)
+    ctx.online_begin(Om)
+    Phi = torch.tensor(ts.initial_factors(sp.seed + 1, sp.K, sp.K), dtype=torch.float32, device="cuda")
+    sampler = ClockSampler(0).start()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    marks1, marks2, nnz_tot, docs = [], [], 0, 0
+    torch.cuda.synchronize()
+    e_start = ev()
+    e_start.record()
+    for ci in range(n_chunks):
+        n = min(chunk, args.billion_docs - ci * chunk)
+        c = gen.generate(ci * chunk, n, out=buf)
+        nnz_tot += c.indices.numel()
+        docs += n
+        ctx.online_accumulate(c)
+        e = ev()
+        e.record()
+        marks1.append(e)
+    e_w0 = ev()
+    e_w0.record()
+    ctx.online_whiten()
+    e_w1 = ev()
+    e_w1.record()
+    lr = 1e-4
+    for ci in range(n_chunks):
+        n = min(chunk, args.billion_docs - ci * chunk)
+        c = gen.generate(ci * chunk, n, out=buf)
+        offs = list(range(0, n, B)) + [n]
+        ctx.cp_pass(c, offs, Phi, lr)
+        e = ev()
+        e.record()
+        marks2.append(e)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t1 = [(marks1[i - 1] if i else e_start).elapsed_time(marks1[i]) for i in range(n_chunks)]
+    t2 = [(marks2[i - 1] if i else e_w1).elapsed_time(marks2[i]) for i in range(n_chunks)]
+    ms_total = e_start.elapsed_time(marks2[-1])
+    w_ms = e_w0.elapsed_time(e_w1)
+    finite = bool(torch.isfinite(Phi).all().item())
+    line = {
+        "metric": "docs/sec of the billion-document workload (V=100k, K=300): on-device generation, "
+                  "one-pass sketch, whitening, CP pass",
+        "value": docs / (ms_total / 1e3), "unit": UNIT, "n_gpus": 1, "steps": n_chunks * ((chunk + B - 1) // B),
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: generated on the device (Zipf(1.07)-shaped Dirichlet topics, Poisson(15) lengths)",
+        "config": {"workload": "billion_v100k_k300", "V": sp.V, "K": sp.K, "D": sp.K, "docs": docs,
+                   "nnz": nnz_tot, "chunk_docs": chunk, "batch": B, "sketch_r": r, "lr": lr,
+                   "l2": "inputs larger than L2: each chunk (about 0.1 GB of CSR) is generated into HBM "
+                         "and read once per pass"},
+        "pass1_sketch_docs_s": docs / (sum(t1) / 1e3),
+        "whiten_ms": w_ms,
+        "pass2_cp_docs_s": docs / (sum(t2) / 1e3),
+        "chunk_ms_pass1": {"mean": float(np.mean(t1)), "std": float(np.std(t1)), "first": t1[0], "last": t1[-1]},
+        "chunk_ms_pass2": {"mean": float(np.mean(t2)), "std": float(np.std(t2)), "first": t2[0], "last": t2[-1]},
+        "host_setup_s": {"topics": round(t_topics, 2), "omega": round(t_omega, 2)},
+        "phi_finite": finite, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.billion:
+        return billion_main(args)
     if args.vi:
         return vi_main(args)
     if args.online:

@@ -277,6 +277,21 @@ tlda_status tlda_online_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_
                              int32_t n_batches, float *Phi, float lr, int32_t rewhiten_every,
                              double *loss_out);
 
+/* The online statistics alone: adds every document of `corpus` (device CSR)
+ * to the token statistics and the sketch, as tlda_online_pass does for a
+ * block, without re-whitening or CP steps.  With tlda_online_whiten this
+ * gives the one-pass sketch of a corpus read in chunks before its CP pass.
+ * Asynchronous; a corrupt document is reported by the next
+ * tlda_online_whiten (TLDA_ERR_INVALID).  TLDA_ERR_STATE before
+ * tlda_online_begin. */
+tlda_status tlda_online_accumulate(tlda_ctx *ctx, const tlda_csr *corpus);
+
+/* Rebuilds the whitening from the statistics accumulated so far, exactly as
+ * tlda_online_pass does before a block's CP steps.  If the context already
+ * had a whitening and Phi (D x K FP32, device) is not NULL, Phi is carried
+ * into the new basis.  Synchronises.  Errors as tlda_online_pass. */
+tlda_status tlda_online_whiten(tlda_ctx *ctx, float *Phi);
+
 /* --------------------------------------------------------------- recovery */
 #define TLDA_HOST_OUTPUT 1u    /* mu_out / alpha_out are host pointers */
 

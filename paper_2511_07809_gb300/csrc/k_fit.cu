@@ -1076,6 +1076,28 @@ tlda_status online_rotate(tlda_ctx *ctx, float *Phi) {
   return TLDA_OK;
 }
 
+// Documents [d0, d0 + nd) of `corpus` into the online statistics and sketch
+// (asynchronous; validation errors land in on_err).
+tlda_status online_accumulate(tlda_ctx *ctx, const tlda_csr *corpus, int64_t d0, int nd) {
+  if (nd <= 0) return TLDA_OK;
+  const long long threads = (long long)nd * 32;
+  k_online_acc<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(
+      corpus->indptr + d0, corpus->indices, corpus->counts, nd, ctx->V, ctx->on_r, ctx->on_Om, ctx->on_Z,
+      ctx->on_C, ctx->on_TS, ctx->on_err);
+  CKF(cudaGetLastError());
+  return TLDA_OK;
+}
+
+// Rebuild the whitening; carry Phi (if given) from the previous one.
+tlda_status online_whiten(tlda_ctx *ctx, float *Phi) {
+  const bool had = ctx->whitened;
+  if (tlda_status st = online_rewhiten(ctx)) return st;
+  if (had && Phi)
+    if (tlda_status st = online_rotate(ctx, Phi)) return st;
+  ctx->whitened = true;
+  return TLDA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1223,31 +1245,31 @@ tlda_status tlda_online_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_
     const int64_t d0 = batch_offsets[b], d1 = batch_offsets[b + 1];
     if (d0 < 0 || d1 < d0 || d1 > corpus->n_docs) return fail(ctx, TLDA_ERR_INVALID, "batch offsets out of range");
   }
-  cudaStream_t s = ctx->stream;
   for (int b0 = 0; b0 < n_batches; b0 += rewhiten_every) {
     const int b1 = std::min(n_batches, b0 + rewhiten_every);
     const int64_t d0 = batch_offsets[b0], d1 = batch_offsets[b1];
-    const int nd = (int)(d1 - d0);
-    if (nd > 0) {
-      const long long threads = (long long)nd * 32;
-      k_online_acc<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(corpus->indptr + d0, corpus->indices,
-                                                                     corpus->counts, nd, ctx->V, ctx->on_r,
-                                                                     ctx->on_Om, ctx->on_Z, ctx->on_C,
-                                                                     ctx->on_TS, ctx->on_err);
-      CKF(cudaGetLastError());
-    }
-    const bool had = ctx->whitened;  // Phi is carried over from the context's current whitening
-    tlda_status st = online_rewhiten(ctx);
-    if (st) return st;
-    if (had) {
-      st = online_rotate(ctx, Phi);
-      if (st) return st;
-    }
-    ctx->whitened = true;
-    st = tlda_cp_pass(ctx, corpus, batch_offsets + b0, b1 - b0, Phi, lr, 0, loss_out ? loss_out + b0 : nullptr);
+    if (tlda_status st = online_accumulate(ctx, corpus, d0, (int)(d1 - d0))) return st;
+    if (tlda_status st = online_whiten(ctx, Phi)) return st;
+    tlda_status st = tlda_cp_pass(ctx, corpus, batch_offsets + b0, b1 - b0, Phi, lr, 0,
+                                  loss_out ? loss_out + b0 : nullptr);
     if (st) return st;
   }
   return TLDA_OK;
+}
+
+tlda_status tlda_online_accumulate(tlda_ctx *ctx, const tlda_csr *corpus) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  if (!ctx->on_active) return fail(ctx, TLDA_ERR_STATE, "tlda_online_begin has not been called");
+  if (!corpus || corpus->vocab != ctx->V || corpus->n_docs < 0 || !corpus->indptr ||
+      (corpus->n_docs > 0 && (!corpus->indices || !corpus->counts)))
+    return fail(ctx, TLDA_ERR_INVALID, "bad corpus");
+  return online_accumulate(ctx, corpus, 0, corpus->n_docs);
+}
+
+tlda_status tlda_online_whiten(tlda_ctx *ctx, float *Phi) {
+  if (!ctx) return TLDA_ERR_INVALID;
+  if (!ctx->on_active) return fail(ctx, TLDA_ERR_STATE, "tlda_online_begin has not been called");
+  return online_whiten(ctx, Phi);
 }
 
 }  // extern "C"

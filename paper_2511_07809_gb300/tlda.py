@@ -39,7 +39,7 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_profile", "tlda_profile_read", "tlda_save_state", "tlda_load_state",
                 "tlda_cp_step_noalloc", "tlda_autotune", "tlda_online_begin",
                 "tlda_online_pass", "tlda_eig_sweeps", "tlda_fit_batched", "tlda_doc_topics",
-                "tlda_generate_docs")
+                "tlda_generate_docs", "tlda_online_accumulate", "tlda_online_whiten")
 
 
 class Params(ctypes.Structure):
@@ -94,6 +94,8 @@ def load(build: bool = True) -> ctypes.CDLL:
                                      vp, P(i64), vp]),
         "tlda_online_begin": (i32, [vp, vp, i32]),
         "tlda_online_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, i32, vp]),
+        "tlda_online_accumulate": (i32, [vp, P(CSR)]),
+        "tlda_online_whiten": (i32, [vp, vp]),
         "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
         "tlda_cp_step_noalloc": (i32, [P(CSR), vp, vp, i32, i32, f64, f32, vp, f32, vp, vp, vp]),
         "tlda_profile": (i32, [vp, u32]),
@@ -326,6 +328,15 @@ class TLDA:
                                               Phi.data_ptr(), float(lr), int(rewhiten_every),
                                               out.ctypes.data if losses else None))
         return out[:nb] if losses else None
+
+    def online_accumulate(self, corpus: DeviceCSR):
+        """Add a corpus chunk to the online statistics and sketch only."""
+        s = corpus.struct()
+        self._check(self.lib.tlda_online_accumulate(self.h, ctypes.byref(s)))
+
+    def online_whiten(self, Phi: torch.Tensor | None = None):
+        """Rebuild the whitening from the statistics so far; carry Phi."""
+        self._check(self.lib.tlda_online_whiten(self.h, Phi.data_ptr() if Phi is not None else None))
 
     def sync(self):
         self._check(self.lib.tlda_sync(self.h))

@@ -48,6 +48,31 @@ def test_online_whitening_matches_oracle_sketch(lib):
     t.close()
 
 
+def test_online_chunks_accumulated_then_whitened(lib):
+    """The sketch of a corpus read in chunks (tlda_online_accumulate), then one
+    whitening (tlda_online_whiten), equals the oracle's whitening of the whole
+    corpus; a corrupt chunk is reported by the next whitening."""
+    sp, c, offs, Om, t = _setup(lib, "small_v500_k10", 10000, 10, "fp32")
+    for a, b in ((0, 3000), (3000, 3001), (3001, 10000)):
+        t.online_accumulate(lib.DeviceCSR.from_corpus(c.rows(a, b)))
+    t.online_whiten()
+    W, m1, ev = t.get_whitening()
+    st = O.ingest(c.indptr, c.indices, c.counts, sp.V)
+    Z = O.sketch_accumulate(c.indptr, c.indices, c.counts, sp.V, Om)
+    Wo, m1o, lam = O.sketch_whitening(Z, st["C"], st["T"], st["S2"], Om, float(sp.alpha0), sp.K)
+    assert np.allclose(ev, lam, rtol=1e-7)
+    assert C.rel(W.cpu().numpy(), Wo) < 1e-5
+    assert C.rel(m1.cpu().numpy(), m1o) < 1e-5
+    bad = c.rows(0, 100)
+    counts = bad.counts.copy()
+    counts[5] = 0
+    t.online_accumulate(lib.DeviceCSR.from_arrays(bad.indptr, bad.indices, counts, sp.V))
+    with pytest.raises(lib.TLDAError) as e:
+        t.online_whiten()
+    assert e.value.status == lib.ERR_INVALID
+    t.close()
+
+
 def test_online_rotations_match_oracle(lib):
     """lr = 0 and a new whitening every batch: Phi only moves by the basis changes."""
     sp, c, offs, Om, t = _setup(lib, "small_v500_k10", 10000, 10, "fp32")

@@ -13,7 +13,10 @@
  *    (index lo, index hi, sub-index, stream tag | retry << 8), key = seed.
  *  - Topic-word Dirichlet: Gamma variates (Marsaglia & Tsang 2000, with the
  *    U^{1/a} boost for a < 1), normalised in FP64 and quantised to a 2^32-scaled
- *    cumulative table; the quantised probabilities are the ground truth.
+ *    cumulative table; the quantised probabilities are the ground truth.  A
+ *    Zipf-shaped concentration is either shared by every topic or laid over
+ *    each topic's own ordering of the vocabulary (a seeded Fisher-Yates
+ *    shuffle with Lemire draws).
  *  - Lengths: Poisson(lambda) by inversion of a 2^32-scaled CDF table, clipped
  *    below at min_len.
  *  - Topics: the Polya urn that gives the exact Dirichlet-multinomial marginal
@@ -35,6 +38,7 @@
 #define TAG_GAMMA 3u
 #define TAG_BATCH 4u
 #define TAG_GAUSS 5u
+#define TAG_PERM 6u
 
 /* ------------------------------------------------------------------ Philox */
 typedef struct {
@@ -160,24 +164,45 @@ static void word_prior(int V, double beta, double zipf_s, double *a) {
   for (int w = 0; w < V; ++w) a[w] = beta * (double)V * pow((double)(w + 1), -zipf_s) / z;
 }
 
+/* rank[w] = the Zipf rank of word w in topic k: a Fisher-Yates shuffle of
+ * 0..V-1 on the topic's own stream. */
+static void topic_ranks(uint64_t seed, int k, int V, int *rank) {
+  for (int w = 0; w < V; ++w) rank[w] = w;
+  rstream s;
+  rs_init(&s, seed, (uint64_t)k, 0, TAG_PERM);
+  for (int i = V - 1; i > 0; --i) {
+    const int j = (int)rs_below(&s, (uint32_t)(i + 1));
+    const int t = rank[i];
+    rank[i] = rank[j];
+    rank[j] = t;
+  }
+}
+
 /* cdf: K x V uint64 (2^32-scaled cumulative, last entry exactly 2^32),
- * mu:  K x V double, the quantised topic-word probabilities (ground truth). */
-int tsyn_topics(uint64_t seed, int V, int K, double beta, double zipf_s, uint64_t *cdf, double *mu) {
+ * mu:  K x V double, the quantised topic-word probabilities (ground truth).
+ * per_topic != 0 (with zipf_s != 0): topic k's word w has the concentration
+ * of Zipf rank rank_k[w] (topic_ranks) instead of rank w. */
+int tsyn_topics(uint64_t seed, int V, int K, double beta, double zipf_s, int per_topic, uint64_t *cdf,
+                double *mu) {
   if (V < 1 || K < 1) return 1;
   double *a = (double *)malloc(sizeof(double) * (size_t)V);
   double *g = (double *)malloc(sizeof(double) * (size_t)V);
-  if (!a || !g) {
+  int *rank = (int *)malloc(sizeof(int) * (size_t)V);
+  if (!a || !g || !rank) {
     free(a);
     free(g);
+    free(rank);
     return 2;
   }
   word_prior(V, beta, zipf_s, a);
+  const int shuffle = per_topic && zipf_s != 0.0;
   for (int k = 0; k < K; ++k) {
     double tot = 0.0;
+    if (shuffle) topic_ranks(seed, k, V, rank);
     for (int w = 0; w < V; ++w) {
       rstream s;
       rs_init(&s, seed, (uint64_t)k * (uint64_t)V + (uint64_t)w, 0, TAG_GAMMA);
-      g[w] = rs_gamma(&s, a[w]);
+      g[w] = rs_gamma(&s, a[shuffle ? rank[w] : w]);
       tot += g[w];
     }
     if (!(tot > 0.0)) { /* all gammas underflowed: put the mass on the first word */
@@ -200,6 +225,7 @@ int tsyn_topics(uint64_t seed, int V, int K, double beta, double zipf_s, uint64_
   }
   free(a);
   free(g);
+  free(rank);
   return 0;
 }
 
