@@ -17,6 +17,7 @@
 
 #include <cstdint>
 
+#include "scan.cuh"
 #include "tlda.h"
 
 namespace {
@@ -24,7 +25,6 @@ namespace {
 constexpr uint32_t kTagLen = 1u, kTagTok = 2u;
 constexpr int kGenMaxLen = 1024;  // longest document (tokens)
 constexpr int kGenWarps = 4;
-constexpr int kScanThreads = 1024;
 
 __device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -199,51 +199,6 @@ __global__ void __launch_bounds__(kGenWarps * 32) k_gen_docs(GenArgs a) {
   }
 }
 
-// In-place inclusive scan of x[1 .. n] (x[0] = 0 stays): block sums, then
-// their exclusive offsets in one block, then the offsets added.
-__global__ void __launch_bounds__(kScanThreads) k_scan_local(int32_t *x, int n, int64_t *bsum) {
-  __shared__ int32_t wsum[kScanThreads / 32];
-  const int i = 1 + blockIdx.x * kScanThreads + threadIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t v = i <= n ? x[i] : 0;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += y;
-  }
-  if (lane == 31) wsum[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    int32_t s = wsum[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    wsum[lane] = s;
-  }
-  __syncthreads();
-  if (w > 0) v += wsum[w - 1];
-  if (i <= n) x[i] = v;
-  if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = v;
-}
-
-__global__ void k_scan_top(int64_t *bsum, int nb, int64_t *total) {
-  if (threadIdx.x == 0) {
-    int64_t run = 0;
-    for (int b = 0; b < nb; ++b) {
-      const int64_t v = bsum[b];
-      bsum[b] = run;
-      run += v;
-    }
-    *total = run;
-  }
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_add(int32_t *x, int n, const int64_t *bsum) {
-  const int i = 1 + blockIdx.x * kScanThreads + threadIdx.x;
-  if (i <= n) x[i] = (int32_t)(x[i] + bsum[blockIdx.x]);
-}
-
 }  // namespace
 
 extern "C" tlda_status tlda_generate_docs(uint64_t seed, int32_t V, int32_t K, const uint64_t *topic_cdf,
@@ -263,7 +218,7 @@ extern "C" tlda_status tlda_generate_docs(uint64_t seed, int32_t V, int32_t K, c
   if (n_docs == 0) {
     return cudaMemsetAsync(indptr_out, 0, sizeof(int32_t), s) == cudaSuccess ? TLDA_OK : TLDA_ERR_CUDA;
   }
-  const int nb = (n_docs + kScanThreads - 1) / kScanThreads;
+  const int nb = scan_blocks(n_docs);
   int64_t *bsum = scratch, *total = scratch + nb;
   int *err = reinterpret_cast<int *>(scratch + nb + 1);
   if (cudaMemsetAsync(err, 0, sizeof(int64_t), s) != cudaSuccess) return TLDA_ERR_CUDA;
@@ -272,9 +227,7 @@ extern "C" tlda_status tlda_generate_docs(uint64_t seed, int32_t V, int32_t K, c
   const unsigned grid = (unsigned)((n_docs + kGenWarps - 1) / kGenWarps);
   const size_t smem = sizeof(int) * 2 * kGenMaxLen * kGenWarps;
   k_gen_docs<1><<<grid, kGenWarps * 32, smem, s>>>(a);
-  k_scan_local<<<nb, kScanThreads, 0, s>>>(indptr_out, n_docs, bsum);
-  k_scan_top<<<1, 32, 0, s>>>(bsum, nb, total);
-  k_scan_add<<<nb, kScanThreads, 0, s>>>(indptr_out, n_docs, bsum);
+  scan_counts(indptr_out, n_docs, bsum, total, s);
   int64_t hv[2] = {0, 0};
   if (cudaMemcpyAsync(hv, total, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
