@@ -516,9 +516,11 @@ def billion_main(args):
     never stored whole.  Pass 1: each chunk is generated and added to the
     one-pass sketch and the token statistics.  Then one whitening from the
     sketch (r = 512).  Pass 2: each chunk is generated again and its
-    minibatches take CP steps (FP32 form).  Reported: docs/s of each pass
-    (generation included) and of the whole job, the per-chunk times (linear
-    scaling: flat), the whitening time."""
+    minibatches take CP steps in the BF16 tensor-core form; then the same
+    pass 2 again in the FP32 form (same whitening, same starting factors),
+    for the comparison.  Reported: docs/s of each pass (generation included)
+    and of the whole job (pass 1, whitening, BF16 pass 2), the per-chunk
+    times (linear scaling: flat), the whitening time."""
     import torch
     import tlda_synth as ts
     from paper_2511_07809_gb300 import tlda
@@ -540,9 +542,10 @@ def billion_main(args):
     buf = tlda.DeviceCSR(torch.empty(chunk + 1, dtype=torch.int32, device="cuda"),
                          torch.empty(cap, dtype=torch.int32, device="cuda"),
                          torch.empty(cap, dtype=torch.int32, device="cuda"), sp.V)
-    ctx = tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="fp32", max_batch=B, seed=1)
+    ctx = tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="bf16", max_batch=B, seed=1)
     ctx.online_begin(Om)
-    Phi = torch.tensor(ts.initial_factors(sp.seed + 1, sp.K, sp.K), dtype=torch.float32, device="cuda")
+    Phi0 = torch.tensor(ts.initial_factors(sp.seed + 1, sp.K, sp.K), dtype=torch.float32, device="cuda")
+    Phi = Phi0.clone()
     sampler = ClockSampler(0).start()
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     marks1, marks2, nnz_tot, docs = [], [], 0, 0
@@ -564,26 +567,41 @@ def billion_main(args):
     e_w1 = ev()
     e_w1.record()
     lr = 1e-4
-    for ci in range(n_chunks):
-        n = min(chunk, args.billion_docs - ci * chunk)
-        c = gen.generate(ci * chunk, n, out=buf)
-        offs = list(range(0, n, B)) + [n]
-        ctx.cp_pass(c, offs, Phi, lr)
-        e = ev()
-        e.record()
-        marks2.append(e)
-    torch.cuda.synchronize()
+
+    def pass2(c_, P, start):
+        marks = []
+        for ci in range(n_chunks):
+            n = min(chunk, args.billion_docs - ci * chunk)
+            c = gen.generate(ci * chunk, n, out=buf)
+            offs = list(range(0, n, B)) + [n]
+            c_.cp_pass(c, offs, P, lr)
+            e = ev()
+            e.record()
+            marks.append(e)
+        torch.cuda.synchronize()
+        return [(marks[i - 1] if i else start).elapsed_time(marks[i]) for i in range(n_chunks)], marks[-1]
+
+    t2, e_end = pass2(ctx, Phi, e_w1)
     clocks = sampler.stop()
     t1 = [(marks1[i - 1] if i else e_start).elapsed_time(marks1[i]) for i in range(n_chunks)]
-    t2 = [(marks2[i - 1] if i else e_w1).elapsed_time(marks2[i]) for i in range(n_chunks)]
-    ms_total = e_start.elapsed_time(marks2[-1])
+    ms_total = e_start.elapsed_time(e_end)
     w_ms = e_w0.elapsed_time(e_w1)
     finite = bool(torch.isfinite(Phi).all().item())
+    # the FP32 form on the same chunks, whitening and starting factors
+    W, m1, _ = ctx.get_whitening()
+    c32 = tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="fp32", max_batch=B, seed=1)
+    c32.set_whitening(W, m1)
+    P32 = Phi0.clone()
+    e32 = ev()
+    e32.record()
+    t2_32, _ = pass2(c32, P32, e32)
+    rel32 = float((torch.linalg.norm(Phi - P32) / torch.linalg.norm(P32)).item())
+    c32.close()
     line = {
         "metric": "docs/sec of the billion-document workload (V=100k, K=300): on-device generation, "
                   "one-pass sketch, whitening, CP pass",
         "value": docs / (ms_total / 1e3), "unit": UNIT, "n_gpus": 1, "steps": n_chunks * ((chunk + B - 1) // B),
-        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic: generated on the device (Zipf(1.07)-shaped Dirichlet topics, Poisson(15) lengths)",
         "config": {"workload": "billion_v100k_k300", "V": sp.V, "K": sp.K, "D": sp.K, "docs": docs,
                    "nnz": nnz_tot, "chunk_docs": chunk, "batch": B, "sketch_r": r, "lr": lr,
@@ -592,6 +610,8 @@ def billion_main(args):
         "pass1_sketch_docs_s": docs / (sum(t1) / 1e3),
         "whiten_ms": w_ms,
         "pass2_cp_docs_s": docs / (sum(t2) / 1e3),
+        "pass2_cp_docs_s_fp32": docs / (sum(t2_32) / 1e3),
+        "phi_rel_diff_bf16_vs_fp32": rel32,
         "chunk_ms_pass1": {"mean": float(np.mean(t1)), "std": float(np.std(t1)), "first": t1[0], "last": t1[-1]},
         "chunk_ms_pass2": {"mean": float(np.mean(t2)), "std": float(np.std(t2)), "first": t2[0], "last": t2[-1]},
         "host_setup_s": {"topics": round(t_topics, 2), "omega": round(t_omega, 2)},

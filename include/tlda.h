@@ -93,8 +93,11 @@ void tlda_default_params(tlda_params *p, int32_t k);
 /* Creates a context for vocabulary size `vocab` on the current CUDA device,
  * with all work enqueued on `cuda_stream` (a cudaStream_t; NULL = the legacy
  * default stream).  Allocates the workspace (device memory linear in V and
- * max_batch).  Returns TLDA_ERR_INVALID for bad sizes/parameters, TLDA_ERR_OOM
- * if the workspace cannot be allocated. */
+ * max_batch).  D and K are padded to multiples of 64, at most 512, in both
+ * forms.  The BF16 form takes the fused tensor-core kernels for D, K in
+ * (64, 128] and the multi-kernel tensor-core form otherwise.  Returns
+ * TLDA_ERR_INVALID for bad sizes/parameters, TLDA_ERR_OOM if the workspace
+ * cannot be allocated. */
 tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, void *cuda_stream);
 
 /* Frees the context and its workspace (synchronises the stream first). */

@@ -5,12 +5,13 @@
 //
 //   k_qy_tc  [Q; Y] = [U; X] Phi   (eq. vec_deriv: Y = X Phi; the same-token
 //            term needs Q = U Phi).  M = 128 rows of [U; X] per CTA, N = Kp,
-//            K = Dp.  A by TMA from the BF16 copy UX16; B = Phi^T built in
-//            shared memory from the FP32 factors.
+//            K = Dp in 64-feature chunks.  A by TMA from the BF16 copy UX16;
+//            B from the swizzled BF16 image of Phi^T.
 //   k_g_tc   G1 + G2 = [X; U_t]^T [Z; Zc] as a split reduction over the
 //            reduction-major copies AT16 (Dp x ldT) and BT16 (Kp x ldT):
-//            each CTA streams 64-column chunks through a 4-stage TMA ring and
-//            accumulates a 128 x Kp tile in TMEM, then writes its partial.
+//            each CTA streams 64-column chunks through a TMA ring and
+//            accumulates a 128-feature x Kp tile in TMEM, then writes its
+//            rows of the partial.  D and K up to 512.
 //   k_zh_tc  Zc rows of the touched words, written transposed (BF16) next to
 //            the touched words' U^T columns.
 // Every wait on an mbarrier is bounded (about one second of clock cycles);
@@ -23,28 +24,39 @@ namespace tlda {
 namespace {
 using namespace tc;
 
+// Operands stream in 64-feature chunks through a ring of NST stages (A by
+// TMA, B as one bulk copy or TMA boxes).  N = KP is one MMA up to 256 columns,
+// two halves of KP/2 above that (each <= 256, a multiple of 16), accumulated
+// side by side in TMEM.
+__host__ __device__ constexpr int tc_stages(int kp) { return kp <= 256 ? 4 : kp <= 448 ? 3 : 2; }
+__host__ __device__ constexpr int tc_stage_bytes(int kp) { return 128 * 128 + kp * 128; }
+
 // ------------------------------------------------------------------ Q and Y
-template <int KA, int KP>
+template <int KP>
 __global__ void __launch_bounds__(128) k_qy_tc(StepArgs a, const __grid_constant__ CUtensorMap tmA) {
+  constexpr int NST = tc_stages(KP), NH = KP > 256 ? 2 : 1, NN = KP / NH;
+  constexpr int A_BYTES = 128 * 128, B_BYTES = KP * 128, STAGE = A_BYTES + B_BYTES;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = align1024(smem_raw);
-  unsigned char *sA = smem;                      // KA x [128 x 64] BF16
-  unsigned char *sB = smem + KA * 16384;         // KA x [KP x 64] BF16
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sB + KA * KP * 128);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + NST * STAGE);
+  uint64_t *empty = full + NST;
+  uint64_t *done = empty + NST;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nd = a.st->cur.n_docs;
   const int rows = a.V + nd;
   const int r0 = blockIdx.x * 128;
   if (r0 >= rows) return;
+  const int KA = a.Dp / 64;
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int i = 0; i < NST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(done, 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(tslot, tmem_cols(KP));
-  // B = Phi^T (KP x Dp, K-major): the swizzled image the scan kernel built
-  fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -52,29 +64,41 @@ __global__ void __launch_bounds__(128) k_qy_tc(StepArgs a, const __grid_constant
   __shared__ int failed;
   if (tid == 0) failed = 0;
   __syncthreads();
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&bars[0], KA * 16384 + KA * KP * 128);
-#pragma unroll
-    for (int kb = 0; kb < KA; ++kb) tma_load_2d(sA + kb * 16384, &tmA, &bars[0], kb * 64, r0);
-    bulk_load(sB, a.PhiImg, KA * KP * 128, &bars[0]);
-    if (mbar_wait(&bars[0], 0)) {
-      tc_fence_after();
-      const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
-#pragma unroll
-      for (int kk = 0; kk < KA * 4; ++kk) {
-        const uint64_t ad = sdesc_sw128(aBase + (kk >> 2) * 16384 + (kk & 3) * 32);
-        const uint64_t bd = sdesc_sw128(bBase + (kk >> 2) * KP * 128 + (kk & 3) * 32);
-        mma_bf16(tmem, ad, bd, idesc_bf16(128, KP), kk > 0 ? 1u : 0u);
+  if (tid == 0) {  // producer: A rows by TMA, B = the Phi^T image chunk (K-major, swizzled) by bulk copy
+    fence_proxy_async();
+    for (int i = 0; i < KA; ++i) {
+      const int st = i % NST;
+      if (i >= NST && !mbar_wait(&empty[st], ((i / NST) - 1) & 1)) {
+        failed = 1;
+        break;
       }
-      mma_commit(&bars[1]);
-    } else {
-      atomicOr(&a.st->err, kErrTimeout);
-      failed = 1;
+      unsigned char *sa = smem + st * STAGE, *sb = sa + A_BYTES;
+      mbar_arrive_expect_tx(&full[st], STAGE);
+      tma_load_2d(sa, &tmA, &full[st], i * 64, r0);
+      bulk_load(sb, a.PhiImg + (long long)i * KP * 64, B_BYTES, &full[st]);
     }
+  } else if (tid == 32) {  // MMA issuer
+    for (int i = 0; i < KA; ++i) {
+      const int st = i % NST;
+      if (!mbar_wait(&full[st], (i / NST) & 1)) {
+        failed = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t aBase = smem_u32(smem + st * STAGE), bBase = aBase + A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int h = 0; h < NH; ++h)
+          mma_bf16(tmem + h * NN, sdesc_sw128(aBase + kk * 32), sdesc_sw128(bBase + h * NN * 128 + kk * 32),
+                   idesc_bf16(128, NN), (i > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[st]);
+    }
+    mma_commit(done);
   }
   __syncthreads();
   // warp-uniform decision: tcgen05.ld below is .sync.aligned
-  const bool ok = __all_sync(0xffffffffu, !failed && mbar_wait(&bars[1], 0));
+  const bool ok = __all_sync(0xffffffffu, !failed && mbar_wait(done, 0));
   if (ok) {
     tc_fence_after();
     const int row = r0 + warp * 32 + lane;
@@ -91,7 +115,7 @@ __global__ void __launch_bounds__(128) k_qy_tc(StepArgs a, const __grid_constant
           *reinterpret_cast<float4 *>(out + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
       }
     }
-  } else if (lane == 0 && !failed) {
+  } else if (lane == 0) {
     atomicOr(&a.st->err, kErrTimeout);
   }
   tc_fence_before();
@@ -100,31 +124,34 @@ __global__ void __launch_bounds__(128) k_qy_tc(StepArgs a, const __grid_constant
 }
 
 // ------------------------------------------------------------------ G1 + G2
-constexpr int kStages = 4;
-
+// Block (s, mt): split s of the reduction chunks, feature rows mt*128 ..
 template <int KP>
 __global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant__ CUtensorMap tmA,
                                               const __grid_constant__ CUtensorMap tmB) {
+  constexpr int NST = tc_stages(KP), NH = KP > 256 ? 2 : 1, NN = KP / NH;
+  constexpr int A_BYTES = 128 * 128, B_BYTES = KP * 128, STAGE = A_BYTES + B_BYTES;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = align1024(smem_raw);
-  constexpr int A_BYTES = 128 * 128, B_BYTES = KP * 128, STAGE = A_BYTES + B_BYTES;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * STAGE);
-  uint64_t *empty = full + kStages;
-  uint64_t *done = empty + kStages;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + NST * STAGE);
+  uint64_t *empty = full + NST;
+  uint64_t *done = empty + NST;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nd = a.st->cur.n_docs, nt = a.same_token ? a.st->n_touched : 0;
   const int cB = (nd + 63) / 64, cT = (nt + 63) / 64, C = cB + cT;
-  const int s = blockIdx.x;
+  const int s = blockIdx.x, m0 = blockIdx.y * 128;
   const int c0 = (int)((long long)C * s / a.nsplit), c1 = (int)((long long)C * (s + 1) / a.nsplit);
   const int n = c1 - c0;
   float *gp = a.Gpart + (long long)s * a.Dp * a.Kp;
   if (n <= 0) {
-    for (int e = tid; e < a.Dp * a.Kp; e += 128) gp[e] = 0.f;
+    for (int e = tid; e < 128 * a.Kp; e += 128) {
+      const int row = m0 + e / a.Kp;
+      if (row < a.Dp) gp[(long long)row * a.Kp + e % a.Kp] = 0.f;
+    }
     return;
   }
   if (tid == 0) {
-    for (int i = 0; i < kStages; ++i) {
+    for (int i = 0; i < NST; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
@@ -141,8 +168,8 @@ __global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant_
   __syncthreads();
   if (tid == 0) {  // TMA producer
     for (int i = 0; i < n; ++i) {
-      const int st = i % kStages;
-      if (i >= kStages && !mbar_wait(&empty[st], ((i / kStages) - 1) & 1)) {
+      const int st = i % NST;
+      if (i >= NST && !mbar_wait(&empty[st], ((i / NST) - 1) & 1)) {
         failed = 1;
         break;
       }
@@ -150,13 +177,14 @@ __global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant_
       const int col = c < cB ? c * 64 : a.Bmax + (c - cB) * 64;
       unsigned char *sa = smem + st * STAGE, *sb = sa + A_BYTES;
       mbar_arrive_expect_tx(&full[st], STAGE);
-      tma_load_2d(sa, &tmA, &full[st], col, 0);
-      tma_load_2d(sb, &tmB, &full[st], col, 0);
+      tma_load_2d(sa, &tmA, &full[st], col, m0);
+#pragma unroll
+      for (int h = 0; h < NH; ++h) tma_load_2d(sb + h * NN * 128, &tmB, &full[st], col, h * NN);
     }
   } else if (tid == 32) {  // MMA issuer
     for (int i = 0; i < n; ++i) {
-      const int st = i % kStages;
-      if (!mbar_wait(&full[st], (i / kStages) & 1)) {
+      const int st = i % NST;
+      if (!mbar_wait(&full[st], (i / NST) & 1)) {
         failed = 1;
         break;
       }
@@ -164,8 +192,10 @@ __global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant_
       const uint32_t aBase = smem_u32(smem + st * STAGE), bBase = aBase + A_BYTES;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        mma_bf16(tmem, sdesc_sw128(aBase + kk * 32), sdesc_sw128(bBase + kk * 32), idesc_bf16(128, KP),
-                 (i > 0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+        for (int h = 0; h < NH; ++h)
+          mma_bf16(tmem + h * NN, sdesc_sw128(aBase + kk * 32), sdesc_sw128(bBase + h * NN * 128 + kk * 32),
+                   idesc_bf16(128, NN), (i > 0 || kk > 0) ? 1u : 0u);
       mma_commit(&empty[st]);
     }
     mma_commit(done);
@@ -174,7 +204,7 @@ __global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant_
   const bool ok = __all_sync(0xffffffffu, !failed && mbar_wait(done, 0));
   if (ok) {
     tc_fence_after();
-    const int row = warp * 32 + lane;
+    const int row = m0 + warp * 32 + lane;
 #pragma unroll
     for (int q0 = 0; q0 < KP; q0 += 16) {
       float v[16];
@@ -301,31 +331,34 @@ struct TcMaps {
   CUtensorMap bt;  // BT16: Kp x ldT, box Kp rows x 64
 };
 
-template <int KA, int KP>
+template <int KP>
+int tc_smem() {
+  return 1024 + tc_stages(KP) * tc_stage_bytes(KP) + 128;
+}
+
+template <int KP>
 void qy_launch(const StepArgs &a, const TcMaps &m, cudaStream_t s) {
-  const int smem = 1024 + KA * 16384 + KA * KP * 128 + 64;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_qy_tc<KA, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_qy_tc<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<KP>());
     attr = true;
   }
-  k_qy_tc<KA, KP><<<(a.V + a.Bmax + 127) / 128, 128, smem, s>>>(a, m.ux);
+  k_qy_tc<KP><<<(a.V + a.Bmax + 127) / 128, 128, tc_smem<KP>(), s>>>(a, m.ux);
 }
 
 template <int KP>
 void g_launch(const StepArgs &a, const TcMaps &m, cudaStream_t s) {
-  const int smem = 1024 + kStages * (128 * 128 + KP * 128) + 128;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_g_tc<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_g_tc<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<KP>());
     attr = true;
   }
-  k_g_tc<KP><<<a.nsplit, 128, smem, s>>>(a, m.at, m.bt);
+  k_g_tc<KP><<<dim3(a.nsplit, (a.Dp + 127) / 128), 128, tc_smem<KP>(), s>>>(a, m.at, m.bt);
 }
 
 }  // namespace
 
-bool tc_supported(int Dp, int Kp) { return Dp <= 128 && Kp <= 256; }
+bool tc_supported(int Dp, int Kp) { return Dp <= 512 && Kp <= 512; }
 
 void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const __nv_bfloat16 *BT16, int V,
                    int Bmax, int Dp, int Kp, int ldT) {
@@ -333,7 +366,7 @@ void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const _
   bool ok = make_map(&m->ug, UX16, Dp, (uint64_t)V, (uint64_t)Dp * 2, 1) &&
             make_map(&m->ux, UX16, Dp, (uint64_t)V + Bmax, (uint64_t)Dp * 2, 128) &&
             make_map(&m->at, AT16, ldT, Dp, (uint64_t)ldT * 2, 128) &&
-            make_map(&m->bt, BT16, ldT, Kp, (uint64_t)ldT * 2, Kp);
+            make_map(&m->bt, BT16, ldT, Kp, (uint64_t)ldT * 2, Kp > 256 ? Kp / 2 : Kp);
   if (!ok) {
     delete m;
     return nullptr;
@@ -345,29 +378,36 @@ void tc_free_maps(void *p) { delete static_cast<TcMaps *>(p); }
 
 const void *tc_gather_map(const void *maps) { return &static_cast<const TcMaps *>(maps)->ug; }
 
+#define TLDA_KP_DISPATCH(F)                                       \
+  switch (a.Kp) {                                                 \
+    case 64: return F<64>(a, m, s);                               \
+    case 128: return F<128>(a, m, s);                             \
+    case 192: return F<192>(a, m, s);                             \
+    case 256: return F<256>(a, m, s);                             \
+    case 320: return F<320>(a, m, s);                             \
+    case 384: return F<384>(a, m, s);                             \
+    case 448: return F<448>(a, m, s);                             \
+    default: return F<512>(a, m, s);                              \
+  }
+
 void launch_qy_tc(const StepArgs &a, cudaStream_t s) {
   const TcMaps &m = *static_cast<const TcMaps *>(a.tc_maps);
-  const int ka = a.Dp / 64;
-#define TLDA_QY(KAv, KPv) \
-  if (ka == KAv && a.Kp == KPv) return qy_launch<KAv, KPv>(a, m, s);
-  TLDA_QY(1, 64) TLDA_QY(1, 128) TLDA_QY(1, 192) TLDA_QY(1, 256)
-  TLDA_QY(2, 64) TLDA_QY(2, 128) TLDA_QY(2, 192) TLDA_QY(2, 256)
-#undef TLDA_QY
+  TLDA_KP_DISPATCH(qy_launch)
 }
 
 void launch_g_tc(const StepArgs &a, cudaStream_t s) {
   const TcMaps &m = *static_cast<const TcMaps *>(a.tc_maps);
-  if (a.Kp == 64) return g_launch<64>(a, m, s);
-  if (a.Kp == 128) return g_launch<128>(a, m, s);
-  if (a.Kp == 192) return g_launch<192>(a, m, s);
-  return g_launch<256>(a, m, s);
+  TLDA_KP_DISPATCH(g_launch)
 }
+#undef TLDA_KP_DISPATCH
 
 void launch_zh_tc(const StepArgs &a, cudaStream_t s) {
   const int nk = (a.Kp + 127) / 128;
   const int grid = round_up(a.V, 64) / 16;
   if (nk == 1) k_zh_tc<1><<<grid, 512, 0, s>>>(a);
-  else k_zh_tc<2><<<grid, 512, 0, s>>>(a);
+  else if (nk == 2) k_zh_tc<2><<<grid, 512, 0, s>>>(a);
+  else if (nk == 3) k_zh_tc<3><<<grid, 512, 0, s>>>(a);
+  else k_zh_tc<4><<<grid, 512, 0, s>>>(a);
 }
 
 }  // namespace tlda

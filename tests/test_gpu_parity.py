@@ -310,3 +310,31 @@ def test_state_roundtrip(lib, tmp_path):
     p.write_bytes(bytes(raw))
     with pytest.raises(lib.TLDAError):
         t2.load_state(str(p))
+
+
+# ----------------------------------------------------------------------------- wide BF16
+@pytest.mark.parametrize("K", [200, 300, 448, 500])
+def test_data_term_bf16_wide(lib, K):
+    """D = K up to 512 in the multi-kernel BF16 form: 64-feature chunks through
+    the TMA ring, N above 256 as two MMA halves, feature tiles of 128."""
+    from dataclasses import replace
+    sp = replace(ts.WORKLOADS["small_v500_k10"], name=f"wide_k{K}", V=1500, K=K, lam=60.0,
+                 seed=ts.WORKLOADS["small_v500_k10"].seed + K)
+    cdf, mu = ts.topics(sp)
+    W, m1 = O.population_whitening(mu, np.full(K, 1.0 / K))
+    W, m1 = W.astype(np.float32).astype(np.float64), m1.astype(np.float32).astype(np.float64)
+    c = ts.corpus(sp.with_docs(1500), cdf=cdf)
+    t = lib.TLDA(sp.V, K, alpha0=float(sp.alpha0), precision="bf16", max_batch=2048)
+    t.set_whitening(torch.tensor(W, dtype=torch.float32), torch.tensor(m1, dtype=torch.float32))
+    Phi0 = _phi0(sp)
+    dev = lib.DeviceCSR.from_corpus(c)
+    G, S3 = t.cp_data_term(dev, torch.tensor(Phi0, dtype=torch.float32, device="cuda"))
+    g = _oracle_grad(c, sp, W, m1, Phi0)
+    assert S3 == g["S3"]
+    assert C.rel(G.cpu().numpy(), g["G_data"]) < TOL16
+    Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(Phi)
+    loss = t.cp_step(dev, Phi, 0.002, grad=grad, want_loss=True)
+    assert C.rel(grad.cpu().numpy(), g["grad"]) < TOL16
+    assert abs(loss - g["loss"]) <= TOL16 * abs(g["loss"])
+    t.close()
