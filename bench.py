@@ -17,6 +17,7 @@ loss read back).
   python bench.py --e1 [--e1-reps N]   (the simulation study's shape check, batched mode)
   python bench.py --vi [--vi-docs N] [--vi-iters I]   (document-topic VI)
   python bench.py --billion [--billion-docs N]   (V = 100k, K = 300, on-device generation)
+  python bench.py --billion --stream-workload scale_v50k_k200 --billion-docs 50000000
 
 With N > 1 (torchrun) each rank runs an independent replica on its own shard
 of documents (the pass has no exchange step in this build); value = docs of
@@ -79,6 +80,8 @@ def parse():
     ap.add_argument("--billion-docs", type=int, default=16_000_000)
     ap.add_argument("--billion-chunk", type=int, default=1_000_000)
     ap.add_argument("--billion-r", type=int, default=512)
+    ap.add_argument("--stream-workload", default="billion_v100k_k300",
+                    help="workload of the chunked pipeline (billion_v100k_k300, scale_v50k_k200)")
     return ap.parse_args()
 
 
@@ -513,7 +516,8 @@ def billion_main(args):
     """`--billion`: the billion-document workload (V = 100,000, K = D = 300,
     Zipf(1.07)-shaped topics, alpha0 = 5, Poisson(15) lengths, minibatches of
     65,536) on the first N documents, in chunks generated on the device and
-    never stored whole.  Pass 1: each chunk is generated and added to the
+    never stored whole (with --stream-workload scale_v50k_k200: V = 50,000,
+    K = D = 200, alpha0 = 1, Poisson(20) lengths, minibatches of 8192).  Pass 1: each chunk is generated and added to the
     one-pass sketch and the token statistics.  Then one whitening from the
     sketch (r = 512).  Pass 2: each chunk is generated again and its
     minibatches take CP steps in the BF16 tensor-core form; then the same
@@ -525,7 +529,7 @@ def billion_main(args):
     import tlda_synth as ts
     from paper_2511_07809_gb300 import tlda
 
-    sp = ts.WORKLOADS["billion_v100k_k300"]
+    sp = ts.WORKLOADS[args.stream_workload]
     t0 = time.perf_counter()
     cdf, mu = ts.topics(sp)
     t_topics = time.perf_counter() - t0
@@ -598,12 +602,13 @@ def billion_main(args):
     rel32 = float((torch.linalg.norm(Phi - P32) / torch.linalg.norm(P32)).item())
     c32.close()
     line = {
-        "metric": "docs/sec of the billion-document workload (V=100k, K=300): on-device generation, "
-                  "one-pass sketch, whitening, CP pass",
+        "metric": f"docs/sec of the chunked streaming workload {sp.name} (V={sp.V}, K={sp.K}): on-device "
+                  "generation, one-pass sketch, whitening, CP pass",
         "value": docs / (ms_total / 1e3), "unit": UNIT, "n_gpus": 1, "steps": n_chunks * ((chunk + B - 1) // B),
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
-        "data": "synthetic: generated on the device (Zipf(1.07)-shaped Dirichlet topics, Poisson(15) lengths)",
-        "config": {"workload": "billion_v100k_k300", "V": sp.V, "K": sp.K, "D": sp.K, "docs": docs,
+        "data": f"synthetic: generated on the device (Dirichlet({sp.beta}) topics"
+                + (f", Zipf({sp.zipf_s})-shaped" if sp.zipf_s else "") + f", Poisson({sp.lam:g}) lengths)",
+        "config": {"workload": sp.name, "V": sp.V, "K": sp.K, "D": sp.K, "docs": docs,
                    "nnz": nnz_tot, "chunk_docs": chunk, "batch": B, "sketch_r": r, "lr": lr,
                    "l2": "inputs larger than L2: each chunk (about 0.1 GB of CSR) is generated into HBM "
                          "and read once per pass"},
