@@ -236,8 +236,9 @@ tlda_status tlda_fit_batched(tlda_ctx *ctx, const tlda_csr *corpus, const int64_
 /* Tile size of the persistent pass kernel: the most documents per tile,
  * 1..32 (each batch is split into ceil(n_docs / SMs) document tiles up to
  * this size).  With fixed_cap > 0 the size is set to fixed_cap and nothing
- * runs (corpus may be NULL).  With fixed_cap = 0 the candidates 8, 16, 24
- * and 32 are timed on up to the first 64 batches of `corpus` (device CSR,
+ * runs (corpus may be NULL).  With fixed_cap = 0 the candidates 8, 14, 16,
+ * 18, 20, 24, 28 and 32 are timed on up to the first 64 batches of `corpus`
+ * (device CSR,
  * batches as in tlda_cp_pass), stepping a scratch copy of Phi (D x K FP32,
  * device; Phi itself and the context's step and error state are left
  * unchanged: a corrupt batch among them is reported by the pass that steps

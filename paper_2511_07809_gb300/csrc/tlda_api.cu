@@ -256,7 +256,7 @@ tlda_status tune_tiles(tlda_ctx *ctx, const float *Phi, int n, cudaStream_t ps) 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int cands[] = {8, 16, 24, 32};
+  const int cands[] = {8, 14, 16, 18, 20, 24, 28, 32};
   int best = ctx->tile_cap;
   float best_ms = 0.f;
   tlda_status s = TLDA_OK;

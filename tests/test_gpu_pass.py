@@ -112,7 +112,7 @@ def test_autotune_leaves_phi_and_state(lib, tmp_path):
     before = Phi.clone()
     t.save_state(tmp_path / "a.tlda")
     cap = t.autotune(dev, offs, Phi)
-    assert cap in (8, 16, 24, 32)
+    assert cap in (8, 14, 16, 18, 20, 24, 28, 32)
     assert torch.equal(Phi, before)
     t.save_state(tmp_path / "b.tlda")
     assert (tmp_path / "a.tlda").read_bytes() == (tmp_path / "b.tlda").read_bytes()
@@ -163,7 +163,7 @@ def test_bench_sized_pass_sampled_steps(lib):
     lr = 5e-4  # with this whitening, SGD at 2e-3 leaves the basin after ~250 steps (the oracle too)
     Phi = torch.tensor(_phi0(sp), dtype=torch.float32, device="cuda")
     cap = t.autotune(dev, offs[:65], Phi)
-    assert cap in (8, 16, 24, 32)
+    assert cap in (8, 14, 16, 18, 20, 24, 28, 32)
     prev = 0
     for s_ in (137, 283, 399):
         t.cp_pass(dev, offs[prev:s_ + 1], Phi, lr)  # steps prev .. s_-1
