@@ -20,7 +20,7 @@ loss read back).
   python bench.py --billion --stream-workload scale_v50k_k200 --billion-docs 50000000
 
 With N > 1 (torchrun) each rank runs an independent replica on its own shard
-of documents (the pass has no exchange step in this build); value = docs of
+of documents (replicas: no exchange step between ranks); value = docs of
 all ranks / max-over-ranks time.
 """
 from __future__ import annotations
