@@ -667,8 +667,9 @@ def main():
     dev = tlda.DeviceCSR.from_corpus(corpus)
     precs = [args.precision] if args.precision != "auto" else ["bf16", "fp32"]
 
-    def make_ctx(prec):
-        return tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision=prec, max_batch=8192, seed=1)
+    def make_ctx(prec, same_token=True):
+        return tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision=prec, max_batch=8192, seed=1,
+                         same_token=same_token)
 
     # whitening fitted by the library on a prefix of the shard (outside the timed region)
     primary = None
@@ -835,6 +836,19 @@ def main():
                        "ms_per_step": ms2 / args.steps,
                        "recovery": recovery_l1(c2, Phi, mu, args.warmup + args.steps)}
             c2.close()
+    # the same primary form with the same-token correction off (the data term
+    # of eq. vec_deriv alone), on the same batches
+    no_st = None
+    if not args.no_compare:
+        c3 = make_ctx(primary, same_token=False)
+        c3.set_whitening(W, m1)
+        Phi = Phi0.clone()
+        ms3, _ = timed(c3, Phi)
+        ms3 = reduce_over_ranks(ms3, "max", world)
+        no_st = {"precision": primary, "same_token_correction": False, "value": docs_all / (ms3 / 1e3),
+                 "ms_per_step": ms3 / args.steps,
+                 "recovery": recovery_l1(c3, Phi, mu, args.warmup + args.steps)}
+        c3.close()
 
     # recovery of the pass (per-topic l1 after Hungarian matching), as a sanity figure
     recovery = recovery_l1(ctx, Phi_final, mu, args.warmup + args.steps)
@@ -868,7 +882,7 @@ def main():
                        "fit_docs": n_fit, "fit_s": round(t_fit, 2), "gen_s": round(t_gen, 2)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_timed,
-            "clocks": clocks, "compare": compare, "recovery": recovery,
+            "clocks": clocks, "compare": compare, "compare_same_token_off": no_st, "recovery": recovery,
             "kernel_shares": {k: round(v[1] / max(sum(x[1] for x in shares.values()), 1e-12), 4)
                               for k, v in shares.items() if v[0]},
         }

@@ -58,6 +58,30 @@ def test_pass_tile_sizes_match_oracle(lib, cap):
     t.close()
 
 
+def test_pass_without_same_token_correction(lib):
+    """same_token_correction = 0 (the data term of eq. vec_deriv alone) in the
+    persistent kernel, against the oracle's steps of the same form."""
+    sp = ts.WORKLOADS[NAME]
+    W, m1 = C.population_whitening(NAME)
+    t = lib.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="bf16", same_token=False)
+    t.set_whitening(torch.tensor(W, dtype=torch.float32), torch.tensor(m1, dtype=torch.float32))
+    t.autotune(fixed=18)
+    c = C.corpus(NAME, 12000)
+    offs = [0, 900, 4000, 9100, 12000]
+    Phi0 = _phi0(sp)
+    Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
+    losses = t.cp_pass(lib.DeviceCSR.from_corpus(c), offs, Phi, 0.002, losses=True)
+    P, lo = Phi0.copy(), []
+    for b in range(len(offs) - 1):
+        r = c.rows(offs[b], offs[b + 1])
+        P, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, 0.002, float(sp.alpha0), 0.0,
+                         same_token=False)
+        lo.append(g["loss"])
+    assert np.all(np.abs(losses - np.array(lo)) <= TOL16 * np.abs(np.array(lo)))
+    assert C.rel(Phi.cpu().numpy(), P) < TOL16
+    t.close()
+
+
 def test_pass_host_segments_equal_device_pass(lib):
     """A host-input pass large enough to be staged in several segments gives
     the device-input pass's Phi bit for bit (same kernel, same tiles)."""
