@@ -406,6 +406,18 @@ tlda_status tlda_generate_docs(uint64_t seed, int32_t V, int32_t K, const uint64
                                int32_t *indices_out, int32_t *counts_out, int64_t nnz_cap,
                                int64_t *scratch, int64_t *nnz_out, void *cuda_stream);
 
+/* ------------------------------------------------------------ self-test */
+
+/* Exercises the bounded grid barrier of the persistent kernels: a
+ * cooperative launch of *blocks_out blocks (the pass kernel's grid) in which
+ * block 0 never arrives.  Every block waits out its bound (about one second
+ * of clock cycles) or sees the abort flag that the first one to give up
+ * raises, and returns.  *gave_up_out counts the blocks that gave up.  The
+ * expected result is TLDA_ERR_TIMEOUT with every block counted; any context
+ * stays usable afterwards.  TLDA_ERR_UNIMPLEMENTED without cooperative
+ * launch.  Synchronises cuda_stream (NULL: the default stream). */
+tlda_status tlda_selftest_barrier(void *cuda_stream, int32_t *blocks_out, int32_t *gave_up_out);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Per-kernel device time, from CUDA events recorded around each launch on

@@ -638,6 +638,16 @@ __device__ bool grid_sync(PassCtl *ctl, unsigned target, int *s_ok) {
   return grid_wait(ctl, target, s_ok);
 }
 
+// Self-test of the bounded grid barrier: block 0 never arrives, so every
+// block waits the bound out (or sees the abort flag the first one raises) and
+// counts itself in S3[0].  Ends in about one second.
+__global__ void k_barrier_selftest(PassCtl *ctl) {
+  __shared__ int s_ok;
+  if (blockIdx.x != 0) grid_arrive(ctl);
+  const bool ok = grid_wait(ctl, gridDim.x, &s_ok);
+  if (threadIdx.x == 0 && !ok) atomicAdd(&ctl->S3[0], 1ull);
+}
+
 __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ float s_red[kFusedThreads / 32];
@@ -935,6 +945,12 @@ int pass_grid() {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass, kFusedThreads, kFusedSmem) != cudaSuccess)
     return 0;
   return (per_sm >= 1 && sms >= kMinPassGrid) ? sms : 0;
+}
+
+cudaError_t launch_barrier_selftest(PassCtl *ctl, cudaStream_t s, int grid) {
+  void *args[] = {&ctl};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_barrier_selftest), dim3(grid), dim3(32), args,
+                                     0, s);
 }
 
 cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, int grid) {

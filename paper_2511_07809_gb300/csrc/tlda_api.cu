@@ -432,6 +432,27 @@ const char *tlda_last_error(const tlda_ctx *ctx) { return ctx ? ctx->err.c_str()
 
 int32_t tlda_eig_sweeps(const tlda_ctx *ctx) { return ctx ? ctx->jacobi_sweeps : -1; }
 
+tlda_status tlda_selftest_barrier(void *cuda_stream, int32_t *blocks_out, int32_t *gave_up_out) {
+  const int grid = pass_grid();
+  if (blocks_out) *blocks_out = grid;
+  if (gave_up_out) *gave_up_out = 0;
+  if (grid <= 0) return TLDA_ERR_UNIMPLEMENTED;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  PassCtl *ctl = nullptr;
+  if (cudaMalloc(&ctl, sizeof(PassCtl)) != cudaSuccess) return TLDA_ERR_OOM;
+  PassCtl h{};
+  tlda_status st = TLDA_ERR_CUDA;
+  if (cudaMemsetAsync(ctl, 0, sizeof(PassCtl), s) == cudaSuccess &&
+      launch_barrier_selftest(ctl, s, grid) == cudaSuccess &&
+      cudaMemcpyAsync(&h, ctl, sizeof(PassCtl), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+      cudaStreamSynchronize(s) == cudaSuccess) {
+    if (gave_up_out) *gave_up_out = (int32_t)h.S3[0];
+    st = (h.abort && (int)h.S3[0] == grid) ? TLDA_ERR_TIMEOUT : TLDA_ERR_CUDA;
+  }
+  cudaFree(ctl);
+  return st;
+}
+
 tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, void *cuda_stream) {
   if (!out || !p) return TLDA_ERR_INVALID;
   *out = nullptr;

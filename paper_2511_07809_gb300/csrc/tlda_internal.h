@@ -224,6 +224,7 @@ bool fused_supported(int Dp, int Kp);
 void launch_fused(const StepArgs &a, cudaStream_t s, int grid);
 int pass_grid();                                  // co-resident blocks of the pass kernel (0: none)
 cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, int grid);
+cudaError_t launch_barrier_selftest(PassCtl *ctl, cudaStream_t s, int grid);
 // k_tc.cu (BF16 tensor-core form)
 bool tc_supported(int Dp, int Kp);
 void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const __nv_bfloat16 *BT16, int V,

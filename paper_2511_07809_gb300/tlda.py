@@ -39,7 +39,8 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_profile", "tlda_profile_read", "tlda_save_state", "tlda_load_state",
                 "tlda_cp_step_noalloc", "tlda_autotune", "tlda_online_begin",
                 "tlda_online_pass", "tlda_eig_sweeps", "tlda_fit_batched", "tlda_doc_topics",
-                "tlda_generate_docs", "tlda_online_accumulate", "tlda_online_whiten")
+                "tlda_generate_docs", "tlda_online_accumulate", "tlda_online_whiten",
+                "tlda_selftest_barrier")
 
 
 class Params(ctypes.Structure):
@@ -95,6 +96,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "tlda_online_begin": (i32, [vp, vp, i32]),
         "tlda_online_pass": (i32, [vp, P(CSR), vp, i32, vp, f32, i32, vp]),
         "tlda_online_accumulate": (i32, [vp, P(CSR)]),
+        "tlda_selftest_barrier": (i32, [vp, P(i32), P(i32)]),
         "tlda_online_whiten": (i32, [vp, vp]),
         "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
         "tlda_cp_step_noalloc": (i32, [P(CSR), vp, vp, i32, i32, f64, f32, vp, f32, vp, vp, vp]),
@@ -375,6 +377,15 @@ class TLDA:
 
     def load_state(self, path: str):
         self._check(self.lib.tlda_load_state(self.h, str(path).encode()))
+
+
+# ---------------------------------------------------------------------------- self-test
+def selftest_barrier():
+    """Run tlda_selftest_barrier: (status, blocks, blocks that gave up)."""
+    lib = load()
+    nb, ng = ctypes.c_int32(), ctypes.c_int32()
+    st = lib.tlda_selftest_barrier(None, ctypes.byref(nb), ctypes.byref(ng))
+    return st, nb.value, ng.value
 
 
 # ---------------------------------------------------------------------------- synthetic corpora
