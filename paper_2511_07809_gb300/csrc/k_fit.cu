@@ -1103,6 +1103,7 @@ tlda_status online_whiten(tlda_ctx *ctx, float *Phi) {
 extern "C" {
 
 tlda_status tlda_fit_moments(tlda_ctx *ctx, const tlda_csr *chunk, uint32_t flags) {
+  TLDA_RANGE();
   if (!ctx) return TLDA_ERR_INVALID;
   if (!(flags & (TLDA_ACCUMULATE | TLDA_FINALIZE))) return fail(ctx, TLDA_ERR_INVALID, "flags must hold ACCUMULATE and/or FINALIZE");
   if (ctx->V > kMaxFitV) return fail(ctx, TLDA_ERR_OOM, "fit_moments keeps a dense V x V pair-count matrix: V <= 65536");
@@ -1155,6 +1156,7 @@ tlda_status tlda_get_counts(const tlda_ctx *cctx, int64_t *C, int64_t *T, int64_
 }
 
 tlda_status tlda_unwhiten_topics(tlda_ctx *ctx, const float *Phi, double *mu_out, double *alpha_out, uint32_t flags) {
+  TLDA_RANGE();
   if (!ctx || !Phi || !mu_out || !alpha_out) return fail(ctx, TLDA_ERR_INVALID, "NULL argument");
   if (!ctx->whitened) return fail(ctx, TLDA_ERR_STATE, "no whitening: fit or set one first");
   cudaStream_t s = ctx->stream;
@@ -1201,6 +1203,7 @@ tlda_status tlda_unwhiten_topics(tlda_ctx *ctx, const float *Phi, double *mu_out
 }
 
 tlda_status tlda_online_begin(tlda_ctx *ctx, const double *Omega, int32_t r) {
+  TLDA_RANGE();
   if (!ctx) return TLDA_ERR_INVALID;
   if (!Omega || r < ctx->D || r > kMaxDim || (r & 1) || r > ctx->V)
     return fail(ctx, TLDA_ERR_INVALID, "the sketch needs an even r with D <= r <= min(V, 512)");
@@ -1234,6 +1237,7 @@ tlda_status tlda_online_begin(tlda_ctx *ctx, const double *Omega, int32_t r) {
 
 tlda_status tlda_online_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets, int32_t n_batches,
                              float *Phi, float lr, int32_t rewhiten_every, double *loss_out) {
+  TLDA_RANGE();
   if (!ctx) return TLDA_ERR_INVALID;
   if (!ctx->on_active) return fail(ctx, TLDA_ERR_STATE, "tlda_online_begin has not been called");
   if (!corpus || corpus->vocab != ctx->V || corpus->n_docs < 0 || !corpus->indptr ||
@@ -1258,6 +1262,7 @@ tlda_status tlda_online_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_
 }
 
 tlda_status tlda_online_accumulate(tlda_ctx *ctx, const tlda_csr *corpus) {
+  TLDA_RANGE();
   if (!ctx) return TLDA_ERR_INVALID;
   if (!ctx->on_active) return fail(ctx, TLDA_ERR_STATE, "tlda_online_begin has not been called");
   if (!corpus || corpus->vocab != ctx->V || corpus->n_docs < 0 || !corpus->indptr ||
@@ -1267,6 +1272,7 @@ tlda_status tlda_online_accumulate(tlda_ctx *ctx, const tlda_csr *corpus) {
 }
 
 tlda_status tlda_online_whiten(tlda_ctx *ctx, float *Phi) {
+  TLDA_RANGE();
   if (!ctx) return TLDA_ERR_INVALID;
   if (!ctx->on_active) return fail(ctx, TLDA_ERR_STATE, "tlda_online_begin has not been called");
   return online_whiten(ctx, Phi);

@@ -19,6 +19,7 @@
 
 #include "scan.cuh"
 #include "tlda.h"
+#include "tlda_internal.h"
 
 namespace {
 
@@ -207,6 +208,7 @@ extern "C" tlda_status tlda_generate_docs(uint64_t seed, int32_t V, int32_t K, c
                                           int32_t *indptr_out, int32_t *indices_out, int32_t *counts_out,
                                           int64_t nnz_cap, int64_t *scratch, int64_t *nnz_out,
                                           void *cuda_stream) {
+  TLDA_RANGE();
   if (V < 1 || K < 1 || !topic_cdf || a_num == 0 || a_den == 0 || !len_cdf || n_len < 1 ||
       n_len > kGenMaxLen + 1 || min_len < 0 || min_len > kGenMaxLen || doc0 < 0 || n_docs < 0 || !indptr_out ||
       !scratch || !nnz_out || nnz_cap < 0 || (nnz_cap > 0 && (!indices_out || !counts_out)))

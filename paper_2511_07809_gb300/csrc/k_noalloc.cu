@@ -75,6 +75,7 @@ extern "C" tlda_status tlda_cp_step_noalloc(const tlda_csr *batch, const float *
                                             int32_t dim, int32_t k, double alpha0, float theta,
                                             float *Phi, float lr, float *grad_out, int32_t *err_out,
                                             void *cuda_stream) {
+  TLDA_RANGE();
   if (!batch || !W || !m1 || !Phi) return TLDA_ERR_INVALID;
   const int V = batch->vocab, K = k, D = dim > 0 ? dim : k, B = batch->n_docs;
   if (V < 1 || K < 1 || D < K || D > V || B < 0 || !(alpha0 > 0.0) || !(theta > -1.f) ||

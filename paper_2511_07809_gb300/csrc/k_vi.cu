@@ -164,6 +164,7 @@ void launch(const tlda_csr &d, const float *mu, const float *alpha, int K, int n
 extern "C" tlda_status tlda_doc_topics(const tlda_csr *docs, const float *mu, const float *alpha, int32_t K,
                                        int32_t n_iter, float *theta_out, float *gamma_out, int32_t *err_out,
                                        void *cuda_stream) {
+  TLDA_RANGE();
   if (!docs || !mu || !alpha || !theta_out || K < 1 || K > tlda::kMaxDim || n_iter < 0 || docs->n_docs < 0 ||
       docs->vocab < 1 || (docs->n_docs > 0 && (!docs->indptr || !docs->indices || !docs->counts)))
     return TLDA_ERR_INVALID;

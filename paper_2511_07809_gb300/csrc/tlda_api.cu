@@ -454,6 +454,7 @@ tlda_status tlda_selftest_barrier(void *cuda_stream, int32_t *blocks_out, int32_
 }
 
 tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, void *cuda_stream) {
+  TLDA_RANGE();
   if (!out || !p) return TLDA_ERR_INVALID;
   *out = nullptr;
   const int K = p->k, D = p->dim > 0 ? p->dim : p->k;
@@ -612,6 +613,7 @@ tlda_status tlda_get_whitening(const tlda_ctx *cctx, float *W, float *m1, double
 }
 
 tlda_status tlda_whiten_batch(tlda_ctx *ctx, const tlda_csr *batch, float *X_out) {
+  TLDA_RANGE();
   if (!ctx) return TLDA_ERR_INVALID;
   tlda_status s = check_csr(ctx, batch);
   if (s) return s;
@@ -659,17 +661,20 @@ static tlda_status step_common(tlda_ctx *ctx, const tlda_csr *batch, float *Phi,
 
 tlda_status tlda_cp_step(tlda_ctx *ctx, const tlda_csr *batch, float *Phi, float lr, float *grad_out,
                          double *loss_out) {
+  TLDA_RANGE();
   return step_common(ctx, batch, Phi, lr, grad_out, loss_out, 0, nullptr, nullptr);
 }
 
 tlda_status tlda_cp_data_term(tlda_ctx *ctx, const tlda_csr *batch, const float *Phi, float *G_data_out,
                               int64_t *S3_out) {
+  TLDA_RANGE();
   if (ctx && !G_data_out) return fail(ctx, TLDA_ERR_INVALID, "G_data_out is NULL");
   return step_common(ctx, batch, const_cast<float *>(Phi), 0.f, nullptr, nullptr, 1, G_data_out, S3_out);
 }
 
 tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets,
                          int32_t n_batches, float *Phi, float lr, uint32_t flags, double *loss_out) {
+  TLDA_RANGE();
   if (!ctx) return TLDA_ERR_INVALID;
   tlda_status s = check_csr(ctx, corpus);
   if (s) return s;
@@ -804,6 +809,7 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
 tlda_status tlda_fit_batched(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets,
                              int32_t n_batches, int32_t epochs, int32_t n_starts, float *Phi, float lr,
                              uint32_t flags, double *loss_out) {
+  TLDA_RANGE();
   if (!ctx) return TLDA_ERR_INVALID;
   if (!corpus || !batch_offsets || !Phi || n_batches < 1 || epochs < 1 || n_starts < 1)
     return fail(ctx, TLDA_ERR_INVALID, "bad batched-fit arguments");
@@ -841,6 +847,7 @@ tlda_status tlda_fit_batched(tlda_ctx *ctx, const tlda_csr *corpus, const int64_
 
 tlda_status tlda_autotune(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets, int32_t n_batches,
                           const float *Phi, int32_t fixed_cap, int32_t *tile_cap_out) {
+  TLDA_RANGE();
   if (!ctx) return TLDA_ERR_INVALID;
   if (ctx->pass_grid <= 0) return fail(ctx, TLDA_ERR_UNIMPLEMENTED, "no persistent pass kernel on this context");
   if (fixed_cap < 0 || fixed_cap > 32) return fail(ctx, TLDA_ERR_INVALID, "tile size %d not in 1..32", fixed_cap);
@@ -900,6 +907,7 @@ tlda_status tlda_profile_read(tlda_ctx *ctx, int32_t kernel, const char **name, 
 }
 
 tlda_status tlda_save_state(const tlda_ctx *cctx, const char *path) {
+  TLDA_RANGE();
   tlda_ctx *ctx = const_cast<tlda_ctx *>(cctx);
   if (!ctx || !path) return TLDA_ERR_INVALID;
   if (!ctx->whitened) return fail(ctx, TLDA_ERR_STATE, "nothing to save: no whitening");
@@ -931,6 +939,7 @@ tlda_status tlda_save_state(const tlda_ctx *cctx, const char *path) {
 }
 
 tlda_status tlda_load_state(tlda_ctx *ctx, const char *path) {
+  TLDA_RANGE();
   if (!ctx || !path) return TLDA_ERR_INVALID;
   FILE *f = fopen(path, "rb");
   if (!f) return fail(ctx, TLDA_ERR_INVALID, "cannot open %s", path);

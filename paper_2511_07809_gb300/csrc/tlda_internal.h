@@ -11,6 +11,8 @@
 
 #include "tlda.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace tlda {
 
 constexpr int kMaxDim = 512;     // D and K are padded to multiples of 64, at most 512
@@ -119,6 +121,16 @@ struct StepArgs {
   float *grad_out;               // D x K or null
   float *gdata_out;              // D x K or null (mode 1)
 };
+
+// An NVTX range around one C-ABI call (named by the function; free when no
+// profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define TLDA_RANGE() ::tlda::NvtxRange tlda_nvtx_range_(__func__)
 
 }  // namespace tlda
 
