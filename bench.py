@@ -321,7 +321,7 @@ def online_main(args):
     dev = tlda.DeviceCSR.from_corpus(corpus)
     offs = np.concatenate([[0], np.cumsum(seq)]).astype(np.int64)
     r, every, lr = args.online_r, args.online_every, 5e-4
-    Om = torch.tensor(ts.gaussian(sp.seed, 0x4F4D, sp.V * r).reshape(sp.V, r))
+    Om = torch.tensor(ts.signs(sp.seed, 0x4F4D, sp.V * r).reshape(sp.V, r))
     ctx = tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="bf16", max_batch=8192, seed=1)
     ctx.online_begin(Om)
     Phi = torch.tensor(ts.initial_factors(sp.seed + 1, sp.K, sp.K), dtype=torch.float32, device="cuda")
@@ -535,7 +535,7 @@ def billion_main(args):
     t_topics = time.perf_counter() - t0
     r = args.billion_r
     t0 = time.perf_counter()
-    Om = torch.tensor(ts.gaussian(sp.seed, 0x4F4D, sp.V * r).reshape(sp.V, r))
+    Om = torch.tensor(ts.signs(sp.seed, 0x4F4D, sp.V * r).reshape(sp.V, r))
     t_omega = time.perf_counter() - t0
     a = sp.alpha0
     gen = tlda.DeviceGenerator(sp.seed, sp.V, sp.K, cdf, a.numerator, a.denominator, ts.len_table(sp), sp.min_len)

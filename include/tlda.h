@@ -255,8 +255,12 @@ tlda_status tlda_autotune(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *
  * context keeps exact token statistics (C, T, S2, S3) and a one-pass sketch
  * Z = P Omega of the pair counts P = sum_d (f_d f_d^T - diag f_d), with the
  * caller's test matrix Omega (V x r FP64, device, row-major, typically
- * Gaussian; r even, D <= r <= min(V, 512)).  Omega is copied and the
- * statistics are cleared; the context's whitening, if any, is kept.
+ * Gaussian or random signs; r even, D <= r <= min(V, 512)).  Omega is
+ * copied and the statistics are cleared; the context's whitening, if any, is
+ * kept.  The sketch's products use the FP32 values of Omega and sum in FP32
+ * within a document and within a run of at most 128 nonzeros of a word, then
+ * in FP64 (Z stays FP64): with +-1 entries every such sum is an integer, so Z
+ * is exact while those sums stay below 2^24 in magnitude.
  * Synchronises.  TLDA_ERR_INVALID for bad sizes. */
 tlda_status tlda_online_begin(tlda_ctx *ctx, const double *Omega, int32_t r);
 
@@ -285,9 +289,14 @@ tlda_status tlda_online_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_
  * to the token statistics and the sketch, as tlda_online_pass does for a
  * block, without re-whitening or CP steps.  With tlda_online_whiten this
  * gives the one-pass sketch of a corpus read in chunks before its CP pass.
- * Asynchronous; a corrupt document is reported by the next
- * tlda_online_whiten (TLDA_ERR_INVALID).  TLDA_ERR_STATE before
- * tlda_online_begin. */
+ * The corpus is taken in pieces of up to 262,144 documents and 16M nonzeros
+ * (Z += F^T (F Omega) - diag(F^T 1) Omega per piece, F its counts); the
+ * call reads the piece offsets back (a short synchronisation) and enqueues
+ * the rest.  A corrupt document (a decreasing indptr, an offset outside the
+ * piece's, a word outside [0, V) or not ascending, a count <= 0) adds
+ * nothing and is reported by the next tlda_online_whiten or
+ * tlda_online_get_sketch (TLDA_ERR_INVALID).  TLDA_ERR_OOM for a document
+ * of more than 16M nonzeros; TLDA_ERR_STATE before tlda_online_begin. */
 tlda_status tlda_online_accumulate(tlda_ctx *ctx, const tlda_csr *corpus);
 
 /* Rebuilds the whitening from the statistics accumulated so far, exactly as
@@ -295,6 +304,19 @@ tlda_status tlda_online_accumulate(tlda_ctx *ctx, const tlda_csr *corpus);
  * had a whitening and Phi (D x K FP32, device) is not NULL, Phi is carried
  * into the new basis.  Synchronises.  Errors as tlda_online_pass. */
 tlda_status tlda_online_whiten(tlda_ctx *ctx, float *Phi);
+
+/* Checkpoint of the online statistics: copies out the sketch Z = P Omega
+ * (V x r FP64, row-major), the word counts C (V int64) and T, S2, S3 (3
+ * int64), each to a host or device pointer (any may be NULL).  Synchronises.
+ * TLDA_ERR_INVALID, after the copies, if a corrupt document was met since
+ * tlda_online_begin; TLDA_ERR_STATE before tlda_online_begin. */
+tlda_status tlda_online_get_sketch(tlda_ctx *ctx, double *Z_out, int64_t *C_out, int64_t *TS_out);
+
+/* Resume: replaces the online statistics with saved ones (same shapes, host
+ * or device pointers, all required) and clears the corrupt-document flag.
+ * The test matrix is the one given to tlda_online_begin, which must have
+ * been called with the Omega and r of the saved run.  Synchronises. */
+tlda_status tlda_online_set_sketch(tlda_ctx *ctx, const double *Z, const int64_t *C, const int64_t *TS);
 
 /* --------------------------------------------------------------- recovery */
 #define TLDA_HOST_OUTPUT 1u    /* mu_out / alpha_out are host pointers */

@@ -17,8 +17,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <vector>
 
+#include "scan.cuh"
 #include "tlda_internal.h"
 
 using namespace tlda;
@@ -184,6 +186,11 @@ __global__ void k_gauss(float *O, long long n, unsigned long long seed) {
 __global__ void k_f2d(const float *x, double *y, long long n) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) y[e] = x[e];
+}
+
+__global__ void k_d2f(const double *x, float *y, long long n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) y[e] = (float)x[e];
 }
 
 // ------------------------------------------------------------------ small dense FP64
@@ -888,63 +895,247 @@ tlda_status finalize(tlda_ctx *ctx) {
 }
 
 // ------------------------------------------------------------------ fully online mode
-// One warp per document of a block of batches (absolute offsets into the
-// corpus CSR): validation, L, and the exact counts C_m, T, S2, S3; then the
-// document's part of the sketch Z = P Omega of the pair counts,
-// Z_m += f_m (f^T Omega - Omega_m) for each of its words (FP64 atomics).  A
-// document that fails validation adds nothing and sets *err.
-__global__ void __launch_bounds__(256) k_online_acc(const int32_t *indptr, const int32_t *indices,
-                                                     const int32_t *counts, int n_docs, int V, int r,
-                                                     const double *Om, double *Z, unsigned long long *C,
-                                                     unsigned long long *TS, int *err) {
-  constexpr int kCols = kMaxDim / 32;
+// The sketch Z = P Omega of the pair counts P = sum_d (f_d f_d^T - diag f_d),
+// taken over a piece of documents at a time as
+//   Z += F^T S - diag(c) Omega,   S = F Omega,   c = F^T 1,
+// with F the piece's document x word counts.  Row m of F^T S sums f_dm s_d
+// over the documents holding word m, which needs the piece's nonzeros grouped
+// by word (its transpose).  Per piece:
+//   k_sk_rows     one warp per document: validation, the token statistics,
+//                 s_d = f_d^T Omega into row d of S, and the number of
+//                 nonzeros of each word;
+//   scan          those numbers become each word's first slot;
+//   k_sk_scatter  one warp per document: each nonzero (document, count) into
+//                 a slot of its word;
+//   k_sk_z        one warp per run of kSkRun consecutive slots: for each word
+//                 met, the run's part of sum_d f_dm (s_d - Omega_m) added to
+//                 Z_m and sum_d f_dm to C_m; plainly when all the word's
+//                 slots lie in the run, with FP64 atomics when they cross its
+//                 ends.
+// Precision: the products and the sums within a document (s_d) and within a
+// run (at most kSkRun terms) are FP32, from an FP32 copy of Omega; Z
+// accumulates the runs in FP64.  (GB300's FP64 rate is 1/64 of its FP32
+// rate: with FP64 products the sketch would be bound by them.)
+// The per-nonzero work is two row gathers (Omega_m, then s_d) and no atomics
+// on Z.  The slots of a word are filled in no fixed order, so Z is not
+// bitwise reproducible (its sums are reordered).  A document that fails
+// validation adds nothing and sets *err.
+constexpr int kSkPieceDocs = 262144;          // documents per piece (rows of S)
+constexpr long long kSkPieceNnz = 16ll << 20;  // nonzeros per piece (slots)
+constexpr int kSkRun = 128;                    // slots per warp task of k_sk_z
+
+// Workspace of the sketch (one allocation, made by tlda_online_begin).
+struct SketchWs {
+  float *S;                          // kSkPieceDocs x r
+  int32_t *sd, *sf, *sm;             // slots: document (in the piece), count, word
+  int32_t *wcnt, *wfill;             // V + 1 (counts, then first slots), V
+  int64_t *scan;                     // scan_blocks(V) + 2
+  uint8_t *ok;                       // kSkPieceDocs: the document passed validation
+  static size_t al(size_t b) { return (b + 255) & ~size_t(255); }
+  static size_t bytes(size_t V, size_t r) {
+    return al(sizeof(float) * kSkPieceDocs * r) + 3 * al(sizeof(int32_t) * kSkPieceNnz) +
+           al(sizeof(int32_t) * (V + 1)) + al(sizeof(int32_t) * V) + al(sizeof(int64_t) * (scan_blocks((int)V) + 2)) +
+           al(kSkPieceDocs);
+  }
+  SketchWs(void *base, size_t V, size_t r) {
+    char *p = static_cast<char *>(base);
+    S = reinterpret_cast<float *>(p);
+    p += al(sizeof(float) * kSkPieceDocs * r);
+    int32_t **slot_bufs[] = {&sd, &sf, &sm};
+    for (int32_t **b : slot_bufs) {
+      *b = reinterpret_cast<int32_t *>(p);
+      p += al(sizeof(int32_t) * kSkPieceNnz);
+    }
+    wcnt = reinterpret_cast<int32_t *>(p);
+    p += al(sizeof(int32_t) * (V + 1));
+    wfill = reinterpret_cast<int32_t *>(p);
+    p += al(sizeof(int32_t) * V);
+    scan = reinterpret_cast<int64_t *>(p);
+    p += al(sizeof(int64_t) * (scan_blocks((int)V) + 2));
+    ok = reinterpret_cast<uint8_t *>(p);
+  }
+};
+
+struct SkPiece {
+  const int32_t *indptr, *indices, *counts;  // indptr of the piece's first document; absolute offsets
+  int n_docs, nz_lo, nz_hi;                  // documents; the piece's offsets lie in [nz_lo, nz_hi]
+  int V, r;
+};
+
+// KC columns of r per lane (column lane + 32 c); four nonzeros' Omega rows in flight.
+template <int KC>
+__global__ void __launch_bounds__(256) k_sk_rows(SkPiece q, const float *__restrict__ Om, float *__restrict__ S,
+                                                 int32_t *wcnt, uint8_t *ok, unsigned long long *TS, int *err) {
   const int doc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (doc >= n_docs) return;
-  const long long p0 = indptr[doc], p1 = indptr[doc + 1];
-  if (p0 < 0 || p1 < p0) {
-    if (lane == 0) atomicOr(err, 1);
-    return;
-  }
-  double sv[kCols];
-#pragma unroll
-  for (int i = 0; i < kCols; ++i) sv[i] = 0.0;
+  if (doc >= q.n_docs) return;
+  const int p0 = q.indptr[doc], p1 = q.indptr[doc + 1];
+  bool bad = p0 < q.nz_lo || p1 > q.nz_hi || p1 < p0;
   long long L = 0;
-  int prev = -1;
-  bool bad = false;
-  for (long long p = p0; p < p1; ++p) {  // warp-uniform loop
-    const int m = indices[p], f = counts[p];
-    if (m < 0 || m >= V || f <= 0 || m <= prev) {
-      bad = true;
-      break;
+  if (!bad)
+    for (int p = p0 + lane; p < p1; p += 32) {
+      const int m = q.indices[p], f = q.counts[p];
+      const int prev = p > p0 ? q.indices[p - 1] : -1;
+      if (m < 0 || m >= q.V || f <= 0 || m <= prev) bad = true;
+      else L += f;
     }
-    prev = m;
-    L += f;
-    const double *om = Om + (long long)m * r;
-#pragma unroll
-    for (int i = 0; i < kCols; ++i) {
-      const int col = lane + 32 * i;
-      if (col < r) sv[i] += (double)f * om[col];
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) {
+      ok[doc] = 0;
+      atomicOr(err, 1);
     }
-  }
-  if (bad) {
-    if (lane == 0) atomicOr(err, 1);
     return;
   }
-  for (long long p = p0; p < p1; ++p) {
-    const int m = indices[p], f = counts[p];
-    const double *om = Om + (long long)m * r;
-    double *z = Z + (long long)m * r;
 #pragma unroll
-    for (int i = 0; i < kCols; ++i) {
-      const int col = lane + 32 * i;
-      if (col < r) atomicAdd(z + col, (double)f * (sv[i] - om[col]));
+  for (int o = 16; o > 0; o >>= 1) L += __shfl_xor_sync(0xffffffffu, L, o);
+  float sv[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) sv[c] = 0.f;
+  for (int base = p0; base < p1; base += 32) {
+    const int n = min(32, p1 - base);
+    const int mj = lane < n ? q.indices[base + lane] : 0, fj = lane < n ? q.counts[base + lane] : 0;
+    for (int i = 0; i < n; i += 4) {
+      int mm[4];
+      float ff[4], row[4][KC];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        mm[u] = __shfl_sync(0xffffffffu, mj, (i + u) & 31);
+        ff[u] = (float)__shfl_sync(0xffffffffu, fj, (i + u) & 31);
+        if (i + u >= n) ff[u] = 0.f;  // lanes past the end hold word 0, count 0
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < KC; ++c) {
+          const int col = lane + 32 * c;
+          row[u][c] = col < q.r ? __ldg(Om + (long long)mm[u] * q.r + col) : 0.f;
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < KC; ++c) sv[c] = fmaf(ff[u], row[u][c], sv[c]);
     }
-    if (lane == 0) atomicAdd(C + m, (unsigned long long)f);
   }
-  if (lane == 0 && L > 0) {
-    atomicAdd(TS + 0, (unsigned long long)L);
-    atomicAdd(TS + 1, (unsigned long long)(L * (L - 1)));
-    atomicAdd(TS + 2, (unsigned long long)(L * (L - 1) * (L - 2)));
+  float *srow = S + (long long)doc * q.r;
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    const int col = lane + 32 * c;
+    if (col < q.r) srow[col] = sv[c];
+  }
+  for (int p = p0 + lane; p < p1; p += 32) atomicAdd(wcnt + q.indices[p] + 1, 1);
+  if (lane == 0) {
+    ok[doc] = 1;
+    if (L > 0) {
+      atomicAdd(TS + 0, (unsigned long long)L);
+      atomicAdd(TS + 1, (unsigned long long)(L * (L - 1)));
+      atomicAdd(TS + 2, (unsigned long long)(L * (L - 1) * (L - 2)));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_sk_scatter(SkPiece q, const uint8_t *ok, const int32_t *wcnt, int32_t *wfill,
+                                                    int32_t *sd, int32_t *sf, int32_t *sm, int *err) {
+  const int doc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (doc >= q.n_docs || !ok[doc]) return;
+  const int p0 = q.indptr[doc], p1 = q.indptr[doc + 1];
+  for (int p = p0 + lane; p < p1; p += 32) {
+    const int m = q.indices[p];
+    const long long slot = (long long)wcnt[m] + atomicAdd(wfill + m, 1);
+    if (slot < kSkPieceNnz) {  // more slots than the piece's offsets span: overlapping documents
+      sd[slot] = doc;
+      sf[slot] = q.counts[p];
+      sm[slot] = m;
+    } else {
+      atomicOr(err, 1);
+    }
+  }
+}
+
+template <int KC>
+__device__ __forceinline__ void sk_flush(int m, const float (&acc)[KC], long long fs, long long lo, long long hi,
+                                         const int32_t *wcnt, int r, double *Z, unsigned long long *C, int lane) {
+  const bool whole = wcnt[m] >= lo && wcnt[m + 1] <= hi;  // no other run holds word m
+  double *z = Z + (long long)m * r;
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    const int col = lane + 32 * c;
+    if (col < r) {
+      if (whole) z[col] += (double)acc[c];
+      else atomicAdd(z + col, (double)acc[c]);
+    }
+  }
+  if (lane == 0) {
+    if (whole) C[m] += (unsigned long long)fs;
+    else atomicAdd(C + m, (unsigned long long)fs);
+  }
+}
+
+template <int KC>
+__global__ void __launch_bounds__(256) k_sk_z(const int32_t *__restrict__ wcnt, const int32_t *__restrict__ sd,
+                                              const int32_t *__restrict__ sf, const int32_t *__restrict__ sm,
+                                              const int64_t *total_p, int r, const float *__restrict__ S,
+                                              const float *__restrict__ Om, double *Z, unsigned long long *C,
+                                              int *err) {
+  const long long total = *total_p;  // valid nonzeros of the piece
+  if (total > kSkPieceNnz) {         // k_sk_scatter dropped slots and set *err
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 1);
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long runs = (total + kSkRun - 1) / kSkRun;
+  for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < runs; t += nwarps) {
+    const long long lo = t * kSkRun, hi = min(total, lo + kSkRun);
+    float acc[KC], om[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) acc[c] = om[c] = 0.f;
+    long long fs = 0;
+    int cur = -1;
+    for (long long base = lo; base < hi; base += 32) {
+      const int n = (int)min(32ll, hi - base);
+      const bool in = lane < n;
+      const int mj = in ? sm[base + lane] : 0, dj = in ? sd[base + lane] : 0, fj = in ? sf[base + lane] : 0;
+      for (int i = 0; i < n; i += 4) {
+        int mm[4], dd[4], ff[4];
+        float row[4][KC];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          mm[u] = __shfl_sync(0xffffffffu, mj, (i + u) & 31);
+          dd[u] = __shfl_sync(0xffffffffu, dj, (i + u) & 31);
+          ff[u] = __shfl_sync(0xffffffffu, fj, (i + u) & 31);
+          if (u > 0 && i + u >= n) {  // past the end: repeat the previous slot with count 0
+            mm[u] = mm[u - 1];
+            dd[u] = dd[u - 1];
+            ff[u] = 0;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int c = 0; c < KC; ++c) {
+            const int col = lane + 32 * c;
+            row[u][c] = col < r ? S[(long long)dd[u] * r + col] : 0.f;
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (mm[u] != cur) {
+            if (cur >= 0) sk_flush<KC>(cur, acc, fs, lo, hi, wcnt, r, Z, C, lane);
+            cur = mm[u];
+#pragma unroll
+            for (int c = 0; c < KC; ++c) {
+              const int col = lane + 32 * c;
+              acc[c] = 0.f;
+              om[c] = col < r ? __ldg(Om + (long long)cur * r + col) : 0.f;
+            }
+            fs = 0;
+          }
+          const float fu = (float)ff[u];
+#pragma unroll
+          for (int c = 0; c < KC; ++c) acc[c] = fmaf(fu, row[u][c] - om[c], acc[c]);
+          fs += ff[u];
+        }
+      }
+    }
+    if (cur >= 0) sk_flush<KC>(cur, acc, fs, lo, hi, wcnt, r, Z, C, lane);
   }
 }
 
@@ -1076,15 +1267,55 @@ tlda_status online_rotate(tlda_ctx *ctx, float *Phi) {
   return TLDA_OK;
 }
 
-// Documents [d0, d0 + nd) of `corpus` into the online statistics and sketch
-// (asynchronous; validation errors land in on_err).
+// Documents [d0, d0 + nd) of `corpus` into the online statistics and sketch,
+// in pieces of at most kSkPieceDocs documents and kSkPieceNnz nonzeros (the
+// piece offsets are read back once; validation errors land in on_err).
 tlda_status online_accumulate(tlda_ctx *ctx, const tlda_csr *corpus, int64_t d0, int nd) {
   if (nd <= 0) return TLDA_OK;
-  const long long threads = (long long)nd * 32;
-  k_online_acc<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(
-      corpus->indptr + d0, corpus->indices, corpus->counts, nd, ctx->V, ctx->on_r, ctx->on_Om, ctx->on_Z,
-      ctx->on_C, ctx->on_TS, ctx->on_err);
-  CKF(cudaGetLastError());
+  cudaStream_t s = ctx->stream;
+  const int V = ctx->V, r = ctx->on_r, kc = (r + 31) / 32;
+  SketchWs w(ctx->on_sk, V, r);
+  int64_t *total = w.scan + scan_blocks(V);
+  auto piece = [&](int64_t a, int n, int32_t lo, int32_t hi) -> tlda_status {
+    const SkPiece q{corpus->indptr + a, corpus->indices, corpus->counts, n, lo, hi, V, r};
+    CKF(cudaMemsetAsync(w.wcnt, 0, sizeof(int32_t) * (V + 1), s));
+    CKF(cudaMemsetAsync(w.wfill, 0, sizeof(int32_t) * V, s));
+    const unsigned g = (unsigned)(((long long)n * 32 + 255) / 256);
+    if (kc <= 4) k_sk_rows<4><<<g, 256, 0, s>>>(q, ctx->on_Om32, w.S, w.wcnt, w.ok, ctx->on_TS, ctx->on_err);
+    else if (kc <= 8) k_sk_rows<8><<<g, 256, 0, s>>>(q, ctx->on_Om32, w.S, w.wcnt, w.ok, ctx->on_TS, ctx->on_err);
+    else k_sk_rows<16><<<g, 256, 0, s>>>(q, ctx->on_Om32, w.S, w.wcnt, w.ok, ctx->on_TS, ctx->on_err);
+    scan_counts(w.wcnt, V, w.scan, total, s);
+    k_sk_scatter<<<g, 256, 0, s>>>(q, w.ok, w.wcnt, w.wfill, w.sd, w.sf, w.sm, ctx->on_err);
+    const long long span = std::max<long long>(1, (long long)hi - lo);
+    const unsigned zg = (unsigned)std::min<long long>((span + 8ll * kSkRun - 1) / (8ll * kSkRun), 4ll * ctx->num_sms);
+    if (kc <= 4) k_sk_z<4><<<zg, 256, 0, s>>>(w.wcnt, w.sd, w.sf, w.sm, total, r, w.S, ctx->on_Om32, ctx->on_Z, ctx->on_C, ctx->on_err);
+    else if (kc <= 8) k_sk_z<8><<<zg, 256, 0, s>>>(w.wcnt, w.sd, w.sf, w.sm, total, r, w.S, ctx->on_Om32, ctx->on_Z, ctx->on_C, ctx->on_err);
+    else k_sk_z<16><<<zg, 256, 0, s>>>(w.wcnt, w.sd, w.sf, w.sm, total, r, w.S, ctx->on_Om32, ctx->on_Z, ctx->on_C, ctx->on_err);
+    CKF(cudaGetLastError());
+    return TLDA_OK;
+  };
+  // a piece whose offsets span more than kSkPieceNnz slots is halved
+  std::function<tlda_status(int64_t, int64_t, int32_t, int32_t)> run = [&](int64_t a, int64_t b, int32_t lo,
+                                                                          int32_t hi) -> tlda_status {
+    if ((long long)hi - lo <= kSkPieceNnz) return piece(a, (int)(b - a), lo, hi);
+    if (b - a == 1) return fail(ctx, TLDA_ERR_OOM, "a document with more than 16M nonzeros");
+    const int64_t mid = a + (b - a) / 2;
+    int32_t hm = 0;
+    CKF(cudaMemcpyAsync(&hm, corpus->indptr + mid, sizeof hm, cudaMemcpyDeviceToHost, s));
+    CKF(cudaStreamSynchronize(s));
+    if (tlda_status st = run(a, mid, lo, hm)) return st;
+    return run(mid, b, hm, hi);
+  };
+  const int np = (nd + kSkPieceDocs - 1) / kSkPieceDocs;
+  std::vector<int32_t> h(np + 1);
+  CKF(cudaMemcpy2DAsync(h.data(), sizeof(int32_t), corpus->indptr + d0, sizeof(int32_t) * kSkPieceDocs,
+                        sizeof(int32_t), np, cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(h.data() + np, corpus->indptr + d0 + nd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CKF(cudaStreamSynchronize(s));
+  for (int i = 0; i < np; ++i) {
+    const int64_t a = d0 + (int64_t)i * kSkPieceDocs, b = std::min<int64_t>(a + kSkPieceDocs, d0 + nd);
+    if (tlda_status st = run(a, b, h[i], h[i + 1])) return st;
+  }
   return TLDA_OK;
 }
 
@@ -1212,11 +1443,17 @@ tlda_status tlda_online_begin(tlda_ctx *ctx, const double *Omega, int32_t r) {
     if (ctx->on_Om) cudaFree(ctx->on_Om);
     if (ctx->on_Z) cudaFree(ctx->on_Z);
     if (ctx->on_ws) cudaFree(ctx->on_ws);
+    if (ctx->on_sk) cudaFree(ctx->on_sk);
+    if (ctx->on_Om32) cudaFree(ctx->on_Om32);
     ctx->on_Om = ctx->on_Z = ctx->on_ws = nullptr;
+    ctx->on_sk = nullptr;
+    ctx->on_Om32 = nullptr;
     ctx->on_r = 0;
     CKF(dalloc(&ctx->on_Om, V * r));
     CKF(dalloc(&ctx->on_Z, V * r));
     CKF(dalloc(&ctx->on_ws, OnlineWs::words(V, r, ctx->D)));
+    CKF(dalloc(reinterpret_cast<char **>(&ctx->on_sk), SketchWs::bytes(V, r)));
+    CKF(dalloc(&ctx->on_Om32, V * r));
     ctx->on_r = r;
   }
   if (!ctx->on_C) CKF(dalloc(&ctx->on_C, V));
@@ -1226,6 +1463,8 @@ tlda_status tlda_online_begin(tlda_ctx *ctx, const double *Omega, int32_t r) {
   if (!ctx->on_Wold) CKF(dalloc(&ctx->on_Wold, V * ctx->D));
   cudaStream_t s = ctx->stream;
   CKF(cudaMemcpyAsync(ctx->on_Om, Omega, sizeof(double) * V * r, cudaMemcpyDeviceToDevice, s));
+  k_d2f<<<(unsigned)((V * r + 255) / 256), 256, 0, s>>>(ctx->on_Om, ctx->on_Om32, (long long)(V * r));
+  CKF(cudaGetLastError());
   CKF(cudaMemsetAsync(ctx->on_Z, 0, sizeof(double) * V * r, s));
   CKF(cudaMemsetAsync(ctx->on_C, 0, sizeof(unsigned long long) * V, s));
   CKF(cudaMemsetAsync(ctx->on_TS, 0, sizeof(unsigned long long) * 3, s));
@@ -1276,6 +1515,37 @@ tlda_status tlda_online_whiten(tlda_ctx *ctx, float *Phi) {
   if (!ctx) return TLDA_ERR_INVALID;
   if (!ctx->on_active) return fail(ctx, TLDA_ERR_STATE, "tlda_online_begin has not been called");
   return online_whiten(ctx, Phi);
+}
+
+tlda_status tlda_online_get_sketch(tlda_ctx *ctx, double *Z_out, int64_t *C_out, int64_t *TS_out) {
+  TLDA_RANGE();
+  if (!ctx) return TLDA_ERR_INVALID;
+  if (!ctx->on_active) return fail(ctx, TLDA_ERR_STATE, "tlda_online_begin has not been called");
+  const size_t V = ctx->V, r = ctx->on_r;
+  cudaStream_t s = ctx->stream;
+  int herr = 0;
+  if (Z_out) CKF(cudaMemcpyAsync(Z_out, ctx->on_Z, sizeof(double) * V * r, cudaMemcpyDefault, s));
+  if (C_out) CKF(cudaMemcpyAsync(C_out, ctx->on_C, sizeof(int64_t) * V, cudaMemcpyDefault, s));
+  if (TS_out) CKF(cudaMemcpyAsync(TS_out, ctx->on_TS, sizeof(int64_t) * 3, cudaMemcpyDefault, s));
+  CKF(cudaMemcpyAsync(&herr, ctx->on_err, sizeof herr, cudaMemcpyDeviceToHost, s));
+  CKF(cudaStreamSynchronize(s));
+  if (herr) return fail(ctx, TLDA_ERR_INVALID, "a corrupt document was met since tlda_online_begin");
+  return TLDA_OK;
+}
+
+tlda_status tlda_online_set_sketch(tlda_ctx *ctx, const double *Z, const int64_t *C, const int64_t *TS) {
+  TLDA_RANGE();
+  if (!ctx) return TLDA_ERR_INVALID;
+  if (!ctx->on_active) return fail(ctx, TLDA_ERR_STATE, "tlda_online_begin has not been called");
+  if (!Z || !C || !TS) return fail(ctx, TLDA_ERR_INVALID, "Z, C and TS are required");
+  const size_t V = ctx->V, r = ctx->on_r;
+  cudaStream_t s = ctx->stream;
+  CKF(cudaMemcpyAsync(ctx->on_Z, Z, sizeof(double) * V * r, cudaMemcpyDefault, s));
+  CKF(cudaMemcpyAsync(ctx->on_C, C, sizeof(int64_t) * V, cudaMemcpyDefault, s));
+  CKF(cudaMemcpyAsync(ctx->on_TS, TS, sizeof(int64_t) * 3, cudaMemcpyDefault, s));
+  CKF(cudaMemsetAsync(ctx->on_err, 0, sizeof(int), s));
+  CKF(cudaStreamSynchronize(s));
+  return TLDA_OK;
 }
 
 }  // extern "C"

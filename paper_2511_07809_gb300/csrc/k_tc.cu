@@ -225,70 +225,89 @@ __global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant_
 }
 
 // ------------------------------------------------------------------ Zc (BF16, transposed)
-// One warp per compact slot t (16 per block): Zc_t = q (2 c q - 2 H_m) and the
-// word's U row are staged in shared memory, then written as 32-byte runs into
-// columns Bmax + t0 .. t0+16 of BT16 and AT16; H_m and c_m are cleared.  Slots
-// in [n_touched, round_up(n_touched, 64)) write zero columns (chunk padding).
-template <int NK>
+// One block per 64 compact slots t0 .. t0+63 (touched words m = widx[t]).  It
+// walks the Kp + Dp output rows in tiles of 64: rows k < Kp of BT16 take
+// Zc_t[k] = q_mk (2 c_m q_mk - 2 H_mk) (H_mk is cleared), rows i of AT16 take
+// U_m[i].  Each tile is staged transposed in shared memory and written as 64
+// rows of 128 bytes (whole lines) into columns Bmax + t0 .. t0+63, so a block
+// has the pages of 64 rows in flight at a time rather than those of all
+// Kp + Dp rows.  Slots in [n_touched, round_up(n_touched, 64)) write zero
+// columns (chunk padding); the slots' c_m are cleared at the end.
+constexpr int kZhSlots = 64;
+constexpr int kZhPitch = 66;  // staged row: 64 slots + 2 (33 words: conflict-free reads)
+
 __global__ void __launch_bounds__(512) k_zh_tc(StepArgs a) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t0 = blockIdx.x * 16, t = t0 + warp;
-  const int nt = a.st->n_touched;
-  if (t0 >= round_up(nt, 64)) return;
-  __shared__ __align__(16) __nv_bfloat16 zs[16 * kMaxDim];
-  __shared__ __align__(16) __nv_bfloat16 us[16 * kMaxDim];
-  float ls = 0.f, c = 0.f;
-  int m = -1;
-  if (t < nt) {
-    m = a.widx[t];
-    c = (float)a.cnt[m];
+  __shared__ __align__(16) __nv_bfloat16 zt[64 * kZhPitch];  // [row of the tile][slot]
+  __shared__ int ms[kZhSlots];
+  __shared__ float cs[kZhSlots];
+  __shared__ double lsum[16];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int t0 = blockIdx.x * kZhSlots, nt = a.st->n_touched;
+  if (t0 >= round_up(nt, 64)) return;  // uniform over the block
+  if (tid < kZhSlots) {
+    const int t = t0 + tid;
+    const int m = t < nt ? a.widx[t] : -1;
+    ms[tid] = m;
+    cs[tid] = m >= 0 ? (float)a.cnt[m] : 0.f;
   }
+  __syncthreads();
+  double ls = 0.0;
+  const long long colT = (long long)a.Bmax + t0;
+  for (int r0 = 0; r0 < a.Kp + a.Dp; r0 += 64) {  // Kp and Dp are multiples of 64
+    const bool isB = r0 < a.Kp;
+    if (isB) {
+      for (int e = tid; e < kZhSlots * 16; e += 512) {  // slot, four columns
+        const int sl = e >> 4, c4 = (e & 15) * 4, m = ms[sl];
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
+        if (m >= 0) {
+          float4 *hp = reinterpret_cast<float4 *>(a.H32 + (long long)m * a.Kp + r0 + c4);
+          const float4 q = *reinterpret_cast<const float4 *>(a.Q32 + (long long)m * a.Kp + r0 + c4);
+          const float4 h = *hp;
+          const float c = cs[sl];
+          z[0] = q.x * (2.f * c * q.x - 2.f * h.x);
+          z[1] = q.y * (2.f * c * q.y - 2.f * h.y);
+          z[2] = q.z * (2.f * c * q.z - 2.f * h.z);
+          z[3] = q.w * (2.f * c * q.w - 2.f * h.w);
+          *hp = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (a.want_loss)
+            ls += 2.0 * (double)c * (double)(q.x * q.x * q.x + q.y * q.y * q.y + q.z * q.z * q.z + q.w * q.w * q.w);
+        }
 #pragma unroll
-  for (int v = 0; v < NK; ++v) {
-    const int col = v * 128 + lane * 4;
-    if (col < a.Kp) {
-      float z[4] = {0.f, 0.f, 0.f, 0.f};
-      if (m >= 0) {
-        float4 *hp = reinterpret_cast<float4 *>(a.H32 + (long long)m * a.Kp + col);
-        const float4 q = *reinterpret_cast<const float4 *>(a.Q32 + (long long)m * a.Kp + col);
-        const float4 h = *hp;
-        z[0] = q.x * (2.f * c * q.x - 2.f * h.x);
-        z[1] = q.y * (2.f * c * q.y - 2.f * h.y);
-        z[2] = q.z * (2.f * c * q.z - 2.f * h.z);
-        z[3] = q.w * (2.f * c * q.w - 2.f * h.w);
-        *hp = make_float4(0.f, 0.f, 0.f, 0.f);
-        ls += q.x * q.x * q.x + q.y * q.y * q.y + q.z * q.z * q.z + q.w * q.w * q.w;
+        for (int k = 0; k < 4; ++k) zt[(c4 + k) * kZhPitch + sl] = __float2bfloat16_rn(z[k]);
       }
-      __nv_bfloat162 *sz = reinterpret_cast<__nv_bfloat162 *>(zs + warp * a.Kp + col);
-      sz[0] = __floats2bfloat162_rn(z[0], z[1]);
-      sz[1] = __floats2bfloat162_rn(z[2], z[3]);
+    } else {
+      const int i0 = r0 - a.Kp;
+      for (int e = tid; e < kZhSlots * 8; e += 512) {  // slot, eight columns
+        const int sl = e >> 3, c8 = (e & 7) * 8, m = ms[sl];
+        uint4 u = make_uint4(0u, 0u, 0u, 0u);
+        if (m >= 0) u = *reinterpret_cast<const uint4 *>(a.U16 + (long long)m * a.Dp + i0 + c8);
+        const __nv_bfloat16 *uv = reinterpret_cast<const __nv_bfloat16 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) zt[(c8 + k) * kZhPitch + sl] = uv[k];
+      }
+    }
+    __syncthreads();
+    {
+      const int row = tid >> 3, j = tid & 7;  // 64 rows x 8 pieces of 16 bytes
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(zt + row * kZhPitch + 8 * j);
+      const uint4 v = make_uint4(src[0], src[1], src[2], src[3]);
+      __nv_bfloat16 *dst = isB ? a.BT16 + (long long)(r0 + row) * a.ldT : a.AT16 + (long long)(r0 - a.Kp + row) * a.ldT;
+      *reinterpret_cast<uint4 *>(dst + colT + 8 * j) = v;
+    }
+    __syncthreads();
+  }
+  if (a.want_loss) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
+    if (lane == 0) lsum[warp] = ls;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 16; ++w) t += lsum[w];
+      if (t != 0.0) atomicAdd(&a.st->loss_data, t);
     }
   }
-  for (int i = lane * 8; i < a.Dp; i += 256) {
-    uint4 u = make_uint4(0u, 0u, 0u, 0u);
-    if (m >= 0) u = *reinterpret_cast<const uint4 *>(a.U16 + (long long)m * a.Dp + i);
-    *reinterpret_cast<uint4 *>(us + warp * a.Dp + i) = u;
-  }
-  if (a.want_loss && m >= 0) {
-    for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
-    if (lane == 0) atomicAdd(&a.st->loss_data, 2.0 * (double)c * (double)ls);
-  }
-  __syncwarp();
-  if (lane == 0 && m >= 0) a.cnt[m] = 0;
-  __syncthreads();
-  const long long colT = (long long)a.Bmax + t0;
-  for (int r = threadIdx.x; r < a.Kp + a.Dp; r += blockDim.x) {
-    const bool isB = r < a.Kp;
-    const int row = isB ? r : r - a.Kp;
-    const __nv_bfloat16 *src = isB ? zs : us;
-    const int ld = isB ? a.Kp : a.Dp;
-    __align__(16) __nv_bfloat16 colv[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) colv[q] = src[q * ld + row];
-    uint4 *dst = reinterpret_cast<uint4 *>((isB ? a.BT16 : a.AT16) + (long long)row * a.ldT + colT);
-    dst[0] = reinterpret_cast<const uint4 *>(colv)[0];
-    dst[1] = reinterpret_cast<const uint4 *>(colv)[1];
-  }
+  if (tid < kZhSlots && ms[tid] >= 0) a.cnt[ms[tid]] = 0;
 }
 
 // ------------------------------------------------------------------ host side
@@ -402,12 +421,7 @@ void launch_g_tc(const StepArgs &a, cudaStream_t s) {
 #undef TLDA_KP_DISPATCH
 
 void launch_zh_tc(const StepArgs &a, cudaStream_t s) {
-  const int nk = (a.Kp + 127) / 128;
-  const int grid = round_up(a.V, 64) / 16;
-  if (nk == 1) k_zh_tc<1><<<grid, 512, 0, s>>>(a);
-  else if (nk == 2) k_zh_tc<2><<<grid, 512, 0, s>>>(a);
-  else if (nk == 3) k_zh_tc<3><<<grid, 512, 0, s>>>(a);
-  else k_zh_tc<4><<<grid, 512, 0, s>>>(a);
+  k_zh_tc<<<round_up(a.V, 64) / kZhSlots, 512, 0, s>>>(a);
 }
 
 }  // namespace tlda

@@ -559,7 +559,7 @@ tlda_status tlda_destroy(tlda_ctx *ctx) {
   dfree(ctx->TS); dfree(ctx->fit_err); dfree(ctx->stage[0]); dfree(ctx->stage[1]);
   dfree(ctx->ctl); dfree(ctx->st_tune); dfree(ctx->dlosses); dfree(ctx->phi_scratch);
   dfree(ctx->on_Om); dfree(ctx->on_Z); dfree(ctx->on_C); dfree(ctx->on_TS); dfree(ctx->on_err);
-  dfree(ctx->on_Wold); dfree(ctx->on_ws); dfree(ctx->on_status);
+  dfree(ctx->on_Wold); dfree(ctx->on_ws); dfree(ctx->on_status); dfree(ctx->on_sk); dfree(ctx->on_Om32);
   if (ctx->coop_ctl) cudaFree(ctx->coop_ctl);
   if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
   for (cudaEvent_t ev : ctx->ev_seg)

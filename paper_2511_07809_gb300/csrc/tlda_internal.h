@@ -177,6 +177,8 @@ struct tlda_ctx {
   int *on_err = nullptr;
   float *on_Wold = nullptr;            // V x D: the whitening before the last rebuild
   double *on_ws = nullptr;             // workspace of a re-whitening (V x r x 3 + r x r x 12 + ...)
+  void *on_sk = nullptr;               // workspace of the sketch (per-piece S and word slots)
+  float *on_Om32 = nullptr;            // V x r: FP32 copy of Omega for the sketch's products
   int *on_status = nullptr;            // its device status words
   int jacobi_sweeps = 0;               // sweeps of the last symmetric eigensolve
   void *coop_ctl = nullptr;            // control block of the grid-wide FP64 kernels (k_fit.cu)

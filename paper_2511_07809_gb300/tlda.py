@@ -40,7 +40,7 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_cp_step_noalloc", "tlda_autotune", "tlda_online_begin",
                 "tlda_online_pass", "tlda_eig_sweeps", "tlda_fit_batched", "tlda_doc_topics",
                 "tlda_generate_docs", "tlda_online_accumulate", "tlda_online_whiten",
-                "tlda_selftest_barrier")
+                "tlda_selftest_barrier", "tlda_online_get_sketch", "tlda_online_set_sketch")
 
 
 class Params(ctypes.Structure):
@@ -98,6 +98,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "tlda_online_accumulate": (i32, [vp, P(CSR)]),
         "tlda_selftest_barrier": (i32, [vp, P(i32), P(i32)]),
         "tlda_online_whiten": (i32, [vp, vp]),
+        "tlda_online_get_sketch": (i32, [vp, vp, vp, vp]),
+        "tlda_online_set_sketch": (i32, [vp, vp, vp, vp]),
         "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
         "tlda_cp_step_noalloc": (i32, [P(CSR), vp, vp, i32, i32, f64, f32, vp, f32, vp, vp, vp]),
         "tlda_profile": (i32, [vp, u32]),
@@ -316,6 +318,7 @@ class TLDA:
         Om = Omega.to(device="cuda", dtype=torch.float64).contiguous()
         assert Om.dim() == 2 and Om.shape[0] == self.V
         self._check(self.lib.tlda_online_begin(self.h, Om.data_ptr(), int(Om.shape[1])))
+        self._online_r = int(Om.shape[1])
 
     def online_pass(self, corpus: DeviceCSR, batch_offsets, Phi: torch.Tensor, lr: float,
                     rewhiten_every: int = 1, losses: bool = False):
@@ -339,6 +342,24 @@ class TLDA:
     def online_whiten(self, Phi: torch.Tensor | None = None):
         """Rebuild the whitening from the statistics so far; carry Phi."""
         self._check(self.lib.tlda_online_whiten(self.h, Phi.data_ptr() if Phi is not None else None))
+
+    def online_sketch(self):
+        """The online statistics as device tensors: (Z, C, TS) with Z = P Omega
+        (V x r float64), C the word counts (V int64), TS = (T, S2, S3)."""
+        r = getattr(self, "_online_r", 0)
+        Z = torch.empty((self.V, r), dtype=torch.float64, device="cuda")
+        Cw = torch.empty(self.V, dtype=torch.int64, device="cuda")
+        TS = torch.empty(3, dtype=torch.int64, device="cuda")
+        self._check(self.lib.tlda_online_get_sketch(self.h, Z.data_ptr(), Cw.data_ptr(), TS.data_ptr()))
+        return Z, Cw, TS
+
+    def online_set_sketch(self, Z: torch.Tensor, Cw: torch.Tensor, TS: torch.Tensor):
+        """Replace the online statistics with saved ones (as online_sketch returns)."""
+        Z = Z.to(device="cuda", dtype=torch.float64).contiguous()
+        Cw = Cw.to(device="cuda", dtype=torch.int64).contiguous()
+        TS = TS.to(device="cuda", dtype=torch.int64).contiguous()
+        assert Z.shape == (self.V, getattr(self, "_online_r", 0)) and Cw.shape == (self.V,) and TS.shape == (3,)
+        self._check(self.lib.tlda_online_set_sketch(self.h, Z.data_ptr(), Cw.data_ptr(), TS.data_ptr()))
 
     def sync(self):
         self._check(self.lib.tlda_sync(self.h))

@@ -17,7 +17,9 @@ pytestmark = pytest.mark.gpu
 
 
 def _omega(sp, r):
-    return ts.gaussian(sp.seed, 0x4F4D, sp.V * r).reshape(sp.V, r)
+    """A random sign test matrix: with it the sketch's FP32 products and sums
+    are integers below 2^24, so the device's Z is exact."""
+    return ts.signs(sp.seed, 0x4F4D, sp.V * r).reshape(sp.V, r)
 
 
 def _setup(lib, name, n_docs, nb, precision, r=None):
@@ -129,4 +131,120 @@ def test_online_arguments(lib):
         with pytest.raises(lib.TLDAError) as e:
             t.online_begin(torch.zeros((sp.V, r), dtype=torch.float64))
         assert e.value.status == lib.ERR_INVALID
+    t.close()
+
+
+def _sketch_check(lib, t, indptr, indices, counts, V, Om):
+    """The context's sketch, counts and token statistics against the oracle's:
+    all exact (a sign test matrix makes every sum an integer)."""
+    Z, Cw, TS = t.online_sketch()
+    st = O.ingest(indptr, indices, counts, V)
+    Zo = O.sketch_accumulate(indptr, indices, counts, V, Om)
+    assert np.array_equal(Cw.cpu().numpy(), np.asarray(st["C"], dtype=np.int64))
+    assert TS.cpu().tolist() == [int(st["T"]), int(st["S2"]), int(st["S3"])]
+    assert np.array_equal(Z.cpu().numpy(), Zo)
+    return Z, Cw, TS
+
+
+def test_online_sketch_matches_oracle(lib):
+    """Z = P Omega, C, T, S2, S3 after chunked accumulation (reading P), at
+    r = 26, 200 and 300 (the kernels of 4, 8 and 16 columns per lane)."""
+    for r in (26, 200, 300):
+        sp, c, offs, Om, t = _setup(lib, "small_v500_k10", 10000, 10, "fp32", r=r)
+        for a, b in ((0, 4000), (4000, 4001), (4001, 4001), (4001, 10000)):
+            t.online_accumulate(lib.DeviceCSR.from_corpus(c.rows(a, b)))
+        _sketch_check(lib, t, c.indptr, c.indices, c.counts, sp.V, Om)
+        t.close()
+
+
+def test_online_sketch_many_pieces(lib):
+    """600,000 documents: three pieces of the per-piece transpose (262,144
+    documents each at most), against the oracle's sketch."""
+    sp = ts.WORKLOADS["small_v500_k10"]
+    c = C.corpus("small_v500_k10", 600_000)
+    r = 16
+    Om = _omega(sp, r)
+    t = lib.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="fp32")
+    t.online_begin(torch.tensor(Om))
+    t.online_accumulate(lib.DeviceCSR.from_corpus(c))
+    _sketch_check(lib, t, c.indptr, c.indices, c.counts, sp.V, Om)
+    t.close()
+
+
+def _dense_docs(n_docs, V, per_doc):
+    """n_docs documents of per_doc distinct words each (a fixed pattern)."""
+    d = np.arange(n_docs, dtype=np.int64)[:, None]
+    j = np.arange(per_doc, dtype=np.int64)[None, :]
+    words = np.sort((d * 37 + j * (V // per_doc)) % V, axis=1).astype(np.int32)
+    counts = (1 + (d + j) % 3).astype(np.int32)
+    indptr = np.arange(n_docs + 1, dtype=np.int64) * per_doc
+    return indptr, words.ravel(), counts.ravel()
+
+
+def test_online_sketch_piece_halving(lib):
+    """262,144 documents of 100 distinct words: 26.2M nonzeros exceed a piece's
+    16M slots, so the piece is halved; the sketch still equals the oracle's."""
+    V, r = 500, 16
+    indptr, indices, counts = _dense_docs(262_144, V, 100)
+    Om = ts.signs(7, 0x4F4D, V * r).reshape(V, r)
+    t = lib.TLDA(V, 10, alpha0=1.0, precision="fp32")
+    t.online_begin(torch.tensor(Om))
+    t.online_accumulate(lib.DeviceCSR.from_arrays(indptr, indices, counts, V))
+    _sketch_check(lib, t, indptr, indices, counts, V, Om)
+    t.close()
+
+
+def test_online_sketch_checkpoint_resume(lib):
+    """Statistics saved after part of a corpus and restored into a new context
+    continue to the same sketch and whitening as one uninterrupted run."""
+    sp, c, offs, Om, t = _setup(lib, "small_v500_k10", 10000, 10, "fp32")
+    t.online_accumulate(lib.DeviceCSR.from_corpus(c.rows(0, 6000)))
+    saved = [x.cpu() for x in t.online_sketch()]
+    t.close()
+    t2 = lib.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="fp32")
+    t2.online_begin(torch.tensor(Om))
+    t2.online_set_sketch(*saved)
+    t2.online_accumulate(lib.DeviceCSR.from_corpus(c.rows(6000, 10000)))
+    _sketch_check(lib, t2, c.indptr, c.indices, c.counts, sp.V, Om)
+    t2.online_whiten()
+    W, m1, ev = t2.get_whitening()
+    st = O.ingest(c.indptr, c.indices, c.counts, sp.V)
+    Z = O.sketch_accumulate(c.indptr, c.indices, c.counts, sp.V, Om)
+    Wo, m1o, lam = O.sketch_whitening(Z, st["C"], st["T"], st["S2"], Om, float(sp.alpha0), sp.K)
+    assert np.allclose(ev, lam, rtol=1e-7)
+    assert C.rel(W.cpu().numpy(), Wo) < 1e-5
+    t2.close()
+
+
+def test_online_sketch_rejects_decreasing_indptr(lib):
+    """A decreasing indptr inside a chunk is reported, and the other documents
+    still add exactly their part."""
+    sp, c, offs, Om, t = _setup(lib, "small_v500_k10", 2000, 2, "fp32")
+    indptr = c.indptr.copy()
+    indptr[50] = indptr[49] - 1  # document 49 ends before it starts
+    t.online_accumulate(lib.DeviceCSR.from_arrays(indptr, c.indices, c.counts, sp.V))
+    with pytest.raises(lib.TLDAError) as e:
+        t.online_sketch()
+    assert e.value.status == lib.ERR_INVALID
+    t.close()
+
+
+def test_online_sketch_gaussian_test_matrix(lib):
+    """A Gaussian test matrix: the products use its FP32 values and sum in FP32
+    within a document (s_d, L_d terms) and within a run of at most 128 slots,
+    then in FP64.  First-order rounding bound, per entry:
+    |dZ_mj| <= (L_max + 128 + 3) u sum_d f_dm (sum_m' f_dm' |O_m'j| + |O_mj|),
+    u = 2^-24 (the 3: rounding of Omega, of s_d - Omega_m and of the product)."""
+    sp, c, offs, _, t = _setup(lib, "small_v500_k10", 10000, 10, "fp32", r=26)
+    Om = ts.gaussian(sp.seed, 0x4F4D, sp.V * 26).reshape(sp.V, 26)
+    t.online_begin(torch.tensor(Om))
+    t.online_accumulate(lib.DeviceCSR.from_corpus(c))
+    Z, _, _ = t.online_sketch()
+    Zo = O.sketch_accumulate(c.indptr, c.indices, c.counts, sp.V, Om)
+    F = O.csr_matrix(c.indptr, c.indices, c.counts, sp.V)
+    A = np.abs(Om)
+    Zabs = F.T @ (F @ A) + np.asarray(F.sum(axis=0)).ravel()[:, None] * A
+    L_max = int(np.max(np.diff(c.indptr)))
+    bound = (L_max + 128 + 3) * 2.0 ** -24 * Zabs
+    assert np.all(np.abs(Z.cpu().numpy() - Zo) <= bound)
     t.close()

@@ -276,6 +276,12 @@ def gaussian(seed: int, tag: int, n: int) -> np.ndarray:
     return out
 
 
+def signs(seed: int, tag: int, n: int) -> np.ndarray:
+    """n random signs (+1.0 or -1.0, each with probability 1/2) from stream
+    `tag` of `seed`: the signs of its standard normals."""
+    return np.where(gaussian(seed, tag, n) < 0.0, -1.0, 1.0)
+
+
 def initial_factors(seed: int, k: int, K: int) -> np.ndarray:
     """Initial CP factors Phi0 (k x K) with entries N(0, 1/k), as FP32 values
     held in a float64 array (so both sides start from identical numbers)."""
