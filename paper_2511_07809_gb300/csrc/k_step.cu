@@ -92,8 +92,7 @@ __device__ __forceinline__ NzChunk load_chunk(const BatchDesc &b, int V, int bas
 // One warp per document: validates the row, accumulates L_d and
 // x_d = sum_m f_dm u_m (FP32) four U rows in flight at a time, and (stats)
 // adds c_m, appends first-seen words to the touched list, adds the block's
-// share of S3.  TC=true also writes X in BF16 row-major (X16) and transposed
-// (AT16 columns, via shared memory).
+// share of S3.  TC=true also writes X in BF16 row-major (X16), whole rows.
 template <int NV, bool TC>
 __global__ void __launch_bounds__(32 * kDocsPerBlock)
     k_scan_whiten(StepArgs a, float *X_out, int stats) {
@@ -103,7 +102,6 @@ __global__ void __launch_bounds__(32 * kDocsPerBlock)
   if (d0 >= (TC ? round_up(b.n_docs, 64) : b.n_docs)) return;
   const int d = d0 + warp;
   __shared__ unsigned long long s3;
-  __shared__ __nv_bfloat16 xs[TC ? kDocsPerBlock * kMaxDim : 1];
   if (threadIdx.x == 0) s3 = 0;
   __syncthreads();
   float4 acc[NV];
@@ -176,40 +174,19 @@ __global__ void __launch_bounds__(32 * kDocsPerBlock)
     }
   }
   if constexpr (TC) {
-    if (!X_out) {
-      // row-major BF16 copy (A operand of Y = X Phi) and a staging copy for X^T
+    if (!X_out && d < b.n_docs) {
+      // row-major BF16 copy: the A operand of Y = X Phi; k_rows_to_cols makes X^T from it
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const int col = v * 128 + lane * 4;
         if (col < a.Dp) {
-          __nv_bfloat162 lo2 = __floats2bfloat162_rn(acc[v].x, acc[v].y);
-          __nv_bfloat162 hi2 = __floats2bfloat162_rn(acc[v].z, acc[v].w);
-          if (d < b.n_docs) {
-            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(a.X16 + (long long)d * a.Dp + col);
-            dst[0] = lo2;
-            dst[1] = hi2;
-          }
-          __nv_bfloat162 *sx = reinterpret_cast<__nv_bfloat162 *>(xs + warp * a.Dp + col);
-          sx[0] = lo2;
-          sx[1] = hi2;
+          __nv_bfloat162 p[2] = {__floats2bfloat162_rn(acc[v].x, acc[v].y), __floats2bfloat162_rn(acc[v].z, acc[v].w)};
+          *reinterpret_cast<uint2 *>(a.X16 + (long long)d * a.Dp + col) = *reinterpret_cast<const uint2 *>(p);
         }
       }
     }
   }
   __syncthreads();
-  if constexpr (TC) {
-    if (!X_out) {
-      // X^T: AT16[i][d0 .. d0+16) = 32 contiguous bytes per feature row i
-      for (int i = threadIdx.x; i < a.Dp; i += blockDim.x) {
-        __align__(16) __nv_bfloat16 col[kDocsPerBlock];
-#pragma unroll
-        for (int q = 0; q < kDocsPerBlock; ++q) col[q] = xs[q * a.Dp + i];
-        uint4 *dst = reinterpret_cast<uint4 *>(a.AT16 + (long long)i * a.ldT + d0);
-        dst[0] = reinterpret_cast<const uint4 *>(col)[0];
-        dst[1] = reinterpret_cast<const uint4 *>(col)[1];
-      }
-    }
-  }
   if (stats && threadIdx.x == 0 && s3) atomicAdd(&a.st->S3, s3);
 }
 
@@ -219,8 +196,12 @@ void launch_whiten(const StepArgs &a, cudaStream_t s, float *X_out, bool stats) 
   const int nv = (a.Dp + 127) / 128;
 #define TLDA_WHITEN(NVv)                                                                        \
   if (nv == NVv) {                                                                              \
-    if (tc) k_scan_whiten<NVv, true><<<grid, 32 * kDocsPerBlock, 0, s>>>(a, X_out, stats);     \
-    else k_scan_whiten<NVv, false><<<grid, 32 * kDocsPerBlock, 0, s>>>(a, X_out, stats);       \
+    if (tc) {                                                                                   \
+      k_scan_whiten<NVv, true><<<grid, 32 * kDocsPerBlock, 0, s>>>(a, X_out, stats);            \
+      launch_rows_to_cols(a, a.X16, a.Dp, 0, 0, s); /* X^T into AT16 */                           \
+    } else {                                                                                    \
+      k_scan_whiten<NVv, false><<<grid, 32 * kDocsPerBlock, 0, s>>>(a, X_out, stats);           \
+    }                                                                                           \
     return;                                                                                     \
   }
   TLDA_WHITEN(1) TLDA_WHITEN(2) TLDA_WHITEN(3) TLDA_WHITEN(4)
@@ -430,7 +411,7 @@ __global__ void __launch_bounds__(256) k_qy_f32(StepArgs a) {
 // ------------------------------------------------------------ a4 + a6 scatter: R, Z, H
 // One warp per document (16 per block): r_d = sum_m f_dm q_m^2 over gathered
 // Q rows (four in flight), z_d = y_d^2 - r_d, H_m += f_dm y_d (vector atomics),
-// and the document part of the loss.  TC=true writes Z^T (BF16) through shared
+// and the document part of the loss.  TC=true writes Z as whole BF16 rows (Z16)
 // memory, 32 bytes per topic row, zero-filling up to the 64-column chunk.
 template <int NK, bool TC>
 __global__ void __launch_bounds__(512) k_rz(StepArgs a) {
@@ -438,7 +419,6 @@ __global__ void __launch_bounds__(512) k_rz(StepArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int d0 = blockIdx.x * 16, d = d0 + warp;
   if (d0 >= (TC ? round_up(b.n_docs, 64) : b.n_docs)) return;
-  __shared__ __nv_bfloat16 zs[TC ? 16 * kMaxDim : 1];
   float4 y[NK], r[NK];
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
@@ -494,9 +474,10 @@ __global__ void __launch_bounds__(512) k_rz(StepArgs a) {
       const float4 z = make_float4(y[v].x * y[v].x - r[v].x, y[v].y * y[v].y - r[v].y,
                                    y[v].z * y[v].z - r[v].z, y[v].w * y[v].w - r[v].w);
       if constexpr (TC) {
-        __nv_bfloat162 *sz = reinterpret_cast<__nv_bfloat162 *>(zs + warp * a.Kp + col);
-        sz[0] = __floats2bfloat162_rn(z.x, z.y);
-        sz[1] = __floats2bfloat162_rn(z.z, z.w);
+        if (d < b.n_docs) {
+          __nv_bfloat162 p[2] = {__floats2bfloat162_rn(z.x, z.y), __floats2bfloat162_rn(z.z, z.w)};
+          *reinterpret_cast<uint2 *>(a.Z16 + (long long)d * a.Kp + col) = *reinterpret_cast<const uint2 *>(p);
+        }
       } else {
         if (d < b.n_docs) *reinterpret_cast<float4 *>(a.Z32 + (long long)d * a.Kp + col) = z;
       }
@@ -508,17 +489,6 @@ __global__ void __launch_bounds__(512) k_rz(StepArgs a) {
   if (a.want_loss) {
     for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
     if (lane == 0 && ls != 0.f) atomicAdd(&a.st->loss_data, (double)ls);
-  }
-  if constexpr (TC) {
-    __syncthreads();
-    for (int n = threadIdx.x; n < a.Kp; n += blockDim.x) {
-      __align__(16) __nv_bfloat16 col[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) col[q] = zs[q * a.Kp + n];
-      uint4 *dst = reinterpret_cast<uint4 *>(a.BT16 + (long long)n * a.ldT + d0);
-      dst[0] = reinterpret_cast<const uint4 *>(col)[0];
-      dst[1] = reinterpret_cast<const uint4 *>(col)[1];
-    }
   }
 }
 
@@ -626,8 +596,12 @@ void launch_rz(const StepArgs &a, cudaStream_t s) {
   const bool tc = a.precision == TLDA_BF16;
 #define TLDA_RZ(NKv)                                                                      \
   if (nk == NKv) {                                                                        \
-    if (tc) k_rz<NKv, true><<<round_up(a.Bmax, 64) / 16, 512, 0, s>>>(a);                 \
-    else k_rz<NKv, false><<<round_up(a.Bmax, 64) / 16, 512, 0, s>>>(a);                   \
+    if (tc) {                                                                             \
+      k_rz<NKv, true><<<round_up(a.Bmax, 64) / 16, 512, 0, s>>>(a);                        \
+      launch_rows_to_cols(a, a.Z16, a.Kp, a.Kp, 0, s); /* Z^T into BT16 */                  \
+    } else {                                                                              \
+      k_rz<NKv, false><<<round_up(a.Bmax, 64) / 16, 512, 0, s>>>(a);                       \
+    }                                                                                     \
     return;                                                                               \
   }
   TLDA_RZ(1) TLDA_RZ(2) TLDA_RZ(3) TLDA_RZ(4)

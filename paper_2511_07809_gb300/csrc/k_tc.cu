@@ -12,8 +12,10 @@
 //            each CTA streams 64-column chunks through a TMA ring and
 //            accumulates a 128-feature x Kp tile in TMEM, then writes its
 //            rows of the partial.  D and K up to 512.
-//   k_zh_tc  Zc rows of the touched words, written transposed (BF16) next to
-//            the touched words' U^T columns.
+//   k_zc_tc  Zc rows of the touched words with their U rows (BF16), then
+//            transposed into the columns after the documents'.
+//   k_rows_to_cols  the transposes of X, Z and [Zc | U_t] into the
+//            reduction-major copies AT16 and BT16 that k_g_tc streams.
 // Every wait on an mbarrier is bounded (about one second of clock cycles);
 // on expiry the kernel sets the context's timeout bit and leaves.
 #include <cstdio>
@@ -225,90 +227,113 @@ __global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant_
 }
 
 // ------------------------------------------------------------------ Zc (BF16, transposed)
-// One block per 64 compact slots t0 .. t0+63 (touched words m = widx[t]).  It
-// walks the Kp + Dp output rows in tiles of 64: rows k < Kp of BT16 take
-// Zc_t[k] = q_mk (2 c_m q_mk - 2 H_mk) (H_mk is cleared), rows i of AT16 take
-// U_m[i].  Each tile is staged transposed in shared memory and written as 64
-// rows of 128 bytes (whole lines) into columns Bmax + t0 .. t0+63, so a block
-// has the pages of 64 rows in flight at a time rather than those of all
-// Kp + Dp rows.  Slots in [n_touched, round_up(n_touched, 64)) write zero
-// columns (chunk padding); the slots' c_m are cleared at the end.
-constexpr int kZhSlots = 64;
-constexpr int kZhPitch = 66;  // staged row: 64 slots + 2 (33 words: conflict-free reads)
+// k_zc_tc: one warp per compact slot t (8 per block): row t of ZU16 takes
+// [Zc_t | U_m] in BF16, Zc_t = q (2 c_m q - 2 H_m) with m = widx[t].  Slots
+// in [n_touched, round_up(n_touched, 64)) get zero rows (chunk padding).
+// k_h_clear then clears H_m and c_m for the next batch: a warp that loads an
+// H row and then stores to it (an L2 miss followed by a write to the pending
+// line) ran about six times slower than the load or the store alone.
+// k_rows_to_cols then moves ZU16 into columns Bmax + t of BT16 (its first Kp
+// columns) and AT16 (the other Dp).
+template <int NK>
+__global__ void __launch_bounds__(256) k_zc_tc(StepArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp, nt = a.st->n_touched;
+  if (t >= round_up(nt, 64)) return;  // per warp: no block barrier follows
+  const int m = t < nt ? a.widx[t] : -1;
+  const float c = m >= 0 ? (float)a.cnt[m] : 0.f;
+  __nv_bfloat16 *row = a.ZU16 + (long long)t * (a.Kp + a.Dp);
+  float ls = 0.f;
+#pragma unroll
+  for (int v = 0; v < NK; ++v) {
+    const int col = v * 128 + lane * 4;
+    if (col < a.Kp) {
+      float z[4] = {0.f, 0.f, 0.f, 0.f};
+      if (m >= 0) {
+        const float4 *hp = reinterpret_cast<const float4 *>(a.H32 + (long long)m * a.Kp + col);
+        const float4 q = *reinterpret_cast<const float4 *>(a.Q32 + (long long)m * a.Kp + col);
+        const float4 h = *hp;
+        z[0] = q.x * (2.f * c * q.x - 2.f * h.x);
+        z[1] = q.y * (2.f * c * q.y - 2.f * h.y);
+        z[2] = q.z * (2.f * c * q.z - 2.f * h.z);
+        z[3] = q.w * (2.f * c * q.w - 2.f * h.w);
+        ls += q.x * q.x * q.x + q.y * q.y * q.y + q.z * q.z * q.z + q.w * q.w * q.w;
+      }
+      __nv_bfloat162 p[2] = {__floats2bfloat162_rn(z[0], z[1]), __floats2bfloat162_rn(z[2], z[3])};
+      *reinterpret_cast<uint2 *>(row + col) = *reinterpret_cast<const uint2 *>(p);
+    }
+  }
+  for (int i = lane * 8; i < a.Dp; i += 256) {
+    uint4 u = make_uint4(0u, 0u, 0u, 0u);
+    if (m >= 0) u = *reinterpret_cast<const uint4 *>(a.U16 + (long long)m * a.Dp + i);
+    *reinterpret_cast<uint4 *>(row + a.Kp + i) = u;
+  }
+  if (a.want_loss && m >= 0) {
+    for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
+    if (lane == 0) atomicAdd(&a.st->loss_data, 2.0 * (double)c * (double)ls);
+  }
+}
 
-__global__ void __launch_bounds__(512) k_zh_tc(StepArgs a) {
-  __shared__ __align__(16) __nv_bfloat16 zt[64 * kZhPitch];  // [row of the tile][slot]
-  __shared__ int ms[kZhSlots];
-  __shared__ float cs[kZhSlots];
-  __shared__ double lsum[16];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int t0 = blockIdx.x * kZhSlots, nt = a.st->n_touched;
-  if (t0 >= round_up(nt, 64)) return;  // uniform over the block
-  if (tid < kZhSlots) {
-    const int t = t0 + tid;
-    const int m = t < nt ? a.widx[t] : -1;
-    ms[tid] = m;
-    cs[tid] = m >= 0 ? (float)a.cnt[m] : 0.f;
+template <int NK>
+__global__ void __launch_bounds__(256) k_h_clear(StepArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= a.st->n_touched) return;
+  const int m = a.widx[t];
+#pragma unroll
+  for (int v = 0; v < NK; ++v) {
+    const int col = v * 128 + lane * 4;
+    if (col < a.Kp) *reinterpret_cast<float4 *>(a.H32 + (long long)m * a.Kp + col) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (lane == 0) a.cnt[m] = 0;
+}
+
+// Rows [0, round_up(n, 64)) of the row-major BF16 matrix src (ld columns; n
+// valid rows: the batch's documents, or with `slots` its touched words; rows
+// from n on read as zero) into columns col0 + row of BT16 (source columns
+// below c_split) and AT16 (source column c_split + i into row i), in 64 x 64
+// tiles: 128-byte rows read and written through shared memory.
+__global__ void __launch_bounds__(256) k_rows_to_cols(StepArgs a, const __nv_bfloat16 *__restrict__ src, int ld,
+                                                      int c_split, int slots) {
+  __shared__ uint32_t tile[64][33];  // [row][column pair]; 33 words: reads and writes at most 2-way
+  const int n = slots ? a.st->n_touched : a.st->cur.n_docs;
+  const int r0 = blockIdx.x * 64;
+  if (r0 >= round_up(n, 64)) return;  // uniform over the block
+  const int c0 = blockIdx.y * 64, tid = threadIdx.x;
+  const long long col0 = slots ? a.Bmax : 0;
+  for (int e = tid; e < 64 * 8; e += 256) {  // 64 rows x 8 pieces of 16 bytes
+    const int rr = e >> 3, j = e & 7;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r0 + rr < n) v = *reinterpret_cast<const uint4 *>(src + (long long)(r0 + rr) * ld + c0 + 8 * j);
+    tile[rr][4 * j + 0] = v.x;
+    tile[rr][4 * j + 1] = v.y;
+    tile[rr][4 * j + 2] = v.z;
+    tile[rr][4 * j + 3] = v.w;
   }
   __syncthreads();
-  double ls = 0.0;
-  const long long colT = (long long)a.Bmax + t0;
-  for (int r0 = 0; r0 < a.Kp + a.Dp; r0 += 64) {  // Kp and Dp are multiples of 64
-    const bool isB = r0 < a.Kp;
-    if (isB) {
-      for (int e = tid; e < kZhSlots * 16; e += 512) {  // slot, four columns
-        const int sl = e >> 4, c4 = (e & 15) * 4, m = ms[sl];
-        float z[4] = {0.f, 0.f, 0.f, 0.f};
-        if (m >= 0) {
-          float4 *hp = reinterpret_cast<float4 *>(a.H32 + (long long)m * a.Kp + r0 + c4);
-          const float4 q = *reinterpret_cast<const float4 *>(a.Q32 + (long long)m * a.Kp + r0 + c4);
-          const float4 h = *hp;
-          const float c = cs[sl];
-          z[0] = q.x * (2.f * c * q.x - 2.f * h.x);
-          z[1] = q.y * (2.f * c * q.y - 2.f * h.y);
-          z[2] = q.z * (2.f * c * q.z - 2.f * h.z);
-          z[3] = q.w * (2.f * c * q.w - 2.f * h.w);
-          *hp = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (a.want_loss)
-            ls += 2.0 * (double)c * (double)(q.x * q.x * q.x + q.y * q.y * q.y + q.z * q.z * q.z + q.w * q.w * q.w);
-        }
+  for (int e = tid; e < 64 * 8; e += 256) {  // 64 output rows (columns c0 + k) x 8 pieces of 8 rows
+    const int k = e >> 3, j = e & 7, sh = (k & 1) * 16;
+    uint32_t w[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) zt[(c4 + k) * kZhPitch + sl] = __float2bfloat16_rn(z[k]);
-      }
-    } else {
-      const int i0 = r0 - a.Kp;
-      for (int e = tid; e < kZhSlots * 8; e += 512) {  // slot, eight columns
-        const int sl = e >> 3, c8 = (e & 7) * 8, m = ms[sl];
-        uint4 u = make_uint4(0u, 0u, 0u, 0u);
-        if (m >= 0) u = *reinterpret_cast<const uint4 *>(a.U16 + (long long)m * a.Dp + i0 + c8);
-        const __nv_bfloat16 *uv = reinterpret_cast<const __nv_bfloat16 *>(&u);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) zt[(c8 + k) * kZhPitch + sl] = uv[k];
-      }
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t lo = (tile[8 * j + 2 * q][k >> 1] >> sh) & 0xffffu;
+      const uint32_t hi = (tile[8 * j + 2 * q + 1][k >> 1] >> sh) & 0xffffu;
+      w[q] = lo | (hi << 16);
     }
-    __syncthreads();
-    {
-      const int row = tid >> 3, j = tid & 7;  // 64 rows x 8 pieces of 16 bytes
-      const uint32_t *src = reinterpret_cast<const uint32_t *>(zt + row * kZhPitch + 8 * j);
-      const uint4 v = make_uint4(src[0], src[1], src[2], src[3]);
-      __nv_bfloat16 *dst = isB ? a.BT16 + (long long)(r0 + row) * a.ldT : a.AT16 + (long long)(r0 - a.Kp + row) * a.ldT;
-      *reinterpret_cast<uint4 *>(dst + colT + 8 * j) = v;
-    }
-    __syncthreads();
+    const int col = c0 + k;
+    __nv_bfloat16 *dst = col < c_split ? a.BT16 + (long long)col * a.ldT : a.AT16 + (long long)(col - c_split) * a.ldT;
+    *reinterpret_cast<uint4 *>(dst + col0 + r0 + 8 * j) = make_uint4(w[0], w[1], w[2], w[3]);
   }
-  if (a.want_loss) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
-    if (lane == 0) lsum[warp] = ls;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < 16; ++w) t += lsum[w];
-      if (t != 0.0) atomicAdd(&a.st->loss_data, t);
-    }
-  }
-  if (tid < kZhSlots && ms[tid] >= 0) a.cnt[ms[tid]] = 0;
 }
+
+}  // namespace
+
+void launch_rows_to_cols(const StepArgs &a, const __nv_bfloat16 *src, int ld, int c_split, int slots, cudaStream_t s) {
+  const int rows = slots ? round_up(a.V, 64) : round_up(a.Bmax, 64);
+  k_rows_to_cols<<<dim3(rows / 64, ld / 64), 256, 0, s>>>(a, src, ld, c_split, slots);
+}
+
+namespace {
 
 // ------------------------------------------------------------------ host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -421,7 +446,22 @@ void launch_g_tc(const StepArgs &a, cudaStream_t s) {
 #undef TLDA_KP_DISPATCH
 
 void launch_zh_tc(const StepArgs &a, cudaStream_t s) {
-  k_zh_tc<<<round_up(a.V, 64) / kZhSlots, 512, 0, s>>>(a);
+  const int nk = (a.Kp + 127) / 128;
+  const unsigned grid = (unsigned)(round_up(a.V, 64) / 8);
+  if (nk == 1) {
+    k_zc_tc<1><<<grid, 256, 0, s>>>(a);
+    k_h_clear<1><<<grid, 256, 0, s>>>(a);
+  } else if (nk == 2) {
+    k_zc_tc<2><<<grid, 256, 0, s>>>(a);
+    k_h_clear<2><<<grid, 256, 0, s>>>(a);
+  } else if (nk == 3) {
+    k_zc_tc<3><<<grid, 256, 0, s>>>(a);
+    k_h_clear<3><<<grid, 256, 0, s>>>(a);
+  } else {
+    k_zc_tc<4><<<grid, 256, 0, s>>>(a);
+    k_h_clear<4><<<grid, 256, 0, s>>>(a);
+  }
+  launch_rows_to_cols(a, a.ZU16, a.Kp + a.Dp, a.Kp, 1, s);
 }
 
 }  // namespace tlda
