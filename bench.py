@@ -587,6 +587,44 @@ def billion_main(args):
 
     t2, e_end = pass2(ctx, Phi, e_w1)
     clocks = sampler.stop()
+
+    def kernel_profile(c_, prec):
+        """Per-kernel device times of one more pass over the first chunk (on a
+        copy of Phi, after the timed region), and the roofline of the two
+        dense contractions: [Q; Y] = [U; X] Phi, algorithmic 2 (n_t + B) D K
+        flop (Q is needed for the n_t touched words only), and
+        [X; U_t]^T [Z; Zc], 2 (B + n_t) D K flop."""
+        n = min(chunk, args.billion_docs)
+        c = gen.generate(0, n, out=buf)
+        offs = list(range(0, n, B)) + [n]
+        ip = c.indptr.cpu().numpy()
+        bt, nt = [], []
+        for a_, b_ in zip(offs[:-1], offs[1:]):
+            bt.append(b_ - a_)
+            nt.append(int(torch.unique(c.indices[int(ip[a_]):int(ip[b_])]).numel()))
+        names = ("scan_whiten", "qy", "rz", "zh", "g_reduce", "reduce_update", "phi_gram", "phi_terms")
+        P = Phi0.clone()
+        c_.profile(names)
+        c_.cp_pass(c, offs, P, lr)
+        torch.cuda.synchronize()
+        pr = c_.profile_read()
+        c_.profile(())
+        peaks, src = measured_peaks()
+        if prec == "bf16":
+            pk, bound = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]), "tensor"
+        else:
+            pk, bound = FP32_ALU_PEAK_TFLOPS, "alu"
+        fl = 2.0 * float(np.sum(np.array(bt) + np.array(nt))) * sp.K * sp.K / len(bt)
+        out = {"ms_per_step": {k: v[1] / v[0] for k, v in pr.items() if v[0] > 0}, "peak_source": src,
+               "mean_touched_words": float(np.mean(nt))}
+        for k in ("qy", "g_reduce"):
+            if pr.get(k, (0, 0))[0] > 0:
+                ach = fl / (pr[k][1] / pr[k][0] / 1e3) / 1e12
+                out[k] = {"bound": bound, "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                          "algorithmic_flop_per_launch": fl}
+        return out
+
+    prof_bf16 = kernel_profile(ctx, "bf16")
     t1 = [(marks1[i - 1] if i else e_start).elapsed_time(marks1[i]) for i in range(n_chunks)]
     ms_total = e_start.elapsed_time(e_end)
     w_ms = e_w0.elapsed_time(e_w1)
@@ -600,6 +638,7 @@ def billion_main(args):
     e32.record()
     t2_32, _ = pass2(c32, P32, e32)
     rel32 = float((torch.linalg.norm(Phi - P32) / torch.linalg.norm(P32)).item())
+    prof_fp32 = kernel_profile(c32, "fp32")
     c32.close()
     line = {
         "metric": f"docs/sec of the chunked streaming workload {sp.name} (V={sp.V}, K={sp.K}): on-device "
@@ -621,6 +660,7 @@ def billion_main(args):
         "chunk_ms_pass2": {"mean": float(np.mean(t2)), "std": float(np.std(t2)), "first": t2[0], "last": t2[-1]},
         "host_setup_s": {"topics": round(t_topics, 2), "omega": round(t_omega, 2)},
         "phi_finite": finite, "clocks": clocks,
+        "pass2_kernels_bf16": prof_bf16, "pass2_kernels_fp32": prof_fp32,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
