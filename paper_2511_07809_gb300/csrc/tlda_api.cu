@@ -498,7 +498,8 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
   const size_t V = vocab, Dp = ctx->Dp, Kp = ctx->Kp, Bm = ctx->Bmax;
   const int tiles = (ctx->Dp / 64) * (ctx->Kp / 64);
   ctx->nsplit = std::max(8, std::min(256, 2 * ctx->num_sms / tiles));
-  ctx->nsplit_tc = 48;
+  // k_g_tc: one block per (split, 128-feature tile); as many splits as fill the SMs once
+  ctx->nsplit_tc = std::max(8, std::min(64, ctx->num_sms / ((ctx->Dp + 127) / 128)));
   ctx->fused = p->precision == TLDA_BF16 && fused_supported(ctx->Dp, ctx->Kp) && !getenv("TLDA_NO_FUSED");
   ctx->fused_grid = std::max(1, ctx->num_sms - 8);
   CA(dalloc(&ctx->W32, V * D, true));
