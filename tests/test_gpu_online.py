@@ -127,6 +127,12 @@ def test_online_arguments(lib):
     with pytest.raises(lib.TLDAError) as e:
         t.online_pass(lib.DeviceCSR.from_corpus(c), [0, 1000], Phi, 0.01)
     assert e.value.status == lib.ERR_STATE
+    with pytest.raises(lib.TLDAError) as e:
+        t.online_sketch()
+    assert e.value.status == lib.ERR_STATE
+    with pytest.raises(lib.TLDAError) as e:
+        t.online_accumulate(lib.DeviceCSR.from_corpus(c))
+    assert e.value.status == lib.ERR_STATE
     for r in (sp.K - 2, sp.K + 3, 600):
         with pytest.raises(lib.TLDAError) as e:
             t.online_begin(torch.zeros((sp.V, r), dtype=torch.float64))
