@@ -95,7 +95,11 @@ void tlda_default_params(tlda_params *p, int32_t k);
  * default stream).  Allocates the workspace (device memory linear in V and
  * max_batch).  D and K are padded to multiples of 64, at most 512, in both
  * forms.  The BF16 form takes the fused tensor-core kernels for D, K in
- * (64, 128] and the multi-kernel tensor-core form otherwise.  Returns
+ * (64, 128] and the multi-kernel tensor-core form otherwise.  Two
+ * environment variables, read here, pin the form for comparisons (the results
+ * agree within the BF16 tolerance): TLDA_NO_FUSED set takes the multi-kernel
+ * tensor-core form at every size; TLDA_NO_PASS set keeps the fused per-step
+ * kernel but not the persistent pass kernel of tlda_cp_pass.  Returns
  * TLDA_ERR_INVALID for bad sizes/parameters, TLDA_ERR_OOM if the workspace
  * cannot be allocated. */
 tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, void *cuda_stream);
