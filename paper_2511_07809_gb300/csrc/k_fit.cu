@@ -962,7 +962,9 @@ struct SkPiece {
   int V, r;
 };
 
-// KC columns of r per lane (column lane + 32 c); four nonzeros' Omega rows in flight.
+// The r columns are split over gridDim.y warps per document (or run): block
+// row y takes columns y 32 KC + lane + 32 c, KC per lane, so that a warp holds
+// few registers and many warps are resident; four rows in flight per warp.
 template <int KC>
 __global__ void __launch_bounds__(256) k_sk_rows(SkPiece q, const float *__restrict__ Om, float *__restrict__ S,
                                                  int32_t *wcnt, uint8_t *ok, unsigned long long *TS, int *err) {
@@ -978,8 +980,10 @@ __global__ void __launch_bounds__(256) k_sk_rows(SkPiece q, const float *__restr
       if (m < 0 || m >= q.V || f <= 0 || m <= prev) bad = true;
       else L += f;
     }
+  const bool first = blockIdx.y == 0;  // the column group that also counts
+  const int cb = blockIdx.y * 32 * KC;
   if (__any_sync(0xffffffffu, bad)) {
-    if (lane == 0) {
+    if (lane == 0 && first) {
       ok[doc] = 0;
       atomicOr(err, 1);
     }
@@ -1006,7 +1010,7 @@ __global__ void __launch_bounds__(256) k_sk_rows(SkPiece q, const float *__restr
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int c = 0; c < KC; ++c) {
-          const int col = lane + 32 * c;
+          const int col = cb + lane + 32 * c;
           row[u][c] = col < q.r ? __ldg(Om + (long long)mm[u] * q.r + col) : 0.f;
         }
 #pragma unroll
@@ -1018,9 +1022,10 @@ __global__ void __launch_bounds__(256) k_sk_rows(SkPiece q, const float *__restr
   float *srow = S + (long long)doc * q.r;
 #pragma unroll
   for (int c = 0; c < KC; ++c) {
-    const int col = lane + 32 * c;
+    const int col = cb + lane + 32 * c;
     if (col < q.r) srow[col] = sv[c];
   }
+  if (!first) return;
   for (int p = p0 + lane; p < p1; p += 32) atomicAdd(wcnt + q.indices[p] + 1, 1);
   if (lane == 0) {
     ok[doc] = 1;
@@ -1052,18 +1057,19 @@ __global__ void __launch_bounds__(256) k_sk_scatter(SkPiece q, const uint8_t *ok
 
 template <int KC>
 __device__ __forceinline__ void sk_flush(int m, const float (&acc)[KC], long long fs, long long lo, long long hi,
-                                         const int32_t *wcnt, int r, double *Z, unsigned long long *C, int lane) {
+                                         const int32_t *wcnt, int r, int cb, double *Z, unsigned long long *C,
+                                         int lane) {
   const bool whole = wcnt[m] >= lo && wcnt[m + 1] <= hi;  // no other run holds word m
   double *z = Z + (long long)m * r;
 #pragma unroll
   for (int c = 0; c < KC; ++c) {
-    const int col = lane + 32 * c;
+    const int col = cb + lane + 32 * c;
     if (col < r) {
       if (whole) z[col] += (double)acc[c];
       else atomicAdd(z + col, (double)acc[c]);
     }
   }
-  if (lane == 0) {
+  if (lane == 0 && cb == 0) {
     if (whole) C[m] += (unsigned long long)fs;
     else atomicAdd(C + m, (unsigned long long)fs);
   }
@@ -1080,7 +1086,7 @@ __global__ void __launch_bounds__(256) k_sk_z(const int32_t *__restrict__ wcnt, 
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 1);
     return;
   }
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, cb = blockIdx.y * 32 * KC;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long runs = (total + kSkRun - 1) / kSkRun;
   for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < runs; t += nwarps) {
@@ -1112,17 +1118,17 @@ __global__ void __launch_bounds__(256) k_sk_z(const int32_t *__restrict__ wcnt, 
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int c = 0; c < KC; ++c) {
-            const int col = lane + 32 * c;
+            const int col = cb + lane + 32 * c;
             row[u][c] = col < r ? S[(long long)dd[u] * r + col] : 0.f;
           }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (mm[u] != cur) {
-            if (cur >= 0) sk_flush<KC>(cur, acc, fs, lo, hi, wcnt, r, Z, C, lane);
+            if (cur >= 0) sk_flush<KC>(cur, acc, fs, lo, hi, wcnt, r, cb, Z, C, lane);
             cur = mm[u];
 #pragma unroll
             for (int c = 0; c < KC; ++c) {
-              const int col = lane + 32 * c;
+              const int col = cb + lane + 32 * c;
               acc[c] = 0.f;
               om[c] = col < r ? __ldg(Om + (long long)cur * r + col) : 0.f;
             }
@@ -1135,7 +1141,7 @@ __global__ void __launch_bounds__(256) k_sk_z(const int32_t *__restrict__ wcnt, 
         }
       }
     }
-    if (cur >= 0) sk_flush<KC>(cur, acc, fs, lo, hi, wcnt, r, Z, C, lane);
+    if (cur >= 0) sk_flush<KC>(cur, acc, fs, lo, hi, wcnt, r, cb, Z, C, lane);
   }
 }
 
@@ -1273,7 +1279,8 @@ tlda_status online_rotate(tlda_ctx *ctx, float *Phi) {
 tlda_status online_accumulate(tlda_ctx *ctx, const tlda_csr *corpus, int64_t d0, int nd) {
   if (nd <= 0) return TLDA_OK;
   cudaStream_t s = ctx->stream;
-  const int V = ctx->V, r = ctx->on_r, kc = (r + 31) / 32;
+  // columns per lane: 4 up to r = 128, else 8, in ny column groups of 32 kc
+  const int V = ctx->V, r = ctx->on_r, kc = r <= 128 ? 4 : 8, ny = (r + 32 * kc - 1) / (32 * kc);
   SketchWs w(ctx->on_sk, V, r);
   int64_t *total = w.scan + scan_blocks(V);
   auto piece = [&](int64_t a, int n, int32_t lo, int32_t hi) -> tlda_status {
@@ -1281,16 +1288,15 @@ tlda_status online_accumulate(tlda_ctx *ctx, const tlda_csr *corpus, int64_t d0,
     CKF(cudaMemsetAsync(w.wcnt, 0, sizeof(int32_t) * (V + 1), s));
     CKF(cudaMemsetAsync(w.wfill, 0, sizeof(int32_t) * V, s));
     const unsigned g = (unsigned)(((long long)n * 32 + 255) / 256);
-    if (kc <= 4) k_sk_rows<4><<<g, 256, 0, s>>>(q, ctx->on_Om32, w.S, w.wcnt, w.ok, ctx->on_TS, ctx->on_err);
-    else if (kc <= 8) k_sk_rows<8><<<g, 256, 0, s>>>(q, ctx->on_Om32, w.S, w.wcnt, w.ok, ctx->on_TS, ctx->on_err);
-    else k_sk_rows<16><<<g, 256, 0, s>>>(q, ctx->on_Om32, w.S, w.wcnt, w.ok, ctx->on_TS, ctx->on_err);
+    const dim3 gr(g, ny);
+    if (kc == 4) k_sk_rows<4><<<gr, 256, 0, s>>>(q, ctx->on_Om32, w.S, w.wcnt, w.ok, ctx->on_TS, ctx->on_err);
+    else k_sk_rows<8><<<gr, 256, 0, s>>>(q, ctx->on_Om32, w.S, w.wcnt, w.ok, ctx->on_TS, ctx->on_err);
     scan_counts(w.wcnt, V, w.scan, total, s);
     k_sk_scatter<<<g, 256, 0, s>>>(q, w.ok, w.wcnt, w.wfill, w.sd, w.sf, w.sm, ctx->on_err);
     const long long span = std::max<long long>(1, (long long)hi - lo);
-    const unsigned zg = (unsigned)std::min<long long>((span + 8ll * kSkRun - 1) / (8ll * kSkRun), 4ll * ctx->num_sms);
-    if (kc <= 4) k_sk_z<4><<<zg, 256, 0, s>>>(w.wcnt, w.sd, w.sf, w.sm, total, r, w.S, ctx->on_Om32, ctx->on_Z, ctx->on_C, ctx->on_err);
-    else if (kc <= 8) k_sk_z<8><<<zg, 256, 0, s>>>(w.wcnt, w.sd, w.sf, w.sm, total, r, w.S, ctx->on_Om32, ctx->on_Z, ctx->on_C, ctx->on_err);
-    else k_sk_z<16><<<zg, 256, 0, s>>>(w.wcnt, w.sd, w.sf, w.sm, total, r, w.S, ctx->on_Om32, ctx->on_Z, ctx->on_C, ctx->on_err);
+    const dim3 zg((unsigned)std::min<long long>((span + 8ll * kSkRun - 1) / (8ll * kSkRun), 8ll * ctx->num_sms / ny), ny);
+    if (kc == 4) k_sk_z<4><<<zg, 256, 0, s>>>(w.wcnt, w.sd, w.sf, w.sm, total, r, w.S, ctx->on_Om32, ctx->on_Z, ctx->on_C, ctx->on_err);
+    else k_sk_z<8><<<zg, 256, 0, s>>>(w.wcnt, w.sd, w.sf, w.sm, total, r, w.S, ctx->on_Om32, ctx->on_Z, ctx->on_C, ctx->on_err);
     CKF(cudaGetLastError());
     return TLDA_OK;
   };
