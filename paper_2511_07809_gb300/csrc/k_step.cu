@@ -409,16 +409,16 @@ __global__ void __launch_bounds__(256) k_qy_f32(StepArgs a) {
 }
 
 // ------------------------------------------------------------ a4 + a6 scatter: R, Z, H
-// One warp per document (16 per block): r_d = sum_m f_dm q_m^2 over gathered
-// Q rows (four in flight), z_d = y_d^2 - r_d, H_m += f_dm y_d (vector atomics),
-// and the document part of the loss.  TC=true writes Z as whole BF16 rows (Z16)
-// memory, 32 bytes per topic row, zero-filling up to the 64-column chunk.
+// One warp per document (8 per block: small blocks keep more warps resident
+// per SM): r_d = sum_m f_dm q_m^2 over gathered Q rows (four in flight),
+// z_d = y_d^2 - r_d, H_m += f_dm y_d (vector atomics), and the document part
+// of the loss.  TC=true writes Z as whole BF16 rows (Z16).
 template <int NK, bool TC>
-__global__ void __launch_bounds__(512) k_rz(StepArgs a) {
+__global__ void __launch_bounds__(256) k_rz(StepArgs a) {
   const BatchDesc b = a.st->cur;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int d0 = blockIdx.x * 16, d = d0 + warp;
-  if (d0 >= (TC ? round_up(b.n_docs, 64) : b.n_docs)) return;
+  const int d0 = blockIdx.x * 8, d = d0 + warp;
+  if (d0 >= b.n_docs) return;
   float4 y[NK], r[NK];
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
@@ -597,10 +597,10 @@ void launch_rz(const StepArgs &a, cudaStream_t s) {
 #define TLDA_RZ(NKv)                                                                      \
   if (nk == NKv) {                                                                        \
     if (tc) {                                                                             \
-      k_rz<NKv, true><<<round_up(a.Bmax, 64) / 16, 512, 0, s>>>(a);                        \
+      k_rz<NKv, true><<<round_up(a.Bmax, 64) / 8, 256, 0, s>>>(a);                          \
       launch_rows_to_cols(a, a.Z16, a.Kp, a.Kp, 0, s); /* Z^T into BT16 */                  \
     } else {                                                                              \
-      k_rz<NKv, false><<<round_up(a.Bmax, 64) / 16, 512, 0, s>>>(a);                       \
+      k_rz<NKv, false><<<round_up(a.Bmax, 64) / 8, 256, 0, s>>>(a);                         \
     }                                                                                     \
     return;                                                                               \
   }
