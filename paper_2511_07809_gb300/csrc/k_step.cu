@@ -174,8 +174,9 @@ __global__ void __launch_bounds__(32 * kDocsPerBlock)
     }
   }
   if constexpr (TC) {
-    if (!X_out && d < b.n_docs) {
-      // row-major BF16 copy: the A operand of Y = X Phi; k_rows_to_cols makes X^T from it
+    if (!X_out && d < round_up(b.n_docs, 64)) {
+      // row-major BF16 copy: the A operand of Y = X Phi and of G1 = X^T Z (rows
+      // past the batch, up to the next multiple of 64, are written as zeros)
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const int col = v * 128 + lane * 4;
@@ -196,12 +197,8 @@ void launch_whiten(const StepArgs &a, cudaStream_t s, float *X_out, bool stats) 
   const int nv = (a.Dp + 127) / 128;
 #define TLDA_WHITEN(NVv)                                                                        \
   if (nv == NVv) {                                                                              \
-    if (tc) {                                                                                   \
-      k_scan_whiten<NVv, true><<<grid, 32 * kDocsPerBlock, 0, s>>>(a, X_out, stats);            \
-      launch_rows_to_cols(a, a.X16, a.Dp, 0, 0, s); /* X^T into AT16 */                           \
-    } else {                                                                                    \
-      k_scan_whiten<NVv, false><<<grid, 32 * kDocsPerBlock, 0, s>>>(a, X_out, stats);           \
-    }                                                                                           \
+    if (tc) k_scan_whiten<NVv, true><<<grid, 32 * kDocsPerBlock, 0, s>>>(a, X_out, stats);     \
+    else k_scan_whiten<NVv, false><<<grid, 32 * kDocsPerBlock, 0, s>>>(a, X_out, stats);       \
     return;                                                                                     \
   }
   TLDA_WHITEN(1) TLDA_WHITEN(2) TLDA_WHITEN(3) TLDA_WHITEN(4)
@@ -412,13 +409,14 @@ __global__ void __launch_bounds__(256) k_qy_f32(StepArgs a) {
 // One warp per document (8 per block: small blocks keep more warps resident
 // per SM): r_d = sum_m f_dm q_m^2 over gathered Q rows (four in flight),
 // z_d = y_d^2 - r_d, H_m += f_dm y_d (vector atomics), and the document part
-// of the loss.  TC=true writes Z as whole BF16 rows (Z16).
+// of the loss.  TC=true writes Z as whole BF16 rows (Z16), zero rows past the
+// batch up to the next multiple of 64.
 template <int NK, bool TC>
 __global__ void __launch_bounds__(256) k_rz(StepArgs a) {
   const BatchDesc b = a.st->cur;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int d0 = blockIdx.x * 8, d = d0 + warp;
-  if (d0 >= b.n_docs) return;
+  if (d0 >= (TC ? round_up(b.n_docs, 64) : b.n_docs)) return;
   float4 y[NK], r[NK];
 #pragma unroll
   for (int v = 0; v < NK; ++v) {
@@ -474,7 +472,7 @@ __global__ void __launch_bounds__(256) k_rz(StepArgs a) {
       const float4 z = make_float4(y[v].x * y[v].x - r[v].x, y[v].y * y[v].y - r[v].y,
                                    y[v].z * y[v].z - r[v].z, y[v].w * y[v].w - r[v].w);
       if constexpr (TC) {
-        if (d < b.n_docs) {
+        if (d < round_up(b.n_docs, 64)) {
           __nv_bfloat162 p[2] = {__floats2bfloat162_rn(z.x, z.y), __floats2bfloat162_rn(z.z, z.w)};
           *reinterpret_cast<uint2 *>(a.Z16 + (long long)d * a.Kp + col) = *reinterpret_cast<const uint2 *>(p);
         }
@@ -596,12 +594,8 @@ void launch_rz(const StepArgs &a, cudaStream_t s) {
   const bool tc = a.precision == TLDA_BF16;
 #define TLDA_RZ(NKv)                                                                      \
   if (nk == NKv) {                                                                        \
-    if (tc) {                                                                             \
-      k_rz<NKv, true><<<round_up(a.Bmax, 64) / 8, 256, 0, s>>>(a);                          \
-      launch_rows_to_cols(a, a.Z16, a.Kp, a.Kp, 0, s); /* Z^T into BT16 */                  \
-    } else {                                                                              \
-      k_rz<NKv, false><<<round_up(a.Bmax, 64) / 8, 256, 0, s>>>(a);                         \
-    }                                                                                     \
+    if (tc) k_rz<NKv, true><<<round_up(a.Bmax, 64) / 8, 256, 0, s>>>(a);                 \
+    else k_rz<NKv, false><<<round_up(a.Bmax, 64) / 8, 256, 0, s>>>(a);                   \
     return;                                                                               \
   }
   TLDA_RZ(1) TLDA_RZ(2) TLDA_RZ(3) TLDA_RZ(4)

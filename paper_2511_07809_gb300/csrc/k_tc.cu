@@ -7,15 +7,13 @@
 //            term needs Q = U Phi).  M = 128 rows of [U; X] per CTA, N = Kp,
 //            K = Dp in 64-feature chunks.  A by TMA from the BF16 copy UX16;
 //            B from the swizzled BF16 image of Phi^T.
-//   k_g_tc   G1 + G2 = [X; U_t]^T [Z; Zc] as a split reduction over the
-//            reduction-major copies AT16 (Dp x ldT) and BT16 (Kp x ldT):
-//            each CTA streams 64-column chunks through a TMA ring and
-//            accumulates a 128-feature x Kp tile in TMEM, then writes its
-//            rows of the partial.  D and K up to 512.
-//   k_zc_tc  Zc rows of the touched words with their U rows (BF16), then
-//            transposed into the columns after the documents'.
-//   k_rows_to_cols  the transposes of X, Z and [Zc | U_t] into the
-//            reduction-major copies AT16 and BT16 that k_g_tc streams.
+//   k_g_tc   G1 + G2 = [X; U_t]^T [Z; Zc] as a split reduction over 64-row
+//            chunks (the batch's documents, then its touched words): both
+//            operands are read MN-major straight from their row-major BF16
+//            copies (X16, Z16 and the [Zc | U_t] rows of ZU16) through a TMA
+//            ring; each CTA accumulates a 128-feature x Kp tile in TMEM, then
+//            writes its rows of the partial.  D and K up to 512.
+//   k_zc_tc  Zc rows of the touched words with their U rows (BF16).
 // Every wait on an mbarrier is bounded (about one second of clock cycles);
 // on expiry the kernel sets the context's timeout bit and leaves.
 #include <cstdio>
@@ -126,12 +124,23 @@ __global__ void __launch_bounds__(128) k_qy_tc(StepArgs a, const __grid_constant
 }
 
 // ------------------------------------------------------------------ G1 + G2
-// Block (s, mt): split s of the reduction chunks, feature rows mt*128 ..
+// Block (s, mt): split s of the 64-row reduction chunks, feature rows
+// mt*128 .. mt*128+127.  A chunk's A tile is two TMA boxes of 64 rows x 64
+// features of X16 (documents) or of the U_t columns of ZU16 (touched words),
+// its B tile Kp/64 boxes of 64 rows x 64 topics of Z16 or of the Zc columns of
+// ZU16; every box lands as 64 rows of 128 swizzled bytes, which is the
+// MN-major operand layout (64-element blocks 8 KB apart).  Rows past the
+// batch's documents (up to the next multiple of 64) are zero in X16 and Z16,
+// and features past Dp read as zero.  N is one MMA up to 256 topics, else
+// 256 + (Kp - 256) side by side in TMEM.
 template <int KP>
-__global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant__ CUtensorMap tmA,
-                                              const __grid_constant__ CUtensorMap tmB) {
-  constexpr int NST = tc_stages(KP), NH = KP > 256 ? 2 : 1, NN = KP / NH;
+__global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant__ CUtensorMap tmX,
+                                              const __grid_constant__ CUtensorMap tmU,
+                                              const __grid_constant__ CUtensorMap tmZ,
+                                              const __grid_constant__ CUtensorMap tmC) {
+  constexpr int NST = tc_stages(KP), N0 = KP > 256 ? 256 : KP, N1 = KP - N0;
   constexpr int A_BYTES = 128 * 128, B_BYTES = KP * 128, STAGE = A_BYTES + B_BYTES;
+  constexpr uint32_t kMN = (1u << 15) | (1u << 16);  // A and B MN-major
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = align1024(smem_raw);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + NST * STAGE);
@@ -176,14 +185,23 @@ __global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant_
         break;
       }
       const int c = c0 + i;
-      const int col = c < cB ? c * 64 : a.Bmax + (c - cB) * 64;
       unsigned char *sa = smem + st * STAGE, *sb = sa + A_BYTES;
       mbar_arrive_expect_tx(&full[st], STAGE);
-      tma_load_2d(sa, &tmA, &full[st], col, m0);
+      if (c < cB) {
+        const int row = c * 64;
+        tma_load_2d(sa, &tmX, &full[st], m0, row);
+        tma_load_2d(sa + 8192, &tmX, &full[st], m0 + 64, row);
 #pragma unroll
-      for (int h = 0; h < NH; ++h) tma_load_2d(sb + h * NN * 128, &tmB, &full[st], col, h * NN);
+        for (int j = 0; j < KP / 64; ++j) tma_load_2d(sb + j * 8192, &tmZ, &full[st], j * 64, row);
+      } else {
+        const int row = (c - cB) * 64;
+        tma_load_2d(sa, &tmU, &full[st], m0, row);
+        tma_load_2d(sa + 8192, &tmU, &full[st], m0 + 64, row);
+#pragma unroll
+        for (int j = 0; j < KP / 64; ++j) tma_load_2d(sb + j * 8192, &tmC, &full[st], j * 64, row);
+      }
     }
-  } else if (tid == 32) {  // MMA issuer
+  } else if (tid == 32) {  // MMA issuer: 16 reduction rows (2 KB of each tile) per MMA
     for (int i = 0; i < n; ++i) {
       const int st = i % NST;
       if (!mbar_wait(&full[st], (i / NST) & 1)) {
@@ -193,11 +211,14 @@ __global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant_
       tc_fence_after();
       const uint32_t aBase = smem_u32(smem + st * STAGE), bBase = aBase + A_BYTES;
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-        for (int h = 0; h < NH; ++h)
-          mma_bf16(tmem + h * NN, sdesc_sw128(aBase + kk * 32), sdesc_sw128(bBase + h * NN * 128 + kk * 32),
-                   idesc_bf16(128, NN), (i > 0 || kk > 0) ? 1u : 0u);
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t ad = sdesc_mn_sw128(aBase + kk * 2048, 8192);
+        const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+        mma_bf16(tmem, ad, sdesc_mn_sw128(bBase + kk * 2048, 8192), idesc_bf16(128, N0) | kMN, acc);
+        if constexpr (N1 > 0)
+          mma_bf16(tmem + N0, ad, sdesc_mn_sw128(bBase + (N0 / 64) * 8192 + kk * 2048, 8192),
+                   idesc_bf16(128, N1) | kMN, acc);
+      }
       mma_commit(&empty[st]);
     }
     mma_commit(done);
@@ -229,12 +250,11 @@ __global__ void __launch_bounds__(128) k_g_tc(StepArgs a, const __grid_constant_
 // ------------------------------------------------------------------ Zc (BF16, transposed)
 // k_zc_tc: one warp per compact slot t (8 per block): row t of ZU16 takes
 // [Zc_t | U_m] in BF16, Zc_t = q (2 c_m q - 2 H_m) with m = widx[t].  Slots
-// in [n_touched, round_up(n_touched, 64)) get zero rows (chunk padding).
-// k_h_clear then clears H_m and c_m for the next batch: a warp that loads an
-// H row and then stores to it (an L2 miss followed by a write to the pending
-// line) ran about six times slower than the load or the store alone.
-// k_rows_to_cols then moves ZU16 into columns Bmax + t of BT16 (its first Kp
-// columns) and AT16 (the other Dp).
+// in [n_touched, round_up(n_touched, 64)) get zero rows (chunk padding);
+// k_g_tc reads the rows directly.  k_h_clear then clears H_m and c_m for the
+// next batch: a warp that loads an H row and then stores to it (an L2 miss
+// followed by a write to the pending line) ran about six times slower than
+// the load or the store alone.
 template <int NK>
 __global__ void __launch_bounds__(256) k_zc_tc(StepArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -288,53 +308,6 @@ __global__ void __launch_bounds__(256) k_h_clear(StepArgs a) {
   if (lane == 0) a.cnt[m] = 0;
 }
 
-// Rows [0, round_up(n, 64)) of the row-major BF16 matrix src (ld columns; n
-// valid rows: the batch's documents, or with `slots` its touched words; rows
-// from n on read as zero) into columns col0 + row of BT16 (source columns
-// below c_split) and AT16 (source column c_split + i into row i), in 64 x 64
-// tiles: 128-byte rows read and written through shared memory.
-__global__ void __launch_bounds__(256) k_rows_to_cols(StepArgs a, const __nv_bfloat16 *__restrict__ src, int ld,
-                                                      int c_split, int slots) {
-  __shared__ uint32_t tile[64][33];  // [row][column pair]; 33 words: reads and writes at most 2-way
-  const int n = slots ? a.st->n_touched : a.st->cur.n_docs;
-  const int r0 = blockIdx.x * 64;
-  if (r0 >= round_up(n, 64)) return;  // uniform over the block
-  const int c0 = blockIdx.y * 64, tid = threadIdx.x;
-  const long long col0 = slots ? a.Bmax : 0;
-  for (int e = tid; e < 64 * 8; e += 256) {  // 64 rows x 8 pieces of 16 bytes
-    const int rr = e >> 3, j = e & 7;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (r0 + rr < n) v = *reinterpret_cast<const uint4 *>(src + (long long)(r0 + rr) * ld + c0 + 8 * j);
-    tile[rr][4 * j + 0] = v.x;
-    tile[rr][4 * j + 1] = v.y;
-    tile[rr][4 * j + 2] = v.z;
-    tile[rr][4 * j + 3] = v.w;
-  }
-  __syncthreads();
-  for (int e = tid; e < 64 * 8; e += 256) {  // 64 output rows (columns c0 + k) x 8 pieces of 8 rows
-    const int k = e >> 3, j = e & 7, sh = (k & 1) * 16;
-    uint32_t w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t lo = (tile[8 * j + 2 * q][k >> 1] >> sh) & 0xffffu;
-      const uint32_t hi = (tile[8 * j + 2 * q + 1][k >> 1] >> sh) & 0xffffu;
-      w[q] = lo | (hi << 16);
-    }
-    const int col = c0 + k;
-    __nv_bfloat16 *dst = col < c_split ? a.BT16 + (long long)col * a.ldT : a.AT16 + (long long)(col - c_split) * a.ldT;
-    *reinterpret_cast<uint4 *>(dst + col0 + r0 + 8 * j) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
-
-}  // namespace
-
-void launch_rows_to_cols(const StepArgs &a, const __nv_bfloat16 *src, int ld, int c_split, int slots, cudaStream_t s) {
-  const int rows = slots ? round_up(a.V, 64) : round_up(a.Bmax, 64);
-  k_rows_to_cols<<<dim3(rows / 64, ld / 64), 256, 0, s>>>(a, src, ld, c_split, slots);
-}
-
-namespace {
-
 // ------------------------------------------------------------------ host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -371,8 +344,10 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, 
 struct TcMaps {
   CUtensorMap ug;  // U16: V x Dp, box 1 row x 64 (row gathers)
   CUtensorMap ux;  // UX16: (V + Bmax) x Dp, box 128 rows x 64
-  CUtensorMap at;  // AT16: Dp x ldT, box 128 rows x 64 (rows >= Dp read as zero)
-  CUtensorMap bt;  // BT16: Kp x ldT, box Kp rows x 64
+  CUtensorMap gx;  // X16: Bmax x Dp, box 64 rows x 64 (features past Dp read as zero)
+  CUtensorMap gu;  // U_t columns of ZU16: round_up(V, 64) x Dp, box 64 x 64
+  CUtensorMap gz;  // Z16: Bmax x Kp, box 64 x 64
+  CUtensorMap gc;  // Zc columns of ZU16: round_up(V, 64) x Kp, box 64 x 64
 };
 
 template <int KP>
@@ -397,20 +372,23 @@ void g_launch(const StepArgs &a, const TcMaps &m, cudaStream_t s) {
     cudaFuncSetAttribute(k_g_tc<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<KP>());
     attr = true;
   }
-  k_g_tc<KP><<<dim3(a.nsplit, (a.Dp + 127) / 128), 128, tc_smem<KP>(), s>>>(a, m.at, m.bt);
+  k_g_tc<KP><<<dim3(a.nsplit, (a.Dp + 127) / 128), 128, tc_smem<KP>(), s>>>(a, m.gx, m.gu, m.gz, m.gc);
 }
 
 }  // namespace
 
 bool tc_supported(int Dp, int Kp) { return Dp <= 512 && Kp <= 512; }
 
-void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const __nv_bfloat16 *BT16, int V,
-                   int Bmax, int Dp, int Kp, int ldT) {
+void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *ZU16, const __nv_bfloat16 *Z16, int V, int Bmax,
+                   int Dp, int Kp) {
   TcMaps *m = new TcMaps();
+  const uint64_t Vr = (uint64_t)(V + 63) / 64 * 64, ldzu = (uint64_t)(Kp + Dp) * 2;
   bool ok = make_map(&m->ug, UX16, Dp, (uint64_t)V, (uint64_t)Dp * 2, 1) &&
             make_map(&m->ux, UX16, Dp, (uint64_t)V + Bmax, (uint64_t)Dp * 2, 128) &&
-            make_map(&m->at, AT16, ldT, Dp, (uint64_t)ldT * 2, 128) &&
-            make_map(&m->bt, BT16, ldT, Kp, (uint64_t)ldT * 2, Kp > 256 ? Kp / 2 : Kp);
+            make_map(&m->gx, UX16 + (size_t)V * Dp, Dp, (uint64_t)Bmax, (uint64_t)Dp * 2, 64) &&
+            make_map(&m->gu, ZU16 + Kp, Dp, Vr, ldzu, 64) &&
+            make_map(&m->gz, Z16, Kp, (uint64_t)Bmax, (uint64_t)Kp * 2, 64) &&
+            make_map(&m->gc, ZU16, Kp, Vr, ldzu, 64);
   if (!ok) {
     delete m;
     return nullptr;
@@ -461,7 +439,6 @@ void launch_zh_tc(const StepArgs &a, cudaStream_t s) {
     k_zc_tc<4><<<grid, 256, 0, s>>>(a);
     k_h_clear<4><<<grid, 256, 0, s>>>(a);
   }
-  launch_rows_to_cols(a, a.ZU16, a.Kp + a.Dp, a.Kp, 1, s);
 }
 
 }  // namespace tlda

@@ -94,11 +94,8 @@ StepArgs make_args(tlda_ctx *c) {
   a.G3 = c->G3;
   a.U16 = c->U16;
   a.X16 = c->X16;
-  a.AT16 = c->AT16;
-  a.BT16 = c->BT16;
   a.ZU16 = c->ZU16;
   a.Z16 = c->Z16;
-  a.ldT = c->ldT;
   a.precision = c->p.precision;
   a.tc_maps = c->tc_maps;
   a.PhiImg = c->PhiImg;
@@ -476,7 +473,6 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
   ctx->Dp = round_up(D, 64);
   ctx->Kp = round_up(K, 64);
   ctx->Bmax = round_up(ctx->p.max_batch, 128);
-  ctx->ldT = ctx->Bmax + round_up(vocab, 128);
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   auto bail = [&](tlda_status s, const char *what, cudaError_t e) {
     fprintf(stderr, "tlda_create: %s: %s\n", what, cudaGetErrorString(e));
@@ -529,12 +525,10 @@ tlda_status tlda_create(tlda_ctx **out, int32_t vocab, const tlda_params *p, voi
     CA(dalloc(&ctx->UX16, (V + Bm) * Dp, true));
     ctx->U16 = ctx->UX16;
     ctx->X16 = ctx->UX16 + V * Dp;
-    CA(dalloc(&ctx->AT16, Dp * (size_t)ctx->ldT, true));
-    CA(dalloc(&ctx->BT16, Kp * (size_t)ctx->ldT, true));
     CA(dalloc(&ctx->ZU16, (size_t)round_up(V, 64) * (Kp + Dp), true));
     CA(dalloc(&ctx->Z16, (size_t)Bm * Kp, true));
     CA(dalloc(&ctx->PhiImg, Dp * Kp, true));
-    ctx->tc_maps = tc_make_maps(ctx->UX16, ctx->AT16, ctx->BT16, vocab, ctx->Bmax, ctx->Dp, ctx->Kp, ctx->ldT);
+    ctx->tc_maps = tc_make_maps(ctx->UX16, ctx->ZU16, ctx->Z16, vocab, ctx->Bmax, ctx->Dp, ctx->Kp);
     if (!ctx->tc_maps) return bail(TLDA_ERR_CUDA, "cuTensorMapEncodeTiled", cudaErrorUnknown);
   }
   if (ctx->fused && !getenv("TLDA_NO_PASS")) ctx->pass_grid = pass_grid();
@@ -559,8 +553,8 @@ tlda_status tlda_destroy(tlda_ctx *ctx) {
   if (ctx->tc_maps) tc_free_maps(ctx->tc_maps);
   dfree(ctx->X32); dfree(ctx->Q32); dfree(ctx->Y32); dfree(ctx->Z32); dfree(ctx->Zc32);
   dfree(ctx->H32); dfree(ctx->cnt); dfree(ctx->widx); dfree(ctx->Gpart); dfree(ctx->Gram);
-  dfree(ctx->avec); dfree(ctx->E); dfree(ctx->G3); dfree(ctx->AT16); dfree(ctx->ZU16); dfree(ctx->Z16); dfree(ctx->PhiImg);
-  dfree(ctx->BT16); dfree(ctx->st); dfree(ctx->descs); dfree(ctx->P64); dfree(ctx->Ccnt);
+  dfree(ctx->avec); dfree(ctx->E); dfree(ctx->G3); dfree(ctx->ZU16); dfree(ctx->Z16); dfree(ctx->PhiImg);
+  dfree(ctx->st); dfree(ctx->descs); dfree(ctx->P64); dfree(ctx->Ccnt);
   dfree(ctx->TS); dfree(ctx->fit_err); dfree(ctx->stage[0]); dfree(ctx->stage[1]);
   dfree(ctx->ctl); dfree(ctx->st_tune); dfree(ctx->dlosses); dfree(ctx->phi_scratch);
   dfree(ctx->on_Om); dfree(ctx->on_Z); dfree(ctx->on_C); dfree(ctx->on_TS); dfree(ctx->on_err);

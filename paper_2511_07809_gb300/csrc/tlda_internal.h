@@ -110,11 +110,8 @@ struct StepArgs {
   // BF16 tensor-core work
   const __nv_bfloat16 *U16;      // V x Dp
   __nv_bfloat16 *X16;            // Bmax x Dp
-  __nv_bfloat16 *AT16;           // Dp x ldT: X^T (docs) then U^T (touched words)
-  __nv_bfloat16 *BT16;           // Kp x ldT: Z^T (docs) then Zc^T (touched words)
   __nv_bfloat16 *ZU16;           // round_up(V, 64) x (Kp + Dp): [Zc | U] rows of the touched words
   __nv_bfloat16 *Z16;            // Bmax x Kp: Z rows of the documents (BF16)
-  int ldT;                       // Bmax + V rounded up
   int precision;
   const void *tc_maps;           // host pointer to the TMA tensor maps (BF16 form)
   __nv_bfloat16 *PhiImg;         // shared-memory image of Phi^T (BF16 form, Kp x Dp, swizzled)
@@ -137,7 +134,7 @@ struct NvtxRange {
 }  // namespace tlda
 
 struct tlda_ctx {
-  int V = 0, D = 0, K = 0, Dp = 0, Kp = 0, Bmax = 0, ldT = 0;
+  int V = 0, D = 0, K = 0, Dp = 0, Kp = 0, Bmax = 0;
   tlda_params p{};
   cudaStream_t stream = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -158,7 +155,7 @@ struct tlda_ctx {
   int nsplit = 0, nsplit_tc = 0;
   bool fused = false;            // BF16 form through the fused kernel
   int fused_grid = 0;            // its persistent CTAs (SMs minus those left to the side stream)
-  __nv_bfloat16 *UX16 = nullptr, *X16 = nullptr, *AT16 = nullptr, *BT16 = nullptr, *ZU16 = nullptr, *Z16 = nullptr;
+  __nv_bfloat16 *UX16 = nullptr, *X16 = nullptr, *ZU16 = nullptr, *Z16 = nullptr;
   void *tc_maps = nullptr;
   __nv_bfloat16 *PhiImg = nullptr;
   tlda::DevState *st = nullptr;
@@ -243,12 +240,11 @@ cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, in
 cudaError_t launch_barrier_selftest(PassCtl *ctl, cudaStream_t s, int grid);
 // k_tc.cu (BF16 tensor-core form)
 bool tc_supported(int Dp, int Kp);
-void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *AT16, const __nv_bfloat16 *BT16, int V,
-                   int Bmax, int Dp, int Kp, int ldT);
+void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *ZU16, const __nv_bfloat16 *Z16, int V, int Bmax,
+                   int Dp, int Kp);
 void tc_free_maps(void *maps);
 const void *tc_gather_map(const void *maps);  // the U16 row-gather map (CUtensorMap)
 void launch_qy_tc(const StepArgs &a, cudaStream_t s);
 void launch_zh_tc(const StepArgs &a, cudaStream_t s);
-void launch_rows_to_cols(const StepArgs &a, const __nv_bfloat16 *src, int ld, int c_split, int slots, cudaStream_t s);
 void launch_g_tc(const StepArgs &a, cudaStream_t s);
 }  // namespace tlda
