@@ -421,35 +421,47 @@ class DeviceGenerator:
         self.cdf = torch.as_tensor(np.ascontiguousarray(topic_cdf, dtype=np.uint64).view(np.int64)).to("cuda")
         self.len_cdf = torch.as_tensor(np.ascontiguousarray(len_cdf, dtype=np.uint64).view(np.int64)).to("cuda")
         self.a_num, self.a_den, self.min_len = int(a_num), int(a_den), int(min_len)
+        self._scratch = None  # kept: the write pass still uses it after a call returns
+        self._last_stream = None
 
-    def _call(self, doc0, n_docs, indptr, indices, counts, cap, scratch):
+    def _call(self, doc0, n_docs, indptr, indices, counts, cap, scratch, stream=None):
         nnz = ctypes.c_int64()
         st = self.lib.tlda_generate_docs(self.seed, self.V, self.K, self.cdf.data_ptr(), self.a_num, self.a_den,
                                          self.len_cdf.data_ptr(), int(self.len_cdf.numel()), self.min_len,
                                          int(doc0), int(n_docs), indptr.data_ptr(),
                                          indices.data_ptr() if indices is not None else None,
                                          counts.data_ptr() if counts is not None else None, int(cap),
-                                         scratch.data_ptr(), ctypes.byref(nnz), None)
+                                         scratch.data_ptr(), ctypes.byref(nnz),
+                                         ctypes.c_void_p(stream.cuda_stream) if stream is not None else None)
         return st, nnz.value
 
-    def generate(self, doc0: int, n_docs: int, out: "DeviceCSR | None" = None) -> DeviceCSR:
+    def generate(self, doc0: int, n_docs: int, out: "DeviceCSR | None" = None,
+                 stream: "torch.cuda.Stream | None" = None) -> DeviceCSR:
         """Documents doc0 .. doc0+n_docs-1 as a device CSR; `out` (with enough
-        capacity in indices/counts) is reused when given."""
-        scratch = torch.empty((n_docs + 1023) // 1024 + 2, dtype=torch.int64, device="cuda")
+        capacity in indices/counts) is reused when given.  The work runs on
+        `stream` (default: the legacy default stream); the call returns once
+        the row counts are known and the write pass is enqueued."""
+        need = (n_docs + 1023) // 1024 + 2
+        if self._scratch is None or self._scratch.numel() < need or stream is not self._last_stream:
+            torch.cuda.synchronize()  # the previous call's write pass may still use the scratch
+            if self._scratch is None or self._scratch.numel() < need:
+                self._scratch = torch.empty(need, dtype=torch.int64, device="cuda")
+            self._last_stream = stream
+        scratch = self._scratch
         if out is not None and out.indptr.numel() >= n_docs + 1:
             indptr, indices, counts = out.indptr[:n_docs + 1], out.indices, out.counts
-            st, nnz = self._call(doc0, n_docs, indptr, indices, counts, indices.numel(), scratch)
+            st, nnz = self._call(doc0, n_docs, indptr, indices, counts, indices.numel(), scratch, stream)
             if st == OK:
                 return DeviceCSR(indptr, indices[:nnz], counts[:nnz], self.V)
             if st != ERR_OOM:
                 raise TLDAError(st, "tlda_generate_docs failed")
         indptr = torch.empty(n_docs + 1, dtype=torch.int32, device="cuda")
-        st, nnz = self._call(doc0, n_docs, indptr, None, None, 0, scratch)
+        st, nnz = self._call(doc0, n_docs, indptr, None, None, 0, scratch, stream)
         if st != OK:
             raise TLDAError(st, "tlda_generate_docs failed")
         indices = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
         counts = torch.empty_like(indices)
-        st, nnz = self._call(doc0, n_docs, indptr, indices, counts, indices.numel(), scratch)
+        st, nnz = self._call(doc0, n_docs, indptr, indices, counts, indices.numel(), scratch, stream)
         if st != OK:
             raise TLDAError(st, "tlda_generate_docs failed")
         return DeviceCSR(indptr, indices[:nnz], counts[:nnz], self.V)
