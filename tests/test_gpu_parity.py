@@ -313,10 +313,13 @@ def test_state_roundtrip(lib, tmp_path):
 
 
 # ----------------------------------------------------------------------------- wide BF16
-@pytest.mark.parametrize("K", [200, 300, 448, 500])
+@pytest.mark.parametrize("K", [150, 200, 300, 350, 448, 500])
 def test_data_term_bf16_wide(lib, K):
-    """D = K up to 512 in the multi-kernel BF16 form: 64-feature chunks through
-    the TMA ring, N above 256 as two MMA halves, feature tiles of 128."""
+    """D = K up to 512 in the multi-kernel BF16 form: 64-row reduction chunks
+    through the TMA ring with MN-major operands, N above 256 as a 256-wide MMA
+    and one of K - 256 (K = 300, 350: 64 and 128 wide), feature tiles of 128
+    (K = 150: the second tile's upper 64 features read past D as zero), and
+    1500 documents, so the last chunk has zero-padded rows."""
     from dataclasses import replace
     sp = replace(ts.WORKLOADS["small_v500_k10"], name=f"wide_k{K}", V=1500, K=K, lam=60.0,
                  seed=ts.WORKLOADS["small_v500_k10"].seed + K)
