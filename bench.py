@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--e1-reps", type=int, default=10)
     ap.add_argument("--e1-epochs", type=int, default=30)
     ap.add_argument("--e1-starts", type=int, default=8)
+    ap.add_argument("--batch-sweep", action="store_true",
+                    help="the pass at fixed minibatch sizes 512..8192: step time against batch size")
     ap.add_argument("--vi", action="store_true", help="time document-topic variational inference")
     ap.add_argument("--vi-docs", type=int, default=2_000_000)
     ap.add_argument("--vi-iters", type=int, default=20)
@@ -434,6 +436,60 @@ def e1_main(args):
     return 0
 
 
+def sweep_main(args):
+    """`--batch-sweep`: the persistent BF16 pass over minibatches of one fixed
+    size B (512, 1024, 2048, 4096, 8192 documents) of the streaming workload,
+    with the whitening fitted on its first 1M documents and the tile size
+    tuned per B.  Reported per B: ms per step and docs/s; and the least-squares
+    line ms = t0 + b B, whose t0 is the per-step cost that does not scale with
+    the batch (barriers, the update, the Phi image, pipeline fill) and whose
+    1/b is the throughput the pass would approach with unbounded batches."""
+    import torch
+    import tlda_synth as ts
+    from paper_2511_07809_gb300 import tlda
+
+    sp = ts.WORKLOADS[WORKLOAD]
+    cdf, _ = ts.topics(sp)
+    n_docs = 4_000_000
+    corpus = ts.corpus(sp.with_docs(n_docs), n_docs=n_docs, cdf=cdf)
+    dev = tlda.DeviceCSR.from_corpus(corpus)
+    Phi0 = torch.tensor(ts.initial_factors(sp.seed + 1, sp.K, sp.K), dtype=torch.float32, device="cuda")
+    sizes, rows = (512, 1024, 2048, 4096, 8192), []
+    sampler = ClockSampler(0).start()
+    for B in sizes:
+        ctx = tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="bf16", max_batch=8192, seed=1)
+        ctx.fit_moments(tlda.DeviceCSR.from_corpus(corpus.rows(0, 1_000_000)), tlda.ACCUMULATE)
+        ctx.fit_moments(None, tlda.FINALIZE)
+        steps = min(2000, n_docs // B)
+        offs = [i * B for i in range(steps + 1)]
+        Phi = Phi0.clone()
+        ctx.cp_pass(dev, offs[:65], Phi, LR)  # tile tuning and warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.cp_pass(dev, offs, Phi, LR)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        rows.append({"batch": B, "steps": steps, "ms_per_step": ms, "docs_s": B / (ms / 1e3)})
+        ctx.close()
+    clocks = sampler.stop()
+    x = np.array([r["batch"] for r in rows], dtype=np.float64)
+    y = np.array([r["ms_per_step"] for r in rows])
+    b, t0 = np.polyfit(x, y, 1)
+    line = {
+        "metric": "ms per CP step of the persistent BF16 pass at k=100,V=20k against the minibatch size",
+        "value": None, "unit": "ms", "n_gpus": 1, "higher_is_better": False, "dtype": "bf16",
+        "data": "synthetic: seeded LDA corpus (Dirichlet(0.1) topics, Poisson(12) lengths)",
+        "config": {"workload": sp.name, "V": sp.V, "K": sp.K, "docs": n_docs,
+                   "l2": "inputs larger than L2: a 0.4 GB device-resident corpus"},
+        "rows": rows, "fit": {"t0_us": t0 * 1e3, "ns_per_doc": b * 1e6, "asymptotic_docs_s": 1e3 / b},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def vi_main(args):
     """`--vi`: docs/s of document-topic variational inference
     (tlda_doc_topics) over the first N documents of the streaming workload,
@@ -673,6 +729,8 @@ def main():
         return reference_arm(args)
     if args.billion:
         return billion_main(args)
+    if args.batch_sweep:
+        return sweep_main(args)
     if args.vi:
         return vi_main(args)
     if args.online:
