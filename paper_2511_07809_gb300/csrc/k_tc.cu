@@ -100,20 +100,33 @@ __global__ void __launch_bounds__(128) k_qy_tc(StepArgs a, const __grid_constant
   // warp-uniform decision: tcgen05.ld below is .sync.aligned
   const bool ok = __all_sync(0xffffffffu, !failed && mbar_wait(done, 0));
   if (ok) {
+    // each warp's 32 rows x 32 columns pass through shared memory (the ring is
+    // free once every MMA is done), so that a store covers four rows of 128
+    // bytes rather than 32 rows of 16
     tc_fence_after();
-    const int row = r0 + warp * 32 + lane;
-    float *out = nullptr;
-    if (row < a.V) out = a.Q32 + (long long)row * a.Kp;
-    else if (row < rows) out = a.Y32 + (long long)(row - a.V) * a.Kp;
-#pragma unroll
-    for (int c0 = 0; c0 < KP; c0 += 16) {
-      float v[16];
+    float *stg = reinterpret_cast<float *>(smem) + warp * (32 * 33);
+    const int rbase = r0 + warp * 32;
+#pragma unroll 1
+    for (int c0 = 0; c0 < KP; c0 += 32) {
+      float v[16], w[16];
       tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
-      if (out) {
+      tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0 + 16, w);
 #pragma unroll
-        for (int q = 0; q < 16; q += 4)
-          *reinterpret_cast<float4 *>(out + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      for (int j = 0; j < 16; ++j) {
+        stg[lane * 33 + j] = v[j];
+        stg[lane * 33 + 16 + j] = w[j];
       }
+      __syncwarp();
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int rr = it * 4 + (lane >> 3), c4 = (lane & 7) * 4, row = rbase + rr;
+        float *out = row < a.V ? a.Q32 + (long long)row * a.Kp
+                               : (row < rows ? a.Y32 + (long long)(row - a.V) * a.Kp : nullptr);
+        if (out)
+          *reinterpret_cast<float4 *>(out + c0 + c4) =
+              make_float4(stg[rr * 33 + c4], stg[rr * 33 + c4 + 1], stg[rr * 33 + c4 + 2], stg[rr * 33 + c4 + 3]);
+      }
+      __syncwarp();
     }
   } else if (lane == 0) {
     atomicOr(&a.st->err, kErrTimeout);
