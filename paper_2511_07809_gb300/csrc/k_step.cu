@@ -439,21 +439,28 @@ __global__ void __launch_bounds__(256) k_rz(StepArgs a) {
             ff[u] = (float)__shfl_sync(0xffffffffu, c.f, (q + u) & 31);
             if (q + u >= c.n) ff[u] = 0.f;
           }
+          // all NK x 4 row pieces are requested before the first H atomic (loads
+          // are not moved across the atomics by the compiler)
+          float4 qv[NK][4];
+#pragma unroll
+          for (int v = 0; v < NK; ++v) {
+            const int col = v * 128 + lane * 4;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              qv[v][u] = col < a.Kp ? *reinterpret_cast<const float4 *>(a.Q32 + (long long)mm[u] * a.Kp + col)
+                                    : f4(0.f);
+          }
 #pragma unroll
           for (int v = 0; v < NK; ++v) {
             const int col = v * 128 + lane * 4;
             if (col < a.Kp) {
-              float4 qv[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u)
-                qv[u] = *reinterpret_cast<const float4 *>(a.Q32 + (long long)mm[u] * a.Kp + col);
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
                 const float ff2 = ff[u];
-                r[v].x = fmaf(ff2 * qv[u].x, qv[u].x, r[v].x);
-                r[v].y = fmaf(ff2 * qv[u].y, qv[u].y, r[v].y);
-                r[v].z = fmaf(ff2 * qv[u].z, qv[u].z, r[v].z);
-                r[v].w = fmaf(ff2 * qv[u].w, qv[u].w, r[v].w);
+                r[v].x = fmaf(ff2 * qv[v][u].x, qv[v][u].x, r[v].x);
+                r[v].y = fmaf(ff2 * qv[v][u].y, qv[v][u].y, r[v].y);
+                r[v].z = fmaf(ff2 * qv[v][u].z, qv[v][u].z, r[v].z);
+                r[v].w = fmaf(ff2 * qv[v][u].w, qv[v][u].w, r[v].w);
                 if (ff2 != 0.f)
                   atomicAdd(reinterpret_cast<float4 *>(a.H32 + (long long)mm[u] * a.Kp + col),
                             make_float4(ff2 * y[v].x, ff2 * y[v].y, ff2 * y[v].z, ff2 * y[v].w));
