@@ -239,16 +239,21 @@ tlda_status tlda_fit_batched(tlda_ctx *ctx, const tlda_csr *corpus, const int64_
 
 /* Tile size of the persistent pass kernel: the most documents per tile,
  * 1..32 (each batch is split into ceil(n_docs / SMs) document tiles up to
- * this size).  With fixed_cap > 0 the size is set to fixed_cap and nothing
- * runs (corpus may be NULL).  With fixed_cap = 0 the candidates 8, 14, 16,
- * 18, 20, 24, 28 and 32 are timed on up to the first 64 batches of `corpus`
- * (device CSR,
- * batches as in tlda_cp_pass), stepping a scratch copy of Phi (D x K FP32,
- * device; Phi itself and the context's step and error state are left
- * unchanged: a corrupt batch among them is reported by the pass that steps
- * it), and the fastest is kept.  *tile_cap_out (may be NULL) receives the size in
- * use.  Synchronises.  TLDA_ERR_UNIMPLEMENTED on a context without the
- * persistent pass kernel; TLDA_ERR_STATE without a whitening. */
+ * this size).  The size is kept per band of batch sizes (512-document bands,
+ * the last one open), since the best one depends on how many 128-nonzero
+ * chunks a tile spans and how many tiles each block takes.  With
+ * fixed_cap > 0 every band gets fixed_cap and nothing runs (corpus may be
+ * NULL).  With fixed_cap = 0 the candidates 8, 14, 16, 18, 20, 24, 28 and 32
+ * are timed on the batches of each band among up to the first 128 batches of
+ * `corpus` (device CSR, batches as in tlda_cp_pass; at least 8 steps per
+ * timing), stepping a scratch copy of Phi (D x K FP32, device; Phi itself and
+ * the context's step and error state are left unchanged: a corrupt batch
+ * among them is reported by the pass that steps it), and the fastest is kept
+ * per band; a band without batches takes the nearest tuned band's size.  A
+ * device-input tlda_cp_pass on an untuned context tunes this way on its own
+ * first batches.  *tile_cap_out (may be NULL) receives the size of the first
+ * batch's band.  Synchronises.  TLDA_ERR_UNIMPLEMENTED on a context without
+ * the persistent pass kernel; TLDA_ERR_STATE without a whitening. */
 tlda_status tlda_autotune(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *batch_offsets,
                           int32_t n_batches, const float *Phi, int32_t fixed_cap,
                           int32_t *tile_cap_out);

@@ -679,7 +679,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const int slot = s & 1;
     const BatchDesc b = p.descs[s];
     const int nd = b.n_docs;
-    const int td = nd > 0 ? max(1, min(p.tile_cap, (nd + G - 1) / G)) : 1;
+    const int cap = p.tile_cap > 0 ? p.tile_cap : (b.tile_cap > 0 ? b.tile_cap : 32);
+    const int td = nd > 0 ? max(1, min(cap, (nd + G - 1) / G)) : 1;
     const int ntiles = nd > 0 ? (nd + td - 1) / td : 0;
     const int nwork = min(G, ntiles);
     const bool has = blk < ntiles;

@@ -213,7 +213,7 @@ tlda_status take_sticky(tlda_ctx *ctx) {
 
 // ------------------------------------------------------------ persistent pass
 constexpr long long kStageWords = 1ll << 23;  // int32 words per host-input staging buffer (32 MB)
-constexpr int kTuneBatches = 64;
+constexpr int kTuneBatches = 128;
 
 tlda_status ensure_descs(tlda_ctx *ctx, int n) {
   if (ctx->descs_cap < n) {
@@ -241,10 +241,15 @@ tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int ca
   return TLDA_OK;
 }
 
-// Times each candidate tile size over steps [0, n) of ctx->descs on a
-// scratch copy of Phi (lr = 0) and a scratch device state (a corrupt batch
-// is left for the real pass to report), and keeps the fastest.
-tlda_status tune_tiles(tlda_ctx *ctx, const float *Phi, int n, cudaStream_t ps) {
+// Times each candidate tile size on the batches of each size band among hd
+// (the first batches of a pass; at least 8 steps per timing, repeating the
+// band's batches), on a scratch copy of Phi (lr = 0) and a scratch device
+// state (a corrupt batch is left for the real pass to report), and keeps the
+// fastest per band.  A band without batches takes the size of the nearest
+// band that has some.  The best size depends on the batch size: it sets how
+// many 128-nonzero chunks a tile spans and how many tiles each block takes.
+// ctx->descs serves as scratch (a pass uploads its own descriptors after).
+tlda_status tune_tiles(tlda_ctx *ctx, const float *Phi, const std::vector<BatchDesc> &hd, cudaStream_t ps) {
   StepArgs a = make_args(ctx);
   a.Phi = ctx->phi_scratch;
   a.st = ctx->st_tune;
@@ -252,32 +257,63 @@ tlda_status tune_tiles(tlda_ctx *ctx, const float *Phi, int n, cudaStream_t ps) 
   CK(cudaMemcpyAsync(ctx->phi_scratch, Phi, sizeof(float) * ctx->D * ctx->K, cudaMemcpyDeviceToDevice, ps));
   launch_phi_img(a, ps);
   CKL();
+  std::vector<BatchDesc> band[kCapBands];
+  for (const BatchDesc &d : hd) band[cap_band(d.n_docs)].push_back(d);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   const int cands[] = {8, 14, 16, 18, 20, 24, 28, 32};
-  int best = ctx->tile_cap;
-  float best_ms = 0.f;
+  bool have[kCapBands] = {};
   tlda_status s = TLDA_OK;
-  for (int c : cands) {
-    float ms = 0.f;
-    for (int rep = 0; rep < 2 && s == TLDA_OK; ++rep) {  // the first run is a warm-up
-      cudaEventRecord(e0, ps);
-      s = pass_launch(ctx, a, 0, n, c, nullptr, 0, ps);
-      cudaEventRecord(e1, ps);
-      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-        s = fail(ctx, TLDA_ERR_CUDA, "tile tuning: %s", cudaGetErrorString(cudaGetLastError()));
-    }
+  for (int bb = 0; bb < kCapBands && s == TLDA_OK; ++bb) {
+    if (band[bb].empty()) continue;
+    std::vector<BatchDesc> v = band[bb];
+    while (v.size() < 8) v.insert(v.end(), band[bb].begin(), band[bb].end());
+    const int n = (int)v.size();
+    s = ensure_descs(ctx, n);
     if (s) break;
-    if (best_ms == 0.f || ms < best_ms) {
-      best_ms = ms;
-      best = c;
+    if (cudaMemcpyAsync(ctx->descs, v.data(), sizeof(BatchDesc) * n, cudaMemcpyHostToDevice, ps) != cudaSuccess ||
+        cudaStreamSynchronize(ps) != cudaSuccess) {  // v is pageable
+      s = fail(ctx, TLDA_ERR_CUDA, "tile tuning: descriptor upload");
+      break;
     }
+    int best = 32;
+    float best_ms = 0.f;
+    for (int c : cands) {
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && s == TLDA_OK; ++rep) {  // the first run is a warm-up
+        cudaEventRecord(e0, ps);
+        s = pass_launch(ctx, a, 0, n, c, nullptr, 0, ps);
+        cudaEventRecord(e1, ps);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+          s = fail(ctx, TLDA_ERR_CUDA, "tile tuning: %s", cudaGetErrorString(cudaGetLastError()));
+      }
+      if (s) break;
+      if (best_ms == 0.f || ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    ctx->cap_band[bb] = best;
+    have[bb] = true;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s) return s;
-  ctx->tile_cap = best;
+  for (int bb = 0; bb < kCapBands; ++bb) {
+    if (have[bb]) continue;
+    for (int dd = 1; dd < kCapBands; ++dd) {
+      if (bb - dd >= 0 && have[bb - dd]) {
+        ctx->cap_band[bb] = ctx->cap_band[bb - dd];
+        break;
+      }
+      if (bb + dd < kCapBands && have[bb + dd]) {
+        ctx->cap_band[bb] = ctx->cap_band[bb + dd];
+        break;
+      }
+    }
+  }
+  ctx->tile_cap = hd.empty() ? ctx->tile_cap : ctx->cap_band[cap_band(hd[0].n_docs)];
   ctx->tuned = true;
   return TLDA_OK;
 }
@@ -341,8 +377,7 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
       d.n_docs = (int32_t)(off[b + 1] - off[b]);
     }
   }
-  tlda_status s = ensure_descs(ctx, nb);
-  if (s) return s;
+  tlda_status s = TLDA_OK;
   if (loss_out && ctx->dlosses_cap < nb) {
     dfree(ctx->dlosses);
     ctx->dlosses_cap = 0;
@@ -352,12 +387,15 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
   cudaStream_t ps = ctx->pstream;
   CK(cudaEventRecord(ctx->ev_pass0, ctx->stream));
   CK(cudaStreamWaitEvent(ps, ctx->ev_pass0, 0));
-  CK(cudaMemcpyAsync(ctx->descs, hd.data(), sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, ps));
-  CK(cudaStreamSynchronize(ps));  // hd is pageable: keep it alive until copied
   if (!ctx->tuned && !host) {
-    s = tune_tiles(ctx, Phi, std::min(nb, kTuneBatches), ps);
+    s = tune_tiles(ctx, Phi, std::vector<BatchDesc>(hd.begin(), hd.begin() + std::min(nb, kTuneBatches)), ps);
     if (s) return s;
   }
+  for (BatchDesc &d : hd) d.tile_cap = ctx->cap_band[cap_band(d.n_docs)];
+  s = ensure_descs(ctx, nb);
+  if (s) return s;
+  CK(cudaMemcpyAsync(ctx->descs, hd.data(), sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, ps));
+  CK(cudaStreamSynchronize(ps));  // hd is pageable: keep it alive until copied
   StepArgs a = make_args(ctx);
   a.lr = lr;
   a.Phi = Phi;
@@ -382,7 +420,7 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
       CK(cudaEventRecord(ctx->ev_seg[g & 1], cs));
       CK(cudaStreamWaitEvent(ps, ctx->ev_seg[g & 1], 0));
     }
-    s = pass_launch(ctx, a, b0, b1, ctx->tile_cap, loss_out ? ctx->dlosses : nullptr, 1, ps);
+    s = pass_launch(ctx, a, b0, b1, 0, loss_out ? ctx->dlosses : nullptr, 1, ps);  // each batch's tile size
     if (host && s == TLDA_OK) CK(cudaEventRecord(ctx->ev_seg[2 + (g & 1)], ps));
   }
   if (s == TLDA_OK && loss_out)
@@ -852,6 +890,7 @@ tlda_status tlda_autotune(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *
   if (fixed_cap < 0 || fixed_cap > 32) return fail(ctx, TLDA_ERR_INVALID, "tile size %d not in 1..32", fixed_cap);
   if (fixed_cap > 0) {
     ctx->tile_cap = fixed_cap;
+    for (int &c : ctx->cap_band) c = fixed_cap;
     ctx->tuned = true;
   } else {
     if (!ctx->whitened) return fail(ctx, TLDA_ERR_STATE, "no whitening: fit or set one first");
@@ -866,13 +905,10 @@ tlda_status tlda_autotune(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *
       if (d1 - d0 > ctx->Bmax) return fail(ctx, TLDA_ERR_INVALID, "batch %d has %lld docs > max_batch", b, (long long)(d1 - d0));
       hd[b] = BatchDesc{corpus->indptr + d0, corpus->indices, corpus->counts, 0, (int32_t)(d1 - d0), 0};
     }
-    s = ensure_descs(ctx, n);
-    if (s) return s;
     cudaStream_t ps = ctx->pstream;
     CK(cudaEventRecord(ctx->ev_pass0, ctx->stream));
     CK(cudaStreamWaitEvent(ps, ctx->ev_pass0, 0));
-    CK(cudaMemcpyAsync(ctx->descs, hd.data(), sizeof(BatchDesc) * n, cudaMemcpyHostToDevice, ps));
-    s = tune_tiles(ctx, Phi, n, ps);
+    s = tune_tiles(ctx, Phi, hd, ps);
     CK(cudaEventRecord(ctx->ev_pass1, ps));
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_pass1, 0));
     if (s) return s;

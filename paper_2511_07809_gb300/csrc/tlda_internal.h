@@ -30,8 +30,13 @@ struct BatchDesc {
   const int32_t *counts;
   long long nz_base;
   int32_t n_docs;
-  int32_t pad;
+  int32_t tile_cap;              // documents per tile of this batch in the pass kernel (0: 32)
 };
+
+// Bands of batch sizes with a tile size of their own: band b holds the
+// batches of (512 b, 512 (b + 1)] documents, the last one everything above.
+constexpr int kCapBands = 16;
+inline int cap_band(int n_docs) { return n_docs <= 0 ? 0 : (n_docs - 1) / 512 < kCapBands ? (n_docs - 1) / 512 : kCapBands - 1; }
 
 // Device-resident per-context state of the CP step.  Every step kernel reads
 // the current batch from `cur`, so one step sequence (or a captured graph of
@@ -68,7 +73,7 @@ struct PassCtl {
 struct PassArgs {
   const BatchDesc *descs;        // all batches of the pass (device)
   int s0, s1;
-  int tile_cap;                  // most documents per tile
+  int tile_cap;                  // most documents per tile (0: each batch's own)
   double *losses;                // per-step loss (device, indexed by step) or null
   PassCtl *ctl;
   int record;                    // 1: advance the context's step state (0 for tuning runs)
@@ -191,6 +196,7 @@ struct tlda_ctx {
   // persistent pass kernel (BF16 fused form)
   int pass_grid = 0;                   // its blocks (0: not available)
   int tile_cap = 32;                   // most documents per tile (tuned on the first pass)
+  int cap_band[tlda::kCapBands] = {32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32, 32};  // per size band
   bool tuned = false;
   tlda::PassCtl *ctl = nullptr;
   tlda::DevState *st_tune = nullptr;   // device state of tuning runs (kept apart from st)
