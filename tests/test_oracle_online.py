@@ -34,6 +34,21 @@ def test_sketch_accumulates_the_pair_counts():
     assert _rel(Z, P @ Om) < 1e-13
 
 
+def test_sketch_with_a_sign_test_matrix_is_exact():
+    """With entries of +-1 every sum of the sketch is an integer: the oracle's
+    FP64 sketch equals the integer pair counts times Omega bit for bit (the
+    premise of the device tests that compare the two for equality)."""
+    rng = np.random.default_rng(5)
+    V, r = 50, 12
+    indptr, indices, counts, _ = _rand_csr(rng, 80, V, 15)
+    Om = ts.signs(0x5EED, 0x4F4D, V * r).reshape(V, r)
+    assert set(np.unique(Om)) == {-1.0, 1.0}
+    Z = O.sketch_accumulate(indptr, indices, counts, V, Om)
+    P = O.pair_counts(indptr, indices, counts, V).astype(np.int64)
+    exact = P @ Om.astype(np.int64)
+    assert np.array_equal(Z, exact.astype(np.float64))
+
+
 def test_sketched_m2_equals_dense_m2_times_omega():
     rng = np.random.default_rng(4)
     V, r, a0 = 30, 7, 1.5
