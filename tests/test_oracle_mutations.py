@@ -40,6 +40,7 @@ MUTATIONS = [
     ("VI without digamma", "p = rows * np.exp(scipy.special.digamma(gamma))[None, :]", "p = rows * gamma[None, :]"),
     ("VI drops the prior", "return phi, alpha + f @ phi", "return phi, f @ phi"),
     ("bound entropy sign", "h_z = -(f[:, None] * phi * logphi).sum()", "h_z = (f[:, None] * phi * logphi).sum()"),
+    ("S2 with repeated tokens", "S2=int(np.sum(L * (L - 1)))", "S2=int(np.sum(L * L))"),
 ]
 PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_online.py", "tests/test_oracle_batched.py",
              "tests/test_oracle_vi.py"]
