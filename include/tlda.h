@@ -425,7 +425,9 @@ tlda_status tlda_doc_topics(const tlda_csr *docs, const float *mu, const float *
  *  - Output, device: indptr_out (n_docs + 1 int32, relative: indptr[0] = 0),
  *    indices_out and counts_out (capacity nnz_cap int32 each).  With
  *    nnz_cap = 0 only indptr and *nnz_out are produced.
- *  - scratch: device, (n_docs + 1023) / 1024 + 2 int64 words.
+ *  - scratch: device, (n_docs + 1023) / 1024 + 2 int64 words.  The write pass
+ *    is still queued on cuda_stream when the call returns and uses it: keep
+ *    it unchanged until the stream has passed that point.
  *  - *nnz_out (host): the chunk's nonzeros.
  * Synchronises the stream once, to learn the nonzeros.  Errors:
  *  - TLDA_ERR_OOM if they exceed nnz_cap (indices not written) or 2^31 - 1;
