@@ -365,9 +365,15 @@ tlda_status tlda_unwhiten_topics(tlda_ctx *ctx, const float *Phi, double *mu_out
  * loads the library holds until the process exits.  Sizes whose scratch does
  * not fit are rejected with TLDA_ERR_OOM and a one-line message on stderr.
  * For example, V = 4096, D = K = 64 and n_docs = 2048 fit.
- * Set-up: the first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with that device current.  Make that first call
- * before any stream capture.
+ * The batch may hold at most 8 MiB / 768 B = 10,922 documents, else
+ * TLDA_ERR_INVALID.
+ * Set-up: every call looks up that array's device address in the current
+ * context (cudaGetSymbolAddress, which allocates nothing).  The address
+ * belongs to the context that loaded the module, so it can change after a
+ * device reset (cudaDeviceReset, or a reset of the primary context) or under
+ * another context; looking it up per call keeps every call on the array of
+ * the context that is current when the call is made.  The first call in a
+ * context loads the module; make it before any stream capture.
  * Sharing: every call uses the same array.  The array keeps the last call's
  * contents, so each call clears what must start at zero.  Calls that overlap
  * on the GPU (on different streams, or from different host threads) race on
@@ -467,6 +473,17 @@ tlda_status tlda_selftest_barrier(void *cuda_stream, int32_t *blocks_out, int32_
 tlda_status tlda_profile(tlda_ctx *ctx, uint32_t mask);
 tlda_status tlda_profile_read(tlda_ctx *ctx, int32_t kernel, const char **name, int64_t *launches,
                               double *total_ms);
+
+/* FP32 CUDA-core throughput probe (diagnostic; the paper has no counterpart:
+ * it measures the peak against which the FP32 plain form's "alu" roofline is
+ * reported).  Launches one kernel on cuda_stream (NULL: the default stream)
+ * that fills every SM with resident 256-thread blocks, each thread running 8
+ * independent FMA chains for iters x 16 steps, and returns at once.
+ * *flops_out (host) receives the kernel's flop count (2 per FMA); time the
+ * launch with CUDA events on the same stream.  sink: device buffer of at
+ * least (SMs x resident blocks per SM) floats, never written in practice.
+ * TLDA_ERR_INVALID for iters < 1 or NULL pointers. */
+tlda_status tlda_ffma_probe(int32_t iters, float *sink, double *flops_out, void *cuda_stream);
 
 /* --------------------------------------------------------------- state */
 

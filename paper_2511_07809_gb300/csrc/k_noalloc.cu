@@ -6,7 +6,6 @@
 // synchronise the device.  Its scratch is one file-scope __device__ array;
 // the kernels are the ones the context-based entry points launch.
 #include <cstdio>
-#include <mutex>
 #include <utility>
 
 #include "tlda_internal.h"
@@ -20,23 +19,21 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
 constexpr int kNoAllocSplit = 32;
-std::mutex g_mu;
-unsigned char *g_dev_addr[kMaxDevices] = {};
+// Largest batch accepted: the scratch cannot hold more documents' rows anyway
+// (each takes at least 3 x 64 FP32 of X, Y and Z), and the bound keeps every
+// size computation below far from int overflow.
+constexpr int kNoAllocMaxDocs = int(kNoAllocScratchBytes / (3 * 64 * sizeof(float)));
 
-// Device address of the scratch array for the current device, looked up once
-// per device (the array's name in host code is only a host-side stand-in).
+// Device address of the scratch array in the current context.  The array's
+// name in host code is only a host-side stand-in, and its device address
+// belongs to the context that loaded the module: after a device reset, or
+// under another (non-primary) context, it can differ.  So it is looked up on
+// every call; cudaGetSymbolAddress allocates nothing.
 tlda_status scratch_address(unsigned char **out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TLDA_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_dev_addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TLDA_ERR_CUDA;
-    g_dev_addr[dev] = static_cast<unsigned char *>(p);
-  }
-  *out = g_dev_addr[dev];
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TLDA_ERR_CUDA;
+  *out = static_cast<unsigned char *>(p);
   return TLDA_OK;
 }
 
@@ -78,8 +75,8 @@ extern "C" tlda_status tlda_cp_step_noalloc(const tlda_csr *batch, const float *
   TLDA_RANGE();
   if (!batch || !W || !m1 || !Phi) return TLDA_ERR_INVALID;
   const int V = batch->vocab, K = k, D = dim > 0 ? dim : k, B = batch->n_docs;
-  if (V < 1 || K < 1 || D < K || D > V || B < 0 || !(alpha0 > 0.0) || !(theta > -1.f) ||
-      round_up(D, 64) > kMaxDim || round_up(K, 64) > kMaxDim || !batch->indptr ||
+  if (V < 1 || K < 1 || D < K || D > V || B < 0 || B > kNoAllocMaxDocs || !(alpha0 > 0.0) || !(theta > -1.f) ||
+      D > kMaxDim || K > kMaxDim || round_up(D, 64) > kMaxDim || round_up(K, 64) > kMaxDim || !batch->indptr ||
       (B > 0 && (!batch->indices || !batch->counts)))
     return TLDA_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
