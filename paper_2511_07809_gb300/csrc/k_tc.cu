@@ -340,7 +340,7 @@ EncodeTiledFn encode_fn() {
 }
 
 // 2D BF16 tensor [outer x inner] (row pitch in bytes), box [box_outer x 64],
-// 128-byte swizzle (box_outer = 1 for tile::gather4 row gathers).
+// 128-byte swizzle.
 bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
               uint32_t box_outer) {
   EncodeTiledFn fn = encode_fn();
@@ -355,7 +355,6 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, 
 }
 
 struct TcMaps {
-  CUtensorMap ug;  // U16: V x Dp, box 1 row x 64 (row gathers)
   CUtensorMap ux;  // UX16: (V + Bmax) x Dp, box 128 rows x 64
   CUtensorMap gx;  // X16: Bmax x Dp, box 64 rows x 64 (features past Dp read as zero)
   CUtensorMap gu;  // U_t columns of ZU16: round_up(V, 64) x Dp, box 64 x 64
@@ -396,8 +395,7 @@ void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *ZU16, const _
                    int Dp, int Kp) {
   TcMaps *m = new TcMaps();
   const uint64_t Vr = (uint64_t)(V + 63) / 64 * 64, ldzu = (uint64_t)(Kp + Dp) * 2;
-  bool ok = make_map(&m->ug, UX16, Dp, (uint64_t)V, (uint64_t)Dp * 2, 1) &&
-            make_map(&m->ux, UX16, Dp, (uint64_t)V + Bmax, (uint64_t)Dp * 2, 128) &&
+  bool ok = make_map(&m->ux, UX16, Dp, (uint64_t)V + Bmax, (uint64_t)Dp * 2, 128) &&
             make_map(&m->gx, UX16 + (size_t)V * Dp, Dp, (uint64_t)Bmax, (uint64_t)Dp * 2, 64) &&
             make_map(&m->gu, ZU16 + Kp, Dp, Vr, ldzu, 64) &&
             make_map(&m->gz, Z16, Kp, (uint64_t)Bmax, (uint64_t)Kp * 2, 64) &&
@@ -410,8 +408,6 @@ void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *ZU16, const _
 }
 
 void tc_free_maps(void *p) { delete static_cast<TcMaps *>(p); }
-
-const void *tc_gather_map(const void *maps) { return &static_cast<const TcMaps *>(maps)->ug; }
 
 #define TLDA_KP_DISPATCH(F)                                       \
   switch (a.Kp) {                                                 \

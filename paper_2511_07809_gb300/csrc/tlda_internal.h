@@ -249,7 +249,6 @@ bool tc_supported(int Dp, int Kp);
 void *tc_make_maps(const __nv_bfloat16 *UX16, const __nv_bfloat16 *ZU16, const __nv_bfloat16 *Z16, int V, int Bmax,
                    int Dp, int Kp);
 void tc_free_maps(void *maps);
-const void *tc_gather_map(const void *maps);  // the U16 row-gather map (CUtensorMap)
 void launch_qy_tc(const StepArgs &a, cudaStream_t s);
 void launch_zh_tc(const StepArgs &a, cudaStream_t s);
 void launch_g_tc(const StepArgs &a, cudaStream_t s);
