@@ -46,8 +46,30 @@ METRIC = "docs/sec per online TLDA pass at k=100,V=20k: BF16 TC form vs FP32 pla
 UNIT = "docs/s"
 LR = 2e-3
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Nominal FP32 CUDA-core peak (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz),
+# reported beside the measured one; the "alu" fractions use the measurement.
+FP32_ALU_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+_ALU_PEAK = None
+
+
+def alu_peak():
+    """FP32 CUDA-core peak measured on this GPU by the library's FFMA probe
+    (tlda_ffma_probe, timed by CUDA events), measured once per process."""
+    global _ALU_PEAK
+    if _ALU_PEAK is None:
+        from paper_2511_07809_gb300 import tlda
+        _ALU_PEAK = {"tflops": tlda.ffma_peak_tflops(), "source": "measured: tlda_ffma_probe (FFMA, CUDA events)",
+                     "nominal_tflops": FP32_ALU_NOMINAL_TFLOPS}
+    return _ALU_PEAK
+
+
+def flush_l2():
+    """Writes a 256 MB buffer (about twice the 129 MB L2) so a timed region
+    starts with none of its inputs in L2."""
+    import torch
+    buf = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    buf.fill_(1.0)
+    del buf
 
 
 def parse():
@@ -178,6 +200,37 @@ def recovery_l1(ctx, Phi, mu, steps):
         return {"l1_mean": float(l1.mean()), "l1_max": float(l1.max()), "after_steps": steps}
     except Exception as e:  # noqa: BLE001
         return {"error": str(e)[:80]}
+
+
+def col_rel(a, b):
+    """Largest per-column max-norm error max_n max_i |a_in - b_in| / max_i |b_in|."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float((np.abs(a - b).max(axis=0) / np.maximum(np.abs(b).max(axis=0), 1e-300)).max())
+
+
+def oracle_step(corpus, a, b, sp, W, m1, Phi):
+    """The FP64 oracle's CP step on documents [a, b) from Phi (the GPU's FP32
+    whitening and factors, widened to FP64)."""
+    from oracle import tlda_oracle as O
+    r = corpus.rows(int(a), int(b))
+    W64 = W.cpu().numpy().astype(np.float64)
+    m64 = m1.cpu().numpy().astype(np.float64)
+    P64 = Phi.cpu().numpy().astype(np.float64)
+    return O.cp_grad_implicit(r.indptr, r.indices, r.counts, sp.V, W64, m64, P64, float(sp.alpha0), 0.0)
+
+
+def step_parity(ctx, dev, a, b, Phi, g):
+    """Error against the oracle step g of one CP step that ctx takes through
+    its pass entry point (the kernel the timed region runs) on documents
+    [a, b) from a copy of Phi: the update Phi_{t+1} - Phi_t against -lr grad
+    (relative Frobenius and worst column) and the loss."""
+    P = Phi.clone()
+    loss = float(ctx.cp_pass(dev, [int(a), int(b)], P, LR, losses=True)[0])
+    upd = (P - Phi).cpu().numpy().astype(np.float64)
+    ref = -LR * g["grad"]
+    rel = float(np.linalg.norm(upd - ref) / np.linalg.norm(ref))
+    return {"update_rel_frobenius": rel, "update_worst_column": col_rel(upd, ref),
+            "loss_rel": abs(loss - g["loss"]) / abs(g["loss"]), "docs": int(b - a)}
 
 
 def batch_plan(ts, sp, n_steps):
@@ -557,7 +610,7 @@ def vi_main(args):
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                      "algorithmic_bytes_per_call": byts, "peak_source": src,
                      "fp32_tflops": flops / (ms / 1e3) / 1e12,
-                     "fp32_frac": flops / (ms / 1e3) / 1e12 / FP32_ALU_PEAK_TFLOPS, "traffic": None},
+                     "fp32_frac": flops / (ms / 1e3) / 1e12 / alu_peak()["tflops"], "traffic": None},
         "cpu_baseline": {"value": ns / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"first {ns} documents, FP64 numpy/scipy E-step, {cpu_s:.1f} s"},
         "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8.0 * nnz + 4.0 * (n + 1),
@@ -669,7 +722,7 @@ def billion_main(args):
         if prec == "bf16":
             pk, bound = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]), "tensor"
         else:
-            pk, bound = FP32_ALU_PEAK_TFLOPS, "alu"
+            pk, bound = alu_peak()["tflops"], "alu"
         fl = 2.0 * float(np.sum(np.array(bt) + np.array(nt))) * sp.K * sp.K / len(bt)
         out = {"ms_per_step": {k: v[1] / v[0] for k, v in pr.items() if v[0] > 0}, "peak_source": src,
                "mean_touched_words": float(np.mean(nt))}
@@ -802,6 +855,7 @@ def main():
         torch.cuda.synchronize()
         if profile:
             c.profile(profile)
+        flush_l2()
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -846,6 +900,16 @@ def main():
     clocks = sampler.stop()
     value, ms_max, docs_all = replica_throughput(ms, float(n_timed_docs), world)
     Phi_final = Phi.clone()
+    # error against the FP64 oracle of one step of each form, on the minibatch
+    # that follows the timed region, from the Phi the timed pass ended with
+    pa = int(timed_segs[-1][-1])
+    pb = pa + int(seq[args.warmup])
+    if pb > n_docs:
+        pa, pb = 0, int(seq[args.warmup])
+    g_par = oracle_step(corpus, pa, pb, sp, W, m1, Phi_final)
+    parity = {primary: step_parity(ctx, dev, pa, pb, Phi_final, g_par),
+              "oracle": "FP64 implicit CP step (oracle/), same whitening and factors",
+              "tolerance": {"fp32": 1e-5, "bf16": 2e-2}}
 
     # roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
@@ -854,8 +918,13 @@ def main():
     nnz_all = np.concatenate([np.diff(corpus.indptr[np.array(s)]) for s in timed_segs])
     D = K = sp.K
     roof = None
+    nt = np.concatenate([distinct_words(corpus, s) for s in timed_segs])
+    # the method's algorithmic flops of every timed step (factored count,
+    # unpadded D, K): X = F U, Y = X Phi, Q = U_t Phi, R = F (Q*Q), G1, H, G2,
+    # and the Phi-only products Phi^T Phi and Phi (G * G)
+    step_flops = float((2.0 * nnz_all * D + 4.0 * B_all * D * K + 4.0 * nt * D * K
+                        + 4.0 * nnz_all * K + 4.0 * D * K * K).sum())
     if dominant in ("qy", "g_reduce", "fused", "pass") and launches:
-        nt = np.concatenate([distinct_words(corpus, s) for s in timed_segs])
         if dominant == "pass":
             # every step of the launches: the data-term contractions as for
             # "fused" below plus the Phi-only products Phi^T Phi and
@@ -874,7 +943,7 @@ def main():
         if primary == "bf16":
             pk, unit, bound = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]), "TFLOP/s", "tensor"
         else:
-            pk, unit, bound = FP32_ALU_PEAK_TFLOPS, "TFLOP/s", "alu"
+            pk, unit, bound = alu_peak()["tflops"], "TFLOP/s", "alu"
         roof = {"bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk,
                 "algorithmic_flop_per_launch": flops}
     elif launches:
@@ -930,8 +999,17 @@ def main():
             Phi = Phi0.clone()
             ms2, _ = timed(c2, Phi)
             ms2 = reduce_over_ranks(ms2, "max", world)
+            ach2 = step_flops / (ms2 / 1e3) / 1e12
+            if other[0] == "fp32":
+                pk2, b2, src2 = alu_peak()["tflops"], "alu", alu_peak()["source"]
+            else:
+                pk2, b2, src2 = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]), "tensor", peak_src
+            parity[other[0]] = step_parity(c2, dev, pa, pb, Phi_final, g_par)
             compare = {"precision": other[0], "value": docs_all / (ms2 / 1e3),
                        "ms_per_step": ms2 / args.steps,
+                       "roofline": {"bound": b2, "achieved": ach2, "peak": pk2, "unit": "TFLOP/s",
+                                    "frac": ach2 / pk2, "kernel": "whole step (every kernel of the pass)",
+                                    "peak_source": src2},
                        "recovery": recovery_l1(c2, Phi, mu, args.warmup + args.steps)}
             c2.close()
     # the same primary form with the same-token correction off (the data term
@@ -973,12 +1051,15 @@ def main():
             "config": {"workload": WORKLOAD, "V": sp.V, "K": sp.K, "D": sp.K, "alpha0": float(sp.alpha0),
                        "batch": "U{512..8192}", "docs_per_rank": n_timed_docs, "precision": primary,
                        "same_token_correction": True, "lr": LR,
-                       "l2": "inputs larger than L2: each step reads a fresh minibatch of a "
-                             f"{(corpus.nnz * 8 + corpus.n_docs * 4) / 1e9:.2f} GB device-resident corpus; "
-                             "the whitening workspace (U, Q) stays L2-resident by design",
+                       "l2": "L2 flushed (256 MB written) before each timed pass; each step reads a fresh "
+                             "minibatch of a "
+                             f"{(corpus.nnz * 8 + corpus.n_docs * 4) / 1e9:.2f} GB device-resident corpus, "
+                             "never re-read in the timed region; the whitening workspace (U) stays "
+                             "L2-resident by design",
                        "parallelism": "replicas" if world > 1 else "single",
                        "fit_docs": n_fit, "fit_s": round(t_fit, 2), "gen_s": round(t_gen, 2)},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "parity": parity,
+            "fp32_alu_peak": alu_peak(),
             "gpu_launches": launches_timed,
             "clocks": clocks, "compare": compare, "compare_same_token_off": no_st, "recovery": recovery,
             "kernel_shares": {k: round(v[1] / max(sum(x[1] for x in shares.values()), 1e-12), 4)

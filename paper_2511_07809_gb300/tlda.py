@@ -40,7 +40,8 @@ ENTRY_POINTS = ("tlda_default_params", "tlda_create", "tlda_destroy", "tlda_last
                 "tlda_cp_step_noalloc", "tlda_autotune", "tlda_online_begin",
                 "tlda_online_pass", "tlda_eig_sweeps", "tlda_fit_batched", "tlda_doc_topics",
                 "tlda_generate_docs", "tlda_online_accumulate", "tlda_online_whiten",
-                "tlda_selftest_barrier", "tlda_online_get_sketch", "tlda_online_set_sketch")
+                "tlda_selftest_barrier", "tlda_online_get_sketch", "tlda_online_set_sketch",
+                "tlda_ffma_probe")
 
 
 class Params(ctypes.Structure):
@@ -102,6 +103,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "tlda_online_set_sketch": (i32, [vp, vp, vp, vp]),
         "tlda_unwhiten_topics": (i32, [vp, vp, vp, vp, u32]),
         "tlda_cp_step_noalloc": (i32, [P(CSR), vp, vp, i32, i32, f64, f32, vp, f32, vp, vp, vp]),
+        "tlda_ffma_probe": (i32, [i32, vp, P(f64), vp]),
         "tlda_profile": (i32, [vp, u32]),
         "tlda_profile_read": (i32, [vp, i32, P(ctypes.c_char_p), P(i64), P(f64)]),
         "tlda_save_state": (i32, [vp, ctypes.c_char_p]),
@@ -407,6 +409,28 @@ def selftest_barrier():
     nb, ng = ctypes.c_int32(), ctypes.c_int32()
     st = lib.tlda_selftest_barrier(None, ctypes.byref(nb), ctypes.byref(ng))
     return st, nb.value, ng.value
+
+
+def ffma_peak_tflops(iters: int = 4096, reps: int = 5) -> float:
+    """Measured FP32 CUDA-core throughput (TFLOP/s): the best of `reps`
+    launches of tlda_ffma_probe after one warm-up, each timed by CUDA events
+    on the current stream."""
+    lib = load()
+    stream = torch.cuda.current_stream()
+    sink = torch.empty(1 << 16, dtype=torch.float32, device="cuda")
+    flops = ctypes.c_double()
+    best = float("inf")
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = lib.tlda_ffma_probe(int(iters), sink.data_ptr(), ctypes.byref(flops), ctypes.c_void_p(stream.cuda_stream))
+        e1.record(stream)
+        if st != OK:
+            raise TLDAError(st, "tlda_ffma_probe")
+        stream.synchronize()
+        if r:
+            best = min(best, e0.elapsed_time(e1))
+    return flops.value / (best / 1e3) / 1e12
 
 
 # ---------------------------------------------------------------------------- synthetic corpora
