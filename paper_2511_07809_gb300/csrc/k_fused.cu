@@ -50,10 +50,14 @@ constexpr int kOffU1 = 65536;       //                               (buffer 1) 
 constexpr int kOffQ = 98304;        // Q chunk (pass 1) / B'' chunk (pass 2)        32 KB
 constexpr int kOffQ2 = 131072;      // Q*Q chunk                                    32 KB
 constexpr int kOffF = 163840;       // F^T chunk   [128 x 64 documents] BF16        16 KB
-constexpr int kOffY = 180224;       // y tile FP32 32 x 128                         16 KB
-constexpr int kOffZ = 196608;       // z tile FP32 32 x 128                         16 KB
+// y and z rows of one document are kYP floats apart: the 4-float pad moves
+// each document's row by four banks, so the lanes of one warp, which read
+// rows of a few different documents at the same topic, do not collide
+constexpr int kYP = 132;
+constexpr int kOffY = 180224;       // y tile FP32 32 x kYP                         16.5 KB
+constexpr int kOffZ = kOffY + 32 * kYP * 4;  // z tile FP32 32 x kYP                16.5 KB
 constexpr int kWin = 1024;          // nonzeros whose metadata sit in shared memory
-constexpr int kOffMeta = 212992;    // window metadata m, f, d (12 KB), indptr slice, L
+constexpr int kOffMeta = kOffZ + 32 * kYP * 4;  // window metadata m, f, d (12 KB), indptr slice, L
 constexpr int kOffBar = kOffMeta + 3 * kWin * 4 + 512;  // 4 mbarriers, TMEM slot, flags
 constexpr int kFusedSmem = 1024 + kOffBar + 64;
 
@@ -64,15 +68,22 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// 4 consecutive values (col multiple of 4, < 128) of row `row` of a
-// 2 x [rows x 64] BF16 tile in the 128-byte swizzle layout.
-__device__ __forceinline__ void st_bf16x4(unsigned char *tile, int sub_bytes, int row, int col, float a, float b,
-                                          float c, float d) {
-  __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
-  uint2 pk;
-  pk.x = *reinterpret_cast<uint32_t *>(&lo);
-  pk.y = *reinterpret_cast<uint32_t *>(&hi);
-  *reinterpret_cast<uint2 *>(tile + (col >> 6) * sub_bytes + sw_chunk(row, (col & 63) >> 3) + ((col & 7) << 1)) = pk;
+// 8 consecutive values (col multiple of 8, < 128) of row `row` of a
+// 2 x [rows x 64] BF16 tile in the 128-byte swizzle layout: one whole
+// 16-byte chunk, so the 32 rows a warp writes at once (8 rows per XOR
+// pattern) fill every bank once per 128 bytes.
+__device__ __forceinline__ void st_bf16x8(unsigned char *tile, int sub_bytes, int row, int col, const float *v) {
+  uint4 pk;
+  __nv_bfloat162 h;
+  h = __floats2bfloat162_rn(v[0], v[1]);
+  pk.x = *reinterpret_cast<uint32_t *>(&h);
+  h = __floats2bfloat162_rn(v[2], v[3]);
+  pk.y = *reinterpret_cast<uint32_t *>(&h);
+  h = __floats2bfloat162_rn(v[4], v[5]);
+  pk.z = *reinterpret_cast<uint32_t *>(&h);
+  h = __floats2bfloat162_rn(v[6], v[7]);
+  pk.w = *reinterpret_cast<uint32_t *>(&h);
+  *reinterpret_cast<uint4 *>(tile + (col >> 6) * sub_bytes + sw_chunk(row, (col & 63) >> 3)) = pk;
 }
 
 // 64 consecutive FP32 TMEM columns of this warp's lanes (4 loads in flight, one wait).
@@ -416,11 +427,12 @@ struct Fused {
             float q[64];
             tmem_ld64(colQ0 + buf * 128 + lane_off + half * 64, q);
 #pragma unroll
-            for (int i = 0; i < 64; i += 4) {
-              const int c0 = half * 64 + i;
-              st_bf16x4(sQ, 16384, row, c0, q[i], q[i + 1], q[i + 2], q[i + 3]);
-              st_bf16x4(sQ2, 16384, row, c0, q[i] * q[i], q[i + 1] * q[i + 1], q[i + 2] * q[i + 2],
-                        q[i + 3] * q[i + 3]);
+            for (int i = 0; i < 64; i += 8) {
+              float q2[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) q2[u] = q[i + u] * q[i + u];
+              st_bf16x8(sQ, 16384, row, half * 64 + i, q + i);
+              st_bf16x8(sQ2, 16384, row, half * 64 + i, q2);
             }
           }
           fence_proxy_async();
@@ -463,8 +475,8 @@ struct Fused {
           const int dd = half * 16 + i;
           const float y = dd < Te ? yv[i] : 0.f;
           const float r = (dd < Te && a.same_token) ? rv[i] : 0.f;
-          sY[dd * 128 + topic] = y;
-          sZ[dd * 128 + topic] = y * y - r;
+          sY[dd * kYP + topic] = y;
+          sZ[dd * kYP + topic] = y * y - r;
           lacc += y * (y * y - 3.f * r);
         }
       }
@@ -513,26 +525,29 @@ struct Fused {
             const int row = quad * 32 + lane, t = c * kChunk + row;
             const int dd = s_d[t];
             const float f = s_f[t];
-            const float4 *yr = reinterpret_cast<const float4 *>(sY + dd * 128 + half * 64);
-            const float4 *zr = reinterpret_cast<const float4 *>(sZ + dd * 128 + half * 64);
+            const float4 *yr = reinterpret_cast<const float4 *>(sY + dd * kYP + half * 64);
+            const float4 *zr = reinterpret_cast<const float4 *>(sZ + dd * kYP + half * 64);
             float q[64];
             tmem_ld64(colQ0 + buf * 128 + lane_off + half * 64, q);
 #pragma unroll
-            for (int i4 = 0; i4 < 16; ++i4) {
-              const float4 y4 = yr[i4], z4 = zr[i4];
-              const float ys[4] = {y4.x, y4.y, y4.z, y4.w}, zs[4] = {z4.x, z4.y, z4.z, z4.w};
-              float bb[4];
+            for (int i8 = 0; i8 < 8; ++i8) {
+              float bb[8];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const float qi = q[i4 * 4 + u];
-                if (a.same_token) {
-                  bb[u] = f * (zs[u] + 2.f * qi * qi - 2.f * qi * ys[u]);
-                  lacc += 2.f * f * qi * qi * qi;
-                } else {
-                  bb[u] = f * zs[u];
+              for (int h4 = 0; h4 < 2; ++h4) {
+                const float4 y4 = yr[i8 * 2 + h4], z4 = zr[i8 * 2 + h4];
+                const float ys[4] = {y4.x, y4.y, y4.z, y4.w}, zs[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const float qi = q[i8 * 8 + h4 * 4 + u];
+                  if (a.same_token) {
+                    bb[h4 * 4 + u] = f * (zs[u] + 2.f * qi * qi - 2.f * qi * ys[u]);
+                    lacc += 2.f * f * qi * qi * qi;
+                  } else {
+                    bb[h4 * 4 + u] = f * zs[u];
+                  }
                 }
               }
-              st_bf16x4(sQ, 16384, row, half * 64 + i4 * 4, bb[0], bb[1], bb[2], bb[3]);
+              st_bf16x8(sQ, 16384, row, half * 64 + i8 * 8, bb);
             }
           }
           fence_proxy_async();
@@ -680,10 +695,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const BatchDesc b = p.descs[s];
     const int nd = b.n_docs;
     const int cap = p.tile_cap > 0 ? p.tile_cap : (b.tile_cap > 0 ? b.tile_cap : 32);
-    const int td = nd > 0 ? max(1, min(cap, (nd + G - 1) / G)) : 1;
+    // the last e_blocks blocks take no tiles: they start on the Phi-only
+    // columns as soon as the step begins
+    const int Gd = G - min(max(p.e_blocks, 0), G / 2);
+    const int td = nd > 0 ? max(1, min(cap, (nd + Gd - 1) / Gd)) : 1;
     const int ntiles = nd > 0 ? (nd + td - 1) / td : 0;
-    const int nwork = min(G, ntiles);
-    const bool has = blk < ntiles;
+    const int nwork = min(Gd, ntiles);
+    const bool has = blk < nwork;
 
     // ---------------- phase A: the data term of this block's tiles.  The
     // first tile's CSR slice and U rows are requested before the wait for the
@@ -704,7 +722,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     if (has) {
       float lacc = 0.f;
       bool g_init = false;
-      f.tiles(a, b, blk, G, td, lacc, g_init, &ctl->S3[slot], &st->err, true, pre);
+      f.tiles(a, b, blk, Gd, td, lacc, g_init, &ctl->S3[slot], &st->err, true, pre);
       if (a.want_loss) {
         const float t = block_sum(lacc, s_red);
         if (tid == 0 && t != 0.f) atomicAdd(&ctl->loss_data[slot], (double)t);
@@ -853,14 +871,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       E_own = __ldcg(a.E + (e / K) * Kp + e % K);
       phi_own = __ldcg(a.Phi + e);
     }
-    if (e1 > e0 && nwork > 0) {  // this slice of every partial: one bulk copy
-      if (tid == 0) {
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        const uint32_t bytes = (uint32_t)(nwork * per * 4);
-        mbar_arrive_expect_tx(&f.bars[0], bytes);
-        bulk_load(f.sm + kOffU0, a.Gpart + (long long)blk * G * per, bytes, &f.bars[0]);
-      }
-      f.phi_wait();  // bounded wait on barrier 0
+    if (e1 > e0 && nwork > 0) {  // this slice of every partial, in 16-byte cp.async pieces
+      const int n16 = nwork * per / 4;
+      const float4 *src = reinterpret_cast<const float4 *>(a.Gpart + (long long)blk * G * per);
+      float4 *dst = reinterpret_cast<float4 *>(f.sm + kOffU0);
+      for (int e = tid; e < n16; e += kFusedThreads) cp_async16(dst + e, src + e);
+      cp_async_commit();
+      cp_async_wait_all();
     }
     if (__syncthreads_or(f.failed())) {
       if (tid == 0) atomicExch(&ctl->abort, 1);

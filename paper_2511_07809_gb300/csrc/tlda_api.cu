@@ -214,6 +214,10 @@ tlda_status take_sticky(tlda_ctx *ctx) {
 // ------------------------------------------------------------ persistent pass
 constexpr long long kStageWords = 1ll << 23;  // int32 words per host-input staging buffer (32 MB)
 constexpr int kTuneBatches = 128;
+// Blocks of the persistent pass that compute only the Phi-only columns
+// (P, G3 and their loss parts), so those columns do not land on whichever
+// data blocks finish first.
+constexpr int kPassEBlocks = 8;
 
 tlda_status ensure_descs(tlda_ctx *ctx, int n) {
   if (ctx->descs_cap < n) {
@@ -235,6 +239,7 @@ tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int ca
   pa.losses = dl;
   pa.ctl = ctx->ctl;
   pa.record = record;
+  pa.e_blocks = kPassEBlocks;
   CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(PassCtl), ps));
   Prof pr(ctx, kPass, ps);
   CK(launch_pass(a, pa, ps, ctx->pass_grid));
@@ -394,8 +399,19 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
   for (BatchDesc &d : hd) d.tile_cap = ctx->cap_band[cap_band(d.n_docs)];
   s = ensure_descs(ctx, nb);
   if (s) return s;
-  CK(cudaMemcpyAsync(ctx->descs, hd.data(), sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, ps));
-  CK(cudaStreamSynchronize(ps));  // hd is pageable: keep it alive until copied
+  // staged through pinned memory, so the upload needs no host wait before
+  // the launch; the pinned copy is rewritten only once the previous pass's
+  // upload is done
+  CK(cudaEventSynchronize(ctx->ev_pass1));  // the previous pass's copy is done (a no-op on success paths)
+  if (ctx->descs_pin_cap < nb) {
+    if (ctx->descs_pin) cudaFreeHost(ctx->descs_pin);
+    ctx->descs_pin = nullptr;
+    ctx->descs_pin_cap = 0;
+    CK(cudaMallocHost(&ctx->descs_pin, sizeof(BatchDesc) * (size_t)nb));
+    ctx->descs_pin_cap = nb;
+  }
+  std::memcpy(ctx->descs_pin, hd.data(), sizeof(BatchDesc) * (size_t)nb);
+  CK(cudaMemcpyAsync(ctx->descs, ctx->descs_pin, sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, ps));
   StepArgs a = make_args(ctx);
   a.lr = lr;
   a.Phi = Phi;
@@ -602,6 +618,7 @@ tlda_status tlda_destroy(tlda_ctx *ctx) {
   for (cudaEvent_t ev : ctx->ev_seg)
     if (ev) cudaEventDestroy(ev);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
+  if (ctx->descs_pin) cudaFreeHost(ctx->descs_pin);
   for (auto &r : ctx->prof_pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

@@ -77,6 +77,7 @@ struct PassArgs {
   double *losses;                // per-step loss (device, indexed by step) or null
   PassCtl *ctl;
   int record;                    // 1: advance the context's step state (0 for tuning runs)
+  int e_blocks;                  // blocks that take only the Phi-only columns (no data tiles)
 };
 
 // Element (topic n, feature k) of the B operand Phi^T in the shared-memory
@@ -167,6 +168,8 @@ struct tlda_ctx {
   tlda::DevState *st_host = nullptr;   // pinned mirror for reads
   tlda::BatchDesc *descs = nullptr;    // pass descriptors (device)
   int descs_cap = 0;
+  tlda::BatchDesc *descs_pin = nullptr;  // pinned staging of the persistent pass's descriptors
+  int descs_pin_cap = 0;
   // fit state
   double *P64 = nullptr;               // V x V pair counts (allocated on first ACCUMULATE)
   unsigned long long *Ccnt = nullptr;  // V word totals
