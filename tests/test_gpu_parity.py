@@ -183,7 +183,7 @@ def test_pass_equals_sequential_oracle_steps(lib, host_input):
 # ----------------------------------------------------------------------------- BF16 tensor-core form
 @pytest.mark.parametrize("name,n", [("small_v500_k10", 1000), ("small_v500_k10", 37),
                                     ("tweet_v5k_k50", 2048), ("stream_v20k_k100", 4099),
-                                    ("stream_v20k_k100", 8192)])
+                                    ("stream_v20k_k100", 8192), ("stream_v20k_k100", 1)])
 def test_data_term_bf16(lib, name, n):
     sp = ts.WORKLOADS[name]
     t, W, m1 = _ctx(lib, name, precision="bf16")
@@ -192,7 +192,11 @@ def test_data_term_bf16(lib, name, n):
     G, S3 = t.cp_data_term(lib.DeviceCSR.from_corpus(c), torch.tensor(Phi, dtype=torch.float32, device="cuda"))
     g = _oracle_grad(c, sp, W, m1, Phi)
     assert S3 == g["S3"]
-    assert C.rel(G.cpu().numpy(), g["G_data"]) < TOL16
+    if n == 1:  # one document: its distinct-token triples cancel; the bar is the rounding-error scale
+        M = C.data_term_magnitude(c, sp.V, W, m1, Phi, float(sp.alpha0))
+        C.assert_bf16_parity_scaled(G.cpu().numpy(), g["G_data"], M, TOL16, f"G_data {name} B={n}")
+    else:
+        C.assert_bf16_parity(G.cpu().numpy(), g["G_data"], TOL16, f"G_data {name} B={n}")
 
 
 @pytest.mark.parametrize("same_token", [True, False])
@@ -207,8 +211,8 @@ def test_cp_step_bf16(lib, same_token):
     lr = 0.002
     loss = t.cp_step(lib.DeviceCSR.from_corpus(c), Phi, lr, grad=grad, want_loss=True)
     g = _oracle_grad(c, sp, W, m1, Phi0, 0.0, same_token)
-    assert C.rel(grad.cpu().numpy(), g["grad"]) < TOL16
-    assert C.rel(Phi.cpu().numpy(), Phi0 - lr * g["grad"]) < TOL16
+    C.assert_bf16_parity(grad.cpu().numpy(), g["grad"], TOL16, "grad")
+    C.assert_bf16_parity(Phi.cpu().numpy() - Phi0, -lr * g["grad"], TOL16, "Phi update")
     assert abs(loss - g["loss"]) <= TOL16 * abs(g["loss"])
 
 
@@ -229,11 +233,11 @@ def test_bf16_fused_and_unfused_forms(lib, monkeypatch, fused, same_token):
     grad = torch.empty_like(Phi)
     loss = t.cp_step(lib.DeviceCSR.from_corpus(b), Phi, 0.002, grad=grad, want_loss=True)
     g = _oracle_grad(b, sp, W, m1, Phi0, 0.0, same_token)
-    assert C.rel(grad.cpu().numpy(), g["grad"]) < TOL16
+    C.assert_bf16_parity(grad.cpu().numpy(), g["grad"], TOL16, f"grad fused={fused}")
     assert abs(loss - g["loss"]) <= TOL16 * abs(g["loss"])
     G, S3 = t.cp_data_term(lib.DeviceCSR.from_corpus(b), torch.tensor(Phi0, dtype=torch.float32, device="cuda"))
     assert S3 == g["S3"]
-    assert C.rel(G.cpu().numpy(), g["G_data"]) < TOL16
+    C.assert_bf16_parity(G.cpu().numpy(), g["G_data"], TOL16, f"G_data fused={fused}")
 
 
 def test_pass_bf16_ragged(lib):
@@ -246,12 +250,18 @@ def test_pass_bf16_ragged(lib):
     Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
     lr = 0.002
     losses = t.cp_pass(lib.DeviceCSR.from_corpus(c), offs, Phi, lr, losses=True)
-    P = Phi0.copy()
+    P, steps, scales = Phi0.copy(), [], []
     for b in range(len(offs) - 1):
         r = c.rows(offs[b], offs[b + 1])
-        P, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, lr, float(sp.alpha0), 0.0)
+        Pn, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, lr, float(sp.alpha0), 0.0)
+        # the one-document step: its rounding-error scale (3 lr times the data term's)
+        scales.append(3.0 * lr * C.data_term_magnitude(r, sp.V, W, m1, P, float(sp.alpha0)).max(axis=0)
+                      if r.n_docs == 1 else None)
+        steps.append(Pn - P)
+        P = Pn
         assert abs(losses[b] - g["loss"]) <= TOL16 * abs(g["loss"]), b
-    assert C.rel(Phi.cpu().numpy(), P) < TOL16
+    C.assert_bf16_pass_parity(Phi.cpu().numpy() - Phi0, P - Phi0, steps, TOL16, "Phi change over the pass",
+                              step_scales=scales)
 
 
 # ----------------------------------------------------------------------------- moments
@@ -277,6 +287,43 @@ def test_fit_moments_small(lib):
     assert C.rel(Wg, Wo) < 1e-4
     assert C.rel(m1g.cpu().numpy(), Wo.T @ M1) < 1e-4
     assert 1 <= t.eig_sweeps() < 40  # the Jacobi eigensolve converged before its sweep cap
+
+
+def test_fit_moments_tweet_v5k_k50(lib):
+    """The fit at the 5k-word workload (V = 5000, K = 50, Zipf-shaped topics),
+    where the randomised subspace iteration does real work: 200,000 documents
+    in four chunks, against the oracle's dense eigendecomposition of the same
+    M2.  Exact integer statistics; eigenvalues to 1e-6; W^T M2 W = I to 1e-5;
+    the spectral projector of the top-K eigenspace, U U^T, to 1e-4 of its norm
+    (sqrt(K)) -- the subspace is what the CP step depends on (reading J)."""
+    name = "tweet_v5k_k50"
+    sp = ts.WORKLOADS[name]
+    n = 200_000
+    c = C.corpus(name, n)
+    t = lib.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), seed=5)
+    for d0 in range(0, n, 50_000):
+        t.fit_moments(lib.DeviceCSR.from_corpus(c.rows(d0, d0 + 50_000)), lib.ACCUMULATE)
+    t.fit_moments(None, lib.FINALIZE)
+    Cg, T, S2, S3 = t.get_counts()
+    st = O.ingest(c.indptr, c.indices, c.counts, sp.V)
+    assert np.array_equal(Cg, st["C"]) and (T, S2, S3) == (st["T"], st["S2"], st["S3"])
+    Wg, m1g, lam_g = t.get_whitening()
+    Wg = Wg.cpu().numpy().astype(np.float64)
+    M1 = O.first_moment(st["C"], st["T"])
+    M2 = O.second_moment(O.pair_counts(c.indptr, c.indices, c.counts, sp.V), st["S2"], M1, float(sp.alpha0))
+    Wo, Uo, lam_o = O.whitening(M2, sp.K)
+    lam_err = float(np.max(np.abs(lam_g - lam_o) / lam_o))
+    Ug = Wg * np.sqrt(lam_g)[None, :]
+    proj = np.linalg.norm(Ug @ Ug.T - Uo @ Uo.T) / np.sqrt(sp.K)
+    ident = C.rel(Wg.T @ M2 @ Wg, np.eye(sp.K))
+    print(f"fit V=5000 K=50: eigenvalue rel err {lam_err:.2e}, W^T M2 W - I {ident:.2e}, "
+          f"projector gap {proj:.2e}, lambda_K / lambda_1 {lam_o[-1] / lam_o[0]:.2e}")
+    assert lam_err < 1e-6
+    assert ident < 1e-5
+    assert proj < 1e-4
+    assert C.rel(m1g.cpu().numpy(), Wg.T @ M1) < 1e-5
+    assert 1 <= t.eig_sweeps() < 40
+    t.close()
 
 
 def test_unwhiten_population_factors(lib):
@@ -334,10 +381,10 @@ def test_data_term_bf16_wide(lib, K):
     G, S3 = t.cp_data_term(dev, torch.tensor(Phi0, dtype=torch.float32, device="cuda"))
     g = _oracle_grad(c, sp, W, m1, Phi0)
     assert S3 == g["S3"]
-    assert C.rel(G.cpu().numpy(), g["G_data"]) < TOL16
+    C.assert_bf16_parity(G.cpu().numpy(), g["G_data"], TOL16, f"G_data K={K}")
     Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
     grad = torch.empty_like(Phi)
     loss = t.cp_step(dev, Phi, 0.002, grad=grad, want_loss=True)
-    assert C.rel(grad.cpu().numpy(), g["grad"]) < TOL16
+    C.assert_bf16_parity(grad.cpu().numpy(), g["grad"], TOL16, f"grad K={K}")
     assert abs(loss - g["loss"]) <= TOL16 * abs(g["loss"])
     t.close()

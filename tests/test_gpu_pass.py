@@ -31,13 +31,22 @@ def _phi0(sp):
     return ts.initial_factors(sp.seed, sp.K, sp.K).astype(np.float64)
 
 
-def _oracle_pass(c, offs, sp, W, m1, Phi0, lr):
-    P, losses = Phi0.copy(), []
+def _oracle_pass(c, offs, sp, W, m1, Phi0, lr, same_token=True, scales=None):
+    """The oracle's sequential steps: final Phi, losses and per-step updates.
+    With a list `scales`, appends per step the rounding-error scale of a
+    one-document step (3 lr times its data term's) or None."""
+    P, losses, steps = Phi0.copy(), [], []
     for b in range(len(offs) - 1):
         r = c.rows(offs[b], offs[b + 1])
-        P, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, lr, float(sp.alpha0), 0.0)
+        Pn, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, lr, float(sp.alpha0), 0.0,
+                          same_token=same_token)
+        if scales is not None:
+            scales.append(3.0 * lr * C.data_term_magnitude(r, sp.V, W, m1, P, float(sp.alpha0)).max(axis=0)
+                          if r.n_docs == 1 else None)
+        steps.append(Pn - P)
+        P = Pn
         losses.append(g["loss"])
-    return P, np.array(losses)
+    return P, np.array(losses), steps
 
 
 @pytest.mark.parametrize("cap", [1, 8, 32])
@@ -52,9 +61,11 @@ def test_pass_tile_sizes_match_oracle(lib, cap):
     Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
     lr = 0.002
     losses = t.cp_pass(lib.DeviceCSR.from_corpus(c), offs, Phi, lr, losses=True)
-    P, lo = _oracle_pass(c, offs, sp, W, m1, Phi0, lr)
+    scales = []
+    P, lo, steps = _oracle_pass(c, offs, sp, W, m1, Phi0, lr, scales=scales)
     assert np.all(np.abs(losses - lo) <= TOL16 * np.abs(lo))
-    assert C.rel(Phi.cpu().numpy(), P) < TOL16
+    C.assert_bf16_pass_parity(Phi.cpu().numpy() - Phi0, P - Phi0, steps, TOL16, f"Phi change, cap {cap}",
+                              step_scales=scales)
     t.close()
 
 
@@ -71,14 +82,9 @@ def test_pass_without_same_token_correction(lib):
     Phi0 = _phi0(sp)
     Phi = torch.tensor(Phi0, dtype=torch.float32, device="cuda")
     losses = t.cp_pass(lib.DeviceCSR.from_corpus(c), offs, Phi, 0.002, losses=True)
-    P, lo = Phi0.copy(), []
-    for b in range(len(offs) - 1):
-        r = c.rows(offs[b], offs[b + 1])
-        P, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, 0.002, float(sp.alpha0), 0.0,
-                         same_token=False)
-        lo.append(g["loss"])
-    assert np.all(np.abs(losses - np.array(lo)) <= TOL16 * np.abs(np.array(lo)))
-    assert C.rel(Phi.cpu().numpy(), P) < TOL16
+    P, lo, steps = _oracle_pass(c, offs, sp, W, m1, Phi0, 0.002, same_token=False)
+    assert np.all(np.abs(losses - lo) <= TOL16 * np.abs(lo))
+    C.assert_bf16_pass_parity(Phi.cpu().numpy() - Phi0, P - Phi0, steps, TOL16, "Phi change, correction off")
     t.close()
 
 
@@ -121,9 +127,9 @@ def test_pass_and_graph_path_agree(lib, monkeypatch):
         t.cp_pass(lib.DeviceCSR.from_corpus(c), offs, Phi, 0.002)
         out.append(Phi.cpu().numpy())
         t.close()
-    P, _ = _oracle_pass(c, offs, sp, W, m1, Phi0, 0.002)
-    assert C.rel(out[0], P) < TOL16 and C.rel(out[1], P) < TOL16
-    assert C.rel(out[0], out[1]) < TOL16
+    P, _, steps = _oracle_pass(c, offs, sp, W, m1, Phi0, 0.002)
+    for o in out:
+        C.assert_bf16_pass_parity(o - Phi0, P - Phi0, steps, TOL16, "Phi change")
 
 
 def test_autotune_leaves_phi_and_state(lib, tmp_path):
@@ -164,8 +170,8 @@ def test_corrupt_batch_stops_updates_from_that_step(lib):
     with pytest.raises(lib.TLDAError) as e:
         t.cp_pass(dev, offs, Phi, 0.002)
     assert e.value.status == lib.ERR_INVALID
-    P, _ = _oracle_pass(c, offs[:3], sp, W, m1, Phi0, 0.002)
-    assert C.rel(Phi.cpu().numpy(), P) < TOL16
+    P, _, steps = _oracle_pass(c, offs[:3], sp, W, m1, Phi0, 0.002)
+    C.assert_bf16_pass_parity(Phi.cpu().numpy() - Phi0, P - Phi0, steps, TOL16, "Phi change up to the corrupt batch")
     # the error was taken: the next pass on valid data runs
     t.cp_pass(lib.DeviceCSR.from_corpus(c), offs[:2], Phi, 0.002)
     t.close()
@@ -196,7 +202,7 @@ def test_bench_sized_pass_sampled_steps(lib):
         r = c.rows(int(offs[s_]), int(offs[s_ + 1]))
         ref, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, before, lr, float(sp.alpha0), 0.0)
         step_gpu = Phi.cpu().numpy().astype(np.float64) - before
-        assert C.rel(step_gpu, ref - before) < TOL16, s_
+        C.assert_bf16_parity(step_gpu, ref - before, TOL16, f"update of step {s_}")
         assert abs(loss - g["loss"]) <= TOL16 * abs(g["loss"]), s_
         prev = s_ + 1
     t.close()

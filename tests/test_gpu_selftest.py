@@ -38,9 +38,11 @@ def test_bounded_grid_barrier_gives_up_and_the_gpu_stays_usable(lib):
     P0 = ts.initial_factors(sp.seed + 1, sp.K, sp.K)
     Phi = torch.tensor(P0, dtype=torch.float32, device="cuda")
     t.cp_pass(lib.DeviceCSR.from_corpus(c), offs, Phi, 0.002)
-    P = P0.astype(np.float64)
+    P, steps = P0.astype(np.float64), []
     for b in range(2):
         r = c.rows(offs[b], offs[b + 1])
-        P, _ = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, 0.002, float(sp.alpha0), 0.0)
-    assert C.rel(Phi.cpu().numpy(), P) < 2e-2
+        Pn, _ = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, P, 0.002, float(sp.alpha0), 0.0)
+        steps.append(Pn - P)
+        P = Pn
+    C.assert_bf16_pass_parity(Phi.cpu().numpy() - P0, P - P0, steps, 2e-2, "Phi change after the self-test")
     t.close()
