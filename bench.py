@@ -208,29 +208,25 @@ def col_rel(a, b):
     return float((np.abs(a - b).max(axis=0) / np.maximum(np.abs(b).max(axis=0), 1e-300)).max())
 
 
-def oracle_step(corpus, a, b, sp, W, m1, Phi):
-    """The FP64 oracle's CP step on documents [a, b) from Phi (the GPU's FP32
-    whitening and factors, widened to FP64)."""
-    from oracle import tlda_oracle as O
-    r = corpus.rows(int(a), int(b))
-    W64 = W.cpu().numpy().astype(np.float64)
-    m64 = m1.cpu().numpy().astype(np.float64)
-    P64 = Phi.cpu().numpy().astype(np.float64)
-    return O.cp_grad_implicit(r.indptr, r.indices, r.counts, sp.V, W64, m64, P64, float(sp.alpha0), 0.0)
-
-
-def step_parity(ctx, dev, a, b, Phi, g):
-    """Error against the oracle step g of one CP step that ctx takes through
-    its pass entry point (the kernel the timed region runs) on documents
-    [a, b) from a copy of Phi: the update Phi_{t+1} - Phi_t against -lr grad
-    (relative Frobenius and worst column) and the loss."""
-    P = Phi.clone()
+def step_parity(make_ctx, dev, first):
+    """Error against the oracle's first step (`first`, from the CPU baseline)
+    of the same step taken by a fresh context of one form through its pass
+    entry point (the kernel the timed region runs), on the same documents
+    from the same Phi and whitening: the update Phi_1 - Phi_0 against
+    -lr grad (relative Frobenius and worst column) and the loss."""
+    import torch
+    ctx = make_ctx()
+    ctx.set_whitening(torch.tensor(first["W"], dtype=torch.float32), torch.tensor(first["m1"], dtype=torch.float32))
+    P0 = torch.tensor(first["Phi0"], dtype=torch.float32, device="cuda")
+    P = P0.clone()
+    a, b = first["docs"]
     loss = float(ctx.cp_pass(dev, [int(a), int(b)], P, LR, losses=True)[0])
-    upd = (P - Phi).cpu().numpy().astype(np.float64)
-    ref = -LR * g["grad"]
+    ctx.close()
+    upd = (P - P0).cpu().numpy().astype(np.float64)
+    ref = -LR * first["grad"]
     rel = float(np.linalg.norm(upd - ref) / np.linalg.norm(ref))
     return {"update_rel_frobenius": rel, "update_worst_column": col_rel(upd, ref),
-            "loss_rel": abs(loss - g["loss"]) / abs(g["loss"]), "docs": int(b - a)}
+            "loss_rel": abs(loss - first["loss"]) / abs(first["loss"]), "docs": int(b - a)}
 
 
 def batch_plan(ts, sp, n_steps):
@@ -273,11 +269,17 @@ def src_sha(path):
 # ----------------------------------------------------------------------------- CPU baseline
 def cpu_baseline(ts, sp, cdf, mu, seconds, shard0=0):
     """The FP64 oracle's implicit CP step (as it stands) over consecutive
-    minibatches of the same workload, for about `seconds` of CPU time."""
+    minibatches of the same workload, for about `seconds` of CPU time, with
+    the population whitening (FP32-rounded) and Phi0.  Also returns the
+    oracle's first step (inputs and outputs), which the bench compares with
+    each form's first step on the same inputs."""
     from oracle import tlda_oracle as O
     h = np.full(sp.K, 1.0 / sp.K)
     W, m1 = O.population_whitening(mu, h)
+    W = W.astype(np.float32).astype(np.float64)
+    m1 = m1.astype(np.float32).astype(np.float64)
     Phi = ts.initial_factors(sp.seed + 1, sp.K, sp.K)
+    first = None
     sizes = ts.batch_sizes(sp)
     n_need = int(sizes[:64].sum())
     c = ts.corpus(sp.with_docs(shard0 + n_need), doc0=shard0, n_docs=n_need, cdf=cdf)
@@ -286,16 +288,19 @@ def cpu_baseline(ts, sp, cdf, mu, seconds, shard0=0):
     while steps < 64:
         b = int(sizes[steps])
         r = c.rows(off, off + b)
-        Phi, _ = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, Phi, LR, float(sp.alpha0), 0.0)
+        Phi_next, g = O.cp_step(r.indptr, r.indices, r.counts, sp.V, W, m1, Phi, LR, float(sp.alpha0), 0.0)
+        if first is None:
+            first = {"docs": (off, off + b), "W": W, "m1": m1, "Phi0": Phi, "grad": g["grad"], "loss": g["loss"]}
+        Phi = Phi_next
         docs += b
         off += b
         steps += 1
         if time.perf_counter() - t0 > seconds and steps >= 2:
             break
     dt = time.perf_counter() - t0
-    return {"value": docs / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{steps} minibatches ({docs} docs) of {WORKLOAD}, FP64 numpy/scipy oracle "
-                      f"implicit CP step, {dt:.1f} s"}
+    return ({"value": docs / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+             "sample": f"{steps} minibatches ({docs} docs) of {WORKLOAD}, FP64 numpy/scipy oracle "
+                       f"implicit CP step, {dt:.1f} s"}, first)
 
 
 def reference_arm(args):
@@ -900,16 +905,6 @@ def main():
     clocks = sampler.stop()
     value, ms_max, docs_all = replica_throughput(ms, float(n_timed_docs), world)
     Phi_final = Phi.clone()
-    # error against the FP64 oracle of one step of each form, on the minibatch
-    # that follows the timed region, from the Phi the timed pass ended with
-    pa = int(timed_segs[-1][-1])
-    pb = pa + int(seq[args.warmup])
-    if pb > n_docs:
-        pa, pb = 0, int(seq[args.warmup])
-    g_par = oracle_step(corpus, pa, pb, sp, W, m1, Phi_final)
-    parity = {primary: step_parity(ctx, dev, pa, pb, Phi_final, g_par),
-              "oracle": "FP64 implicit CP step (oracle/), same whitening and factors",
-              "tolerance": {"fp32": 1e-5, "bf16": 2e-2}}
 
     # roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
@@ -1004,7 +999,6 @@ def main():
                 pk2, b2, src2 = alu_peak()["tflops"], "alu", alu_peak()["source"]
             else:
                 pk2, b2, src2 = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]), "tensor", peak_src
-            parity[other[0]] = step_parity(c2, dev, pa, pb, Phi_final, g_par)
             compare = {"precision": other[0], "value": docs_all / (ms2 / 1e3),
                        "ms_per_step": ms2 / args.steps,
                        "roofline": {"bound": b2, "achieved": ach2, "peak": pk2, "unit": "TFLOP/s",
@@ -1029,9 +1023,19 @@ def main():
     # recovery of the pass (per-topic l1 after Hungarian matching), as a sanity figure
     recovery = recovery_l1(ctx, Phi_final, mu, args.warmup + args.steps)
 
-    cpu = None
+    cpu, parity = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(ts, sp, cdf, mu, args.cpu_seconds)
+        cpu, first = cpu_baseline(ts, sp, cdf, mu, args.cpu_seconds)
+        # each form's first step against the oracle's (same documents,
+        # whitening and Phi0): the error of each result against the FP64 oracle
+        parity = {"oracle": "FP64 implicit CP step (oracle/), population whitening (FP32 values), Phi0, "
+                            "first minibatch", "tolerance": {"fp32": 1e-5, "bf16": 2e-2}}
+        for p in precs:
+            try:
+                parity[p] = step_parity(lambda: make_ctx(p), dev, first)
+            except tlda.TLDAError as e:
+                if e.status != tlda.ERR_UNIMPLEMENTED:
+                    raise
 
     if rank == 0:
         # kernels per step: fused BF16 form (D, K padded to 128): Phi-only x2,

@@ -8,7 +8,11 @@ library; the only common module is the seeded input generator ``tlda_synth``.
 Plain numpy/scipy in float64, written step by step from the paper
 "Analyzing Political Text at Scale with Online Tensor LDA" (Kangaslahti et al.).
 Library primitives (dense matmul, sparse CSR products, symmetric eigh, the
-Hungarian assignment) serve as single steps; nothing is blocked or fused.
+Hungarian assignment) serve as single steps; nothing is blocked or fused,
+except in whitened_third_moment_chunked, which adds the same per-document and
+per-word sums as whitened_third_moment in chunks (so that the k^3 tensor of a
+corpus of millions of documents fits in memory and time) and takes the pair
+term as Z^T Z - W^T diag(C) W instead of forming the V x V pair counts.
 
 Notation: F is the B x V count matrix of a batch (CSR), f_d its rows,
 L_d = sum_m f_dm, W (V x k) the whitening, m1 = W^T M1, u_m = w_m - m1
@@ -204,6 +208,45 @@ def whitened_third_moment(indptr, indices, counts, V, W, M1, alpha0):
 
 
 # ----------------------------------------------------------------------------- O6 batch tensor
+
+
+def whitened_third_moment_chunked(indptr, indices, counts, V, W, M1, alpha0, chunk=2048):
+    """The tensor of whitened_third_moment (same definition, readings A and C),
+    for corpora too large for its einsums: the sums over documents and over
+    words are added chunk by chunk, each chunk's sum of outer products taken
+    as one matrix product (Z_c^T times the rows z_d (x) z_d of the chunk), and
+    W^T P W = sum_d (z_d z_d^T) - W^T diag(C) W, the pair counts
+    P = sum_d (f_d f_d^T - diag f_d) mapped through W without forming P."""
+    st = ingest(indptr, indices, counts, V)
+    F = csr_matrix(indptr, indices, counts, V)
+    k = W.shape[1]
+    C = st["C"].astype(np.float64)
+    zzz = np.zeros((k, k * k))
+    ZtZ = np.zeros((k, k))
+    Hm = np.zeros((V, k))
+    n = F.shape[0]
+    for d0 in range(0, n, chunk):
+        Fc = F[d0:d0 + chunk]
+        Zc = np.asarray(Fc @ W)                                  # z_d rows
+        zzz += Zc.T @ (Zc[:, :, None] * Zc[:, None, :]).reshape(-1, k * k)
+        ZtZ += Zc.T @ Zc
+        Hm += np.asarray(Fc.T @ Zc)                              # h_m = sum_d f_dm z_d
+    zzz = zzz.reshape(k, k, k)
+    wwh = np.zeros((k * k, k))
+    www = np.zeros((k * k, k))
+    for m0 in range(0, V, chunk):
+        Wc = W[m0:m0 + chunk]
+        ww = (Wc[:, :, None] * Wc[:, None, :]).reshape(-1, k * k)  # rows w_m (x) w_m
+        wwh += ww.T @ Hm[m0:m0 + chunk]
+        www += ww.T @ (C[m0:m0 + chunk, None] * Wc)
+    wwh = wwh.reshape(k, k, k)                                   # sum_m w_m (x) w_m (x) h_m
+    awz = wwh + wwh.transpose(0, 2, 1) + wwh.transpose(2, 0, 1)  # the three placements of h_m
+    E3w = (zzz - awz + 2.0 * www.reshape(k, k, k)) / float(st["S3"])
+    E2w = (ZtZ - W.T @ (C[:, None] * W)) / float(st["S2"])
+    m1 = W.T @ M1
+    c3 = (alpha0 + 1.0) * (alpha0 + 2.0) / 2.0
+    return (c3 * E3w - alpha0 * (alpha0 + 1.0) / 2.0 * perm3(E2w, m1)
+            + alpha0 ** 2 * sym3(m1, m1, m1))
 
 
 def centred_triples(indptr, indices, counts, V, W, m1):

@@ -57,13 +57,19 @@ def test_batched_fit_matches_oracle(lib):
 
 def test_batched_fit_reuses_whitening(lib):
     """With TLDA_REUSE_WHITENING only the epochs run: equal to the oracle's CP
-    steps on the context's own whitening."""
+    steps on the whitening installed in the context (the oracle's own, from
+    the corpus's M2)."""
     sp, mu, c, offs = _e1(1000, 1)
     dev = lib.DeviceCSR.from_corpus(c)
+    st = O.ingest(c.indptr, c.indices, c.counts, sp.V)
+    M1 = O.first_moment(st["C"], st["T"])
+    M2 = O.second_moment(O.pair_counts(c.indptr, c.indices, c.counts, sp.V), st["S2"], M1, float(sp.alpha0))
+    Wo, _, _ = O.whitening(M2, sp.K)
+    W = Wo.astype(np.float32).astype(np.float64)
+    m1 = (W.T @ M1).astype(np.float32).astype(np.float64)
     t = lib.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="fp32")
-    t.fit_batched(dev, offs, torch.zeros((1, sp.K, sp.K), dtype=torch.float32, device="cuda"), LR, epochs=1)
-    Wg, m1g, _ = t.get_whitening()
-    W, m1 = Wg.cpu().numpy().astype(np.float64), m1g.cpu().numpy().astype(np.float64)
+    t.set_whitening(torch.tensor(W, dtype=torch.float32), torch.tensor(m1, dtype=torch.float32))
+    Wg, _, _ = t.get_whitening()
     starts = _starts(sp, 2)
     Ps = torch.tensor(starts, dtype=torch.float32, device="cuda")
     means = t.fit_batched(dev, offs, Ps, LR, epochs=2, reuse_whitening=True)

@@ -1,11 +1,18 @@
 """Topic recovery on the small workload (V = 500, K = 10, 10,000 documents,
-10 minibatches x 5 epochs): the FP32 and BF16 forms follow the FP64
-oracle's SGD trajectory and give the same per-topic l1 recovery error
-(section "Recovering the Topic Model Parameters"; Hungarian matching).
+minibatches of 1000; section "Recovering the Topic Model Parameters",
+Hungarian matching on per-topic l1).
 
-The recovery bar itself is statistical.  Even the exact orthogonal
-decomposition of this corpus's tensor, by the tensor power method, is
-reported here beside SGD and is not asserted."""
+test_sgd_trajectory_parity: from one Gaussian start, 5 epochs of the FP32
+and BF16 forms follow the FP64 oracle's SGD trajectory and give its per-topic
+l1.  That start ends at a spurious stationary point (one topic collapsed,
+l1 about 1.65 for it) on every side alike: this test pins the trajectory,
+not recovery.
+
+test_batched_orthonormal_starts_recover: the batched mode (reading R) from
+32 orthonormal starts, keeping the lowest-loss start, recovers every topic
+(no collapsed topic) at the floor set by the sample size, in both forms and
+in the oracle (tests/test_oracle_recovery.py pins that floor: the power
+method's l1 halves at 4x the documents)."""
 from __future__ import annotations
 
 import numpy as np
@@ -29,17 +36,20 @@ def _recovery(mu_est, mu):
     return l1
 
 
-def test_recovery_equal_across_forms_and_oracle(lib):
+def test_sgd_trajectory_parity(lib):
     sp = ts.WORKLOADS[NAME]
     _, mu = C.topics(NAME)
     c = C.corpus(NAME, sp.n_docs)
     dev = lib.DeviceCSR.from_corpus(c)
-    # whitening fitted by the library (FP32 values used by every run below)
-    fit = lib.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="fp32")
-    fit.fit([dev])
-    W, m1, _ = fit.get_whitening()
-    W64 = W.cpu().numpy().astype(np.float64)
-    m164 = m1.cpu().numpy().astype(np.float64)
+    # the oracle's whitening of the corpus's M2 (FP32 values used by every run below)
+    st = O.ingest(c.indptr, c.indices, c.counts, sp.V)
+    M1 = O.first_moment(st["C"], st["T"])
+    M2 = O.second_moment(O.pair_counts(c.indptr, c.indices, c.counts, sp.V), st["S2"], M1, float(sp.alpha0))
+    Wo, _, _ = O.whitening(M2, sp.K)
+    W64 = Wo.astype(np.float32).astype(np.float64)
+    m164 = (W64.T @ M1).astype(np.float32).astype(np.float64)
+    W = torch.tensor(W64, dtype=torch.float32)
+    m1 = torch.tensor(m164, dtype=torch.float32)
     offs = list(range(0, sp.n_docs + 1, 1000))
     Phi0 = ts.initial_factors(sp.seed + 1, sp.K, sp.K)
 
@@ -67,19 +77,42 @@ def test_recovery_equal_across_forms_and_oracle(lib):
 
     assert C.rel(Phis["fp32"], P) < 1e-3  # 50 steps of FP32 rounding
     assert C.rel(Phis["bf16"], P) < 5e-2  # 50 steps of BF16 operand rounding
-    # equal recovery error: per topic, and on average
+    # the same per-topic l1 as the oracle's trajectory, per topic and on average
     assert np.max(np.abs(np.sort(l1["fp32"]) - np.sort(l1_o))) < 1e-3
     assert np.max(np.abs(np.sort(l1["bf16"]) - np.sort(l1_o))) < 2e-2
     assert abs(l1["bf16"].mean() - l1["fp32"].mean()) < 1e-2
+    print(f"trajectory l1 mean/max: fp32 {l1['fp32'].mean():.3f}/{l1['fp32'].max():.3f}, "
+          f"bf16 {l1['bf16'].mean():.3f}/{l1['bf16'].max():.3f}, oracle {l1_o.mean():.3f}/{l1_o.max():.3f}")
 
-    # context: the exact orthogonal decomposition of the corpus tensor
-    st = O.ingest(c.indptr, c.indices, c.counts, sp.V)
-    M1 = O.first_moment(st["C"], st["T"])
-    T = O.whitened_third_moment(c.indptr, c.indices, c.counts, sp.V, W64, M1, float(sp.alpha0))
-    lams, V = O.tensor_power_method(T, sp.K, n_restarts=10, n_iters=50, seed=0)
-    mu_p, _ = O.unwhiten_power(lams, V, W64)
-    l1_p = _recovery(mu_p, mu)
-    print(f"recovery l1 mean/max: sgd fp32 {l1['fp32'].mean():.3f}/{l1['fp32'].max():.3f}, "
-          f"bf16 {l1['bf16'].mean():.3f}/{l1['bf16'].max():.3f}, oracle sgd {l1_o.mean():.3f}/{l1_o.max():.3f}, "
-          f"power method {l1_p.mean():.3f}/{l1_p.max():.3f}")
-    fit.close()
+
+def test_batched_orthonormal_starts_recover(lib):
+    sp = ts.WORKLOADS[NAME]
+    _, mu = C.topics(NAME)
+    c = C.corpus(NAME, sp.n_docs)
+    dev = lib.DeviceCSR.from_corpus(c)
+    offs = np.arange(0, sp.n_docs + 1, 1000, dtype=np.int64)
+    starts = np.stack([ts.orthonormal_factors(sp.seed + 1 + s, sp.K, sp.K) for s in range(32)])
+    P, W, m1, means_o, finals = O.batched_fit(c.indptr, c.indices, c.counts, sp.V, offs, EPOCHS,
+                                              float(sp.alpha0), 0.0, LR, starts, sp.K)
+    l1_starts = [_recovery(O.unwhiten_cp(F, W)[0], mu) for F in finals]
+    kept_o = int(np.argmin(means_o))
+    out = {}
+    for prec in ("fp32", "bf16"):
+        t = lib.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision=prec)
+        Ps = torch.tensor(starts, dtype=torch.float32, device="cuda")
+        means = t.fit_batched(dev, offs, Ps, LR, epochs=EPOCHS)
+        kept = int(np.argmin(means))
+        if prec == "fp32":
+            assert np.allclose(means, means_o, rtol=1e-3)
+        # the kept start is one of the oracle's lowest-loss starts (several
+        # starts reach the same decomposition, to within 1e-3 of the loss)
+        assert means_o[kept] <= means_o.min() + 0.05, (prec, kept, kept_o)
+        l1 = _recovery(t.unwhiten_topics(Ps[0])[0], mu)
+        out[prec] = (kept, l1)
+        assert l1.max() < 0.12, (prec, l1)                  # no collapsed topic
+        assert abs(l1.mean() - l1_starts[kept].mean()) < (1e-3 if prec == "fp32" else 1e-2), prec
+        t.close()
+    print(f"batched, 32 orthonormal starts: kept (fp32, bf16, oracle) {out['fp32'][0]}, {out['bf16'][0]}, "
+          f"{kept_o}; l1 mean/max fp32 {out['fp32'][1].mean():.4f}/{out['fp32'][1].max():.4f}, "
+          f"bf16 {out['bf16'][1].mean():.4f}/{out['bf16'][1].max():.4f}, "
+          f"oracle {l1_starts[kept_o].mean():.4f}/{l1_starts[kept_o].max():.4f}")

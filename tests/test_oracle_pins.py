@@ -315,3 +315,20 @@ def test_grad_is_sum_over_documents():
     b = O.cp_grad_implicit(indptr[h:], indices, counts, V, W, m1, Phi, 1.0, 0.0)
     assert a["S3"] + b["S3"] == full["S3"]
     assert _rel(a["G1"] + a["G2"] + b["G1"] + b["G2"], full["G1"] + full["G2"]) < 1e-12
+
+
+def test_chunked_third_moment_equals_einsum_form():
+    """whitened_third_moment_chunked adds the same sums in chunks (ragged last
+    chunk) and maps the pair counts through W without forming them: equal to
+    whitened_third_moment to rounding, for a D > K whitening too."""
+    sp = ts.WORKLOADS["small_v500_k10"]
+    cdf, _ = ts.topics(sp)
+    c = ts.corpus(sp.with_docs(2500), cdf=cdf)
+    st = O.ingest(c.indptr, c.indices, c.counts, sp.V)
+    M1 = O.first_moment(st["C"], st["T"])
+    M2 = O.second_moment(O.pair_counts(c.indptr, c.indices, c.counts, sp.V), st["S2"], M1, 1.0)
+    for k in (10, 13):
+        W, _, _ = O.whitening(M2, k)
+        T1 = O.whitened_third_moment(c.indptr, c.indices, c.counts, sp.V, W, M1, 1.0)
+        T2 = O.whitened_third_moment_chunked(c.indptr, c.indices, c.counts, sp.V, W, M1, 1.0, chunk=333)
+        assert np.abs(T1 - T2).max() <= 1e-12 * np.abs(T1).max()

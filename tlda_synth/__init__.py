@@ -9,7 +9,8 @@ fewer than three words are clipped to three (the paper drops such documents
 in pre-processing, section "Recommendations for Data Pre-processing").
 
 All sampling lives in ``synth.c`` (Philox4x32-10 counters, integer sampling);
-this module only compiles it and marshals arrays.  It holds none of the
+this module compiles it, marshals arrays, and derives orthonormal starting
+factors from the Gaussian ones by a QR factorisation.  It holds none of the
 estimation method's arithmetic, so both sides of a parity test may use it.
 """
 from __future__ import annotations
@@ -287,3 +288,15 @@ def initial_factors(seed: int, k: int, K: int) -> np.ndarray:
     held in a float64 array (so both sides start from identical numbers)."""
     g = gaussian(seed, 7, k * K).reshape(k, K) / np.sqrt(k)
     return g.astype(np.float32).astype(np.float64)
+
+
+def orthonormal_factors(seed: int, k: int, K: int) -> np.ndarray:
+    """Initial CP factors with orthonormal columns (K <= k): the Q factor of
+    the Gaussian start initial_factors(seed, k, K), each column's sign fixed
+    so that the diagonal of R is positive, as FP32 values held in a float64
+    array.  A start whose columns point in distinct directions, as the
+    whitened topics do."""
+    g = initial_factors(seed, k, K)
+    q, r = np.linalg.qr(g)
+    q = q * np.sign(np.diag(r))[None, :]
+    return q.astype(np.float32).astype(np.float64)
