@@ -104,6 +104,11 @@ def parse():
     ap.add_argument("--billion-docs", type=int, default=16_000_000)
     ap.add_argument("--billion-chunk", type=int, default=1_000_000)
     ap.add_argument("--billion-r", type=int, default=512)
+    ap.add_argument("--recovery", action="store_true",
+                    help="topic recovery of one full streamed pass (10M documents) in both forms, "
+                         "warm-started by the batched mode on a slice")
+    ap.add_argument("--recovery-docs", type=int, default=10_000_000)
+    ap.add_argument("--recovery-lr", type=float, default=1e-4)
     ap.add_argument("--stream-workload", default="billion_v100k_k300",
                     help="workload of the chunked pipeline (billion_v100k_k300, scale_v50k_k200)")
     return ap.parse_args()
@@ -197,7 +202,8 @@ def recovery_l1(ctx, Phi, mu, steps):
         Dm = np.abs(mu[:, :, None] - mu_e[None, :, :]).sum(axis=1)
         r_, c_ = linear_sum_assignment(Dm)
         l1 = Dm[r_, c_]
-        return {"l1_mean": float(l1.mean()), "l1_max": float(l1.max()), "after_steps": steps}
+        return {"l1_mean": float(l1.mean()), "l1_median": float(np.median(l1)), "l1_max": float(l1.max()),
+                "topics_above_1": int((l1 > 1.0).sum()), "after_steps": steps}
     except Exception as e:  # noqa: BLE001
         return {"error": str(e)[:80]}
 
@@ -489,6 +495,98 @@ def e1_main(args):
         "config": {"workload": "e1_v{500,1000,1500}_k2", "reps": args.e1_reps, "epochs": args.e1_epochs,
                    "starts": args.e1_starts, "batch": 1000, "lr": 1e-2},
         "per_V": per_v,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def recovery_main(args):
+    """`--recovery`: topic recovery at the stream workload through the
+    library alone, as a user would run it (section "Fully Online
+    Implementation": initial factors from the batched mode run to convergence
+    on a small portion of the data, then one CP step per minibatch):
+      1. the moments and the whitening from all N documents (tlda_fit_moments);
+      2. a warm start: the batched mode (reading R) on the first 1M documents,
+         batches of 4096, 20 epochs, from 8 orthonormal starts, the start with
+         the lowest mean last-epoch loss kept;
+      3. one streamed pass over all N documents (the seeded 512..8192
+         minibatch sizes, about 2300 steps) in the BF16 form and, from the
+         same W and warm start, in the FP32 form.
+    Reported per stage: per-topic l1 to the generator's topics (Hungarian
+    matching) as mean, median, max and the count above 1 (a collapsed or
+    missing topic), and each form's docs/s over the pass.  The oracle's
+    power-method floor (tests/golden/recovery_floor_stream_v20k_k100.txt,
+    written by an oracle-only script with the population whitening) is quoted
+    as context."""
+    import torch
+    import tlda_synth as ts
+    from paper_2511_07809_gb300 import tlda
+
+    sp = ts.WORKLOADS[WORKLOAD]
+    cdf, mu = ts.topics(sp)
+    N = int(args.recovery_docs)
+    t0 = time.perf_counter()
+    c = ts.corpus(sp.with_docs(N), n_docs=N, cdf=cdf)
+    gen_s = time.perf_counter() - t0
+    dev = tlda.DeviceCSR.from_corpus(c)
+    sizes = ts.batch_sizes(sp.with_docs(N))
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    offs = offs[offs <= N]
+    if offs[-1] != N:
+        offs = np.append(offs, N)
+    fit = tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision="fp32", max_batch=8192, seed=1)
+    t0 = time.perf_counter()
+    for d0 in range(0, N, 1_000_000):
+        fit.fit_moments(tlda.DeviceCSR.from_corpus(c.rows(d0, min(d0 + 1_000_000, N))), tlda.ACCUMULATE)
+    fit.fit_moments(None, tlda.FINALIZE)
+    W, m1, ev = fit.get_whitening()
+    fit_s = time.perf_counter() - t0
+    slice_docs = min(1_000_000, N)
+    so = np.arange(0, slice_docs + 1, 4096)
+    so[-1] = slice_docs
+    starts = np.stack([ts.orthonormal_factors(sp.seed + 1 + s, sp.K, sp.K) for s in range(8)])
+    Ps = torch.tensor(starts, dtype=torch.float32, device="cuda")
+    means = fit.fit_batched(dev, so, Ps, LR, epochs=20, reuse_whitening=True)
+    Pw = Ps[0].clone()
+    warm = recovery_l1(fit, Pw, mu, 0)
+    fit.close()
+    res = {}
+    for prec in ("bf16", "fp32"):
+        t = tlda.TLDA(sp.V, sp.K, alpha0=float(sp.alpha0), precision=prec, max_batch=8192, seed=1)
+        t.set_whitening(W, m1)
+        P = Pw.clone()
+        t.cp_pass(dev, offs[:65], P.clone(), args.recovery_lr)  # tile tuning, on a copy
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        t.cp_pass(dev, offs, P, args.recovery_lr)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[prec] = {"recovery": recovery_l1(t, P, mu, len(offs) - 1), "docs_s": N / (ms / 1e3)}
+        t.close()
+    floor = None
+    fpath = os.path.join(ROOT, "tests", "golden", "recovery_floor_stream_v20k_k100.txt")
+    if os.path.exists(fpath):
+        floor = {}
+        for ln in open(fpath):
+            if ln.strip() and not ln.startswith("#"):
+                k, v = ln.split()
+                floor[k] = float(v)
+        floor["source"] = "oracle tensor power method, population whitening (tests/golden)"
+    line = {
+        "metric": "per-topic l1 recovery after one streamed online pass at k=100,V=20k (BF16 and FP32 forms)",
+        "value": res["bf16"]["recovery"]["l1_mean"], "unit": "l1", "higher_is_better": False, "n_gpus": 1,
+        "dtype": "bf16", "data": "synthetic: seeded LDA corpus (Dirichlet(0.1) topics, Poisson(12) lengths)",
+        "config": {"workload": WORKLOAD, "docs": N, "steps": int(len(offs) - 1), "stream_lr": args.recovery_lr,
+                   "whitening": f"tlda_fit_moments on all {N} documents", "warm_start":
+                   f"batched mode, first {slice_docs} documents, batches of 4096, 20 epochs, 8 orthonormal "
+                   f"starts, lr {LR}", "gen_s": round(gen_s, 1), "fit_s": round(fit_s, 2)},
+        "eigenvalues": {"lambda_1": float(ev[0]), "lambda_K": float(ev[-1])},
+        "warm_start": warm, "warm_start_mean_losses": [float(x) for x in np.sort(means)],
+        "bf16": res["bf16"], "fp32": res["fp32"],
+        "l1_mean_diff_bf16_fp32": abs(res["bf16"]["recovery"]["l1_mean"] - res["fp32"]["recovery"]["l1_mean"]),
+        "oracle_floor": floor,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -789,6 +887,8 @@ def main():
         return billion_main(args)
     if args.batch_sweep:
         return sweep_main(args)
+    if args.recovery:
+        return recovery_main(args)
     if args.vi:
         return vi_main(args)
     if args.online:
