@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["auto", "bf16", "fp32"], default="auto")
     ap.add_argument("--fit-docs", type=int, default=1_000_000)
+    ap.add_argument("--tile-cap", type=int, default=0,
+                    help="fix the persistent pass's tile size (documents per tile) instead of tuning it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
@@ -500,6 +502,58 @@ def e1_main(args):
     return 0
 
 
+def restart_duplicate_factors(P, rng, thr=0.5):
+    """Warm-start step of the recovery run (reading R): among the columns of
+    the factors P (D x K), every pair whose directions have |cosine| above
+    thr is taken for two components on one topic (a spurious stationary
+    point of the unconstrained objective); the shorter of the pair is
+    replaced by a random direction orthogonal to the kept columns, at the
+    median column norm.  Uses the factors alone (no ground truth).  Returns
+    (new P, number of columns replaced)."""
+    P = np.array(P, dtype=np.float64)
+    n = np.linalg.norm(P, axis=0)
+    U = P / np.maximum(n, 1e-300)
+    G = U.T @ U
+    np.fill_diagonal(G, 0.0)
+    bad = set()
+    for i in range(P.shape[1]):
+        for j in range(i + 1, P.shape[1]):
+            if abs(G[i, j]) > thr and i not in bad and j not in bad:
+                bad.add(j if n[j] < n[i] else i)
+    keep = [i for i in range(P.shape[1]) if i not in bad]
+    for b in sorted(bad):
+        Q, _ = np.linalg.qr(P[:, keep])
+        v = rng.standard_normal(P.shape[0])
+        v -= Q @ (Q.T @ v)
+        P[:, b] = v / np.linalg.norm(v) * np.median(n)
+        keep.append(b)
+    return P, len(bad)
+
+
+def warm_start(ctx, dev, slice_docs, starts, lr, epochs=20, rounds=6, seed=0):
+    """The batched mode on documents [0, slice_docs) in batches of 4096 from
+    the given starts (the lowest-loss start kept), then rounds of duplicate
+    restarts each followed by 10 more epochs, until no pair is duplicated.
+    Returns (factors, mean last-epoch losses of the starts, restarts per round)."""
+    import torch
+    so = np.arange(0, slice_docs + 1, 4096)
+    so[-1] = slice_docs
+    Ps = torch.tensor(starts, dtype=torch.float32, device="cuda")
+    means = ctx.fit_batched(dev, so, Ps, lr, epochs=epochs, reuse_whitening=True)
+    P = Ps[0].cpu().numpy()
+    rng = np.random.default_rng(seed)
+    hist = []
+    for _ in range(rounds):
+        P, nb = restart_duplicate_factors(P, rng)
+        hist.append(nb)
+        if nb == 0:
+            break
+        Pt = torch.tensor(P[None], dtype=torch.float32, device="cuda")
+        ctx.fit_batched(dev, so, Pt, lr, epochs=10, reuse_whitening=True)
+        P = Pt[0].cpu().numpy()
+    return torch.tensor(P, dtype=torch.float32, device="cuda"), means, hist
+
+
 def recovery_main(args):
     """`--recovery`: topic recovery at the stream workload through the
     library alone, as a user would run it (section "Fully Online
@@ -508,7 +562,8 @@ def recovery_main(args):
       1. the moments and the whitening from all N documents (tlda_fit_moments);
       2. a warm start: the batched mode (reading R) on the first 1M documents,
          batches of 4096, 20 epochs, from 8 orthonormal starts, the start with
-         the lowest mean last-epoch loss kept;
+         the lowest mean last-epoch loss kept, then rounds of restarts of
+         duplicated components (warm_start);
       3. one streamed pass over all N documents (the seeded 512..8192
          minibatch sizes, about 2300 steps) in the BF16 form and, from the
          same W and warm start, in the FP32 form.
@@ -542,12 +597,8 @@ def recovery_main(args):
     W, m1, ev = fit.get_whitening()
     fit_s = time.perf_counter() - t0
     slice_docs = min(1_000_000, N)
-    so = np.arange(0, slice_docs + 1, 4096)
-    so[-1] = slice_docs
     starts = np.stack([ts.orthonormal_factors(sp.seed + 1 + s, sp.K, sp.K) for s in range(8)])
-    Ps = torch.tensor(starts, dtype=torch.float32, device="cuda")
-    means = fit.fit_batched(dev, so, Ps, LR, epochs=20, reuse_whitening=True)
-    Pw = Ps[0].clone()
+    Pw, means, restarts = warm_start(fit, dev, slice_docs, starts, LR)
     warm = recovery_l1(fit, Pw, mu, 0)
     fit.close()
     res = {}
@@ -581,7 +632,9 @@ def recovery_main(args):
         "config": {"workload": WORKLOAD, "docs": N, "steps": int(len(offs) - 1), "stream_lr": args.recovery_lr,
                    "whitening": f"tlda_fit_moments on all {N} documents", "warm_start":
                    f"batched mode, first {slice_docs} documents, batches of 4096, 20 epochs, 8 orthonormal "
-                   f"starts, lr {LR}", "gen_s": round(gen_s, 1), "fit_s": round(fit_s, 2)},
+                   f"starts, lr {LR}, then restarts of duplicated components", "gen_s": round(gen_s, 1),
+                   "fit_s": round(fit_s, 2)},
+        "warm_start_restarts_per_round": restarts,
         "eigenvalues": {"lambda_1": float(ev[0]), "lambda_K": float(ev[-1])},
         "warm_start": warm, "warm_start_mean_losses": [float(x) for x in np.sort(means)],
         "bf16": res["bf16"], "fp32": res["fp32"],
@@ -946,6 +999,8 @@ def main():
     t_fit = time.perf_counter() - t_fit
     W, m1, eig = ctx.get_whitening()
     Phi0 = torch.tensor(ts.initial_factors(sp.seed + 1, sp.K, sp.K), dtype=torch.float32, device="cuda")
+    if args.tile_cap > 0 and primary == "bf16":
+        ctx.autotune(fixed=args.tile_cap)
 
     warm_segs = segments(seq[:args.warmup], n_docs, 0)
     last_off = warm_segs[-1][-1] if warm_segs else 0

@@ -663,6 +663,45 @@ __global__ void k_barrier_selftest(PassCtl *ctl) {
   if (threadIdx.x == 0 && !ok) atomicAdd(&ctl->S3[0], 1ull);
 }
 
+// Per step, the n_blocks + 1 split points of its documents: split_i is the
+// first document whose start offset reaches i nnz / n_blocks (a lower bound
+// by binary search on indptr), made non-decreasing by a running maximum, so
+// the ranges partition [0, n_docs) even when indptr is corrupt (the tiles'
+// validation then sees every document once).
+__global__ void k_pass_splits(const BatchDesc *descs, int s0, int s1, int n_blocks, int stride, int *splits) {
+  __shared__ int sv[1024];
+  const int s = s0 + blockIdx.x;
+  if (s >= s1) return;
+  const BatchDesc b = descs[s];
+  const int nd = b.n_docs;
+  const long long base = nd > 0 ? b.indptr[0] : 0;
+  const long long nnz = nd > 0 ? (long long)b.indptr[nd] - base : 0;
+  for (int i = threadIdx.x; i <= n_blocks; i += blockDim.x) {
+    int v = nd;
+    if (i == 0) {
+      v = 0;
+    } else if (i < n_blocks && nnz > 0) {
+      const long long target = base + nnz * i / n_blocks;
+      int lo = 0, hi = nd;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((long long)b.indptr[mid] < target) lo = mid + 1;
+        else hi = mid;
+      }
+      v = lo;
+    }
+    sv[i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int i = 0; i <= n_blocks; ++i) {
+      run = max(run, min(sv[i], nd));
+      splits[(long long)s * stride + i] = i == n_blocks ? nd : run;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ float s_red[kFusedThreads / 32];
@@ -698,10 +737,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     // the last e_blocks blocks take no tiles: they start on the Phi-only
     // columns as soon as the step begins
     const int Gd = G - min(max(p.e_blocks, 0), G / 2);
-    const int td = nd > 0 ? max(1, min(cap, (nd + Gd - 1) / Gd)) : 1;
-    const int ntiles = nd > 0 ? (nd + td - 1) / td : 0;
-    const int nwork = min(Gd, ntiles);
+    // this block's documents [d_lo, d_hi): equal shares of the batch's
+    // nonzeros, in tiles of at most `cap` documents
+    const int nwork = nd > 0 ? Gd : 0;
     const bool has = blk < nwork;
+    BatchDesc bs = b;
+    int td = 1;
+    if (has) {
+      const int *sp = p.splits + (long long)s * p.split_stride + blk;
+      const int d_lo = sp[0], d_hi = sp[1];
+      bs.indptr = b.indptr + d_lo;
+      bs.n_docs = max(0, d_hi - d_lo);
+      const int nt = (bs.n_docs + cap - 1) / cap;
+      td = nt > 0 ? (bs.n_docs + nt - 1) / nt : 1;
+    }
 
     // ---------------- phase A: the data term of this block's tiles.  The
     // first tile's CSR slice and U rows are requested before the wait for the
@@ -722,7 +771,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     if (has) {
       float lacc = 0.f;
       bool g_init = false;
-      f.tiles(a, b, blk, Gd, td, lacc, g_init, &ctl->S3[slot], &st->err, true, pre);
+      f.tiles(a, bs, 0, 1, td, lacc, g_init, &ctl->S3[slot], &st->err, true, pre);
       if (a.want_loss) {
         const float t = block_sum(lacc, s_red);
         if (tid == 0 && t != 0.f) atomicAdd(&ctl->loss_data[slot], (double)t);
@@ -969,6 +1018,14 @@ cudaError_t launch_barrier_selftest(PassCtl *ctl, cudaStream_t s, int grid) {
   void *args[] = {&ctl};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_barrier_selftest), dim3(grid), dim3(32), args,
                                      0, s);
+}
+
+cudaError_t launch_pass_splits(const BatchDesc *descs, int s0, int s1, int n_blocks, int stride, int *splits,
+                               cudaStream_t s) {
+  if (s1 <= s0) return cudaSuccess;
+  if (n_blocks < 1 || n_blocks > 1023 || stride < n_blocks + 1) return cudaErrorInvalidValue;
+  k_pass_splits<<<s1 - s0, 256, 0, s>>>(descs, s0, s1, n_blocks, stride, splits);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, int grid) {

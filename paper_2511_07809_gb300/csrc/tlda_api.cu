@@ -222,7 +222,10 @@ constexpr int kPassEBlocks = 8;
 tlda_status ensure_descs(tlda_ctx *ctx, int n) {
   if (ctx->descs_cap < n) {
     dfree(ctx->descs);
+    dfree(ctx->splits);
+    ctx->descs_cap = 0;
     CK(dalloc(&ctx->descs, (size_t)n));
+    CK(dalloc(&ctx->splits, (size_t)n * (ctx->pass_grid + 1)));
     ctx->descs_cap = n;
   }
   return TLDA_OK;
@@ -240,6 +243,10 @@ tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int ca
   pa.ctl = ctx->ctl;
   pa.record = record;
   pa.e_blocks = kPassEBlocks;
+  pa.splits = ctx->splits;
+  pa.split_stride = ctx->pass_grid + 1;
+  const int n_data = ctx->pass_grid - std::min(std::max(kPassEBlocks, 0), ctx->pass_grid / 2);
+  CK(launch_pass_splits(ctx->descs, s0, s1, n_data, pa.split_stride, ctx->splits, ps));
   CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(PassCtl), ps));
   Prof pr(ctx, kPass, ps);
   CK(launch_pass(a, pa, ps, ctx->pass_grid));
@@ -608,7 +615,7 @@ tlda_status tlda_destroy(tlda_ctx *ctx) {
   dfree(ctx->X32); dfree(ctx->Q32); dfree(ctx->Y32); dfree(ctx->Z32); dfree(ctx->Zc32);
   dfree(ctx->H32); dfree(ctx->cnt); dfree(ctx->widx); dfree(ctx->Gpart); dfree(ctx->Gram);
   dfree(ctx->avec); dfree(ctx->E); dfree(ctx->G3); dfree(ctx->ZU16); dfree(ctx->Z16); dfree(ctx->PhiImg);
-  dfree(ctx->st); dfree(ctx->descs); dfree(ctx->P64); dfree(ctx->Ccnt);
+  dfree(ctx->st); dfree(ctx->descs); dfree(ctx->splits); dfree(ctx->P64); dfree(ctx->Ccnt);
   dfree(ctx->TS); dfree(ctx->fit_err); dfree(ctx->stage[0]); dfree(ctx->stage[1]);
   dfree(ctx->ctl); dfree(ctx->st_tune); dfree(ctx->dlosses); dfree(ctx->phi_scratch);
   dfree(ctx->on_Om); dfree(ctx->on_Z); dfree(ctx->on_C); dfree(ctx->on_TS); dfree(ctx->on_err);
@@ -744,10 +751,9 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
   if (ctx->pass_grid > 0 && (ctx->prof_mask & ~(1u << kPass)) == 0)
     return cp_pass_persistent(ctx, corpus, batch_offsets, n_batches, Phi, lr, host, loss_out);
   // descriptors
-  if (ctx->descs_cap < n_batches) {
-    dfree(ctx->descs);
-    CK(dalloc(&ctx->descs, (size_t)n_batches));
-    ctx->descs_cap = n_batches;
+  {
+    const tlda_status es = ensure_descs(ctx, n_batches);
+    if (es) return es;
   }
   std::vector<BatchDesc> hd(n_batches);
   long long max_nnz = 0;

@@ -78,6 +78,8 @@ struct PassArgs {
   PassCtl *ctl;
   int record;                    // 1: advance the context's step state (0 for tuning runs)
   int e_blocks;                  // blocks that take only the Phi-only columns (no data tiles)
+  const int *splits;             // per step, split_stride entries: the data blocks' document
+  int split_stride;              //   ranges, equal in nonzeros (launch_pass_splits)
 };
 
 // Element (topic n, feature k) of the B operand Phi^T in the shared-memory
@@ -168,6 +170,7 @@ struct tlda_ctx {
   tlda::DevState *st_host = nullptr;   // pinned mirror for reads
   tlda::BatchDesc *descs = nullptr;    // pass descriptors (device)
   int descs_cap = 0;
+  int *splits = nullptr;               // per pass step, the data blocks' document ranges (device)
   tlda::BatchDesc *descs_pin = nullptr;  // pinned staging of the persistent pass's descriptors
   int descs_pin_cap = 0;
   // fit state
@@ -246,6 +249,11 @@ bool fused_supported(int Dp, int Kp);
 void launch_fused(const StepArgs &a, cudaStream_t s, int grid);
 int pass_grid();                                  // co-resident blocks of the pass kernel (0: none)
 cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, int grid);
+// Document ranges of the data blocks of steps [s0, s1): for step s, entries
+// s * stride + i, i = 0..n_blocks, with range i = [split_i, split_{i+1}) equal
+// in nonzeros (lower bounds of i nnz / n_blocks), non-decreasing.
+cudaError_t launch_pass_splits(const BatchDesc *descs, int s0, int s1, int n_blocks, int stride, int *splits,
+                               cudaStream_t s);
 cudaError_t launch_barrier_selftest(PassCtl *ctl, cudaStream_t s, int grid);
 // k_tc.cu (BF16 tensor-core form)
 bool tc_supported(int Dp, int Kp);
