@@ -86,6 +86,49 @@ __device__ __forceinline__ void st_bf16x8(unsigned char *tile, int sub_bytes, in
   *reinterpret_cast<uint4 *>(tile + (col >> 6) * sub_bytes + sw_chunk(row, (col & 63) >> 3)) = pk;
 }
 
+// One row of B'' = f (z + 2 q^2 - 2 q y) (same-token correction on) or f z
+// (off), 64 topics from col0, staged as BF16 into `tile`; y and z rows of the
+// row's document from shared memory.  With kLoss the row's loss part
+// 2 f sum q^3 is added to lacc (skipped when the caller wants no loss).
+template <bool kSame, bool kLoss>
+__device__ __forceinline__ void b2_row(const float (&q)[64], const float4 *yr, const float4 *zr, float f,
+                                       unsigned char *tile, int row, int col0, float &lacc) {
+#pragma unroll
+  for (int i8 = 0; i8 < 8; ++i8) {
+    float bb[8];
+#pragma unroll
+    for (int h4 = 0; h4 < 2; ++h4) {
+      const float4 z4 = zr[i8 * 2 + h4];
+      const float zs[4] = {z4.x, z4.y, z4.z, z4.w};
+      if (kSame) {
+        const float4 y4 = yr[i8 * 2 + h4];
+        const float ys[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float qi = q[i8 * 8 + h4 * 4 + u];
+          bb[h4 * 4 + u] = f * (zs[u] + 2.f * qi * (qi - ys[u]));
+          if (kLoss) lacc += 2.f * f * qi * qi * qi;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) bb[h4 * 4 + u] = f * zs[u];
+      }
+    }
+    st_bf16x8(tile, 16384, row, col0 + i8 * 8, bb);
+  }
+}
+
+__device__ __forceinline__ void b2_row_any(bool same, bool loss, const float (&q)[64], const float4 *yr,
+                                           const float4 *zr, float f, unsigned char *tile, int row, int col0,
+                                           float &lacc) {
+  if (same) {
+    if (loss) b2_row<true, true>(q, yr, zr, f, tile, row, col0, lacc);
+    else b2_row<true, false>(q, yr, zr, f, tile, row, col0, lacc);
+  } else {
+    b2_row<false, false>(q, yr, zr, f, tile, row, col0, lacc);
+  }
+}
+
 // 64 consecutive FP32 TMEM columns of this warp's lanes (4 loads in flight, one wait).
 __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
   uint32_t r[64];
@@ -226,25 +269,43 @@ struct Fused {
   __device__ void write_g_sliced(float *dst, int D, int K, int G, int blk, int per, bool g_init) {
     const int row = quad * 32 + lane;
     tc_fence_after();
+    if ((K & 3) == 0) {
+      // staged row-major in the U buffers (free once the tiles are done),
+      // then copied out slice by slice: each slice's `per` entries are one
+      // contiguous run in global memory, so the stores are whole lines
+      float *stage = reinterpret_cast<float *>(sm + kOffU0);
 #pragma unroll 1
-    for (int p = 0; p < 4; ++p) {
-      const int c0 = half * 64 + p * 16;
-      if (c0 >= K) break;  // warp-uniform
-      float v[16];
-      if (g_init) tmem_ld16(colG + (static_cast<uint32_t>(quad * 32) << 16) + c0, v);
-      else
-        for (int i = 0; i < 16; ++i) v[i] = 0.f;
-      if (row < D) {
-        if ((K & 3) == 0) {  // 4 entries never straddle a slice (per is a multiple of 4)
+      for (int p = 0; p < 4; ++p) {
+        const int c0 = half * 64 + p * 16;
+        if (c0 >= K) break;  // warp-uniform
+        float v[16];
+        if (g_init) tmem_ld16(colG + (static_cast<uint32_t>(quad * 32) << 16) + c0, v);
+        else
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        if (row < D) {
 #pragma unroll
-          for (int q = 0; q < 16; q += 4) {
-            if (c0 + q < K) {
-              const int e = row * K + c0 + q, sl = e / per;
-              *reinterpret_cast<float4 *>(dst + ((long long)sl * G + blk) * per + (e - sl * per)) =
-                  make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-            }
-          }
-        } else {
+          for (int q = 0; q < 16; q += 4)
+            if (c0 + q < K)
+              *reinterpret_cast<float4 *>(stage + row * K + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        }
+      }
+      __syncthreads();
+      const int n4 = D * K / 4;
+      for (int v4 = tid; v4 < n4; v4 += kFusedThreads) {
+        const int e = v4 * 4, sl = e / per;  // per is a multiple of 4: a float4 never straddles slices
+        *reinterpret_cast<float4 *>(dst + ((long long)sl * G + blk) * per + (e - sl * per)) =
+            *reinterpret_cast<const float4 *>(stage + e);
+      }
+    } else {
+#pragma unroll 1
+      for (int p = 0; p < 4; ++p) {
+        const int c0 = half * 64 + p * 16;
+        if (c0 >= K) break;  // warp-uniform
+        float v[16];
+        if (g_init) tmem_ld16(colG + (static_cast<uint32_t>(quad * 32) << 16) + c0, v);
+        else
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        if (row < D) {
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             if (c0 + q < K) {
@@ -255,18 +316,17 @@ struct Fused {
         }
       }
     }
-    asm volatile("fence.proxy.async.global;" ::: "memory");  // the slices are read by bulk copies
     tc_fence_before();
   }
 
   // The data term of tiles tile0, tile0 + tstride, ... of batch b (td <= kT
   // documents each), added to the G columns.  S3 and validation bits go to
   // S3_dst and err_dst, the per-document loss parts to lacc.  Expects the Phi
-  // image in shared memory, or (phi_pending) its bulk copy on barrier 0: then
-  // pre() runs once, by every thread, after the first window's CSR slice and
-  // U rows are requested and before the first MMA (it starts the copy, after
-  // whatever the image waits for; false if that failed), and the copy is
-  // waited for.  Returns false on an expired wait.
+  // image in shared memory, or (phi_pending) pre() to bring it there: pre()
+  // then runs once, by every thread, after the first window's CSR slice and
+  // U rows are requested and before the first MMA (it waits for whatever the
+  // image waits for and copies it in; false if that failed).  Returns false
+  // on an expired wait.
   template <class Pre = NoPre>
   __device__ bool tiles(const StepArgs &a, const BatchDesc &b, int tile0, int tstride, int td, float &lacc,
                         bool &g_init, unsigned long long *S3_dst, int *err_dst, bool phi_pending = false,
@@ -402,9 +462,8 @@ struct Fused {
         else cp_async_wait_all();
         put_f(0, true);
         fence_proxy_async();
-        if (phi_pending) {  // the Phi^T image: its bulk copy, started by pre()
-          if (pre()) phi_wait();
-          else fail();
+        if (phi_pending) {  // the Phi^T image: pre() brings it into shared memory
+          if (!pre()) fail();
           phi_pending = false;
         }
         __syncthreads();
@@ -477,7 +536,7 @@ struct Fused {
           const float r = (dd < Te && a.same_token) ? rv[i] : 0.f;
           sY[dd * kYP + topic] = y;
           sZ[dd * kYP + topic] = y * y - r;
-          lacc += y * (y * y - 3.f * r);
+          if (a.want_loss) lacc += y * (y * y - 3.f * r);
         }
       }
       if (warp == 0) {
@@ -529,26 +588,7 @@ struct Fused {
             const float4 *zr = reinterpret_cast<const float4 *>(sZ + dd * kYP + half * 64);
             float q[64];
             tmem_ld64(colQ0 + buf * 128 + lane_off + half * 64, q);
-#pragma unroll
-            for (int i8 = 0; i8 < 8; ++i8) {
-              float bb[8];
-#pragma unroll
-              for (int h4 = 0; h4 < 2; ++h4) {
-                const float4 y4 = yr[i8 * 2 + h4], z4 = zr[i8 * 2 + h4];
-                const float ys[4] = {y4.x, y4.y, y4.z, y4.w}, zs[4] = {z4.x, z4.y, z4.z, z4.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  const float qi = q[i8 * 8 + h4 * 4 + u];
-                  if (a.same_token) {
-                    bb[h4 * 4 + u] = f * (zs[u] + 2.f * qi * qi - 2.f * qi * ys[u]);
-                    lacc += 2.f * f * qi * qi * qi;
-                  } else {
-                    bb[h4 * 4 + u] = f * zs[u];
-                  }
-                }
-              }
-              st_bf16x8(sQ, 16384, row, half * 64 + i8 * 8, bb);
-            }
+            b2_row_any(a.same_token, a.want_loss, q, yr, zr, f, sQ, row, half * 64, lacc);
           }
           fence_proxy_async();
           tc_fence_before();
@@ -572,9 +612,8 @@ struct Fused {
       if (__syncthreads_or(failed())) break;
     }
     cp_async_wait_all();
-    if (phi_pending) {  // no tile reached an MMA: still run pre() and consume the copy's phase
-      if (pre()) phi_wait();
-      else fail();
+    if (phi_pending) {  // no tile reached an MMA: still run pre() (the grid barrier's wait)
+      if (!pre()) fail();
     }
     __syncthreads();
     return !failed();
@@ -755,17 +794,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     // ---------------- phase A: the data term of this block's tiles.  The
     // first tile's CSR slice and U rows are requested before the wait for the
     // previous step's barrier (they need nothing from phase B); then the Phi^T
-    // image (written by every block in that phase B) comes by one bulk copy.
+    // image (written by every block in that phase B) comes in 16-byte cp.async
+    // pieces (plain global reads, so its writers need no proxy fence).
     auto pre = [&]() -> bool {
       if (bar_pending) {
         bar_pending = false;
         if (!grid_wait(ctl, nbar * G, &s_ok)) return false;
       }
-      if (tid == 0) {
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        mbar_arrive_expect_tx(&f.bars[0], 32768);
-        bulk_load(f.sPhi, a.PhiImg, 32768, &f.bars[0]);
-      }
+      const uint4 *src = reinterpret_cast<const uint4 *>(a.PhiImg);
+      uint4 *dstp = reinterpret_cast<uint4 *>(f.sPhi);
+      for (int e = tid; e < 32768 / 16; e += kFusedThreads) cp_async16(dstp + e, src + e);
+      cp_async_commit();
+      cp_async_wait_all();
+      fence_proxy_async();  // read by the tensor cores
       return true;
     };
     if (has) {
@@ -958,7 +999,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
           a.Phi[e] = phi;
         }
         a.PhiImg[phi_img_index(n, i, Kp)] = __float2bfloat16_rn(phi);
-        asm volatile("fence.proxy.async.global;" ::: "memory");  // read by bulk copies next step
       }
       __syncthreads();
     }
