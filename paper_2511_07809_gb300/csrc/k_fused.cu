@@ -478,8 +478,7 @@ struct Fused {
             tc_fence_after();
             issue_q(buf ^ 1);
           }
-          q_wait(buf);
-          if (__syncthreads_or(failed())) break;
+          q_wait(buf);  // each thread waits itself: the buffer and Q(c) are free to use
           if (c + 2 < wch) gather(c + 2, buf);  // this buffer's Q product is done
           {  // Q and Q*Q rows (BF16) for the MN-major reductions over nonzeros
             const int row = quad * 32 + lane;
@@ -496,7 +495,7 @@ struct Fused {
           }
           fence_proxy_async();
           tc_fence_before();
-          __syncthreads();
+          if (__syncthreads_or(failed())) break;  // also orders the previous chunk's F^T entries
           tc_fence_after();
           if (tid == 0) {  // Y^T += Q^T F^T, R^T += (Q*Q)^T F^T  (M = topics, N = 64 documents)
             const uint32_t qb = smem_u32(sQ), q2b = smem_u32(sQ2), fb = smem_u32(sF);
@@ -511,9 +510,8 @@ struct Fused {
           }
           mma_wait();
           put_f(c, false);                     // these products are done: clear c's entries
-          if (c + 1 < wch) put_f(c + 1, true);  // and place c+1's
+          if (c + 1 < wch) put_f(c + 1, true);  // and place c+1's (read after the next staging barrier)
           fence_proxy_async();
-          if (__syncthreads_or(failed())) break;
         }
       }
       cp_async_wait_all();
@@ -579,7 +577,6 @@ struct Fused {
           }
           if (!resident(c)) q_wait(buf);
           else tc_fence_after();
-          if (__syncthreads_or(failed())) break;
           {
             const int row = quad * 32 + lane, t = c * kChunk + row;
             const int dd = s_d[t];
@@ -592,7 +589,7 @@ struct Fused {
           }
           fence_proxy_async();
           tc_fence_before();
-          __syncthreads();
+          if (__syncthreads_or(failed())) break;
           tc_fence_after();
           if (tid == 0) {  // G += U_chunk^T B''_chunk (M = features, N = topics)
             const uint32_t ub = smem_u32(sm + (buf ? kOffU1 : kOffU0)), bq = smem_u32(sQ);
@@ -603,8 +600,7 @@ struct Fused {
             mma_commit(&bars[1]);
           }
           g_init = true;
-          mma_wait();
-          if (__syncthreads_or(failed())) break;
+          mma_wait();  // each thread waits itself: the B'' tile and this U buffer are free
           if (c > 1 && !resident(c - 2)) gather(c - 2, buf);  // this buffer's products are done
         }
       }
@@ -706,38 +702,58 @@ __global__ void k_barrier_selftest(PassCtl *ctl) {
 // first document whose start offset reaches i nnz / n_blocks (a lower bound
 // by binary search on indptr), made non-decreasing by a running maximum, so
 // the ranges partition [0, n_docs) even when indptr is corrupt (the tiles'
-// validation then sees every document once).
-__global__ void k_pass_splits(const BatchDesc *descs, int s0, int s1, int n_blocks, int stride, int *splits) {
-  __shared__ int sv[1024];
+// validation then sees every document once).  The batch's offsets are read
+// into shared memory first (one coalesced pass) when they fit `cap` entries.
+constexpr int kSplitThreads = 256;
+__global__ void __launch_bounds__(kSplitThreads) k_pass_splits(const BatchDesc *descs, int s0, int s1, int n_blocks,
+                                                              int stride, int *splits, int cap) {
+  extern __shared__ int s_ip[];
+  __shared__ int s_wmax[kSplitThreads / 32];
   const int s = s0 + blockIdx.x;
   if (s >= s1) return;
   const BatchDesc b = descs[s];
   const int nd = b.n_docs;
-  const long long base = nd > 0 ? b.indptr[0] : 0;
-  const long long nnz = nd > 0 ? (long long)b.indptr[nd] - base : 0;
-  for (int i = threadIdx.x; i <= n_blocks; i += blockDim.x) {
-    int v = nd;
-    if (i == 0) {
-      v = 0;
-    } else if (i < n_blocks && nnz > 0) {
-      const long long target = base + nnz * i / n_blocks;
-      int lo = 0, hi = nd;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((long long)b.indptr[mid] < target) lo = mid + 1;
-        else hi = mid;
-      }
-      v = lo;
-    }
-    sv[i] = v;
-  }
+  const bool in_smem = nd + 1 <= cap;
+  if (in_smem)
+    for (int d = threadIdx.x; d <= nd; d += kSplitThreads) s_ip[d] = b.indptr[d];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int i = 0; i <= n_blocks; ++i) {
-      run = max(run, min(sv[i], nd));
-      splits[(long long)s * stride + i] = i == n_blocks ? nd : run;
+  auto ip = [&](int d) -> long long { return in_smem ? s_ip[d] : b.indptr[d]; };
+  const long long base = nd > 0 ? ip(0) : 0;
+  const long long nnz = nd > 0 ? ip(nd) - base : 0;
+  int carry = 0;  // running maximum of the earlier rounds
+  for (int i0 = 0; i0 <= n_blocks; i0 += kSplitThreads) {
+    const int i = i0 + threadIdx.x;
+    int v = 0;
+    if (i <= n_blocks) {
+      v = nd;
+      if (i == 0) {
+        v = 0;
+      } else if (i < n_blocks && nnz > 0) {
+        const long long target = base + nnz * i / n_blocks;
+        int lo = 0, hi = nd;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (ip(mid) < target) lo = mid + 1;
+          else hi = mid;
+        }
+        v = lo;
+      }
+      v = min(v, nd);
     }
+    // inclusive running maximum over this round (warp shuffles, then the warps)
+    int m = max(v, carry);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, m, o);
+      if ((threadIdx.x & 31) >= o) m = max(m, t);
+    }
+    if ((threadIdx.x & 31) == 31) s_wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) m = max(m, s_wmax[w]);
+    if (i <= n_blocks) splits[(long long)s * stride + i] = i == n_blocks ? nd : m;
+    __syncthreads();
+    carry = s_wmax[0];
+    for (int w = 1; w < kSplitThreads / 32; ++w) carry = max(carry, s_wmax[w]);
+    __syncthreads();
   }
 }
 
@@ -1061,10 +1077,14 @@ cudaError_t launch_barrier_selftest(PassCtl *ctl, cudaStream_t s, int grid) {
 }
 
 cudaError_t launch_pass_splits(const BatchDesc *descs, int s0, int s1, int n_blocks, int stride, int *splits,
-                               cudaStream_t s) {
+                               int max_docs, cudaStream_t s) {
   if (s1 <= s0) return cudaSuccess;
-  if (n_blocks < 1 || n_blocks > 1023 || stride < n_blocks + 1) return cudaErrorInvalidValue;
-  k_pass_splits<<<s1 - s0, 256, 0, s>>>(descs, s0, s1, n_blocks, stride, splits);
+  if (n_blocks < 1 || stride < n_blocks + 1) return cudaErrorInvalidValue;
+  // the offsets of batches up to 11,999 documents go through shared memory
+  // (at most 48,000 bytes: within the default dynamic shared-memory limit)
+  const int cap = max_docs + 1 <= 12000 ? max_docs + 1 : 0;
+  k_pass_splits<<<s1 - s0, kSplitThreads, (size_t)cap * sizeof(int), s>>>(descs, s0, s1, n_blocks, stride, splits,
+                                                                        cap);
   return cudaGetLastError();
 }
 

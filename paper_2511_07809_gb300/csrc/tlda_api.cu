@@ -246,7 +246,7 @@ tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int ca
   pa.splits = ctx->splits;
   pa.split_stride = ctx->pass_grid + 1;
   const int n_data = ctx->pass_grid - std::min(std::max(kPassEBlocks, 0), ctx->pass_grid / 2);
-  CK(launch_pass_splits(ctx->descs, s0, s1, n_data, pa.split_stride, ctx->splits, ps));
+  CK(launch_pass_splits(ctx->descs, s0, s1, n_data, pa.split_stride, ctx->splits, ctx->Bmax, ps));
   CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(PassCtl), ps));
   Prof pr(ctx, kPass, ps);
   CK(launch_pass(a, pa, ps, ctx->pass_grid));
@@ -350,7 +350,9 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
         return fail(ctx, TLDA_ERR_INVALID, "host indptr not monotone at batch %d", b);
       max_need = std::max(max_need, need(b, b + 1));
     }
-    const long long cap = std::max(max_need, std::min(need(0, nb), kStageWords));
+    // the staging buffers take a whole segment's size on first use, so a later
+    // pass with more batches does not reallocate them (cudaFree synchronises)
+    const long long cap = std::max(max_need, kStageWords);
     if (ctx->stage_cap < cap) {
       dfree(ctx->stage[0]);
       dfree(ctx->stage[1]);

@@ -251,9 +251,10 @@ int pass_grid();                                  // co-resident blocks of the p
 cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, int grid);
 // Document ranges of the data blocks of steps [s0, s1): for step s, entries
 // s * stride + i, i = 0..n_blocks, with range i = [split_i, split_{i+1}) equal
-// in nonzeros (lower bounds of i nnz / n_blocks), non-decreasing.
+// in nonzeros (lower bounds of i nnz / n_blocks), non-decreasing.  max_docs:
+// the largest batch among the steps (sizes the shared-memory offsets).
 cudaError_t launch_pass_splits(const BatchDesc *descs, int s0, int s1, int n_blocks, int stride, int *splits,
-                               cudaStream_t s);
+                               int max_docs, cudaStream_t s);
 cudaError_t launch_barrier_selftest(PassCtl *ctl, cudaStream_t s, int grid);
 // k_tc.cu (BF16 tensor-core form)
 bool tc_supported(int Dp, int Kp);
