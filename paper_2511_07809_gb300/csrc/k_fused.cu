@@ -760,8 +760,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_splits(const BatchDesc *
 __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ float s_red[kFusedThreads / 32];
-  __shared__ float s_am4[4];
-  __shared__ int s_ok, s_col;
+  __shared__ float s_am8[8];
+  __shared__ int s_ok;
   Fused f;
   f.init(smem_raw);
   PassCtl *ctl = p.ctl;
@@ -840,14 +840,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       bar_pending = false;
       if (!grid_wait(ctl, nbar * G, &s_ok)) break;
     }
-    // the Phi-only terms, four columns at a time, handed out by a counter:
-    // the blocks that finish their tiles first (or have none) take them.  Phi
-    // is staged once per block (in the U slots, free after the tiles; rows
-    // padded to K + 1 floats against bank conflicts).
-    for (bool staged = false;;) {
-      if (tid == 0) s_col = (int)atomicAdd(&ctl->col_next[slot], 4u);
-      __syncthreads();
-      const int n0 = s_col;
+    // the Phi-only terms, four columns at a time: the dedicated blocks take
+    // the groups of four columns round-robin (group j to dedicated block
+    // j mod n), a fixed assignment with no counter round trip; with no
+    // dedicated blocks every block takes them the same way.  Phi is staged
+    // once per block (in the U slots; rows padded to K + 1 floats against
+    // bank conflicts).
+    const int e_idx = G > Gd ? blk - Gd : blk;  // < 0: a data block, no columns
+    const int e_cnt = G > Gd ? G - Gd : G;
+    bool staged = false;
+    constexpr int kEC = 8;  // columns per job
+    for (int job = 0; e_idx >= 0; ++job) {
+      const int n0 = (e_idx + job * e_cnt) * kEC;
       if (n0 >= K) break;
       if (!staged) {
         constexpr int kRows = 128 / (kFusedThreads / 32);  // rows of Phi per warp (16)
@@ -869,76 +873,95 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
         __syncthreads();
         staged = true;
       }
-      // columns n = n0 .. n0+3 (those < K): G_{b,n} = phi_b . phi_n for all b
+      // columns n = n0 .. n0+7 (those < K): G_{b,n} = phi_b . phi_n for all b
       // (Phi^T Phi is symmetric), a_n = m1 . phi_n, then for every row r
       //   P_rn = sum_b Phi_rb G_{b,n}^2,
       //   G3_rn = 2 Phi_rn a_n + m1_r |phi_n|^2 - 2 m1_r a_n^2,
       //   E_rn = 3(1+theta) P_rn - 3 G3_rn,
-      // and the columns' loss part (1+theta)/2 sum_b G^3 - (3 a |phi|^2 - 2 a^3)
-      float4 *sg4 = reinterpret_cast<float4 *>(f.sZ);  // [0, 256): half sums; [256, 384): the columns
-      int nn[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) nn[k] = min(n0 + k, K - 1);  // past K: repeat column K-1, not stored
+      // and the columns' loss part (1+theta)/2 sum_b G^3 - (3 a |phi|^2 - 2 a^3).
+      // The job's columns are staged [row][8] (two float4 per row, read as
+      // broadcasts), so each step of the two reductions is one load of the
+      // thread's own entry, two float4 loads and eight FMAs.
+      float *sC = f.sZ;                 // D x 8: Phi columns n0..n0+7 (zero past K)
+      float *sGh = f.sZ + 128 * kEC;    // 2 x 128 x 8: half sums
+      float *sGc = sGh + 2 * 128 * kEC; // 128 x 8: the Gram columns
+      for (int i = tid; i < 128 * kEC; i += kFusedThreads) {
+        const int r = i >> 3, k = i & 7;
+        sC[i] = (r < D && n0 + k < K) ? sPh[r * ldp + n0 + k] : 0.f;
+      }
+      __syncthreads();
       {
         const int b = tid & 127, rh = tid >> 7;
-        float g[4] = {0.f, 0.f, 0.f, 0.f};
+        float g[kEC];
+#pragma unroll
+        for (int k = 0; k < kEC; ++k) g[k] = 0.f;
         if (b < K) {
           const int r0 = rh ? (D + 1) / 2 : 0, r1 = rh ? D : (D + 1) / 2;
 #pragma unroll 2
           for (int r = r0; r < r1; ++r) {
             const float x = sPh[r * ldp + b];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) g[k] = fmaf(x, sPh[r * ldp + nn[k]], g[k]);
+            const float4 c0 = reinterpret_cast<const float4 *>(sC)[r * 2];
+            const float4 c1 = reinterpret_cast<const float4 *>(sC)[r * 2 + 1];
+            g[0] = fmaf(x, c0.x, g[0]);
+            g[1] = fmaf(x, c0.y, g[1]);
+            g[2] = fmaf(x, c0.z, g[2]);
+            g[3] = fmaf(x, c0.w, g[3]);
+            g[4] = fmaf(x, c1.x, g[4]);
+            g[5] = fmaf(x, c1.y, g[5]);
+            g[6] = fmaf(x, c1.z, g[6]);
+            g[7] = fmaf(x, c1.w, g[7]);
           }
         }
-        sg4[rh * 128 + b] = make_float4(g[0], g[1], g[2], g[3]);
-        if (f.warp < 4) {  // warp k: a for column k
+        float4 *dst = reinterpret_cast<float4 *>(sGh + (rh * 128 + b) * kEC);
+        dst[0] = make_float4(g[0], g[1], g[2], g[3]);
+        dst[1] = make_float4(g[4], g[5], g[6], g[7]);
+        {  // warp k: a for column n0 + k
           float am = 0.f;
-          const int nw = min(n0 + f.warp, K - 1);
-          for (int r = f.lane; r < D; r += 32) am = fmaf(s_m1[r], sPh[r * ldp + nw], am);
+          for (int r = f.lane; r < D; r += 32) am = fmaf(s_m1[r], sC[r * kEC + f.warp], am);
           for (int o = 16; o > 0; o >>= 1) am += __shfl_xor_sync(0xffffffffu, am, o);
-          if (f.lane == 0) s_am4[f.warp] = am;
+          if (f.lane == 0) s_am8[f.warp] = am;
         }
         __syncthreads();
-        if (tid < 128) {
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (tid < K) {
-            const float4 x = sg4[tid], y = sg4[128 + tid];
-            v = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
-          }
-          sg4[256 + tid] = v;
-        }
+        for (int i = tid; i < 128 * kEC; i += kFusedThreads)
+          sGc[i] = (i >> 3) < K ? sGh[i] + sGh[128 * kEC + i] : 0.f;
         __syncthreads();
       }
       {
         const int r = tid & 127, bh = tid >> 7;
-        float pv[4] = {0.f, 0.f, 0.f, 0.f};
+        float pv[kEC];
+#pragma unroll
+        for (int k = 0; k < kEC; ++k) pv[k] = 0.f;
         if (r < D) {
           const int b0 = bh ? (K + 1) / 2 : 0, b1 = bh ? K : (K + 1) / 2;
 #pragma unroll 2
           for (int bb = b0; bb < b1; ++bb) {
             const float x = sPh[r * ldp + bb];
-            const float4 gv = sg4[256 + bb];
-            pv[0] = fmaf(x, gv.x * gv.x, pv[0]);
-            pv[1] = fmaf(x, gv.y * gv.y, pv[1]);
-            pv[2] = fmaf(x, gv.z * gv.z, pv[2]);
-            pv[3] = fmaf(x, gv.w * gv.w, pv[3]);
+            const float4 g0 = reinterpret_cast<const float4 *>(sGc)[bb * 2];
+            const float4 g1 = reinterpret_cast<const float4 *>(sGc)[bb * 2 + 1];
+            pv[0] = fmaf(x, g0.x * g0.x, pv[0]);
+            pv[1] = fmaf(x, g0.y * g0.y, pv[1]);
+            pv[2] = fmaf(x, g0.z * g0.z, pv[2]);
+            pv[3] = fmaf(x, g0.w * g0.w, pv[3]);
+            pv[4] = fmaf(x, g1.x * g1.x, pv[4]);
+            pv[5] = fmaf(x, g1.y * g1.y, pv[5]);
+            pv[6] = fmaf(x, g1.z * g1.z, pv[6]);
+            pv[7] = fmaf(x, g1.w * g1.w, pv[7]);
           }
         }
-        sg4[bh * 128 + r] = make_float4(pv[0], pv[1], pv[2], pv[3]);  // the half sums are free again
+        float4 *dst = reinterpret_cast<float4 *>(sGh + (bh * 128 + r) * kEC);  // the half sums are free again
+        dst[0] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        dst[1] = make_float4(pv[4], pv[5], pv[6], pv[7]);
         __syncthreads();
         if (tid < D) {
-          const float4 x = sg4[tid], y = sg4[128 + tid];
-          const float P[4] = {x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w};
           const float mr = s_m1[tid];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
+          for (int k = 0; k < kEC; ++k) {
             if (n0 + k < K) {
-              const float am = s_am4[k];
-              const float4 gc = sg4[256 + nn[k]];
-              const float n2 = k == 0 ? gc.x : k == 1 ? gc.y : k == 2 ? gc.z : gc.w;
-              const float g3 = 2.f * sPh[tid * ldp + nn[k]] * am + mr * n2 - 2.f * mr * am * am;
-              a.E[tid * Kp + nn[k]] = 3.f * (1.f + a.theta) * P[k] - 3.f * g3;
+              const float P = sGh[tid * kEC + k] + sGh[(128 + tid) * kEC + k];
+              const float am = s_am8[k];
+              const float n2 = sGc[(n0 + k) * kEC + k];
+              const float g3 = 2.f * sC[tid * kEC + k] * am + mr * n2 - 2.f * mr * am * am;
+              a.E[tid * Kp + n0 + k] = 3.f * (1.f + a.theta) * P - 3.f * g3;
             }
           }
         }
@@ -946,16 +969,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       if (a.want_loss) {
         float v = 0.f;
         if (tid < K) {
-          const float4 gv = sg4[256 + tid];
-          const float gs[4] = {gv.x, gv.y, gv.z, gv.w};
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (n0 + k < K) v += 0.5f * (1.f + a.theta) * gs[k] * gs[k] * gs[k];
+          for (int k = 0; k < kEC; ++k) {
+            const float gk = sGc[tid * kEC + k];
+            if (n0 + k < K) v += 0.5f * (1.f + a.theta) * gk * gk * gk;
+          }
         }
-        if (tid < 4 && n0 + tid < K) {
-          const float am = s_am4[tid];
-          const float4 gc = sg4[256 + n0 + tid];
-          const float n2 = tid == 0 ? gc.x : tid == 1 ? gc.y : tid == 2 ? gc.z : gc.w;
+        if (tid < kEC && n0 + tid < K) {
+          const float am = s_am8[tid];
+          const float n2 = sGc[(n0 + tid) * kEC + tid];
           v -= 3.f * am * n2 - 2.f * am * am * am;
         }
         const float t = block_sum(v, s_red);
