@@ -42,6 +42,7 @@ constexpr int kT = 32;        // documents per tile, at most
 constexpr int kChunk = 128;   // nonzeros per chunk
 constexpr int kFusedThreads = 256;
 constexpr int kMinPassGrid = 128;  // at least one block per Phi column (K <= 128)
+constexpr int kPhiCols = 8;        // Phi-only columns per job of the pass kernel (a multiple of 4, <= 16)
 
 // shared-memory map (bytes from the 1024-aligned base)
 constexpr int kOffPhi = 0;          // Phi^T image 2 x [128 x 64] BF16               32 KB
@@ -705,14 +706,15 @@ __global__ void k_barrier_selftest(PassCtl *ctl) {
 // validation then sees every document once).  The batch's offsets are read
 // into shared memory first (one coalesced pass) when they fit `cap` entries.
 constexpr int kSplitThreads = 256;
-__global__ void __launch_bounds__(kSplitThreads) k_pass_splits(const BatchDesc *descs, int s0, int s1, int n_blocks,
-                                                              int stride, int *splits, int cap) {
+__global__ void __launch_bounds__(kSplitThreads) k_pass_splits(const BatchDesc *descs, int s0, int s1, PassArgs p,
+                                                              int grid, int *splits, int cap) {
   extern __shared__ int s_ip[];
   __shared__ int s_wmax[kSplitThreads / 32];
   const int s = s0 + blockIdx.x;
   if (s >= s1) return;
   const BatchDesc b = descs[s];
   const int nd = b.n_docs;
+  const int n_blocks = pass_data_blocks(p, grid, nd), stride = p.split_stride;
   const bool in_smem = nd + 1 <= cap;
   if (in_smem)
     for (int d = threadIdx.x; d <= nd; d += kSplitThreads) s_ip[d] = b.indptr[d];
@@ -760,7 +762,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_splits(const BatchDesc *
 __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ float s_red[kFusedThreads / 32];
-  __shared__ float s_am8[8];
+  __shared__ float s_am[kPhiCols];
   __shared__ int s_ok;
   Fused f;
   f.init(smem_raw);
@@ -791,7 +793,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const int cap = p.tile_cap > 0 ? p.tile_cap : (b.tile_cap > 0 ? b.tile_cap : 32);
     // the last e_blocks blocks take no tiles: they start on the Phi-only
     // columns as soon as the step begins
-    const int Gd = G - min(max(p.e_blocks, 0), G / 2);
+    const int Gd = pass_data_blocks(p, G, nd);
     // this block's documents [d_lo, d_hi): equal shares of the batch's
     // nonzeros, in tiles of at most `cap` documents
     const int nwork = nd > 0 ? Gd : 0;
@@ -849,7 +851,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const int e_idx = G > Gd ? blk - Gd : blk;  // < 0: a data block, no columns
     const int e_cnt = G > Gd ? G - Gd : G;
     bool staged = false;
-    constexpr int kEC = 8;  // columns per job
+    constexpr int kEC = kPhiCols;  // columns per job (a multiple of 4, at most 16)
+    constexpr int kEC4 = kEC / 4;
     for (int job = 0; e_idx >= 0; ++job) {
       const int n0 = (e_idx + job * e_cnt) * kEC;
       if (n0 >= K) break;
@@ -873,20 +876,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
         __syncthreads();
         staged = true;
       }
-      // columns n = n0 .. n0+7 (those < K): G_{b,n} = phi_b . phi_n for all b
-      // (Phi^T Phi is symmetric), a_n = m1 . phi_n, then for every row r
+      // columns n = n0 .. n0+kEC-1 (those < K): G_{b,n} = phi_b . phi_n for
+      // all b (Phi^T Phi is symmetric), a_n = m1 . phi_n, then for every row r
       //   P_rn = sum_b Phi_rb G_{b,n}^2,
       //   G3_rn = 2 Phi_rn a_n + m1_r |phi_n|^2 - 2 m1_r a_n^2,
       //   E_rn = 3(1+theta) P_rn - 3 G3_rn,
       // and the columns' loss part (1+theta)/2 sum_b G^3 - (3 a |phi|^2 - 2 a^3).
-      // The job's columns are staged [row][8] (two float4 per row, read as
+      // The job's columns are staged [row][kEC] (float4-aligned, read as
       // broadcasts), so each step of the two reductions is one load of the
-      // thread's own entry, two float4 loads and eight FMAs.
-      float *sC = f.sZ;                 // D x 8: Phi columns n0..n0+7 (zero past K)
-      float *sGh = f.sZ + 128 * kEC;    // 2 x 128 x 8: half sums
-      float *sGc = sGh + 2 * 128 * kEC; // 128 x 8: the Gram columns
+      // thread's own entry, kEC/4 float4 loads and kEC FMAs.  The y and z
+      // tiles (free in these blocks) hold the staging and the sums.
+      float *sC = f.sY;                 // 128 x kEC: Phi columns n0.. (zero past K)
+      float *sGh = sC + 128 * kEC;      // 2 x 128 x kEC: half sums
+      float *sGc = sGh + 2 * 128 * kEC; // 128 x kEC: the Gram columns
       for (int i = tid; i < 128 * kEC; i += kFusedThreads) {
-        const int r = i >> 3, k = i & 7;
+        const int r = i / kEC, k = i % kEC;
         sC[i] = (r < D && n0 + k < K) ? sPh[r * ldp + n0 + k] : 0.f;
       }
       __syncthreads();
@@ -900,30 +904,28 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
 #pragma unroll 2
           for (int r = r0; r < r1; ++r) {
             const float x = sPh[r * ldp + b];
-            const float4 c0 = reinterpret_cast<const float4 *>(sC)[r * 2];
-            const float4 c1 = reinterpret_cast<const float4 *>(sC)[r * 2 + 1];
-            g[0] = fmaf(x, c0.x, g[0]);
-            g[1] = fmaf(x, c0.y, g[1]);
-            g[2] = fmaf(x, c0.z, g[2]);
-            g[3] = fmaf(x, c0.w, g[3]);
-            g[4] = fmaf(x, c1.x, g[4]);
-            g[5] = fmaf(x, c1.y, g[5]);
-            g[6] = fmaf(x, c1.z, g[6]);
-            g[7] = fmaf(x, c1.w, g[7]);
+#pragma unroll
+            for (int q = 0; q < kEC4; ++q) {
+              const float4 c = reinterpret_cast<const float4 *>(sC)[r * kEC4 + q];
+              g[4 * q] = fmaf(x, c.x, g[4 * q]);
+              g[4 * q + 1] = fmaf(x, c.y, g[4 * q + 1]);
+              g[4 * q + 2] = fmaf(x, c.z, g[4 * q + 2]);
+              g[4 * q + 3] = fmaf(x, c.w, g[4 * q + 3]);
+            }
           }
         }
         float4 *dst = reinterpret_cast<float4 *>(sGh + (rh * 128 + b) * kEC);
-        dst[0] = make_float4(g[0], g[1], g[2], g[3]);
-        dst[1] = make_float4(g[4], g[5], g[6], g[7]);
-        {  // warp k: a for column n0 + k
+#pragma unroll
+        for (int q = 0; q < kEC4; ++q) dst[q] = make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+        for (int k = f.warp; k < kEC; k += kFusedThreads / 32) {  // a for column n0 + k
           float am = 0.f;
-          for (int r = f.lane; r < D; r += 32) am = fmaf(s_m1[r], sC[r * kEC + f.warp], am);
+          for (int r = f.lane; r < D; r += 32) am = fmaf(s_m1[r], sC[r * kEC + k], am);
           for (int o = 16; o > 0; o >>= 1) am += __shfl_xor_sync(0xffffffffu, am, o);
-          if (f.lane == 0) s_am8[f.warp] = am;
+          if (f.lane == 0) s_am[k] = am;
         }
         __syncthreads();
         for (int i = tid; i < 128 * kEC; i += kFusedThreads)
-          sGc[i] = (i >> 3) < K ? sGh[i] + sGh[128 * kEC + i] : 0.f;
+          sGc[i] = i / kEC < K ? sGh[i] + sGh[128 * kEC + i] : 0.f;
         __syncthreads();
       }
       {
@@ -936,21 +938,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
 #pragma unroll 2
           for (int bb = b0; bb < b1; ++bb) {
             const float x = sPh[r * ldp + bb];
-            const float4 g0 = reinterpret_cast<const float4 *>(sGc)[bb * 2];
-            const float4 g1 = reinterpret_cast<const float4 *>(sGc)[bb * 2 + 1];
-            pv[0] = fmaf(x, g0.x * g0.x, pv[0]);
-            pv[1] = fmaf(x, g0.y * g0.y, pv[1]);
-            pv[2] = fmaf(x, g0.z * g0.z, pv[2]);
-            pv[3] = fmaf(x, g0.w * g0.w, pv[3]);
-            pv[4] = fmaf(x, g1.x * g1.x, pv[4]);
-            pv[5] = fmaf(x, g1.y * g1.y, pv[5]);
-            pv[6] = fmaf(x, g1.z * g1.z, pv[6]);
-            pv[7] = fmaf(x, g1.w * g1.w, pv[7]);
+#pragma unroll
+            for (int q = 0; q < kEC4; ++q) {
+              const float4 gq = reinterpret_cast<const float4 *>(sGc)[bb * kEC4 + q];
+              pv[4 * q] = fmaf(x, gq.x * gq.x, pv[4 * q]);
+              pv[4 * q + 1] = fmaf(x, gq.y * gq.y, pv[4 * q + 1]);
+              pv[4 * q + 2] = fmaf(x, gq.z * gq.z, pv[4 * q + 2]);
+              pv[4 * q + 3] = fmaf(x, gq.w * gq.w, pv[4 * q + 3]);
+            }
           }
         }
         float4 *dst = reinterpret_cast<float4 *>(sGh + (bh * 128 + r) * kEC);  // the half sums are free again
-        dst[0] = make_float4(pv[0], pv[1], pv[2], pv[3]);
-        dst[1] = make_float4(pv[4], pv[5], pv[6], pv[7]);
+#pragma unroll
+        for (int q = 0; q < kEC4; ++q) dst[q] = make_float4(pv[4 * q], pv[4 * q + 1], pv[4 * q + 2], pv[4 * q + 3]);
         __syncthreads();
         if (tid < D) {
           const float mr = s_m1[tid];
@@ -958,7 +958,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
           for (int k = 0; k < kEC; ++k) {
             if (n0 + k < K) {
               const float P = sGh[tid * kEC + k] + sGh[(128 + tid) * kEC + k];
-              const float am = s_am8[k];
+              const float am = s_am[k];
               const float n2 = sGc[(n0 + k) * kEC + k];
               const float g3 = 2.f * sC[tid * kEC + k] * am + mr * n2 - 2.f * mr * am * am;
               a.E[tid * Kp + n0 + k] = 3.f * (1.f + a.theta) * P - 3.f * g3;
@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
           }
         }
         if (tid < kEC && n0 + tid < K) {
-          const float am = s_am8[tid];
+          const float am = s_am[tid];
           const float n2 = sGc[(n0 + tid) * kEC + tid];
           v -= 3.f * am * n2 - 2.f * am * am * am;
         }
@@ -1098,15 +1098,15 @@ cudaError_t launch_barrier_selftest(PassCtl *ctl, cudaStream_t s, int grid) {
                                      0, s);
 }
 
-cudaError_t launch_pass_splits(const BatchDesc *descs, int s0, int s1, int n_blocks, int stride, int *splits,
-                               int max_docs, cudaStream_t s) {
+cudaError_t launch_pass_splits(const BatchDesc *descs, int s0, int s1, const PassArgs &p, int grid, int max_docs,
+                               cudaStream_t s) {
   if (s1 <= s0) return cudaSuccess;
-  if (n_blocks < 1 || stride < n_blocks + 1) return cudaErrorInvalidValue;
+  if (grid < 2 || p.split_stride < grid + 1) return cudaErrorInvalidValue;
   // the offsets of batches up to 11,999 documents go through shared memory
   // (at most 48,000 bytes: within the default dynamic shared-memory limit)
   const int cap = max_docs + 1 <= 12000 ? max_docs + 1 : 0;
-  k_pass_splits<<<s1 - s0, kSplitThreads, (size_t)cap * sizeof(int), s>>>(descs, s0, s1, n_blocks, stride, splits,
-                                                                        cap);
+  k_pass_splits<<<s1 - s0, kSplitThreads, (size_t)cap * sizeof(int), s>>>(descs, s0, s1, p, grid,
+                                                                        const_cast<int *>(p.splits), cap);
   return cudaGetLastError();
 }
 

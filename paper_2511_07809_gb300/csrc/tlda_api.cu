@@ -215,9 +215,11 @@ tlda_status take_sticky(tlda_ctx *ctx) {
 constexpr long long kStageWords = 1ll << 23;  // int32 words per host-input staging buffer (32 MB)
 constexpr int kTuneBatches = 128;
 // Blocks of the persistent pass that compute only the Phi-only columns
-// (P, G3 and their loss parts), so those columns do not land on whichever
-// data blocks finish first.
+// (P, G3 and their loss parts); more of them for small batches, whose data
+// blocks finish early.
 constexpr int kPassEBlocks = 8;
+constexpr int kPassEBlocksSmall = 16;
+constexpr int kPassSmallDocs = 2048;
 
 tlda_status ensure_descs(tlda_ctx *ctx, int n) {
   if (ctx->descs_cap < n) {
@@ -243,10 +245,11 @@ tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int ca
   pa.ctl = ctx->ctl;
   pa.record = record;
   pa.e_blocks = kPassEBlocks;
+  pa.e_blocks_small = kPassEBlocksSmall;
+  pa.e_small_docs = kPassSmallDocs;
   pa.splits = ctx->splits;
   pa.split_stride = ctx->pass_grid + 1;
-  const int n_data = ctx->pass_grid - std::min(std::max(kPassEBlocks, 0), ctx->pass_grid / 2);
-  CK(launch_pass_splits(ctx->descs, s0, s1, n_data, pa.split_stride, ctx->splits, ctx->Bmax, ps));
+  CK(launch_pass_splits(ctx->descs, s0, s1, pa, ctx->pass_grid, ctx->Bmax, ps));
   CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(PassCtl), ps));
   Prof pr(ctx, kPass, ps);
   CK(launch_pass(a, pa, ps, ctx->pass_grid));

@@ -77,7 +77,9 @@ struct PassArgs {
   double *losses;                // per-step loss (device, indexed by step) or null
   PassCtl *ctl;
   int record;                    // 1: advance the context's step state (0 for tuning runs)
-  int e_blocks;                  // blocks that take only the Phi-only columns (no data tiles)
+  int e_blocks;                  // blocks that take only the Phi-only columns (no data tiles),
+  int e_blocks_small;            //   e_blocks_small of them for a batch of at most
+  int e_small_docs;              //   e_small_docs documents (pass_data_blocks)
   const int *splits;             // per step, split_stride entries: the data blocks' document
   int split_stride;              //   ranges, equal in nonzeros (launch_pass_splits)
 };
@@ -250,11 +252,19 @@ void launch_fused(const StepArgs &a, cudaStream_t s, int grid);
 int pass_grid();                                  // co-resident blocks of the pass kernel (0: none)
 cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, int grid);
 // Document ranges of the data blocks of steps [s0, s1): for step s, entries
-// s * stride + i, i = 0..n_blocks, with range i = [split_i, split_{i+1}) equal
-// in nonzeros (lower bounds of i nnz / n_blocks), non-decreasing.  max_docs:
-// the largest batch among the steps (sizes the shared-memory offsets).
-cudaError_t launch_pass_splits(const BatchDesc *descs, int s0, int s1, int n_blocks, int stride, int *splits,
-                               int max_docs, cudaStream_t s);
+// s * p.split_stride + i, i = 0..n (n = pass_data_blocks of the step's batch),
+// with range i = [split_i, split_{i+1}) equal in nonzeros (lower bounds of
+// i nnz / n), non-decreasing.  max_docs: the largest batch among the steps
+// (sizes the shared-memory offsets).
+cudaError_t launch_pass_splits(const BatchDesc *descs, int s0, int s1, const PassArgs &p, int grid, int max_docs,
+                               cudaStream_t s);
+
+// Data blocks of a pass step over a batch of n_docs documents (the other
+// blocks of the grid take only the Phi-only columns).
+__host__ __device__ inline int pass_data_blocks(const PassArgs &p, int grid, int n_docs) {
+  const int eb = n_docs <= p.e_small_docs ? p.e_blocks_small : p.e_blocks;
+  return grid - (eb < 0 ? 0 : eb > grid / 2 ? grid / 2 : eb);
+}
 cudaError_t launch_barrier_selftest(PassCtl *ctl, cudaStream_t s, int grid);
 // k_tc.cu (BF16 tensor-core form)
 bool tc_supported(int Dp, int Kp);
