@@ -42,7 +42,7 @@ constexpr int kT = 32;        // documents per tile, at most
 constexpr int kChunk = 128;   // nonzeros per chunk
 constexpr int kFusedThreads = 256;
 constexpr int kMinPassGrid = 128;  // at least one block per Phi column (K <= 128)
-constexpr int kPhiCols = 8;        // Phi-only columns per job of the pass kernel (a multiple of 4, <= 16)
+constexpr int kPhiCols = kPassPhiCols;
 
 // shared-memory map (bytes from the 1024-aligned base)
 constexpr int kOffPhi = 0;          // Phi^T image 2 x [128 x 64] BF16               32 KB

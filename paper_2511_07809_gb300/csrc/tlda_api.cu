@@ -218,8 +218,7 @@ constexpr int kTuneBatches = 128;
 // (P, G3 and their loss parts); more of them for small batches, whose data
 // blocks finish early.
 constexpr int kPassEBlocks = 8;
-constexpr int kPassEBlocksSmall = 16;
-constexpr int kPassSmallDocs = 2048;
+constexpr int kPassSmallDocs = 2560;
 
 tlda_status ensure_descs(tlda_ctx *ctx, int n) {
   if (ctx->descs_cap < n) {
@@ -245,7 +244,8 @@ tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int ca
   pa.ctl = ctx->ctl;
   pa.record = record;
   pa.e_blocks = kPassEBlocks;
-  pa.e_blocks_small = kPassEBlocksSmall;
+  // for small batches, one block per job of Phi-only columns (one round)
+  pa.e_blocks_small = std::max(kPassEBlocks, (ctx->K + kPassPhiCols - 1) / kPassPhiCols);
   pa.e_small_docs = kPassSmallDocs;
   pa.splits = ctx->splits;
   pa.split_stride = ctx->pass_grid + 1;

@@ -259,6 +259,8 @@ cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, in
 cudaError_t launch_pass_splits(const BatchDesc *descs, int s0, int s1, const PassArgs &p, int grid, int max_docs,
                                cudaStream_t s);
 
+constexpr int kPassPhiCols = 8;  // Phi-only columns per job of the pass kernel (a multiple of 4, <= 16)
+
 // Data blocks of a pass step over a batch of n_docs documents (the other
 // blocks of the grid take only the Phi-only columns).
 __host__ __device__ inline int pass_data_blocks(const PassArgs &p, int grid, int n_docs) {
