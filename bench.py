@@ -1198,9 +1198,10 @@ def main():
         # R/Z/H, Zc, reduction over rows, reduction, step end
         fused = primary == "bf16" and sp.K <= 128 and sp.K > 64
         per_step_kernels = 5 if fused else 9
-        # persistent form: per cp_pass call, the Phi^T image kernel and one
-        # pass kernel for all of its steps
-        launches_timed = (2 * len(timed_segs) if persistent
+        # persistent form: per cp_pass call over a device-resident corpus, the
+        # Phi^T image kernel, the split-point kernel and one pass kernel for
+        # all of its steps
+        launches_timed = (3 * len(timed_segs) if persistent
                           else per_step_kernels * args.steps + len(timed_segs))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -699,20 +699,33 @@ __global__ void k_barrier_selftest(PassCtl *ctl) {
   if (threadIdx.x == 0 && !ok) atomicAdd(&ctl->S3[0], 1ull);
 }
 
-// Per step, the n_blocks + 1 split points of its documents: split_i is the
-// first document whose start offset reaches i nnz / n_blocks (a lower bound
-// by binary search on indptr), made non-decreasing by a running maximum, so
-// the ranges partition [0, n_docs) even when indptr is corrupt (the tiles'
-// validation then sees every document once).  The batch's offsets are read
-// into shared memory first (one coalesced pass) when they fit `cap` entries.
+// What a pass launch needs before it starts, in one launch:
+// * blocks [0, s1 - s0): per step, the n_blocks + 1 split points of its
+//   documents.  split_i is the first document whose start offset reaches
+//   i nnz / n_blocks (a lower bound by binary search on indptr), made
+//   non-decreasing by a running maximum, so the ranges partition
+//   [0, n_docs) even when indptr is corrupt (the tiles' validation then sees
+//   every document once).  The batch's offsets are read into shared memory
+//   first (one coalesced pass) when they fit `cap` entries;
+// * the blocks after them (when `image`): the BF16 Phi^T image from Phi;
+// * block 0 also clears the pass's control block.
 constexpr int kSplitThreads = 256;
-__global__ void __launch_bounds__(kSplitThreads) k_pass_splits(const BatchDesc *descs, int s0, int s1, PassArgs p,
-                                                              int grid, int *splits, int cap) {
+constexpr int kPrepImgBlocks = 8;
+__global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int image, PassArgs p, int grid, int *splits,
+                                                            int cap) {
   extern __shared__ int s_ip[];
   __shared__ int s_wmax[kSplitThreads / 32];
-  const int s = s0 + blockIdx.x;
-  if (s >= s1) return;
-  const BatchDesc b = descs[s];
+  const int n_steps = p.s1 - p.s0;
+  if (blockIdx.x == 0) {
+    unsigned int *w = reinterpret_cast<unsigned int *>(p.ctl);
+    for (int i = threadIdx.x; i < (int)(sizeof(PassCtl) / sizeof(unsigned int)); i += kSplitThreads) w[i] = 0u;
+  }
+  if ((int)blockIdx.x >= n_steps) {
+    if (image) phi_img_groups(a, (blockIdx.x - n_steps) * kSplitThreads + threadIdx.x, kPrepImgBlocks * kSplitThreads);
+    return;
+  }
+  const int s = p.s0 + blockIdx.x;
+  const BatchDesc b = p.descs[s];
   const int nd = b.n_docs;
   const int n_blocks = pass_data_blocks(p, grid, nd), stride = p.split_stride;
   const bool in_smem = nd + 1 <= cap;
@@ -1052,7 +1065,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       ctl->S3[slot ^ 1] = 0;
       ctl->loss_data[slot ^ 1] = 0.0;
       ctl->loss_phi[slot ^ 1] = 0.0;
-      ctl->col_next[slot ^ 1] = 0;
     }
     if (s + 1 < p.s1) {  // waited for in the next step, once its first tile is requested
       grid_arrive(ctl);
@@ -1098,15 +1110,16 @@ cudaError_t launch_barrier_selftest(PassCtl *ctl, cudaStream_t s, int grid) {
                                      0, s);
 }
 
-cudaError_t launch_pass_splits(const BatchDesc *descs, int s0, int s1, const PassArgs &p, int grid, int max_docs,
-                               cudaStream_t s) {
-  if (s1 <= s0) return cudaSuccess;
+cudaError_t launch_pass_prep(const StepArgs &a, bool image, const PassArgs &p, int grid, int max_docs,
+                             cudaStream_t s) {
+  if (p.s1 <= p.s0) return cudaSuccess;
   if (grid < 2 || p.split_stride < grid + 1) return cudaErrorInvalidValue;
   // the offsets of batches up to 11,999 documents go through shared memory
   // (at most 48,000 bytes: within the default dynamic shared-memory limit)
   const int cap = max_docs + 1 <= 12000 ? max_docs + 1 : 0;
-  k_pass_splits<<<s1 - s0, kSplitThreads, (size_t)cap * sizeof(int), s>>>(descs, s0, s1, p, grid,
-                                                                        const_cast<int *>(p.splits), cap);
+  const int blocks = (p.s1 - p.s0) + (image ? kPrepImgBlocks : 0);
+  k_pass_prep<<<blocks, kSplitThreads, (size_t)cap * sizeof(int), s>>>(a, image ? 1 : 0, p, grid,
+                                                                      const_cast<int *>(p.splits), cap);
   return cudaGetLastError();
 }
 

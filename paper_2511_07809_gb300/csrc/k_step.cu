@@ -315,19 +315,7 @@ void launch_phi_terms(const StepArgs &a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ Phi^T image (BF16 forms)
-__global__ void k_phi_img(StepArgs a) {
-  const int groups = a.Kp * (a.Dp / 8);
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
-    const int n = g % a.Kp, kc = g / a.Kp;
-    __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int k = kc * 8 + q;
-      v[q] = __float2bfloat16_rn((k < a.D && n < a.K) ? a.Phi[(long long)k * a.K + n] : 0.f);
-    }
-    *reinterpret_cast<uint4 *>(a.PhiImg + phi_img_index(n, kc * 8, a.Kp)) = *reinterpret_cast<const uint4 *>(v);
-  }
-}
+__global__ void k_phi_img(StepArgs a) { phi_img_groups(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x); }
 
 void launch_phi_img(const StepArgs &a, cudaStream_t s) { k_phi_img<<<16, 256, 0, s>>>(a); }
 

@@ -220,21 +220,34 @@ constexpr int kTuneBatches = 128;
 constexpr int kPassEBlocks = 8;
 constexpr int kPassSmallDocs = 2560;
 
+// Capacity, in steps, of the descriptor, split-point and pinned staging
+// buffers: at least kDescsMin on first use, then doubled, so that a pass
+// longer than the one before rarely reallocates (cudaMalloc, cudaFree and
+// cudaMallocHost synchronise with the device).
+constexpr int kDescsMin = 4096;
+int desc_capacity(int have, int n) {
+  const int grown = have > (1 << 29) ? n : 2 * have;
+  return std::max(n, std::max(kDescsMin, grown));
+}
+
 tlda_status ensure_descs(tlda_ctx *ctx, int n) {
   if (ctx->descs_cap < n) {
+    const int cap = desc_capacity(ctx->descs_cap, n);
     dfree(ctx->descs);
     dfree(ctx->splits);
     ctx->descs_cap = 0;
-    CK(dalloc(&ctx->descs, (size_t)n));
-    CK(dalloc(&ctx->splits, (size_t)n * (ctx->pass_grid + 1)));
-    ctx->descs_cap = n;
+    CK(dalloc(&ctx->descs, (size_t)cap));
+    CK(dalloc(&ctx->splits, (size_t)cap * (ctx->pass_grid + 1)));
+    ctx->descs_cap = cap;
   }
   return TLDA_OK;
 }
 
-// One cooperative launch: steps [s0, s1) of the descriptors in ctx->descs.
+// One cooperative launch: steps [s0, s1) of the descriptors in ctx->descs,
+// after the launch that computes their split points, clears the control block
+// and (when `image`) writes the Phi^T image from a.Phi.
 tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int cap, double *dl, int record,
-                        cudaStream_t ps) {
+                        bool image, cudaStream_t ps) {
   PassArgs pa{};
   pa.descs = ctx->descs;
   pa.s0 = s0;
@@ -249,8 +262,7 @@ tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int ca
   pa.e_small_docs = kPassSmallDocs;
   pa.splits = ctx->splits;
   pa.split_stride = ctx->pass_grid + 1;
-  CK(launch_pass_splits(ctx->descs, s0, s1, pa, ctx->pass_grid, ctx->Bmax, ps));
-  CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(PassCtl), ps));
+  CK(launch_pass_prep(a, image, pa, ctx->pass_grid, ctx->Bmax, ps));
   Prof pr(ctx, kPass, ps);
   CK(launch_pass(a, pa, ps, ctx->pass_grid));
   return TLDA_OK;
@@ -298,7 +310,7 @@ tlda_status tune_tiles(tlda_ctx *ctx, const float *Phi, const std::vector<BatchD
       float ms = 0.f;
       for (int rep = 0; rep < 2 && s == TLDA_OK; ++rep) {  // the first run is a warm-up
         cudaEventRecord(e0, ps);
-        s = pass_launch(ctx, a, 0, n, c, nullptr, 0, ps);
+        s = pass_launch(ctx, a, 0, n, c, nullptr, 0, false, ps);
         cudaEventRecord(e1, ps);
         if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
           s = fail(ctx, TLDA_ERR_CUDA, "tile tuning: %s", cudaGetErrorString(cudaGetLastError()));
@@ -416,11 +428,12 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
   // upload is done
   CK(cudaEventSynchronize(ctx->ev_pass1));  // the previous pass's copy is done (a no-op on success paths)
   if (ctx->descs_pin_cap < nb) {
+    const int cap = desc_capacity(ctx->descs_pin_cap, nb);
     if (ctx->descs_pin) cudaFreeHost(ctx->descs_pin);
     ctx->descs_pin = nullptr;
     ctx->descs_pin_cap = 0;
-    CK(cudaMallocHost(&ctx->descs_pin, sizeof(BatchDesc) * (size_t)nb));
-    ctx->descs_pin_cap = nb;
+    CK(cudaMallocHost(&ctx->descs_pin, sizeof(BatchDesc) * (size_t)cap));
+    ctx->descs_pin_cap = cap;
   }
   std::memcpy(ctx->descs_pin, hd.data(), sizeof(BatchDesc) * (size_t)nb);
   CK(cudaMemcpyAsync(ctx->descs, ctx->descs_pin, sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, ps));
@@ -428,8 +441,6 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
   a.lr = lr;
   a.Phi = Phi;
   a.want_loss = loss_out ? 1 : 0;
-  launch_phi_img(a, ps);
-  CKL();
   for (size_t g = 0; g + 1 < seg.size() && s == TLDA_OK; ++g) {
     const int b0 = seg[g], b1 = seg[g + 1];
     if (host) {
@@ -448,7 +459,9 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
       CK(cudaEventRecord(ctx->ev_seg[g & 1], cs));
       CK(cudaStreamWaitEvent(ps, ctx->ev_seg[g & 1], 0));
     }
-    s = pass_launch(ctx, a, b0, b1, 0, loss_out ? ctx->dlosses : nullptr, 1, ps);  // each batch's tile size
+    // each batch's own tile size; the Phi^T image before the first segment
+    // (each pass launch keeps it current)
+    s = pass_launch(ctx, a, b0, b1, 0, loss_out ? ctx->dlosses : nullptr, 1, g == 0, ps);
     if (host && s == TLDA_OK) CK(cudaEventRecord(ctx->ev_seg[2 + (g & 1)], ps));
   }
   if (s == TLDA_OK && loss_out)

@@ -66,7 +66,6 @@ struct PassCtl {
   unsigned long long S3[2];
   double loss_data[2];
   double loss_phi[2];
-  unsigned int col_next[2];      // next column of the Phi-only terms to hand out
 };
 
 // Steps [s0, s1) of a pass of the persistent kernel.
@@ -81,7 +80,7 @@ struct PassArgs {
   int e_blocks_small;            //   e_blocks_small of them for a batch of at most
   int e_small_docs;              //   e_small_docs documents (pass_data_blocks)
   const int *splits;             // per step, split_stride entries: the data blocks' document
-  int split_stride;              //   ranges, equal in nonzeros (launch_pass_splits)
+  int split_stride;              //   ranges, equal in nonzeros (launch_pass_prep)
 };
 
 // Element (topic n, feature k) of the B operand Phi^T in the shared-memory
@@ -130,6 +129,25 @@ struct StepArgs {
   float *grad_out;               // D x K or null
   float *gdata_out;              // D x K or null (mode 1)
 };
+
+#ifdef __CUDACC__
+// Groups g = g0, g0 + gs, ... of the BF16 Phi^T image: group g holds the 8
+// features kc*8 .. kc*8+7 of topic n (g = kc*Kp + n) as one 16-byte chunk
+// (zero outside D x K).
+__device__ inline void phi_img_groups(const StepArgs &a, int g0, int gs) {
+  const int groups = a.Kp * (a.Dp / 8);
+  for (int g = g0; g < groups; g += gs) {
+    const int n = g % a.Kp, kc = g / a.Kp;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = kc * 8 + q;
+      v[q] = __float2bfloat16_rn((k < a.D && n < a.K) ? a.Phi[(long long)k * a.K + n] : 0.f);
+    }
+    *reinterpret_cast<uint4 *>(a.PhiImg + phi_img_index(n, kc * 8, a.Kp)) = *reinterpret_cast<const uint4 *>(v);
+  }
+}
+#endif
 
 // An NVTX range around one C-ABI call (named by the function; free when no
 // profiler is attached).
@@ -256,7 +274,7 @@ cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, in
 // with range i = [split_i, split_{i+1}) equal in nonzeros (lower bounds of
 // i nnz / n), non-decreasing.  max_docs: the largest batch among the steps
 // (sizes the shared-memory offsets).
-cudaError_t launch_pass_splits(const BatchDesc *descs, int s0, int s1, const PassArgs &p, int grid, int max_docs,
+cudaError_t launch_pass_prep(const StepArgs &a, bool image, const PassArgs &p, int grid, int max_docs,
                                cudaStream_t s);
 
 constexpr int kPassPhiCols = 8;  // Phi-only columns per job of the pass kernel (a multiple of 4, <= 16)
