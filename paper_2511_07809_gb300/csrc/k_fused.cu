@@ -32,6 +32,8 @@
 //      image the next step's MMAs read.
 // Every wait (mbarrier or grid barrier) is bounded; an expired wait sets an
 // abort flag that ends every block's loop and is reported as a timeout.
+#include <algorithm>
+
 #include "tc_ptx.cuh"
 
 namespace tlda {
@@ -320,18 +322,117 @@ struct Fused {
     tc_fence_before();
   }
 
+  // Tile header: the row offsets of documents [d0, d0 + Te) into s_ptr
+  // (checked), the token counts and the window state cleared.
+  __device__ void tile_head(const BatchDesc &b, int d0, int Te) {
+    if (tid <= Te) s_ptr[tid] = b.indptr[d0 + tid];
+    if (tid < kT) s_L[tid] = 0;
+    if (tid == 0) {
+      sh[1] = 0;
+      sh[2] = -1;
+    }
+    __syncthreads();
+    if (tid < Te && (s_ptr[tid + 1] < s_ptr[tid] || s_ptr[tid] < b.nz_base)) sh[1] = 1;
+  }
+
+  // Metadata of nonzeros [w0, w0 + kWin) of the tile (nonzeros nz0 .. nz0 +
+  // nnz of Te documents); pass 1 (check) also validates the entries and adds
+  // the documents' token counts.
+  __device__ void load_window(const StepArgs &a, const BatchDesc &b, int nz0, int nnz, int Te, int w0, bool check) {
+    constexpr int kPer = kWin / kFusedThreads;
+    int mr[kPer], fr[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {  // all loads in flight first
+      const int j = w0 + tid + u * kFusedThreads;
+      mr[u] = -1;
+      fr[u] = 0;
+      if (j < nnz) {
+        mr[u] = __ldg(b.indices + ((long long)(nz0 + j) - b.nz_base));
+        fr[u] = __ldg(b.counts + ((long long)(nz0 + j) - b.nz_base));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int t = tid + u * kFusedThreads, j = w0 + t;
+      int dd = 0;
+      float f = 0.f;
+      if (j < nnz) {
+        const int p = nz0 + j;
+        int lo = 0, hi = Te - 1;  // last document whose range starts at or before p
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_ptr[mid] <= p) lo = mid;
+          else hi = mid - 1;
+        }
+        dd = lo;
+        const bool valid = mr[u] >= 0 && mr[u] < a.V && fr[u] > 0;
+        f = valid ? (float)fr[u] : 0.f;
+        if (check) {
+          if (!valid) sh[1] = 1;
+          else atomicAdd(s_L + dd, fr[u]);
+        }
+      }
+      s_m[t] = mr[u];
+      s_f[t] = f;
+      s_d[t] = dd;
+    }
+    __syncthreads();
+    if (check) {  // words strictly ascending within a document
+      for (int t = tid; t < kWin; t += kFusedThreads) {
+        const int j = w0 + t;
+        if (j < nnz && nz0 + j > s_ptr[s_d[t]]) {
+          const int mp = t > 0 ? s_m[t - 1] : sh[2];
+          if (s_m[t] <= mp) sh[1] = 1;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) sh[2] = s_m[kWin - 1];
+    }
+  }
+
+  // cp.async gather of the BF16 U rows of window chunk c into buffer buf.
+  __device__ void gather(const StepArgs &a, int c, int buf) {
+    unsigned char *sU = sm + (buf ? kOffU1 : kOffU0);
+    for (int pce = tid; pce < kChunk * 16; pce += kFusedThreads) {
+      const int r = pce >> 4, pc = pce & 15;
+      const int m = s_m[c * kChunk + r];
+      unsigned char *dst = sU + (pc >> 3) * 16384 + sw_chunk(r, pc & 7);
+      if (m >= 0 && m < a.V) cp_async16(dst, a.U16 + (long long)m * a.Dp + pc * 8);
+      else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    cp_async_commit();
+  }
+
+  // The first tile of batch b (tiles of td documents) requested ahead, by
+  // every thread: its header, its first window's metadata and the U rows of
+  // its first two chunks (still in flight on return).  A later
+  // tiles(..., prefetched = true) on the same batch starts from them.  Uses
+  // s_ptr, the window metadata and both U buffers.
+  __device__ void prefetch(const StepArgs &a, const BatchDesc &b, int td) {
+    if (b.n_docs <= 0) return;
+    const int Te = min(td, b.n_docs);
+    tile_head(b, 0, Te);
+    const int nz0 = s_ptr[0], nnz = max(0, s_ptr[Te] - nz0);
+    if (nnz == 0) return;
+    const int wch = min(kWin, nnz + kChunk - 1) / kChunk;
+    load_window(a, b, nz0, nnz, Te, 0, true);
+    gather(a, 0, 0);
+    if (wch > 1) gather(a, 1, 1);
+  }
+
   // The data term of tiles tile0, tile0 + tstride, ... of batch b (td <= kT
   // documents each), added to the G columns.  S3 and validation bits go to
   // S3_dst and err_dst, the per-document loss parts to lacc.  Expects the Phi
   // image in shared memory, or (phi_pending) pre() to bring it there: pre()
   // then runs once, by every thread, after the first window's CSR slice and
   // U rows are requested and before the first MMA (it waits for whatever the
-  // image waits for and copies it in; false if that failed).  Returns false
-  // on an expired wait.
+  // image waits for and copies it in; false if that failed).  With
+  // `prefetched`, prefetch(a, b, td) has already requested tile tile0's
+  // header, first window and first U rows.  Returns false on an expired wait.
   template <class Pre = NoPre>
   __device__ bool tiles(const StepArgs &a, const BatchDesc &b, int tile0, int tstride, int td, float &lacc,
                         bool &g_init, unsigned long long *S3_dst, int *err_dst, bool phi_pending = false,
-                        Pre pre = Pre()) {
+                        Pre pre = Pre(), bool prefetched = false) {
     const int nd = b.n_docs;
     const int ntiles = nd > 0 ? (nd + td - 1) / td : 0;
     const uint32_t idQ = idesc_bf16(128, 128);
@@ -354,84 +455,14 @@ struct Fused {
     for (int tile = tile0; tile < ntiles; tile += tstride) {
       if (failed()) break;
       const int d0 = tile * td, Te = min(td, nd - d0);
-      if (tid <= Te) s_ptr[tid] = b.indptr[d0 + tid];
-      if (tid < kT) s_L[tid] = 0;
-      if (tid == 0) {
-        sh[1] = 0;
-        sh[2] = -1;
-      }
-      __syncthreads();
-      if (tid < Te && (s_ptr[tid + 1] < s_ptr[tid] || s_ptr[tid] < b.nz_base)) sh[1] = 1;
+      const bool pf = prefetched && tile == tile0;  // header, first window and U rows requested already
+      if (!pf) tile_head(b, d0, Te);
       const int nz0 = s_ptr[0];
       const int nnz = max(0, s_ptr[Te] - nz0);
       const int nch = (nnz + kChunk - 1) / kChunk;
       const int nwin = (nnz + kWin - 1) / kWin;
-
-      // metadata of nonzeros [w0, w0 + kWin) of the tile; pass 1 also validates
-      // the entries and adds the documents' token counts
-      auto load_window = [&](int w0, bool check) {
-        constexpr int kPer = kWin / kFusedThreads;
-        int mr[kPer], fr[kPer];
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {  // all loads in flight first
-          const int j = w0 + tid + u * kFusedThreads;
-          mr[u] = -1;
-          fr[u] = 0;
-          if (j < nnz) {
-            mr[u] = __ldg(b.indices + ((long long)(nz0 + j) - b.nz_base));
-            fr[u] = __ldg(b.counts + ((long long)(nz0 + j) - b.nz_base));
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-          const int t = tid + u * kFusedThreads, j = w0 + t;
-          int dd = 0;
-          float f = 0.f;
-          if (j < nnz) {
-            const int p = nz0 + j;
-            int lo = 0, hi = Te - 1;  // last document whose range starts at or before p
-            while (lo < hi) {
-              const int mid = (lo + hi + 1) >> 1;
-              if (s_ptr[mid] <= p) lo = mid;
-              else hi = mid - 1;
-            }
-            dd = lo;
-            const bool valid = mr[u] >= 0 && mr[u] < a.V && fr[u] > 0;
-            f = valid ? (float)fr[u] : 0.f;
-            if (check) {
-              if (!valid) sh[1] = 1;
-              else atomicAdd(s_L + dd, fr[u]);
-            }
-          }
-          s_m[t] = mr[u];
-          s_f[t] = f;
-          s_d[t] = dd;
-        }
-        __syncthreads();
-        if (check) {  // words strictly ascending within a document
-          for (int t = tid; t < kWin; t += kFusedThreads) {
-            const int j = w0 + t;
-            if (j < nnz && nz0 + j > s_ptr[s_d[t]]) {
-              const int mp = t > 0 ? s_m[t - 1] : sh[2];
-              if (s_m[t] <= mp) sh[1] = 1;
-            }
-          }
-          __syncthreads();
-          if (tid == 0) sh[2] = s_m[kWin - 1];
-        }
-      };
-      // cp.async gather of the BF16 U rows of window chunk c into buffer buf
-      auto gather = [&](int c, int buf) {
-        unsigned char *sU = sm + (buf ? kOffU1 : kOffU0);
-        for (int pce = tid; pce < kChunk * 16; pce += kFusedThreads) {
-          const int r = pce >> 4, pc = pce & 15;
-          const int m = s_m[c * kChunk + r];
-          unsigned char *dst = sU + (pc >> 3) * 16384 + sw_chunk(r, pc & 7);
-          if (m >= 0 && m < a.V) cp_async16(dst, a.U16 + (long long)m * a.Dp + pc * 8);
-          else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
-        }
-        cp_async_commit();
-      };
+      auto load_window = [&](int w0, bool check) { this->load_window(a, b, nz0, nnz, Te, w0, check); };
+      auto gather = [&](int c, int buf) { this->gather(a, c, buf); };
       // Q chunk = U chunk Phi (rows = nonzeros) into TMEM buffer buf; committed
       // to barrier 2 + buf
       auto issue_q = [&](int buf) {
@@ -456,9 +487,11 @@ struct Fused {
       // The Q product of chunk c+1 runs while chunk c's Q rows are read out.
       for (int w = 0; w < nwin && !failed(); ++w) {
         const int w0 = w * kWin, wch = min(kWin, nnz - w0 + kChunk - 1) / kChunk, gb = w0 / kChunk;
-        load_window(w0, true);
-        gather(0, gb & 1);
-        if (wch > 1) gather(1, (gb + 1) & 1);
+        if (!(pf && w == 0)) {
+          load_window(w0, true);
+          gather(0, gb & 1);
+          if (wch > 1) gather(1, (gb + 1) & 1);
+        }
         if (wch > 1) cp_async_wait_one();
         else cp_async_wait_all();
         put_f(0, true);
@@ -667,7 +700,9 @@ __device__ bool grid_wait(PassCtl *ctl, unsigned target, int *s_ok) {
   if (threadIdx.x == 0) {
     int ok = 1;
     const long long t0 = clock64();
+    unsigned polls = 0;
     while (ld_acquire(&ctl->bar) < target) {
+      if ((++polls & 15u) != 0u) continue;
       if (*reinterpret_cast<volatile int *>(&ctl->abort)) {
         ok = 0;
         break;
@@ -682,11 +717,6 @@ __device__ bool grid_wait(PassCtl *ctl, unsigned target, int *s_ok) {
   }
   __syncthreads();
   return *reinterpret_cast<volatile int *>(s_ok) != 0;
-}
-
-__device__ bool grid_sync(PassCtl *ctl, unsigned target, int *s_ok) {
-  grid_arrive(ctl);
-  return grid_wait(ctl, target, s_ok);
 }
 
 // Self-test of the bounded grid barrier: block 0 never arrives, so every
@@ -799,28 +829,37 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
   double last_loss = 0.0;
   unsigned long long last_S3 = 0;
 
-  for (int s = p.s0; s < p.s1; ++s) {
-    const int slot = s & 1;
+  // this block's documents of step s: [d_lo, d_hi), an equal share of the
+  // batch's nonzeros, in tiles of td <= cap documents; false for a block
+  // without documents (the last blocks take only the Phi-only columns)
+  auto block_range = [&](int s, BatchDesc &bs, int &td) -> bool {
     const BatchDesc b = p.descs[s];
     const int nd = b.n_docs;
     const int cap = p.tile_cap > 0 ? p.tile_cap : (b.tile_cap > 0 ? b.tile_cap : 32);
+    const int nwork = nd > 0 ? pass_data_blocks(p, G, nd) : 0;
+    bs = b;
+    td = 1;
+    if (blk >= nwork) return false;
+    const int *sp = p.splits + (long long)s * p.split_stride + blk;
+    const int d_lo = sp[0], d_hi = sp[1];
+    bs.indptr = b.indptr + d_lo;
+    bs.n_docs = max(0, d_hi - d_lo);
+    const int nt = (bs.n_docs + cap - 1) / cap;
+    td = nt > 0 ? (bs.n_docs + nt - 1) / nt : 1;
+    return true;
+  };
+  bool prefetched = false;  // this step's first tile requested during the previous step
+
+  for (int s = p.s0; s < p.s1; ++s) {
+    const int slot = s & 1;
+    const int nd = p.descs[s].n_docs;
     // the last e_blocks blocks take no tiles: they start on the Phi-only
     // columns as soon as the step begins
     const int Gd = pass_data_blocks(p, G, nd);
-    // this block's documents [d_lo, d_hi): equal shares of the batch's
-    // nonzeros, in tiles of at most `cap` documents
     const int nwork = nd > 0 ? Gd : 0;
-    const bool has = blk < nwork;
-    BatchDesc bs = b;
-    int td = 1;
-    if (has) {
-      const int *sp = p.splits + (long long)s * p.split_stride + blk;
-      const int d_lo = sp[0], d_hi = sp[1];
-      bs.indptr = b.indptr + d_lo;
-      bs.n_docs = max(0, d_hi - d_lo);
-      const int nt = (bs.n_docs + cap - 1) / cap;
-      td = nt > 0 ? (bs.n_docs + nt - 1) / nt : 1;
-    }
+    BatchDesc bs;
+    int td;
+    const bool has = block_range(s, bs, td);
 
     // ---------------- phase A: the data term of this block's tiles.  The
     // first tile's CSR slice and U rows are requested before the wait for the
@@ -843,7 +882,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     if (has) {
       float lacc = 0.f;
       bool g_init = false;
-      f.tiles(a, bs, 0, 1, td, lacc, g_init, &ctl->S3[slot], &st->err, true, pre);
+      f.tiles(a, bs, 0, 1, td, lacc, g_init, &ctl->S3[slot], &st->err, true, pre, prefetched);
       if (a.want_loss) {
         const float t = block_sum(lacc, s_red);
         if (tid == 0 && t != 0.f) atomicAdd(&ctl->loss_data[slot], (double)t);
@@ -999,7 +1038,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       __syncthreads();
     }
     if (f.failed() && tid == 0) atomicExch(&ctl->abort, 1);
-    if (!grid_sync(ctl, ++nbar * G, &s_ok)) break;
+    grid_arrive(ctl);
+    ++nbar;
+    // while the other blocks finish phase A: the next step's first tile
+    // (header, first window, first U rows), which needs nothing of this step
+    // (phase B keeps its partial slices in the Q buffers)
+    prefetched = false;
+    if (s + 1 < p.s1 && !f.failed()) {
+      BatchDesc bn;
+      int tdn;
+      if (block_range(s + 1, bn, tdn)) {
+        f.prefetch(a, bn, tdn);
+        prefetched = true;
+      }
+    }
+    if (!grid_wait(ctl, nbar * G, &s_ok)) break;
 
     // ---------------- phase B: sum the partials of this block's entries,
     // grad = E - 3 c3/S3 (G1 + G2), Phi -= lr grad, the Phi^T image
@@ -1015,7 +1068,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     if (e1 > e0 && nwork > 0) {  // this slice of every partial, in 16-byte cp.async pieces
       const int n16 = nwork * per / 4;
       const float4 *src = reinterpret_cast<const float4 *>(a.Gpart + (long long)blk * G * per);
-      float4 *dst = reinterpret_cast<float4 *>(f.sm + kOffU0);
+      float4 *dst = reinterpret_cast<float4 *>(f.sm + kOffQ);  // the Q and Q*Q buffers: 64 KB
       for (int e = tid; e < n16; e += kFusedThreads) cp_async16(dst + e, src + e);
       cp_async_commit();
       cp_async_wait_all();
@@ -1026,7 +1079,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     }
     if (e1 > e0) {
       const int cnt = e1 - e0;  // <= per <= 128
-      const float *sG = reinterpret_cast<const float *>(f.sm + kOffU0);
+      const float *sG = reinterpret_cast<const float *>(f.sm + kOffQ);
       const int q = tid & 127, part = tid >> 7;
       float g4[4] = {0.f, 0.f, 0.f, 0.f};
       if (q < cnt) {
@@ -1077,6 +1130,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     }
   }
   if (tid == 0 && (f.failed() || *reinterpret_cast<volatile int *>(&ctl->abort))) atomicOr(&st->err, kErrTimeout);
+  cp_async_wait_all();  // a prefetch left in flight by an early exit
   f.finish();
 }
 
@@ -1124,6 +1178,11 @@ cudaError_t launch_pass_prep(const StepArgs &a, bool image, const PassArgs &p, i
 }
 
 cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, int grid) {
+  // phase B copies its slice of every data block's partial into the Q and
+  // Q*Q buffers (64 KB)
+  const int per = ((a.D * a.K + grid - 1) / grid + 3) & ~3;
+  const int most = std::max(pass_data_blocks(p, grid, 0), pass_data_blocks(p, grid, p.e_small_docs + 1));
+  if ((long long)most * per * 4 > 65536) return cudaErrorInvalidValue;
   StepArgs aa = a;
   PassArgs pp = p;
   void *args[] = {&aa, &pp};
