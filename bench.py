@@ -145,6 +145,13 @@ class ClockSampler:
                  "-lms", "200", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        # nvidia-smi's start-up (driver queries) would otherwise overlap a
+        # short timed region: wait for its first sample (at most 3 s)
+        t_end = time.time() + 3.0
+        while self.proc is not None and time.time() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.01)
         return self
 
     def stop(self):

@@ -729,79 +729,6 @@ __global__ void k_barrier_selftest(PassCtl *ctl) {
   if (threadIdx.x == 0 && !ok) atomicAdd(&ctl->S3[0], 1ull);
 }
 
-// What a pass launch needs before it starts, in one launch:
-// * blocks [0, s1 - s0): per step, the n_blocks + 1 split points of its
-//   documents.  split_i is the first document whose start offset reaches
-//   i nnz / n_blocks (a lower bound by binary search on indptr), made
-//   non-decreasing by a running maximum, so the ranges partition
-//   [0, n_docs) even when indptr is corrupt (the tiles' validation then sees
-//   every document once).  The batch's offsets are read into shared memory
-//   first (one coalesced pass) when they fit `cap` entries;
-// * the blocks after them (when `image`): the BF16 Phi^T image from Phi;
-// * block 0 also clears the pass's control block.
-constexpr int kSplitThreads = 256;
-constexpr int kPrepImgBlocks = 8;
-__global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int image, PassArgs p, int grid, int *splits,
-                                                            int cap) {
-  extern __shared__ int s_ip[];
-  __shared__ int s_wmax[kSplitThreads / 32];
-  const int n_steps = p.s1 - p.s0;
-  if (blockIdx.x == 0) {
-    unsigned int *w = reinterpret_cast<unsigned int *>(p.ctl);
-    for (int i = threadIdx.x; i < (int)(sizeof(PassCtl) / sizeof(unsigned int)); i += kSplitThreads) w[i] = 0u;
-  }
-  if ((int)blockIdx.x >= n_steps) {
-    if (image) phi_img_groups(a, (blockIdx.x - n_steps) * kSplitThreads + threadIdx.x, kPrepImgBlocks * kSplitThreads);
-    return;
-  }
-  const int s = p.s0 + blockIdx.x;
-  const BatchDesc b = p.descs[s];
-  const int nd = b.n_docs;
-  const int n_blocks = pass_data_blocks(p, grid, nd), stride = p.split_stride;
-  const bool in_smem = nd + 1 <= cap;
-  if (in_smem)
-    for (int d = threadIdx.x; d <= nd; d += kSplitThreads) s_ip[d] = b.indptr[d];
-  __syncthreads();
-  auto ip = [&](int d) -> long long { return in_smem ? s_ip[d] : b.indptr[d]; };
-  const long long base = nd > 0 ? ip(0) : 0;
-  const long long nnz = nd > 0 ? ip(nd) - base : 0;
-  int carry = 0;  // running maximum of the earlier rounds
-  for (int i0 = 0; i0 <= n_blocks; i0 += kSplitThreads) {
-    const int i = i0 + threadIdx.x;
-    int v = 0;
-    if (i <= n_blocks) {
-      v = nd;
-      if (i == 0) {
-        v = 0;
-      } else if (i < n_blocks && nnz > 0) {
-        const long long target = base + nnz * i / n_blocks;
-        int lo = 0, hi = nd;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (ip(mid) < target) lo = mid + 1;
-          else hi = mid;
-        }
-        v = lo;
-      }
-      v = min(v, nd);
-    }
-    // inclusive running maximum over this round (warp shuffles, then the warps)
-    int m = max(v, carry);
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, m, o);
-      if ((threadIdx.x & 31) >= o) m = max(m, t);
-    }
-    if ((threadIdx.x & 31) == 31) s_wmax[threadIdx.x >> 5] = m;
-    __syncthreads();
-    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) m = max(m, s_wmax[w]);
-    if (i <= n_blocks) splits[(long long)s * stride + i] = i == n_blocks ? nd : m;
-    __syncthreads();
-    carry = s_wmax[0];
-    for (int w = 1; w < kSplitThreads / 32; ++w) carry = max(carry, s_wmax[w]);
-    __syncthreads();
-  }
-}
-
 __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ float s_red[kFusedThreads / 32];
@@ -1162,19 +1089,6 @@ cudaError_t launch_barrier_selftest(PassCtl *ctl, cudaStream_t s, int grid) {
   void *args[] = {&ctl};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_barrier_selftest), dim3(grid), dim3(32), args,
                                      0, s);
-}
-
-cudaError_t launch_pass_prep(const StepArgs &a, bool image, const PassArgs &p, int grid, int max_docs,
-                             cudaStream_t s) {
-  if (p.s1 <= p.s0) return cudaSuccess;
-  if (grid < 2 || p.split_stride < grid + 1) return cudaErrorInvalidValue;
-  // the offsets of batches up to 11,999 documents go through shared memory
-  // (at most 48,000 bytes: within the default dynamic shared-memory limit)
-  const int cap = max_docs + 1 <= 12000 ? max_docs + 1 : 0;
-  const int blocks = (p.s1 - p.s0) + (image ? kPrepImgBlocks : 0);
-  k_pass_prep<<<blocks, kSplitThreads, (size_t)cap * sizeof(int), s>>>(a, image ? 1 : 0, p, grid,
-                                                                      const_cast<int *>(p.splits), cap);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, int grid) {
