@@ -967,6 +967,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     if (f.failed() && tid == 0) atomicExch(&ctl->abort, 1);
     grid_arrive(ctl);
     ++nbar;
+    if (blk >= Gd && s + 2 < p.s1) {
+      // a Phi-only block, done before the data blocks: batch s + 2's CSR
+      // into L2 (the lines dealt round-robin over this step's Phi-only
+      // blocks), so that its first-tile requests meet L2, not HBM
+      const BatchDesc b2 = p.descs[s + 2];
+      const int *nz2 = p.splits + (long long)(s + 2) * p.split_stride + p.split_stride - 2;
+      const long long lo = nz2[0], hi = nz2[1];
+      if (b2.n_docs > 0 && lo >= 0 && hi > lo) {
+        const int e_idx = blk - Gd, e_cnt = G - Gd;
+        l2_prefetch_lines(b2.indptr, (long long)(b2.n_docs + 1) * 4, e_idx, e_cnt);
+        l2_prefetch_lines(b2.indices + lo, (hi - lo) * 4, e_idx, e_cnt);
+        l2_prefetch_lines(b2.counts + lo, (hi - lo) * 4, e_idx, e_cnt);
+      }
+    }
     // while the other blocks finish phase A: the next step's first tile
     // (header, first window, first U rows), which needs nothing of this step
     // (phase B keeps its partial slices in the Q buffers)

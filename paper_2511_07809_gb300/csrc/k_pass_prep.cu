@@ -21,6 +21,9 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
 //   every document once).  The batch's offsets are read into shared memory
 //   first (4-byte cp.async copies, all of a thread's in flight together)
 //   when they fit `cap` entries;
+//   The last two entries of a step's row take the batch's nonzeros [lo, hi)
+//   relative to nz_base, and the blocks of the first two steps bring those
+//   nonzeros' indices and counts into L2;
 // * the blocks after them (when `image`): the BF16 Phi^T image from Phi;
 // * block 0 also clears the pass's control block.
 constexpr int kSplitThreads = 256;
@@ -51,6 +54,16 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int ima
   auto ip = [&](int d) -> long long { return in_smem ? s_ip[d] : b.indptr[d]; };
   const long long base = nd > 0 ? ip(0) : 0;
   const long long nnz = nd > 0 ? ip(nd) - base : 0;
+  if (threadIdx.x == 0) {  // the batch's nonzeros, relative to nz_base
+    splits[(long long)s * stride + stride - 2] = (int)(base - b.nz_base);
+    splits[(long long)s * stride + stride - 1] = (int)(base + nnz - b.nz_base);
+  }
+  if (blockIdx.x < 2 && nd > 0 && nnz > 0 && base >= b.nz_base) {
+    // the first two steps' CSR into L2 (later steps: the pass's Phi-only
+    // blocks, two steps ahead)
+    l2_prefetch_lines(b.indices + (base - b.nz_base), nnz * 4, 0, 1);
+    l2_prefetch_lines(b.counts + (base - b.nz_base), nnz * 4, 0, 1);
+  }
   int carry = 0;  // running maximum of the earlier rounds
   for (int i0 = 0; i0 <= n_blocks; i0 += kSplitThreads) {
     const int i = i0 + threadIdx.x;
@@ -93,7 +106,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int ima
 cudaError_t launch_pass_prep(const StepArgs &a, bool image, const PassArgs &p, int grid, int max_docs,
                              cudaStream_t s) {
   if (p.s1 <= p.s0) return cudaSuccess;
-  if (grid < 2 || p.split_stride < grid + 1) return cudaErrorInvalidValue;
+  if (grid < 2 || p.split_stride < grid + 3) return cudaErrorInvalidValue;
   // the offsets of batches up to 11,999 documents go through shared memory
   // (at most 48,000 bytes: within the default dynamic shared-memory limit)
   const int cap = max_docs + 1 <= 12000 ? max_docs + 1 : 0;

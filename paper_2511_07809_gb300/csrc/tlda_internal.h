@@ -80,7 +80,8 @@ struct PassArgs {
   int e_blocks_small;            //   e_blocks_small of them for a batch of at most
   int e_small_docs;              //   e_small_docs documents (pass_data_blocks)
   const int *splits;             // per step, split_stride entries: the data blocks' document
-  int split_stride;              //   ranges, equal in nonzeros (launch_pass_prep)
+  int split_stride;              //   ranges, equal in nonzeros, and in the last two entries the
+                                 //   batch's nonzeros [lo, hi) relative to nz_base (launch_pass_prep)
 };
 
 // Element (topic n, feature k) of the B operand Phi^T in the shared-memory
@@ -131,6 +132,16 @@ struct StepArgs {
 };
 
 #ifdef __CUDACC__
+// Lines first, first + stride, ... (128 bytes each, line 0 at p) of the
+// `bytes` bytes at p into L2, spread over the threads of this block.  Every
+// address lies inside [p, p + bytes).
+__device__ inline void l2_prefetch_lines(const void *p, long long bytes, int first, int stride) {
+  const char *c = static_cast<const char *>(p);
+  for (long long off = (long long)(first + (long long)threadIdx.x * stride) * 128; off < bytes;
+       off += (long long)stride * 128 * blockDim.x)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
+}
+
 // Groups g = g0, g0 + gs, ... of the BF16 Phi^T image: group g holds the 8
 // features kc*8 .. kc*8+7 of topic n (g = kc*Kp + n) as one 16-byte chunk
 // (zero outside D x K).
