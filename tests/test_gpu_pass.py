@@ -2,7 +2,8 @@
 every step of a pass in one cooperative launch, against the FP64 oracle's
 sequential CP steps (section "Fully Online Implementation", eq. vec_deriv),
 for several tile sizes; host-input staging in several segments against the
-device-input pass; the tile tuner; a corrupt batch in the middle of a pass."""
+device-input pass; empty minibatches inside a pass; the tile tuner; a corrupt
+batch in the middle of a pass."""
 from __future__ import annotations
 
 import numpy as np
@@ -109,6 +110,33 @@ def test_pass_host_segments_equal_device_pass(lib):
     assert torch.equal(Pd, Ph)
     assert np.allclose(ld, lh, rtol=1e-9, atol=0)
     assert np.isfinite(Pd.cpu().numpy()).all()
+    t.close()
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_pass_with_empty_batches_equals_pass_without(lib, host):
+    """Empty minibatches in a persistent pass: first, two in a row in the
+    middle, and last.  An empty batch has S3 = 0, so its step leaves Phi as it
+    is and its loss is 0.  With those steps taken out the pass is the same,
+    bit for bit (fixed tile size, so both passes run the same tiles), and a
+    pass of empty minibatches only changes nothing."""
+    sp = ts.WORKLOADS[NAME]
+    c = C.corpus(NAME, 9000)
+    dev = lib.DeviceCSR.from_corpus(c, device="cpu", pin=True) if host else lib.DeviceCSR.from_corpus(c)
+    with_empty = [0, 0, 700, 700, 700, 4800, 4801, 9000, 9000]
+    without = [0, 700, 4800, 4801, 9000]
+    t, W, m1 = _ctx(lib)
+    t.autotune(fixed=32)
+    Phi0 = torch.tensor(_phi0(sp), dtype=torch.float32, device="cuda")
+    Pa, Pb, Pe = Phi0.clone(), Phi0.clone(), Phi0.clone()
+    la = t.cp_pass(dev, with_empty, Pa, 2e-3, host_input=host, losses=True)
+    lb = t.cp_pass(dev, without, Pb, 2e-3, host_input=host, losses=True)
+    t.cp_pass(dev, [0, 0, 0, 0], Pe, 2e-3, host_input=host)
+    assert torch.equal(Pa, Pb)
+    assert not torch.equal(Pb, Phi0)
+    assert torch.equal(Pe, Phi0)
+    assert la[0] == 0.0 and la[2] == 0.0 and la[3] == 0.0 and la[-1] == 0.0
+    assert np.allclose(la[[1, 4, 5, 6]], lb, rtol=1e-9, atol=0)  # block sums in atomic order
     t.close()
 
 
