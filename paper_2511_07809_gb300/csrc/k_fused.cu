@@ -91,13 +91,16 @@ __device__ __forceinline__ void st_bf16x8(unsigned char *tile, int sub_bytes, in
 
 // One row of B'' = f (z + 2 q^2 - 2 q y) (same-token correction on) or f z
 // (off), 64 topics from col0, staged as BF16 into `tile`; y and z rows of the
-// row's document from shared memory.  With kLoss the row's loss part
-// 2 f sum q^3 is added to lacc (skipped when the caller wants no loss).
+// row's document from shared memory.  Groups of 8 topics that start at or
+// past `ncols` (padding topics, whose G columns are never read) are neither
+// computed nor stored.  With kLoss the row's loss part 2 f sum q^3 is added
+// to lacc (skipped when the caller wants no loss).
 template <bool kSame, bool kLoss>
 __device__ __forceinline__ void b2_row(const float (&q)[64], const float4 *yr, const float4 *zr, float f,
-                                       unsigned char *tile, int row, int col0, float &lacc) {
+                                       unsigned char *tile, int row, int col0, int ncols, float &lacc) {
 #pragma unroll
   for (int i8 = 0; i8 < 8; ++i8) {
+    if (i8 * 8 >= ncols) break;
     float bb[8];
 #pragma unroll
     for (int h4 = 0; h4 < 2; ++h4) {
@@ -123,12 +126,12 @@ __device__ __forceinline__ void b2_row(const float (&q)[64], const float4 *yr, c
 
 __device__ __forceinline__ void b2_row_any(bool same, bool loss, const float (&q)[64], const float4 *yr,
                                            const float4 *zr, float f, unsigned char *tile, int row, int col0,
-                                           float &lacc) {
+                                           int ncols, float &lacc) {
   if (same) {
-    if (loss) b2_row<true, true>(q, yr, zr, f, tile, row, col0, lacc);
-    else b2_row<true, false>(q, yr, zr, f, tile, row, col0, lacc);
+    if (loss) b2_row<true, true>(q, yr, zr, f, tile, row, col0, ncols, lacc);
+    else b2_row<true, false>(q, yr, zr, f, tile, row, col0, ncols, lacc);
   } else {
-    b2_row<false, false>(q, yr, zr, f, tile, row, col0, lacc);
+    b2_row<false, false>(q, yr, zr, f, tile, row, col0, ncols, lacc);
   }
 }
 
@@ -215,6 +218,10 @@ struct Fused {
     // the F^T tile starts (and is kept) at zero; entries are written and cleared per chunk
     for (int e = tid; e < 16384 / 16; e += kFusedThreads)
       reinterpret_cast<uint4 *>(sF)[e] = make_uint4(0u, 0u, 0u, 0u);
+    // the Q and Q*Q tiles start at zero: their padding-topic columns are
+    // never written by the staging, so they only ever hold finite values
+    for (int e = tid; e < 65536 / 16; e += kFusedThreads)
+      reinterpret_cast<uint4 *>(sQ)[e] = make_uint4(0u, 0u, 0u, 0u);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -520,6 +527,7 @@ struct Fused {
             tmem_ld64(colQ0 + buf * 128 + lane_off + half * 64, q);
 #pragma unroll
             for (int i = 0; i < 64; i += 8) {
+              if (half * 64 + i >= a.K) break;  // padding topics: their Y, R rows are never read
               float q2[8];
 #pragma unroll
               for (int u = 0; u < 8; ++u) q2[u] = q[i + u] * q[i + u];
@@ -568,7 +576,7 @@ struct Fused {
           const float r = (dd < Te && a.same_token) ? rv[i] : 0.f;
           sY[dd * kYP + topic] = y;
           sZ[dd * kYP + topic] = y * y - r;
-          if (a.want_loss) lacc += y * (y * y - 3.f * r);
+          if (a.want_loss && topic < a.K) lacc += y * (y * y - 3.f * r);
         }
       }
       if (warp == 0) {
@@ -619,7 +627,7 @@ struct Fused {
             const float4 *zr = reinterpret_cast<const float4 *>(sZ + dd * kYP + half * 64);
             float q[64];
             tmem_ld64(colQ0 + buf * 128 + lane_off + half * 64, q);
-            b2_row_any(a.same_token, a.want_loss, q, yr, zr, f, sQ, row, half * 64, lacc);
+            b2_row_any(a.same_token, a.want_loss, q, yr, zr, f, sQ, row, half * 64, a.K - half * 64, lacc);
           }
           fence_proxy_async();
           tc_fence_before();
