@@ -202,7 +202,11 @@ tlda_status tlda_cp_data_term(tlda_ctx *ctx, const tlda_csr *batch, const float 
  * the device inside the call (double-buffered, each copy overlapped with the
  * compute of the batches before it); otherwise it is in device memory.
  * loss_out (host, n_batches doubles) may be NULL; if given, it receives each
- * step's loss.  Synchronises at the end and returns any sticky status.
+ * step's loss.  An empty batch (equal offsets) is a step with S3 = 0: Phi
+ * unchanged, loss 0.  Synchronises at the end and returns any sticky status.
+ * A device-input pass runs on the context's stream; a host-input pass runs
+ * on internal streams, after the context stream's earlier work and before
+ * its later work.
  *
  * In the BF16 form with D, K in (64, 128] the whole pass runs in one
  * persistent cooperative kernel (host input: one launch per staged

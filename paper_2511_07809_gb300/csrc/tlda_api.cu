@@ -413,9 +413,13 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
     CK(dalloc(&ctx->dlosses, (size_t)nb));
     ctx->dlosses_cap = nb;
   }
-  cudaStream_t ps = ctx->pstream;
-  CK(cudaEventRecord(ctx->ev_pass0, ctx->stream));
-  CK(cudaStreamWaitEvent(ps, ctx->ev_pass0, 0));
+  // a device-input pass runs on the context's stream; a host-input pass on
+  // the pass stream, so that the copy stream's staging overlaps its kernels
+  cudaStream_t ps = host ? ctx->pstream : ctx->stream;
+  if (host) {
+    CK(cudaEventRecord(ctx->ev_pass0, ctx->stream));
+    CK(cudaStreamWaitEvent(ps, ctx->ev_pass0, 0));
+  }
   if (!ctx->tuned && !host) {
     s = tune_tiles(ctx, Phi, std::vector<BatchDesc>(hd.begin(), hd.begin() + std::min(nb, kTuneBatches)), ps);
     if (s) return s;
@@ -424,9 +428,14 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
   s = ensure_descs(ctx, nb);
   if (s) return s;
   // staged through pinned memory, so the upload needs no host wait before
-  // the launch; the pinned copy is rewritten only once the previous pass's
-  // upload is done
-  CK(cudaEventSynchronize(ctx->ev_pass1));  // the previous pass's copy is done (a no-op on success paths)
+  // the launch.  The pinned copy is rewritten only once the previous pass's
+  // upload is done: known once that pass synchronised at its end, waited for
+  // here after a pass that returned before it did
+  if (ctx->descs_pin_busy) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaStreamSynchronize(ctx->pstream));
+    ctx->descs_pin_busy = false;
+  }
   if (ctx->descs_pin_cap < nb) {
     const int cap = desc_capacity(ctx->descs_pin_cap, nb);
     if (ctx->descs_pin) cudaFreeHost(ctx->descs_pin);
@@ -437,6 +446,7 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
   }
   std::memcpy(ctx->descs_pin, hd.data(), sizeof(BatchDesc) * (size_t)nb);
   CK(cudaMemcpyAsync(ctx->descs, ctx->descs_pin, sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, ps));
+  ctx->descs_pin_busy = true;
   StepArgs a = make_args(ctx);
   a.lr = lr;
   a.Phi = Phi;
@@ -466,10 +476,13 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
   }
   if (s == TLDA_OK && loss_out)
     CK(cudaMemcpyAsync(loss_out, ctx->dlosses, sizeof(double) * nb, cudaMemcpyDeviceToHost, ps));
-  CK(cudaEventRecord(ctx->ev_pass1, ps));
-  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_pass1, 0));
+  if (host) {
+    CK(cudaEventRecord(ctx->ev_pass1, ps));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_pass1, 0));
+  }
   if (s) return s;
-  s = read_state(ctx);
+  s = read_state(ctx);  // synchronises the context's stream, which follows the pass
+  if (s == TLDA_OK) ctx->descs_pin_busy = false;
   if (s == TLDA_OK) s = take_sticky(ctx);
   return s;
 }

@@ -204,6 +204,7 @@ struct tlda_ctx {
   int *splits = nullptr;               // per pass step, the data blocks' document ranges (device)
   tlda::BatchDesc *descs_pin = nullptr;  // pinned staging of the persistent pass's descriptors
   int descs_pin_cap = 0;
+  bool descs_pin_busy = false;          // its last upload may still be in flight
   // fit state
   double *P64 = nullptr;               // V x V pair counts (allocated on first ACCUMULATE)
   unsigned long long *Ccnt = nullptr;  // V word totals

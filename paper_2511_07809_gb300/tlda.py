@@ -153,9 +153,16 @@ class DeviceCSR:
         return DeviceCSR.from_arrays(c.indptr, c.indices, c.counts, c.V, device=device, pin=pin)
 
     def struct(self) -> CSR:
-        return CSR(self.n_docs, self.vocab, self.indptr.data_ptr(),
-                   self.indices.data_ptr() if self.indices.numel() else 0,
-                   self.counts.data_ptr() if self.counts.numel() else 0)
+        # built once per set of arrays (a call's marshalling is on the
+        # critical path of a short pass)
+        key = (id(self.indptr), id(self.indices), id(self.counts), self.vocab)
+        cached = self.__dict__.get("_csr")
+        if cached is None or cached[0] != key:
+            cached = (key, CSR(self.n_docs, self.vocab, self.indptr.data_ptr(),
+                               self.indices.data_ptr() if self.indices.numel() else 0,
+                               self.counts.data_ptr() if self.counts.numel() else 0))
+            self.__dict__["_csr"] = cached
+        return cached[1]
 
 
 def _ptr(t):
