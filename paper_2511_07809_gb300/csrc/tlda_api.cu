@@ -213,6 +213,7 @@ tlda_status take_sticky(tlda_ctx *ctx) {
 
 // ------------------------------------------------------------ persistent pass
 constexpr long long kStageWords = 1ll << 23;  // int32 words per host-input staging buffer (32 MB)
+constexpr long long kFirstStageWords = 1ll << 18;  // int32 words of a host-input pass's first segment (1 MB)
 constexpr int kTuneBatches = 128;
 // Blocks of the persistent pass that compute only the Phi-only columns
 // (P, G3 and their loss parts); more of them for small batches, whose data
@@ -376,9 +377,12 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
       CK(dalloc(&ctx->stage[1], (size_t)cap));
       ctx->stage_cap = cap;
     }
+    // the first segment small (about 1 MB), so that the kernels start while
+    // the next segment is still being copied; then whole staging buffers
     for (int b0 = 0; b0 < nb;) {
+      const long long lim = b0 == 0 ? std::min(ctx->stage_cap, kFirstStageWords) : ctx->stage_cap;
       int b1 = b0 + 1;
-      while (b1 < nb && need(b0, b1 + 1) <= ctx->stage_cap) ++b1;
+      while (b1 < nb && need(b0, b1 + 1) <= lim) ++b1;
       seg.push_back(b1);
       b0 = b1;
     }
@@ -407,11 +411,12 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
     }
   }
   tlda_status s = TLDA_OK;
-  if (loss_out && ctx->dlosses_cap < nb) {
+  if (loss_out && ctx->dlosses_cap < nb) {  // grown like the descriptor buffers
+    const int cap = desc_capacity(ctx->dlosses_cap, nb);
     dfree(ctx->dlosses);
     ctx->dlosses_cap = 0;
-    CK(dalloc(&ctx->dlosses, (size_t)nb));
-    ctx->dlosses_cap = nb;
+    CK(dalloc(&ctx->dlosses, (size_t)cap));
+    ctx->dlosses_cap = cap;
   }
   // a device-input pass runs on the context's stream; a host-input pass on
   // the pass stream, so that the copy stream's staging overlaps its kernels
