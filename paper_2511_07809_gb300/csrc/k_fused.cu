@@ -22,14 +22,18 @@
 // k_fused runs the data term of one step (the reduction and the update are
 // separate kernels).  k_pass runs steps [s0, s1) of a pass in one cooperative
 // launch, each step in two phases separated by grid barriers:
-//   A  the first blocks: the data term of the step's batch, in tiles of
-//      ceil(n_docs / blocks) documents (at most tile_cap); then every block
-//      takes columns of the Phi-only terms E = 3(1+theta) P - 3 G3
-//      (P = Phi (Phi^T Phi * Phi^T Phi)) and their loss parts from a counter
-//      until all K are done;
+//   A  the data blocks (all but the last few): the data term of the step's
+//      batch over a range of documents equal in nonzeros (split points from
+//      k_pass_prep), in tiles of at most the batch's tuned size; the last
+//      blocks: the Phi-only terms E = 3(1+theta) P - 3 G3
+//      (P = Phi (Phi^T Phi * Phi^T Phi)) and their loss parts, in jobs of
+//      kPassPhiCols columns dealt round-robin;
 //   B  block b: its slice of the entries of Phi: the partials summed,
 //      grad = E - 3 c3/S3 (G1 + G2), Phi -= lr grad, and the BF16 Phi^T
 //      image the next step's MMAs read.
+// Between its arrival at the mid-step barrier and its wait, a block that has
+// documents in the next step requests that step's first tile, and a Phi-only
+// block brings the CSR of the step after next into L2.
 // Every wait (mbarrier or grid barrier) is bounded; an expired wait sets an
 // abort flag that ends every block's loop and is reported as a timeout.
 #include <algorithm>
@@ -696,8 +700,9 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 // Grid barrier (every block is resident: cooperative launch) in two halves:
 // grid_arrive is a release increment of the launch's monotone arrival
 // counter, grid_wait polls it with acquire loads until it reaches `target`
-// (bounded; false if it expired here, or if any block flagged an abort).
-// Work that needs nothing from the other blocks can run between the two.
+// and checks the abort flag and the bound every 16th poll (bounded; false if
+// it expired here, or if any block flagged an abort).  Work that needs
+// nothing from the other blocks can run between the two.
 __device__ void grid_arrive(PassCtl *ctl) {
   __syncthreads();
   // release: this block's writes (ordered before by the block barrier)
@@ -829,12 +834,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       bar_pending = false;
       if (!grid_wait(ctl, nbar * G, &s_ok)) break;
     }
-    // the Phi-only terms, four columns at a time: the dedicated blocks take
-    // the groups of four columns round-robin (group j to dedicated block
-    // j mod n), a fixed assignment with no counter round trip; with no
-    // dedicated blocks every block takes them the same way.  Phi is staged
-    // once per block (in the U slots; rows padded to K + 1 floats against
-    // bank conflicts).
+    // the Phi-only terms, kPhiCols columns per job: the dedicated blocks take
+    // the jobs round-robin (job j to dedicated block j mod n), a fixed
+    // assignment with no counter round trip; with no dedicated blocks every
+    // block takes them the same way.  Phi is staged once per block (in the U
+    // slots; rows padded to K + 1 floats against bank conflicts).
     const int e_idx = G > Gd ? blk - Gd : blk;  // < 0: a data block, no columns
     const int e_cnt = G > Gd ? G - Gd : G;
     bool staged = false;
