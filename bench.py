@@ -1209,9 +1209,9 @@ def main():
         fused = primary == "bf16" and sp.K <= 128 and sp.K > 64
         per_step_kernels = 5 if fused else 9
         # persistent form: per cp_pass call over a device-resident corpus, the
-        # Phi^T image kernel, the split-point kernel and one pass kernel for
-        # all of its steps
-        launches_timed = (3 * len(timed_segs) if persistent
+        # prologue kernel (split points, Phi^T image, control block) and one
+        # pass kernel for all of its steps
+        launches_timed = (2 * len(timed_segs) if persistent
                           else per_step_kernels * args.steps + len(timed_segs))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
