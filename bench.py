@@ -266,7 +266,8 @@ def segments(seq, n_docs, first):
         off += int(b)
         cur.append(off)
     segs.append(cur)
-    return [s for s in segs if len(s) > 1]
+    # int64 arrays: what the binding passes through without a conversion
+    return [np.asarray(s, dtype=np.int64) for s in segs if len(s) > 1]
 
 
 def distinct_words(c, offs):
@@ -1025,10 +1026,12 @@ def main():
         torch.cuda.synchronize()
         if profile:
             c.profile(profile)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        e1.record()  # both CUDA events exist before the timed region (created at first record)
         flush_l2()
         barrier()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for s in timed_segs:
             c.cp_pass(dev_or_host, s, Phi, LR, host_input=host, losses=losses)
