@@ -25,11 +25,13 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
 //   relative to nz_base, and the blocks of the first two steps bring those
 //   nonzeros' indices and counts into L2;
 // * the blocks after them (when `image`): the BF16 Phi^T image from Phi;
-// * block 0 also clears the pass's control block.
+// * block 0 also clears the pass's control block;
+// * with inline descriptors (a short pass), each step's block takes its
+//   batch's descriptor from the launch parameters and stores it for k_pass.
 constexpr int kSplitThreads = 256;
 constexpr int kPrepImgBlocks = 8;
 __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int image, PassArgs p, int grid, int *splits,
-                                                            int cap) {
+                                                            int cap, InlineDescs inl) {
   extern __shared__ int s_ip[];
   __shared__ int s_wmax[kSplitThreads / 32];
   const int n_steps = p.s1 - p.s0;
@@ -42,7 +44,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int ima
     return;
   }
   const int s = p.s0 + blockIdx.x;
-  const BatchDesc b = p.descs[s];
+  const BatchDesc b = inl.n > 0 ? inl.d[blockIdx.x] : p.descs[s];
+  if (inl.n > 0 && threadIdx.x == 0) const_cast<BatchDesc *>(p.descs)[s] = b;  // for the pass kernel
   const int nd = b.n_docs;
   const int n_blocks = pass_data_blocks(p, grid, nd), stride = p.split_stride;
   const bool in_smem = nd + 1 <= cap;
@@ -104,15 +107,16 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int ima
 }  // namespace
 
 cudaError_t launch_pass_prep(const StepArgs &a, bool image, const PassArgs &p, int grid, int max_docs,
-                             cudaStream_t s) {
+                             const InlineDescs &inl, cudaStream_t s) {
   if (p.s1 <= p.s0) return cudaSuccess;
   if (grid < 2 || p.split_stride < grid + 3) return cudaErrorInvalidValue;
+  if (inl.n != 0 && inl.n != p.s1 - p.s0) return cudaErrorInvalidValue;  // one inline descriptor per step
   // the offsets of batches up to 11,999 documents go through shared memory
   // (at most 48,000 bytes: within the default dynamic shared-memory limit)
   const int cap = max_docs + 1 <= 12000 ? max_docs + 1 : 0;
   const int blocks = (p.s1 - p.s0) + (image ? kPrepImgBlocks : 0);
   k_pass_prep<<<blocks, kSplitThreads, (size_t)cap * sizeof(int), s>>>(a, image ? 1 : 0, p, grid,
-                                                                      const_cast<int *>(p.splits), cap);
+                                                                      const_cast<int *>(p.splits), cap, inl);
   return cudaGetLastError();
 }
 

@@ -248,7 +248,7 @@ tlda_status ensure_descs(tlda_ctx *ctx, int n) {
 // after the launch that computes their split points, clears the control block
 // and (when `image`) writes the Phi^T image from a.Phi.
 tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int cap, double *dl, int record,
-                        bool image, cudaStream_t ps) {
+                        bool image, cudaStream_t ps, const InlineDescs *inl = nullptr) {
   PassArgs pa{};
   pa.descs = ctx->descs;
   pa.s0 = s0;
@@ -263,7 +263,8 @@ tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int ca
   pa.e_small_docs = kPassSmallDocs;
   pa.splits = ctx->splits;
   pa.split_stride = ctx->pass_grid + 3;
-  CK(launch_pass_prep(a, image, pa, ctx->pass_grid, ctx->Bmax, ps));
+  static const InlineDescs kNone{};  // n = 0: the descriptors are in ctx->descs
+  CK(launch_pass_prep(a, image, pa, ctx->pass_grid, ctx->Bmax, inl ? *inl : kNone, ps));
   Prof pr(ctx, kPass, ps);
   CK(launch_pass(a, pa, ps, ctx->pass_grid));
   return TLDA_OK;
@@ -436,12 +437,21 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
   // the launch.  The pinned copy is rewritten only once the previous pass's
   // upload is done: known once that pass synchronised at its end, waited for
   // here after a pass that returned before it did
-  if (ctx->descs_pin_busy) {
+  // A short device-input pass hands its descriptors to the prologue kernel
+  // in the launch parameters instead.
+  const bool inline_descs = !host && nb <= kInlineDescs;
+  InlineDescs inl;
+  inl.n = 0;
+  if (inline_descs) {
+    inl.n = nb;
+    std::memcpy(inl.d, hd.data(), sizeof(BatchDesc) * (size_t)nb);
+  }
+  if (!inline_descs && ctx->descs_pin_busy) {
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaStreamSynchronize(ctx->pstream));
     ctx->descs_pin_busy = false;
   }
-  if (ctx->descs_pin_cap < nb) {
+  if (!inline_descs && ctx->descs_pin_cap < nb) {
     const int cap = desc_capacity(ctx->descs_pin_cap, nb);
     if (ctx->descs_pin) cudaFreeHost(ctx->descs_pin);
     ctx->descs_pin = nullptr;
@@ -449,9 +459,11 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
     CK(cudaMallocHost(&ctx->descs_pin, sizeof(BatchDesc) * (size_t)cap));
     ctx->descs_pin_cap = cap;
   }
-  std::memcpy(ctx->descs_pin, hd.data(), sizeof(BatchDesc) * (size_t)nb);
-  CK(cudaMemcpyAsync(ctx->descs, ctx->descs_pin, sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, ps));
-  ctx->descs_pin_busy = true;
+  if (!inline_descs) {
+    std::memcpy(ctx->descs_pin, hd.data(), sizeof(BatchDesc) * (size_t)nb);
+    CK(cudaMemcpyAsync(ctx->descs, ctx->descs_pin, sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, ps));
+    ctx->descs_pin_busy = true;
+  }
   StepArgs a = make_args(ctx);
   a.lr = lr;
   a.Phi = Phi;
@@ -476,7 +488,8 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
     }
     // each batch's own tile size; the Phi^T image before the first segment
     // (each pass launch keeps it current)
-    s = pass_launch(ctx, a, b0, b1, 0, loss_out ? ctx->dlosses : nullptr, 1, g == 0, ps);
+    s = pass_launch(ctx, a, b0, b1, 0, loss_out ? ctx->dlosses : nullptr, 1, g == 0, ps,
+                    inline_descs ? &inl : nullptr);
     if (host && s == TLDA_OK) CK(cudaEventRecord(ctx->ev_seg[2 + (g & 1)], ps));
   }
   if (s == TLDA_OK && loss_out)

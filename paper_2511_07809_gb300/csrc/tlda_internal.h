@@ -286,7 +286,16 @@ cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, in
 // with range i = [split_i, split_{i+1}) equal in nonzeros (lower bounds of
 // i nnz / n), non-decreasing.  max_docs: the largest batch among the steps
 // (sizes the shared-memory offsets).
+// The descriptors of a short pass, handed to the prologue kernel in its
+// launch parameters (no separate upload); the kernel writes them to
+// PassArgs::descs for the pass kernel.  n = 0: they are there already.
+constexpr int kInlineDescs = 64;
+struct InlineDescs {
+  int n;
+  BatchDesc d[kInlineDescs];
+};
 cudaError_t launch_pass_prep(const StepArgs &a, bool image, const PassArgs &p, int grid, int max_docs,
+                             const InlineDescs &inl,
                                cudaStream_t s);
 
 constexpr int kPassPhiCols = 8;  // Phi-only columns per job of the pass kernel (a multiple of 4, <= 16)
