@@ -73,6 +73,23 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Named block barrier over the n threads (a multiple of 32) that use barrier
+// `id`; id 0 with every thread of the block is __syncthreads().  The _or form
+// also returns whether any of them passed a true `v`.
+__device__ __forceinline__ void bar_sync_n(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ bool bar_or_n(int id, int n, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(v)), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // 8 consecutive values (col multiple of 8, < 128) of row `row` of a
@@ -335,26 +352,31 @@ struct Fused {
 
   // Tile header: the row offsets of documents [d0, d0 + Te) into s_ptr
   // (checked), the token counts and the window state cleared.
-  __device__ void tile_head(const BatchDesc &b, int d0, int Te) {
-    if (tid <= Te) s_ptr[tid] = b.indptr[d0 + tid];
-    if (tid < kT) s_L[tid] = 0;
-    if (tid == 0) {
+  // Run by threads gt = 0 .. gn - 1 (gn >= 64) that share barrier `bid`.
+  __device__ void tile_head(const BatchDesc &b, int d0, int Te, int gt = -1, int gn = kFusedThreads, int bid = 0) {
+    if (gt < 0) gt = tid;
+    if (gt <= Te) s_ptr[gt] = b.indptr[d0 + gt];
+    if (gt < kT) s_L[gt] = 0;
+    if (gt == 0) {
       sh[1] = 0;
       sh[2] = -1;
     }
-    __syncthreads();
-    if (tid < Te && (s_ptr[tid + 1] < s_ptr[tid] || s_ptr[tid] < b.nz_base)) sh[1] = 1;
+    bar_sync_n(bid, gn);
+    if (gt < Te && (s_ptr[gt + 1] < s_ptr[gt] || s_ptr[gt] < b.nz_base)) sh[1] = 1;
   }
 
   // Metadata of nonzeros [w0, w0 + kWin) of the tile (nonzeros nz0 .. nz0 +
   // nnz of Te documents); pass 1 (check) also validates the entries and adds
   // the documents' token counts.
-  __device__ void load_window(const StepArgs &a, const BatchDesc &b, int nz0, int nnz, int Te, int w0, bool check) {
-    constexpr int kPer = kWin / kFusedThreads;
+  template <int kGn = kFusedThreads>
+  __device__ void load_window(const StepArgs &a, const BatchDesc &b, int nz0, int nnz, int Te, int w0, bool check,
+                              int gt = -1, int bid = 0) {
+    constexpr int kPer = kWin / kGn;
+    if (gt < 0) gt = tid;
     int mr[kPer], fr[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {  // all loads in flight first
-      const int j = w0 + tid + u * kFusedThreads;
+      const int j = w0 + gt + u * kGn;
       mr[u] = -1;
       fr[u] = 0;
       if (j < nnz) {
@@ -364,7 +386,7 @@ struct Fused {
     }
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-      const int t = tid + u * kFusedThreads, j = w0 + t;
+      const int t = gt + u * kGn, j = w0 + t;
       int dd = 0;
       float f = 0.f;
       if (j < nnz) {
@@ -387,24 +409,25 @@ struct Fused {
       s_f[t] = f;
       s_d[t] = dd;
     }
-    __syncthreads();
+    bar_sync_n(bid, kGn);
     if (check) {  // words strictly ascending within a document
-      for (int t = tid; t < kWin; t += kFusedThreads) {
+      for (int t = gt; t < kWin; t += kGn) {
         const int j = w0 + t;
         if (j < nnz && nz0 + j > s_ptr[s_d[t]]) {
           const int mp = t > 0 ? s_m[t - 1] : sh[2];
           if (s_m[t] <= mp) sh[1] = 1;
         }
       }
-      __syncthreads();
-      if (tid == 0) sh[2] = s_m[kWin - 1];
+      bar_sync_n(bid, kGn);
+      if (gt == 0) sh[2] = s_m[kWin - 1];
     }
   }
 
   // cp.async gather of the BF16 U rows of window chunk c into buffer buf.
-  __device__ void gather(const StepArgs &a, int c, int buf) {
+  __device__ void gather(const StepArgs &a, int c, int buf, int gt = -1, int gn = kFusedThreads) {
     unsigned char *sU = sm + (buf ? kOffU1 : kOffU0);
-    for (int pce = tid; pce < kChunk * 16; pce += kFusedThreads) {
+    if (gt < 0) gt = tid;
+    for (int pce = gt; pce < kChunk * 16; pce += gn) {
       const int r = pce >> 4, pc = pce & 15;
       const int m = s_m[c * kChunk + r];
       unsigned char *dst = sU + (pc >> 3) * 16384 + sw_chunk(r, pc & 7);
@@ -419,16 +442,18 @@ struct Fused {
   // its first two chunks (still in flight on return).  A later
   // tiles(..., prefetched = true) on the same batch starts from them.  Uses
   // s_ptr, the window metadata and both U buffers.
-  __device__ void prefetch(const StepArgs &a, const BatchDesc &b, int td) {
+  // Run by the 128 threads gt = 0 .. 127 that share barrier `bid` (the
+  // rest of the block may do other work meanwhile).
+  __device__ void prefetch(const StepArgs &a, const BatchDesc &b, int td, int gt, int bid) {
     if (b.n_docs <= 0) return;
     const int Te = min(td, b.n_docs);
-    tile_head(b, 0, Te);
+    tile_head(b, 0, Te, gt, 128, bid);
     const int nz0 = s_ptr[0], nnz = max(0, s_ptr[Te] - nz0);
     if (nnz == 0) return;
     const int wch = min(kWin, nnz + kChunk - 1) / kChunk;
-    load_window(a, b, nz0, nnz, Te, 0, true);
-    gather(a, 0, 0);
-    if (wch > 1) gather(a, 1, 1);
+    load_window<128>(a, b, nz0, nnz, Te, 0, true, gt, bid);
+    gather(a, 0, 0, gt, 128);
+    if (wch > 1) gather(a, 1, 1, gt, 128);
   }
 
   // The data term of tiles tile0, tile0 + tstride, ... of batch b (td <= kT
@@ -746,9 +771,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
   extern __shared__ unsigned char smem_raw[];
   __shared__ float s_red[kFusedThreads / 32];
   __shared__ float s_am[kPhiCols];
-  __shared__ int s_ok;
+  __shared__ int s_ok, s_stop;
   Fused f;
   f.init(smem_raw);
+  if (threadIdx.x == 0) s_stop = 0;
   PassCtl *ctl = p.ctl;
   DevState *st = a.st;
   const int G = gridDim.x, blk = blockIdx.x, tid = f.tid;
@@ -979,99 +1005,114 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     if (f.failed() && tid == 0) atomicExch(&ctl->abort, 1);
     grid_arrive(ctl);
     ++nbar;
-    if (blk >= Gd && s + 2 < p.s1) {
-      // a Phi-only block, done before the data blocks: batch s + 2's CSR
-      // into L2 (the lines dealt round-robin over this step's Phi-only
-      // blocks), so that its first-tile requests meet L2, not HBM
-      const BatchDesc b2 = p.descs[s + 2];
-      const int *nz2 = p.splits + (long long)(s + 2) * p.split_stride + p.split_stride - 2;
-      const long long lo = nz2[0], hi = nz2[1];
-      if (b2.n_docs > 0 && lo >= 0 && hi > lo) {
-        const int e_idx = blk - Gd, e_cnt = G - Gd;
-        l2_prefetch_lines(b2.indptr, (long long)(b2.n_docs + 1) * 4, e_idx, e_cnt);
-        l2_prefetch_lines(b2.indices + lo, (hi - lo) * 4, e_idx, e_cnt);
-        l2_prefetch_lines(b2.counts + lo, (hi - lo) * 4, e_idx, e_cnt);
+    // Between the arrival and phase B the block splits in two groups of four
+    // warps.  Warps 4..7 do what needs nothing of this step's other blocks:
+    // the next step's first tile (header, first window, first U rows) and, in
+    // a Phi-only block, the CSR of the step after next into L2.  Warps 0..3
+    // wait for the barrier and run phase B (partial slices in the Q buffers,
+    // so the two do not touch the same shared memory).  They join before the
+    // end-of-step arrival; a failure is carried past the join in s_stop.
+    BatchDesc bn;
+    int tdn = 1;
+    const bool pf_next = s + 1 < p.s1 && !f.failed() && block_range(s + 1, bn, tdn);
+    if (tid >= 128) {
+      const int gt = tid - 128;
+      if (blk >= Gd && s + 2 < p.s1) {
+        // lines dealt round-robin over this step's Phi-only blocks, so that
+        // the first-tile requests of batch s + 2 meet L2, not HBM
+        const BatchDesc b2 = p.descs[s + 2];
+        const int *nz2 = p.splits + (long long)(s + 2) * p.split_stride + p.split_stride - 2;
+        const long long lo = nz2[0], hi = nz2[1];
+        if (b2.n_docs > 0 && lo >= 0 && hi > lo) {
+          const int e_i = blk - Gd, e_n = G - Gd;
+          l2_prefetch_lines(b2.indptr, (long long)(b2.n_docs + 1) * 4, e_i, e_n, gt, 128);
+          l2_prefetch_lines(b2.indices + lo, (hi - lo) * 4, e_i, e_n, gt, 128);
+          l2_prefetch_lines(b2.counts + lo, (hi - lo) * 4, e_i, e_n, gt, 128);
+        }
       }
-    }
-    // while the other blocks finish phase A: the next step's first tile
-    // (header, first window, first U rows), which needs nothing of this step
-    // (phase B keeps its partial slices in the Q buffers)
-    prefetched = false;
-    if (s + 1 < p.s1 && !f.failed()) {
-      BatchDesc bn;
-      int tdn;
-      if (block_range(s + 1, bn, tdn)) {
-        f.prefetch(a, bn, tdn);
-        prefetched = true;
+      if (pf_next) f.prefetch(a, bn, tdn, gt, 1);
+    } else {
+      // ---------------- phase B (warps 0..3): sum the partials of this
+      // block's entries, grad = E - 3 c3/S3 (G1 + G2), Phi -= lr grad, the
+      // Phi^T image
+      bool ok = true;
+      if (tid == 0) {
+        const long long t0 = clock64();
+        unsigned polls = 0;
+        while (ld_acquire(&ctl->bar) < nbar * G) {
+          if ((++polls & 15u) != 0u) continue;
+          if (*reinterpret_cast<volatile int *>(&ctl->abort) || clock64() - t0 > kWaitCycles) {
+            atomicExch(&ctl->abort, 1);
+            ok = false;
+            break;
+          }
+        }
       }
-    }
-    if (!grid_wait(ctl, nbar * G, &s_ok)) break;
-
-    // ---------------- phase B: sum the partials of this block's entries,
-    // grad = E - 3 c3/S3 (G1 + G2), Phi -= lr grad, the Phi^T image
-    const unsigned long long S3 = *reinterpret_cast<volatile unsigned long long *>(&ctl->S3[slot]);
-    const int err = *reinterpret_cast<volatile int *>(&st->err);
-    const double scale = S3 ? a.c3 / (double)S3 : 0.0;
-    float E_own = 0.f, phi_own = 0.f;  // this thread's entry: loads in flight during the copy
-    if (tid < e1 - e0) {
-      const int e = e0 + tid;
-      E_own = __ldcg(a.E + (e / K) * Kp + e % K);
-      phi_own = __ldcg(a.Phi + e);
-    }
-    if (e1 > e0 && nwork > 0) {  // this slice of every partial, in 16-byte cp.async pieces
-      const int n16 = nwork * per / 4;
-      const float4 *src = reinterpret_cast<const float4 *>(a.Gpart + (long long)blk * G * per);
-      float4 *dst = reinterpret_cast<float4 *>(f.sm + kOffQ);  // the Q and Q*Q buffers: 64 KB
-      for (int e = tid; e < n16; e += kFusedThreads) cp_async16(dst + e, src + e);
-      cp_async_commit();
-      cp_async_wait_all();
-    }
-    if (__syncthreads_or(f.failed())) {
-      if (tid == 0) atomicExch(&ctl->abort, 1);
-      break;
-    }
-    if (e1 > e0) {
-      const int cnt = e1 - e0;  // <= per <= 128
-      const float *sG = reinterpret_cast<const float *>(f.sm + kOffQ);
-      const int q = tid & 127, part = tid >> 7;
-      float g4[4] = {0.f, 0.f, 0.f, 0.f};
-      if (q < cnt) {
-        int c = part;
-        for (; c + 6 < nwork; c += 8) {
+      float E_own = 0.f, phi_own = 0.f;
+      // the other threads of the group learn the barrier's outcome here
+      if (bar_or_n(2, 128, tid == 0 && !ok)) {
+        if (tid == 0) s_stop = 1;
+      } else {
+        const unsigned long long S3g = *reinterpret_cast<volatile unsigned long long *>(&ctl->S3[slot]);
+        const int err = *reinterpret_cast<volatile int *>(&st->err);
+        const double scale = S3g ? a.c3 / (double)S3g : 0.0;
+        if (tid < e1 - e0) {  // this thread's entry: loads in flight during the copy
+          const int e = e0 + tid;
+          E_own = __ldcg(a.E + (e / K) * Kp + e % K);
+          phi_own = __ldcg(a.Phi + e);
+        }
+        if (e1 > e0 && nwork > 0) {  // this slice of every partial, in 16-byte cp.async pieces
+          const int n16 = nwork * per / 4;
+          const float4 *src = reinterpret_cast<const float4 *>(a.Gpart + (long long)blk * G * per);
+          float4 *dst = reinterpret_cast<float4 *>(f.sm + kOffQ);  // the Q and Q*Q buffers: 64 KB
+          for (int e = tid; e < n16; e += 128) cp_async16(dst + e, src + e);
+          cp_async_commit();
+          cp_async_wait_all();
+        }
+        if (bar_or_n(2, 128, f.failed())) {
+          if (tid == 0) {
+            atomicExch(&ctl->abort, 1);
+            s_stop = 1;
+          }
+        } else {
+          if (tid < e1 - e0) {
+            const float *sG = reinterpret_cast<const float *>(f.sm + kOffQ);
+            float g4[4] = {0.f, 0.f, 0.f, 0.f};
+            int c = 0;
+            for (; c + 3 < nwork; c += 4) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) g4[u] += sG[(c + 2 * u) * per + q];
+              for (int u = 0; u < 4; ++u) g4[u] += sG[(c + u) * per + tid];
+            }
+            for (; c < nwork; ++c) g4[0] += sG[c * per + tid];
+            const float g = (g4[0] + g4[1]) + (g4[2] + g4[3]);
+            const int e = e0 + tid, i = e / K, n = e % K;
+            const float grad = S3g ? E_own - (float)(3.0 * scale * (double)g) : 0.f;
+            float phi = phi_own;
+            if (!err && S3g) {
+              phi -= a.lr * grad;
+              a.Phi[e] = phi;
+            }
+            a.PhiImg[phi_img_index(n, i, Kp)] = __float2bfloat16_rn(phi);
+          }
+          if (blk == 0 && tid == 0) {
+            last_S3 = S3g;
+            last_loss = 0.0;
+            if (S3g) {
+              const double lp = *reinterpret_cast<volatile double *>(&ctl->loss_phi[slot]);
+              const double ld = *reinterpret_cast<volatile double *>(&ctl->loss_data[slot]);
+              last_loss = lp - scale * ld;
+            }
+            if (p.losses) p.losses[s] = last_loss;
+            ctl->S3[slot ^ 1] = 0;
+            ctl->loss_data[slot ^ 1] = 0.0;
+            ctl->loss_phi[slot ^ 1] = 0.0;
+          }
         }
-        for (; c < nwork; c += 2) g4[0] += sG[c * per + q];
       }
-      float *red = f.sY;
-      red[part * 128 + q] = (g4[0] + g4[1]) + (g4[2] + g4[3]);
-      __syncthreads();
-      if (tid < cnt) {
-        const int e = e0 + tid, i = e / K, n = e % K;
-        const float g = red[tid] + red[128 + tid];
-        const float grad = S3 ? E_own - (float)(3.0 * scale * (double)g) : 0.f;
-        float phi = phi_own;
-        if (!err && S3) {
-          phi -= a.lr * grad;
-          a.Phi[e] = phi;
-        }
-        a.PhiImg[phi_img_index(n, i, Kp)] = __float2bfloat16_rn(phi);
-      }
-      __syncthreads();
     }
-    if (blk == 0 && tid == 0) {
-      last_S3 = S3;
-      last_loss = 0.0;
-      if (S3) {
-        const double lp = *reinterpret_cast<volatile double *>(&ctl->loss_phi[slot]);
-        const double ld = *reinterpret_cast<volatile double *>(&ctl->loss_data[slot]);
-        last_loss = lp - scale * ld;
-      }
-      if (p.losses) p.losses[s] = last_loss;
-      ctl->S3[slot ^ 1] = 0;
-      ctl->loss_data[slot ^ 1] = 0.0;
-      ctl->loss_phi[slot ^ 1] = 0.0;
-    }
+    __syncthreads();  // the two groups join
+    if (s_stop) break;
+    prefetched = pf_next;
     if (s + 1 < p.s1) {  // waited for in the next step, once its first tile is requested
       grid_arrive(ctl);
       ++nbar;

@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int ima
   if (blockIdx.x < 2 && nd > 0 && nnz > 0 && base >= b.nz_base) {
     // the first two steps' CSR into L2 (later steps: the pass's Phi-only
     // blocks, two steps ahead)
-    l2_prefetch_lines(b.indices + (base - b.nz_base), nnz * 4, 0, 1);
-    l2_prefetch_lines(b.counts + (base - b.nz_base), nnz * 4, 0, 1);
+    l2_prefetch_lines(b.indices + (base - b.nz_base), nnz * 4, 0, 1, threadIdx.x, blockDim.x);
+    l2_prefetch_lines(b.counts + (base - b.nz_base), nnz * 4, 0, 1, threadIdx.x, blockDim.x);
   }
   int carry = 0;  // running maximum of the earlier rounds
   for (int i0 = 0; i0 <= n_blocks; i0 += kSplitThreads) {

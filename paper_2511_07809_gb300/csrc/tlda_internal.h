@@ -133,12 +133,12 @@ struct StepArgs {
 
 #ifdef __CUDACC__
 // Lines first, first + stride, ... (128 bytes each, line 0 at p) of the
-// `bytes` bytes at p into L2, spread over the threads of this block.  Every
+// `bytes` bytes at p into L2, spread over threads t = 0 .. nt - 1.  Every
 // address lies inside [p, p + bytes).
-__device__ inline void l2_prefetch_lines(const void *p, long long bytes, int first, int stride) {
+__device__ inline void l2_prefetch_lines(const void *p, long long bytes, int first, int stride, int t, int nt) {
   const char *c = static_cast<const char *>(p);
-  for (long long off = (long long)(first + (long long)threadIdx.x * stride) * 128; off < bytes;
-       off += (long long)stride * 128 * blockDim.x)
+  for (long long off = (long long)(first + (long long)t * stride) * 128; off < bytes;
+       off += (long long)stride * 128 * nt)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
 }
 
