@@ -1107,14 +1107,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
             ctl->loss_data[slot ^ 1] = 0.0;
             ctl->loss_phi[slot ^ 1] = 0.0;
           }
+          // the end-of-step arrival: only this group wrote what the other
+          // blocks need (Phi, its image, the step's sums), so it arrives
+          // without waiting for the request of warps 4..7
+          if (s + 1 < p.s1) {
+            bar_sync_n(2, 128);  // orders the group's writes before the release
+            if (tid == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar) : "memory");
+          }
         }
       }
     }
     __syncthreads();  // the two groups join
     if (s_stop) break;
     prefetched = pf_next;
-    if (s + 1 < p.s1) {  // waited for in the next step, once its first tile is requested
-      grid_arrive(ctl);
+    if (s + 1 < p.s1) {  // waited for in the next step (the arrival is above)
       ++nbar;
       bar_pending = true;
     } else if (p.record && blk == 0 && tid == 0) {
