@@ -71,6 +71,12 @@ constexpr int kFusedSmem = 1024 + kOffBar + 64;
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -367,27 +373,40 @@ struct Fused {
 
   // Metadata of nonzeros [w0, w0 + kWin) of the tile (nonzeros nz0 .. nz0 +
   // nnz of Te documents); pass 1 (check) also validates the entries and adds
-  // the documents' token counts.
+  // the documents' token counts.  In two halves: window_loads requests the
+  // words and counts of nonzeros nz0 + j, j < lim, into registers (all in
+  // flight together); window_fill files them with their documents (needs
+  // s_ptr) into shared memory, nonzeros past nnz as empty.
   template <int kGn = kFusedThreads>
-  __device__ void load_window(const StepArgs &a, const BatchDesc &b, int nz0, int nnz, int Te, int w0, bool check,
-                              int gt = -1, int bid = 0) {
-    constexpr int kPer = kWin / kGn;
-    if (gt < 0) gt = tid;
-    int mr[kPer], fr[kPer];
+  __device__ void window_loads(const BatchDesc &b, long long nz0, int lim, int w0, int gt, int (&mr)[kWin / kGn],
+                               int (&fr)[kWin / kGn]) {
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) {  // all loads in flight first
+    for (int u = 0; u < kWin / kGn; ++u) {
       const int j = w0 + gt + u * kGn;
       mr[u] = -1;
       fr[u] = 0;
-      if (j < nnz) {
-        mr[u] = __ldg(b.indices + ((long long)(nz0 + j) - b.nz_base));
-        fr[u] = __ldg(b.counts + ((long long)(nz0 + j) - b.nz_base));
+      if (j < lim) {
+        mr[u] = __ldg(b.indices + (nz0 + j - b.nz_base));
+        fr[u] = __ldg(b.counts + (nz0 + j - b.nz_base));
       }
     }
+  }
+  template <int kGn = kFusedThreads>
+  __device__ void load_window(const StepArgs &a, const BatchDesc &b, int nz0, int nnz, int Te, int w0, bool check,
+                              int gt = -1, int bid = 0) {
+    if (gt < 0) gt = tid;
+    int mr[kWin / kGn], fr[kWin / kGn];
+    window_loads<kGn>(b, nz0, nnz, w0, gt, mr, fr);
+    window_fill<kGn>(a, nz0, nnz, Te, w0, check, gt, bid, mr, fr);
+  }
+  template <int kGn = kFusedThreads>
+  __device__ void window_fill(const StepArgs &a, int nz0, int nnz, int Te, int w0, bool check, int gt, int bid,
+                              const int (&mr)[kWin / kGn], const int (&fr)[kWin / kGn]) {
+    constexpr int kPer = kWin / kGn;
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int t = gt + u * kGn, j = w0 + t;
-      int dd = 0;
+      int dd = 0, m = -1;
       float f = 0.f;
       if (j < nnz) {
         const int p = nz0 + j;
@@ -398,14 +417,15 @@ struct Fused {
           else hi = mid - 1;
         }
         dd = lo;
-        const bool valid = mr[u] >= 0 && mr[u] < a.V && fr[u] > 0;
+        m = mr[u];
+        const bool valid = m >= 0 && m < a.V && fr[u] > 0;
         f = valid ? (float)fr[u] : 0.f;
         if (check) {
           if (!valid) sh[1] = 1;
           else atomicAdd(s_L + dd, fr[u]);
         }
       }
-      s_m[t] = mr[u];
+      s_m[t] = m;
       s_f[t] = f;
       s_d[t] = dd;
     }
@@ -442,16 +462,24 @@ struct Fused {
   // its first two chunks (still in flight on return).  A later
   // tiles(..., prefetched = true) on the same batch starts from them.  Uses
   // s_ptr, the window metadata and both U buffers.
+  // nzh is the offset of the tile's first nonzero as the split rows give it,
+  // lim the nonzeros of the batch from there on (at most kWin): the window's
+  // words and counts are requested together with the header's offsets, not
+  // after them (a header that disagrees, only possible for a corrupt batch,
+  // falls back to the plain order).
   // Run by the 128 threads gt = 0 .. 127 that share barrier `bid` (the
   // rest of the block may do other work meanwhile).
-  __device__ void prefetch(const StepArgs &a, const BatchDesc &b, int td, int gt, int bid) {
+  __device__ void prefetch(const StepArgs &a, const BatchDesc &b, int td, int gt, int bid, long long nzh, int lim) {
     if (b.n_docs <= 0) return;
     const int Te = min(td, b.n_docs);
+    int mr[kWin / 128], fr[kWin / 128];
+    window_loads<128>(b, nzh, lim, 0, gt, mr, fr);
     tile_head(b, 0, Te, gt, 128, bid);
     const int nz0 = s_ptr[0], nnz = max(0, s_ptr[Te] - nz0);
     if (nnz == 0) return;
     const int wch = min(kWin, nnz + kChunk - 1) / kChunk;
-    load_window<128>(a, b, nz0, nnz, Te, 0, true, gt, bid);
+    if (nz0 == nzh && min(nnz, kWin) <= lim) window_fill<128>(a, nz0, nnz, Te, 0, true, gt, bid, mr, fr);
+    else load_window<128>(a, b, nz0, nnz, Te, 0, true, gt, bid);
     gather(a, 0, 0, gt, 128);
     if (wch > 1) gather(a, 1, 1, gt, 128);
   }
@@ -767,6 +795,14 @@ __global__ void k_barrier_selftest(PassCtl *ctl) {
   if (threadIdx.x == 0 && !ok) atomicAdd(&ctl->S3[0], 1ull);
 }
 
+// What a block of the pass needs to know of one step before it starts: the
+// batch's descriptor and the block's entries of the step's split row (its
+// documents [d_lo, d_hi), indptr at d_lo, the batch's nonzeros [lo, hi)).
+struct StepPlan {
+  BatchDesc d;
+  int w[5];
+};
+
 __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ float s_red[kFusedThreads / 32];
@@ -789,6 +825,26 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
   const int ldp = K + 1;
   __shared__ float s_m1[128];
   if (tid < 128) s_m1[tid] = tid < D ? a.m1[tid] : 0.f;
+  // the steps' plans in shared memory, three slots (step s in slot
+  // (s - s0) mod 3): the first two now, each later one two steps ahead (by
+  // the second warp group after the mid-step arrival), so that neither the
+  // step's start nor the next step's first-tile request waits for them
+  __shared__ __align__(16) StepPlan s_plan[3];
+  auto request_plan = [&](int s, int t) {  // by threads t = 0 .. 9 (cp.async)
+    if (s >= p.s1 || t < 0 || t >= 10) return;
+    StepPlan *pl = &s_plan[(s - p.s0) % 3];
+    if (t < 5) {
+      cp_async8(reinterpret_cast<char *>(&pl->d) + 8 * t, reinterpret_cast<const char *>(p.descs + s) + 8 * t);
+    } else {
+      const int k = t - 5;
+      const int off = k < 2 ? blk + k : k == 2 ? G + 1 + blk : p.split_stride - 2 + (k - 3);
+      cp_async4(&pl->w[k], p.splits + (long long)s * p.split_stride + off);
+    }
+  };
+  request_plan(p.s0, tid);
+  request_plan(p.s0 + 1, tid - 10);
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   unsigned nbar = 0;
   bool bar_pending = false;
@@ -799,15 +855,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
   // batch's nonzeros, in tiles of td <= cap documents; false for a block
   // without documents (the last blocks take only the Phi-only columns)
   auto block_range = [&](int s, BatchDesc &bs, int &td) -> bool {
-    const BatchDesc b = p.descs[s];
+    const StepPlan &pl = s_plan[(s - p.s0) % 3];
+    const BatchDesc b = pl.d;
     const int nd = b.n_docs;
     const int cap = p.tile_cap > 0 ? p.tile_cap : (b.tile_cap > 0 ? b.tile_cap : 32);
     const int nwork = nd > 0 ? pass_data_blocks(p, G, nd) : 0;
     bs = b;
     td = 1;
     if (blk >= nwork) return false;
-    const int *sp = p.splits + (long long)s * p.split_stride + blk;
-    const int d_lo = sp[0], d_hi = sp[1];
+    const int d_lo = pl.w[0], d_hi = pl.w[1];
     bs.indptr = b.indptr + d_lo;
     bs.n_docs = max(0, d_hi - d_lo);
     const int nt = (bs.n_docs + cap - 1) / cap;
@@ -818,7 +874,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
 
   for (int s = p.s0; s < p.s1; ++s) {
     const int slot = s & 1;
-    const int nd = p.descs[s].n_docs;
+    const int nd = s_plan[(s - p.s0) % 3].d.n_docs;
     // the last e_blocks blocks take no tiles: they start on the Phi-only
     // columns as soon as the step begins
     const int Gd = pass_data_blocks(p, G, nd);
@@ -1003,6 +1059,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
       __syncthreads();
     }
     if (f.failed() && tid == 0) atomicExch(&ctl->abort, 1);
+    cp_async_wait_all();  // the plan requested a step ago (blocks without tiles wait nowhere else)
     grid_arrive(ctl);
     ++nbar;
     // Between the arrival and phase B the block splits in two groups of four
@@ -1017,6 +1074,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const bool pf_next = s + 1 < p.s1 && !f.failed() && block_range(s + 1, bn, tdn);
     if (tid >= 128) {
       const int gt = tid - 128;
+      request_plan(s + 2, gt);
+      cp_async_commit();
       if (blk >= Gd && s + 2 < p.s1) {
         // lines dealt round-robin over this step's Phi-only blocks, so that
         // the first-tile requests of batch s + 2 meet L2, not HBM
@@ -1030,7 +1089,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
           l2_prefetch_lines(b2.counts + lo, (hi - lo) * 4, e_i, e_n, gt, 128);
         }
       }
-      if (pf_next) f.prefetch(a, bn, tdn, gt, 1);
+      if (pf_next) {
+        // the first nonzero of this block's range and the batch's nonzeros
+        // from there on bound the window requested with the header
+        const StepPlan &pn = s_plan[(s + 1 - p.s0) % 3];
+        const long long nzh = pn.w[2];
+        const long long lo = bn.nz_base + max(0, pn.w[3]), hi = bn.nz_base + pn.w[4];
+        const int lim = nzh >= lo && nzh < hi ? (int)min((long long)kWin, hi - nzh) : 0;
+        f.prefetch(a, bn, tdn, gt, 1, nzh, lim);
+      }
     } else {
       // ---------------- phase B (warps 0..3): sum the partials of this
       // block's entries, grad = E - 3 c3/S3 (G1 + G2), Phi -= lr grad, the

@@ -18,7 +18,9 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
 //   i nnz / n_blocks (a lower bound by binary search on indptr), made
 //   non-decreasing by a running maximum, so the ranges partition
 //   [0, n_docs) even when indptr is corrupt (the tiles' validation then sees
-//   every document once).  The batch's offsets are read into shared memory
+//   every document once).  Beside each split point goes indptr there, the
+//   offset of the range's first nonzero (the pass requests a range's first
+//   window of metadata together with its offsets).  The batch's offsets are read into shared memory
 //   first (4-byte cp.async copies, all of a thread's in flight together)
 //   when they fit `cap` entries;
 //   The last two entries of a step's row take the batch's nonzeros [lo, hi)
@@ -96,7 +98,11 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int ima
     if ((threadIdx.x & 31) == 31) s_wmax[threadIdx.x >> 5] = m;
     __syncthreads();
     for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) m = max(m, s_wmax[w]);
-    if (i <= n_blocks) splits[(long long)s * stride + i] = i == n_blocks ? nd : m;
+    if (i <= n_blocks) {
+      const int v_i = i == n_blocks ? nd : m;
+      splits[(long long)s * stride + i] = v_i;
+      splits[(long long)s * stride + grid + 1 + i] = nd > 0 ? (int)ip(v_i) : 0;  // its first nonzero
+    }
     __syncthreads();
     carry = s_wmax[0];
     for (int w = 1; w < kSplitThreads / 32; ++w) carry = max(carry, s_wmax[w]);
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int ima
 cudaError_t launch_pass_prep(const StepArgs &a, bool image, const PassArgs &p, int grid, int max_docs,
                              const InlineDescs &inl, cudaStream_t s) {
   if (p.s1 <= p.s0) return cudaSuccess;
-  if (grid < 2 || p.split_stride < grid + 3) return cudaErrorInvalidValue;
+  if (grid < 2 || p.split_stride < pass_split_stride(grid)) return cudaErrorInvalidValue;
   if (inl.n != 0 && inl.n != p.s1 - p.s0) return cudaErrorInvalidValue;  // one inline descriptor per step
   // the offsets of batches up to 11,999 documents go through shared memory
   // (at most 48,000 bytes: within the default dynamic shared-memory limit)

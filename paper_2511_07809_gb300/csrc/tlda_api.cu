@@ -238,7 +238,7 @@ tlda_status ensure_descs(tlda_ctx *ctx, int n) {
     dfree(ctx->splits);
     ctx->descs_cap = 0;
     CK(dalloc(&ctx->descs, (size_t)cap));
-    CK(dalloc(&ctx->splits, (size_t)cap * (ctx->pass_grid + 3)));
+    CK(dalloc(&ctx->splits, (size_t)cap * pass_split_stride(ctx->pass_grid)));
     ctx->descs_cap = cap;
   }
   return TLDA_OK;
@@ -262,7 +262,7 @@ tlda_status pass_launch(tlda_ctx *ctx, const StepArgs &a, int s0, int s1, int ca
   pa.e_blocks_small = std::max(kPassEBlocks, (ctx->K + kPassPhiCols - 1) / kPassPhiCols);
   pa.e_small_docs = kPassSmallDocs;
   pa.splits = ctx->splits;
-  pa.split_stride = ctx->pass_grid + 3;
+  pa.split_stride = pass_split_stride(ctx->pass_grid);
   static const InlineDescs kNone{};  // n = 0: the descriptors are in ctx->descs
   CK(launch_pass_prep(a, image, pa, ctx->pass_grid, ctx->Bmax, inl ? *inl : kNone, ps));
   Prof pr(ctx, kPass, ps);

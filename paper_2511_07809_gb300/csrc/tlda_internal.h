@@ -79,10 +79,16 @@ struct PassArgs {
   int e_blocks;                  // blocks that take only the Phi-only columns (no data tiles),
   int e_blocks_small;            //   e_blocks_small of them for a batch of at most
   int e_small_docs;              //   e_small_docs documents (pass_data_blocks)
-  const int *splits;             // per step, split_stride entries: the data blocks' document
-  int split_stride;              //   ranges, equal in nonzeros, and in the last two entries the
-                                 //   batch's nonzeros [lo, hi) relative to nz_base (launch_pass_prep)
+  const int *splits;             // per step, split_stride entries (pass_split_stride): the data
+  int split_stride;              //   blocks' document ranges, equal in nonzeros; the offset of
+                                 //   each range's first nonzero; the batch's nonzeros [lo, hi)
+                                 //   relative to nz_base (launch_pass_prep)
 };
+
+// Row of one step in PassArgs::splits for a pass of `grid` blocks: entries
+// 0..grid the split documents, grid+1..2 grid+1 indptr at those documents
+// (absolute offsets), then lo and hi.
+inline int pass_split_stride(int grid) { return 2 * grid + 4; }
 
 // Element (topic n, feature k) of the B operand Phi^T in the shared-memory
 // layout of the tensor-core kernels: (Dp/64) sub-tiles of [Kp rows x 64]
@@ -284,8 +290,9 @@ cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, in
 // Document ranges of the data blocks of steps [s0, s1): for step s, entries
 // s * p.split_stride + i, i = 0..n (n = pass_data_blocks of the step's batch),
 // with range i = [split_i, split_{i+1}) equal in nonzeros (lower bounds of
-// i nnz / n), non-decreasing.  max_docs: the largest batch among the steps
-// (sizes the shared-memory offsets).
+// i nnz / n), non-decreasing; entry grid + 1 + i is indptr[split_i], the
+// offset of range i's first nonzero.  max_docs: the largest batch among the
+// steps (sizes the shared-memory offsets).
 // The descriptors of a short pass, handed to the prologue kernel in its
 // launch parameters (no separate upload); the kernel writes them to
 // PassArgs::descs for the pass kernel.  n = 0: they are there already.
