@@ -44,7 +44,7 @@ namespace tlda {
 namespace {
 using namespace tc;
 
-constexpr int kT = 32;        // documents per tile, at most
+constexpr int kT = kPassTileDocs;  // documents per tile, at most
 constexpr int kChunk = 128;   // nonzeros per chunk
 constexpr int kFusedThreads = 256;
 constexpr int kMinPassGrid = 128;  // at least one block per Phi column (K <= 128)
@@ -492,13 +492,15 @@ struct Fused {
   // U rows are requested and before the first MMA (it waits for whatever the
   // image waits for and copies it in; false if that failed).  With
   // `prefetched`, prefetch(a, b, td) has already requested tile tile0's
-  // header, first window and first U rows.  Returns false on an expired wait.
+  // header, first window and first U rows.  tsplit > 0 (tile0 = 0, tstride = 1)
+  // makes two tiles, documents [0, tsplit) and [tsplit, nd), instead of
+  // tiles of td.  Returns false on an expired wait.
   template <class Pre = NoPre>
   __device__ bool tiles(const StepArgs &a, const BatchDesc &b, int tile0, int tstride, int td, float &lacc,
                         bool &g_init, unsigned long long *S3_dst, int *err_dst, bool phi_pending = false,
-                        Pre pre = Pre(), bool prefetched = false) {
+                        Pre pre = Pre(), bool prefetched = false, int tsplit = 0) {
     const int nd = b.n_docs;
-    const int ntiles = nd > 0 ? (nd + td - 1) / td : 0;
+    const int ntiles = tsplit > 0 ? 2 : nd > 0 ? (nd + td - 1) / td : 0;
     const uint32_t idQ = idesc_bf16(128, 128);
     const uint32_t idYR = idesc_bf16(128, 64) | (1u << 15) | (1u << 16);
     const uint32_t idG = idesc_bf16(128, 128) | (1u << 15) | (1u << 16);
@@ -518,7 +520,8 @@ struct Fused {
 
     for (int tile = tile0; tile < ntiles; tile += tstride) {
       if (failed()) break;
-      const int d0 = tile * td, Te = min(td, nd - d0);
+      const int d0 = tsplit > 0 ? (tile ? tsplit : 0) : tile * td;
+      const int Te = tsplit > 0 ? (tile ? nd - tsplit : tsplit) : min(td, nd - d0);
       const bool pf = prefetched && tile == tile0;  // header, first window and U rows requested already
       if (!pf) tile_head(b, d0, Te);
       const int nz0 = s_ptr[0];
@@ -797,10 +800,11 @@ __global__ void k_barrier_selftest(PassCtl *ctl) {
 
 // What a block of the pass needs to know of one step before it starts: the
 // batch's descriptor and the block's entries of the step's split row (its
-// documents [d_lo, d_hi), indptr at d_lo, the batch's nonzeros [lo, hi)).
+// documents [d_lo, d_hi), indptr at d_lo, the batch's nonzeros [lo, hi), the
+// documents of its first tile when it takes two).
 struct StepPlan {
   BatchDesc d;
-  int w[5];
+  int w[6];
 };
 
 __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs p) {
@@ -830,19 +834,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
   // the second warp group after the mid-step arrival), so that neither the
   // step's start nor the next step's first-tile request waits for them
   __shared__ __align__(16) StepPlan s_plan[3];
-  auto request_plan = [&](int s, int t) {  // by threads t = 0 .. 9 (cp.async)
-    if (s >= p.s1 || t < 0 || t >= 10) return;
+  auto request_plan = [&](int s, int t) {  // by threads t = 0 .. 10 (cp.async)
+    if (s >= p.s1 || t < 0 || t >= 11) return;
     StepPlan *pl = &s_plan[(s - p.s0) % 3];
     if (t < 5) {
       cp_async8(reinterpret_cast<char *>(&pl->d) + 8 * t, reinterpret_cast<const char *>(p.descs + s) + 8 * t);
     } else {
       const int k = t - 5;
-      const int off = k < 2 ? blk + k : k == 2 ? G + 1 + blk : p.split_stride - 2 + (k - 3);
+      const int off = k < 2 ? blk + k : k == 2 ? G + 1 + blk : k < 5 ? p.split_stride - 2 + (k - 3) : 2 * G + 2 + blk;
       cp_async4(&pl->w[k], p.splits + (long long)s * p.split_stride + off);
     }
   };
   request_plan(p.s0, tid);
-  request_plan(p.s0 + 1, tid - 10);
+  request_plan(p.s0 + 1, tid - 11);
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
@@ -854,7 +858,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
   // this block's documents of step s: [d_lo, d_hi), an equal share of the
   // batch's nonzeros, in tiles of td <= cap documents; false for a block
   // without documents (the last blocks take only the Phi-only columns)
-  auto block_range = [&](int s, BatchDesc &bs, int &td) -> bool {
+  // (ts > 0: two tiles, the first of ts documents, as the split rows give them)
+  auto block_range = [&](int s, BatchDesc &bs, int &td, int &ts) -> bool {
     const StepPlan &pl = s_plan[(s - p.s0) % 3];
     const BatchDesc b = pl.d;
     const int nd = b.n_docs;
@@ -862,12 +867,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const int nwork = nd > 0 ? pass_data_blocks(p, G, nd) : 0;
     bs = b;
     td = 1;
+    ts = 0;
     if (blk >= nwork) return false;
     const int d_lo = pl.w[0], d_hi = pl.w[1];
     bs.indptr = b.indptr + d_lo;
     bs.n_docs = max(0, d_hi - d_lo);
     const int nt = (bs.n_docs + cap - 1) / cap;
     td = nt > 0 ? (bs.n_docs + nt - 1) / nt : 1;
+    const int t1 = pl.w[5];
+    if (nt == 2 && t1 > 0 && t1 < bs.n_docs && t1 <= min(cap, kT) && bs.n_docs - t1 <= min(cap, kT)) ts = t1;
     return true;
   };
   bool prefetched = false;  // this step's first tile requested during the previous step
@@ -880,8 +888,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     const int Gd = pass_data_blocks(p, G, nd);
     const int nwork = nd > 0 ? Gd : 0;
     BatchDesc bs;
-    int td;
-    const bool has = block_range(s, bs, td);
+    int td, ts;
+    const bool has = block_range(s, bs, td, ts);
 
     // ---------------- phase A: the data term of this block's tiles.  The
     // first tile's CSR slice and U rows are requested before the wait for the
@@ -904,7 +912,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     if (has) {
       float lacc = 0.f;
       bool g_init = false;
-      f.tiles(a, bs, 0, 1, td, lacc, g_init, &ctl->S3[slot], &st->err, true, pre, prefetched);
+      f.tiles(a, bs, 0, 1, td, lacc, g_init, &ctl->S3[slot], &st->err, true, pre, prefetched, ts);
       if (a.want_loss) {
         const float t = block_sum(lacc, s_red);
         if (tid == 0 && t != 0.f) atomicAdd(&ctl->loss_data[slot], (double)t);
@@ -1070,8 +1078,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     // so the two do not touch the same shared memory).  They join before the
     // end-of-step arrival; a failure is carried past the join in s_stop.
     BatchDesc bn;
-    int tdn = 1;
-    const bool pf_next = s + 1 < p.s1 && !f.failed() && block_range(s + 1, bn, tdn);
+    int tdn = 1, tsn = 0;
+    const bool pf_next = s + 1 < p.s1 && !f.failed() && block_range(s + 1, bn, tdn, tsn);
     if (tid >= 128) {
       const int gt = tid - 128;
       request_plan(s + 2, gt);
@@ -1096,7 +1104,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
         const long long nzh = pn.w[2];
         const long long lo = bn.nz_base + max(0, pn.w[3]), hi = bn.nz_base + pn.w[4];
         const int lim = nzh >= lo && nzh < hi ? (int)min((long long)kWin, hi - nzh) : 0;
-        f.prefetch(a, bn, tdn, gt, 1, nzh, lim);
+        f.prefetch(a, bn, tsn > 0 ? tsn : tdn, gt, 1, nzh, lim);  // the first tile's documents
       }
     } else {
       // ---------------- phase B (warps 0..3): sum the partials of this

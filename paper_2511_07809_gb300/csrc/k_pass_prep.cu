@@ -23,6 +23,8 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
 //   window of metadata together with its offsets).  The batch's offsets are read into shared memory
 //   first (4-byte cp.async copies, all of a thread's in flight together)
 //   when they fit `cap` entries;
+//   For a range that takes two tiles, the documents of the first go beside
+//   them (the boundary with the fewest 128-nonzero chunks in the two).
 //   The last two entries of a step's row take the batch's nonzeros [lo, hi)
 //   relative to nz_base, and the blocks of the first two steps bring those
 //   nonzeros' indices and counts into L2;
@@ -69,6 +71,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int ima
     l2_prefetch_lines(b.indices + (base - b.nz_base), nnz * 4, 0, 1, threadIdx.x, blockDim.x);
     l2_prefetch_lines(b.counts + (base - b.nz_base), nnz * 4, 0, 1, threadIdx.x, blockDim.x);
   }
+  __shared__ int s_spl[kSplitThreads + 1];
   int carry = 0;  // running maximum of the earlier rounds
   for (int i0 = 0; i0 <= n_blocks; i0 += kSplitThreads) {
     const int i = i0 + threadIdx.x;
@@ -102,11 +105,40 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int ima
       const int v_i = i == n_blocks ? nd : m;
       splits[(long long)s * stride + i] = v_i;
       splits[(long long)s * stride + grid + 1 + i] = nd > 0 ? (int)ip(v_i) : 0;  // its first nonzero
+      if (i <= kSplitThreads) s_spl[i] = v_i;
     }
     __syncthreads();
     carry = s_wmax[0];
     for (int w = 1; w < kSplitThreads / 32; ++w) carry = max(carry, s_wmax[w]);
     __syncthreads();
+  }
+  // A range of more than cap documents (at most 2 cap) takes two tiles.  The
+  // pass processes a tile in chunks of 128 nonzeros, so the boundary between
+  // them is the one with the fewest chunks in the two (then the most even),
+  // rather than the middle document.  0: tiles of equal size.
+  const int b_cap = p.tile_cap > 0 ? p.tile_cap : (b.tile_cap > 0 ? b.tile_cap : kPassTileDocs);
+  const int cap2 = min(b_cap, kPassTileDocs);
+  const bool pick = in_smem && nd > 0 && n_blocks < kSplitThreads;
+  for (int i = threadIdx.x; i < n_blocks; i += kSplitThreads) {
+    int t1 = 0;
+    if (pick) {
+      const int da = s_spl[i], D = s_spl[i + 1] - da;
+      if (D > cap2 && D <= 2 * cap2) {
+        const long long za = ip(da), zb = ip(da + D);
+        int best = 1 << 30, even = 1 << 30;
+        for (int m1 = max(1, D - cap2); m1 <= min(D - 1, cap2); ++m1) {
+          const long long zm = ip(da + m1);
+          const long long n1 = zm > za ? zm - za : 0, n2 = zb > zm ? zb - zm : 0;
+          const int c = (int)((n1 + 127) / 128 + (n2 + 127) / 128), e = abs(2 * m1 - D);
+          if (c < best || (c == best && e < even)) {
+            best = c;
+            even = e;
+            t1 = m1;
+          }
+        }
+      }
+    }
+    splits[(long long)s * stride + 2 * grid + 2 + i] = t1;
   }
 }
 

@@ -81,14 +81,17 @@ struct PassArgs {
   int e_small_docs;              //   e_small_docs documents (pass_data_blocks)
   const int *splits;             // per step, split_stride entries (pass_split_stride): the data
   int split_stride;              //   blocks' document ranges, equal in nonzeros; the offset of
-                                 //   each range's first nonzero; the batch's nonzeros [lo, hi)
-                                 //   relative to nz_base (launch_pass_prep)
+                                 //   each range's first nonzero; the first tile of each range
+                                 //   that takes two; the batch's nonzeros [lo, hi) relative to
+                                 //   nz_base (launch_pass_prep)
 };
 
 // Row of one step in PassArgs::splits for a pass of `grid` blocks: entries
 // 0..grid the split documents, grid+1..2 grid+1 indptr at those documents
-// (absolute offsets), then lo and hi.
-inline int pass_split_stride(int grid) { return 2 * grid + 4; }
+// (absolute offsets), 2 grid+2..3 grid+1 the documents of each range's first
+// tile (0: tiles of equal size), then lo and hi.
+inline int pass_split_stride(int grid) { return 3 * grid + 4; }
+constexpr int kPassTileDocs = 32;  // most documents in one tile of the pass kernel
 
 // Element (topic n, feature k) of the B operand Phi^T in the shared-memory
 // layout of the tensor-core kernels: (Dp/64) sub-tiles of [Kp rows x 64]
@@ -291,8 +294,10 @@ cudaError_t launch_pass(const StepArgs &a, const PassArgs &p, cudaStream_t s, in
 // s * p.split_stride + i, i = 0..n (n = pass_data_blocks of the step's batch),
 // with range i = [split_i, split_{i+1}) equal in nonzeros (lower bounds of
 // i nnz / n), non-decreasing; entry grid + 1 + i is indptr[split_i], the
-// offset of range i's first nonzero.  max_docs: the largest batch among the
-// steps (sizes the shared-memory offsets).
+// offset of range i's first nonzero; entry 2 grid + 2 + i, for a range that
+// takes two tiles, the documents of its first tile (the boundary with the
+// fewest 128-nonzero chunks in the two), else 0.  max_docs: the largest batch
+// among the steps (sizes the shared-memory offsets).
 // The descriptors of a short pass, handed to the prologue kernel in its
 // launch parameters (no separate upload); the kernel writes them to
 // PassArgs::descs for the pass kernel.  n = 0: they are there already.
