@@ -112,6 +112,42 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int ima
     for (int w = 1; w < kSplitThreads / 32; ++w) carry = max(carry, s_wmax[w]);
     __syncthreads();
   }
+  // Repair of the range boundaries where a range would need one more
+  // 128-nonzero chunk (or a second tile) than its neighbours: when the
+  // batch averages at most one tile per block, each inner boundary may move
+  // by up to two documents to lower the larger chunk count of its two
+  // ranges (ranges of more than cap documents count as eight more); even
+  // boundaries first, then odd ones (they share no range), twice.
+  const int r_cap = min(p.tile_cap > 0 ? p.tile_cap : (b.tile_cap > 0 ? b.tile_cap : kPassTileDocs), kPassTileDocs);
+  if (in_smem && nd > 0 && n_blocks > 1 && n_blocks < kSplitThreads && nd <= (long long)n_blocks * r_cap) {
+    auto cost = [&](int da, int db) -> int {
+      const long long z = ip(db) - ip(da);
+      return (int)((z > 0 ? z : 0) + 127) / 128 + (db - da > r_cap ? 8 : 0);
+    };
+    for (int round = 0; round < 4; ++round) {
+      const int j = 2 * threadIdx.x + 1 + (round & 1);  // boundary j between ranges j - 1 and j
+      if (j < n_blocks) {
+        const int lo_b = s_spl[j - 1], hi_b = s_spl[j + 1], cur = s_spl[j];
+        int best = max(cost(lo_b, cur), cost(cur, hi_b)), at = cur;
+        for (int dlt = -2; dlt <= 2; ++dlt) {
+          const int c = cur + dlt;
+          if (dlt == 0 || c <= lo_b || c >= hi_b) continue;  // ranges stay non-empty
+          const int v = max(cost(lo_b, c), cost(c, hi_b));
+          if (v < best) {
+            best = v;
+            at = c;
+          }
+        }
+        s_spl[j] = at;
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i <= n_blocks; i += kSplitThreads) {
+      splits[(long long)s * stride + i] = s_spl[i];
+      splits[(long long)s * stride + grid + 1 + i] = (int)ip(s_spl[i]);
+    }
+    __syncthreads();
+  }
   // A range of more than cap documents (at most 2 cap) takes two tiles.  The
   // pass processes a tile in chunks of 128 nonzeros, so the boundary between
   // them is the one with the fewest chunks in the two (then the most even),
