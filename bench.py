@@ -8,9 +8,11 @@ A step is one pass of the whole hot path over one minibatch: CSR scan and
 validation, demean + whiten (SpMM), Y = X Phi, Q = U Phi, the same-token terms,
 the data-term contraction, the Dirichlet/M1 corrections, the orthogonality
 term and the SGD update.  `value` is device-resident throughput (corpus
-already in HBM); `e2e` goes through the host-input pass of the public API
-(every step's CSR copied host->device inside the timed region, every step's
-loss read back).
+already in HBM): the timed calls are the library's no-wait passes, which
+return once the pass is enqueued, so the timed region ends with the pass's
+last kernel (the device status is read after it).  `e2e` goes through the
+host-input pass of the public API, which waits (every step's CSR copied
+host->device inside the timed region, every step's loss read back).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --online [--online-every E] [--online-r R]   (fully online mode)
@@ -1018,12 +1020,16 @@ def main():
     timed_segs = segments(seq[args.warmup:], n_docs, last_off)
     n_timed_docs = int(seq[args.warmup:].sum())
 
-    def timed(c, Phi, host=False, losses=False, profile=()):
+    def timed(c, Phi, host=False, losses=False, profile=(), wait=True):
+        # wait=False: the device-resident calls return once the pass is
+        # enqueued (the library's no-wait mode); their status is read by
+        # sync() after the timed region
         nonlocal dev_or_host
         dev_or_host = host_corpus if host else dev
         for s in warm_segs:  # the same calls as the timed ones (buffers sized before timing)
-            c.cp_pass(dev_or_host, s, Phi, LR, host_input=host, losses=losses)
+            c.cp_pass(dev_or_host, s, Phi, LR, host_input=host, losses=losses, wait=wait)
         torch.cuda.synchronize()
+        c.sync()
         if profile:
             c.profile(profile)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1034,9 +1040,10 @@ def main():
         torch.cuda.synchronize()
         e0.record()
         for s in timed_segs:
-            c.cp_pass(dev_or_host, s, Phi, LR, host_input=host, losses=losses)
+            c.cp_pass(dev_or_host, s, Phi, LR, host_input=host, losses=losses, wait=wait)
         e1.record()
         torch.cuda.synchronize()
+        c.sync()
         barrier()
         ms = e0.elapsed_time(e1)
         prof = c.profile_read() if profile else None
@@ -1069,7 +1076,7 @@ def main():
     # 2) the timed region (device-resident corpus), dominant kernel bracketed by events
     sampler = ClockSampler(local).start()
     Phi = Phi0.clone()
-    ms, prof = timed(ctx, Phi, profile=(dominant,))
+    ms, prof = timed(ctx, Phi, profile=(dominant,), wait=False)
     clocks = sampler.stop()
     value, ms_max, docs_all = replica_throughput(ms, float(n_timed_docs), world)
     Phi_final = Phi.clone()

@@ -193,6 +193,7 @@ tlda_status tlda_cp_data_term(tlda_ctx *ctx, const tlda_csr *batch, const float 
                               float *G_data_out, int64_t *S3_out);
 
 #define TLDA_HOST_INPUT 1u     /* corpus arrays are in host memory (pinned for overlap) */
+#define TLDA_NO_WAIT 4u        /* tlda_cp_pass: return without waiting; loss_out in device memory */
 
 /* One online pass (section "Fully Online Implementation", with W fixed):
  * batch b is documents [batch_offsets[b], batch_offsets[b+1]) of `corpus`;
@@ -204,6 +205,11 @@ tlda_status tlda_cp_data_term(tlda_ctx *ctx, const tlda_csr *batch, const float 
  * loss_out (host, n_batches doubles) may be NULL; if given, it receives each
  * step's loss.  An empty batch (equal offsets) is a step with S3 = 0: Phi
  * unchanged, loss 0.  Synchronises at the end and returns any sticky status.
+ * With TLDA_NO_WAIT (device input only, else TLDA_ERR_INVALID) the call
+ * returns once the pass is enqueued, without waiting for it; loss_out, if
+ * not NULL, is then device memory.  The sticky status (a corrupt batch, an
+ * expired wait) is returned by the next tlda_sync, and Phi and loss_out are
+ * ready when the context's stream has passed the call.
  * A device-input pass runs on the context's stream; a host-input pass runs
  * on internal streams, after the context stream's earlier work and before
  * its later work.

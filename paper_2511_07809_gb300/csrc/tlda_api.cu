@@ -353,7 +353,7 @@ tlda_status tune_tiles(tlda_ctx *ctx, const float *Phi, const std::vector<BatchD
 // (after the kernel of segment g - 2 is done with it) while the kernel of
 // segment g - 1 runs.
 tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *off, int nb, float *Phi,
-                               float lr, bool host, double *loss_out) {
+                               float lr, bool host, double *loss_out, bool no_wait) {
   std::vector<int> seg{0};
   std::vector<BatchDesc> hd(nb);
   if (host) {
@@ -412,7 +412,7 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
     }
   }
   tlda_status s = TLDA_OK;
-  if (loss_out && ctx->dlosses_cap < nb) {  // grown like the descriptor buffers
+  if (loss_out && !no_wait && ctx->dlosses_cap < nb) {  // grown like the descriptor buffers
     const int cap = desc_capacity(ctx->dlosses_cap, nb);
     dfree(ctx->dlosses);
     ctx->dlosses_cap = 0;
@@ -488,17 +488,22 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
     }
     // each batch's own tile size; the Phi^T image before the first segment
     // (each pass launch keeps it current)
-    s = pass_launch(ctx, a, b0, b1, 0, loss_out ? ctx->dlosses : nullptr, 1, g == 0, ps,
+    s = pass_launch(ctx, a, b0, b1, 0, no_wait ? loss_out : loss_out ? ctx->dlosses : nullptr, 1, g == 0, ps,
                     inline_descs ? &inl : nullptr);
     if (host && s == TLDA_OK) CK(cudaEventRecord(ctx->ev_seg[2 + (g & 1)], ps));
   }
-  if (s == TLDA_OK && loss_out)
+  if (s == TLDA_OK && loss_out && !no_wait)
     CK(cudaMemcpyAsync(loss_out, ctx->dlosses, sizeof(double) * nb, cudaMemcpyDeviceToHost, ps));
   if (host) {
     CK(cudaEventRecord(ctx->ev_pass1, ps));
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_pass1, 0));
   }
   if (s) return s;
+  // TLDA_NO_WAIT: no wait here (losses, if asked for, went to device
+  // memory); the device status goes to the next tlda_sync, and a pinned
+  // descriptor buffer in use stays marked busy (the next pass that needs it
+  // waits for this one first)
+  if (no_wait) return TLDA_OK;
   s = read_state(ctx);  // synchronises the context's stream, which follows the pass
   if (s == TLDA_OK) ctx->descs_pin_busy = false;
   if (s == TLDA_OK) s = take_sticky(ctx);
@@ -791,14 +796,15 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
   if (!Phi || !batch_offsets || n_batches < 0) return fail(ctx, TLDA_ERR_INVALID, "bad pass arguments");
   if (!ctx->whitened) return fail(ctx, TLDA_ERR_STATE, "no whitening: fit or set one first");
   if (n_batches == 0) return TLDA_OK;
-  const bool host = flags & TLDA_HOST_INPUT;
+  const bool host = flags & TLDA_HOST_INPUT, no_wait = flags & TLDA_NO_WAIT;
+  if (no_wait && host) return fail(ctx, TLDA_ERR_INVALID, "TLDA_NO_WAIT needs device input");
   for (int b = 0; b < n_batches; ++b) {
     const int64_t d0 = batch_offsets[b], d1 = batch_offsets[b + 1];
     if (d0 < 0 || d1 < d0 || d1 > corpus->n_docs) return fail(ctx, TLDA_ERR_INVALID, "batch_offsets[%d] out of range", b);
     if (d1 - d0 > ctx->Bmax) return fail(ctx, TLDA_ERR_INVALID, "batch %d has %lld docs > max_batch", b, (long long)(d1 - d0));
   }
   if (ctx->pass_grid > 0 && (ctx->prof_mask & ~(1u << kPass)) == 0)
-    return cp_pass_persistent(ctx, corpus, batch_offsets, n_batches, Phi, lr, host, loss_out);
+    return cp_pass_persistent(ctx, corpus, batch_offsets, n_batches, Phi, lr, host, loss_out, no_wait);
   // descriptors
   {
     const tlda_status es = ensure_descs(ctx, n_batches);
@@ -853,7 +859,7 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
   a.Phi = Phi;
   a.want_loss = loss_out ? 1 : 0;
   double *losses = nullptr;
-  if (loss_out) CK(cudaMallocHost(reinterpret_cast<void **>(&losses), sizeof(double) * n_batches));
+  if (loss_out && !no_wait) CK(cudaMallocHost(reinterpret_cast<void **>(&losses), sizeof(double) * n_batches));
   launch_begin_pass(ctx->st, ctx->descs, n_batches, ps);
   if (a.PhiImg) launch_phi_img(a, ps);
   CKL();
@@ -898,7 +904,8 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
     if (use_graph) CK(cudaGraphLaunch(ctx->step_exec, ps));
     else s = enqueue_step(ctx, a, ps);
     if (loss_out && s == TLDA_OK)
-      CK(cudaMemcpyAsync(losses + b, &ctx->st->loss, sizeof(double), cudaMemcpyDeviceToHost, ps));
+      CK(cudaMemcpyAsync(no_wait ? loss_out + b : losses + b, &ctx->st->loss, sizeof(double),
+                         no_wait ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ps));
   }
   CK(cudaEventRecord(ctx->ev_pass1, ps));
   CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_pass1, 0));
@@ -906,6 +913,7 @@ tlda_status tlda_cp_pass(tlda_ctx *ctx, const tlda_csr *corpus, const int64_t *b
     if (losses) cudaFreeHost(losses);
     return s;
   }
+  if (no_wait) return TLDA_OK;  // the device status goes to the next tlda_sync
   s = read_state(ctx);
   if (s == TLDA_OK) {
     if (loss_out) std::memcpy(loss_out, losses, sizeof(double) * n_batches);

@@ -23,6 +23,7 @@ OK, ERR_INVALID, ERR_CUDA, ERR_NUMERIC, ERR_TIMEOUT, ERR_OOM, ERR_STATE, ERR_UNI
 FP32, BF16 = 0, 1
 ACCUMULATE, FINALIZE = 1, 2
 HOST_INPUT = 1
+NO_WAIT = 4
 HOST_OUTPUT = 1
 REUSE_WHITENING = 2
 
@@ -274,11 +275,27 @@ class TLDA:
         return G, S3.value
 
     def cp_pass(self, corpus: DeviceCSR, batch_offsets, Phi: torch.Tensor, lr: float,
-                host_input: bool = False, losses: bool = False):
+                host_input: bool = False, losses: bool = False, wait: bool = True,
+                device_losses: torch.Tensor | None = None):
+        """One online pass (tlda_cp_pass).  wait=False (device input only)
+        returns once the pass is enqueued; its status comes from the next
+        sync().  The step losses then go, if asked for, to device_losses (a
+        CUDA float64 tensor of at least one entry per batch)."""
         off = np.ascontiguousarray(np.asarray(batch_offsets, dtype=np.int64))
         nb = len(off) - 1
-        out = np.zeros(max(nb, 1), dtype=np.float64) if losses else None
         s = corpus.struct()
+        if not wait:
+            assert not host_input and not losses
+            lp = None
+            if device_losses is not None:
+                assert device_losses.is_cuda and device_losses.dtype == torch.float64
+                assert device_losses.is_contiguous() and device_losses.numel() >= nb
+                lp = device_losses.data_ptr()
+            self._check(self.lib.tlda_cp_pass(self.h, ctypes.byref(s), off.ctypes.data, nb,
+                                              Phi.data_ptr(), float(lr), NO_WAIT, lp))
+            return None
+        assert device_losses is None
+        out = np.zeros(max(nb, 1), dtype=np.float64) if losses else None
         self._check(self.lib.tlda_cp_pass(self.h, ctypes.byref(s), off.ctypes.data, nb,
                                           Phi.data_ptr(), float(lr),
                                           HOST_INPUT if host_input else 0,

@@ -234,3 +234,56 @@ def test_bench_sized_pass_sampled_steps(lib):
         assert abs(loss - g["loss"]) <= TOL16 * abs(g["loss"]), s_
         prev = s_ + 1
     t.close()
+
+
+def test_no_wait_pass_equals_waiting_pass(lib):
+    """tlda_cp_pass with TLDA_NO_WAIT returns once the pass is enqueued: the
+    same Phi bit for bit, the same step losses (in device memory; the loss
+    sums are double atomics, so equal to rounding), and a corrupt batch is
+    reported by the next sync instead of by the call.  Host input cannot
+    skip the wait."""
+    import ctypes
+    sp = ts.WORKLOADS[NAME]
+    t, W, m1 = _ctx(lib)
+    t.autotune(fixed=16)
+    c = C.corpus(NAME, 12000)
+    offs = [0, 3000, 3001, 6000, 6000, 9000, 12000]  # a one-document and an empty batch
+    nb = len(offs) - 1
+    dev = lib.DeviceCSR.from_corpus(c)
+    Phi0 = torch.tensor(_phi0(sp), dtype=torch.float32, device="cuda")
+    P1 = Phi0.clone()
+    l1 = t.cp_pass(dev, offs, P1, 0.002, losses=True)
+    P2 = Phi0.clone()
+    dl = torch.full((nb,), float("nan"), dtype=torch.float64, device="cuda")
+    assert t.cp_pass(dev, offs, P2, 0.002, wait=False, device_losses=dl) is None
+    t.sync()
+    assert torch.equal(P1, P2)
+    np.testing.assert_allclose(dl.cpu().numpy(), l1, rtol=1e-12, atol=0.0)
+    assert dl[3].item() == 0.0  # the empty batch
+    P3 = Phi0.clone()
+    t.cp_pass(dev, offs, P3, 0.002, wait=False)  # no losses asked for
+    t.sync()
+    assert torch.equal(P1, P3)
+    # a corrupt batch (inside batch 4): the waiting call raises, the no-wait
+    # call returns and the next sync raises; Phi the same either way
+    counts = c.counts.copy()
+    counts[c.indptr[7000] + 1] = 0
+    bad = lib.DeviceCSR.from_arrays(c.indptr, c.indices, counts, sp.V)
+    P4 = Phi0.clone()
+    with pytest.raises(lib.TLDAError) as e:
+        t.cp_pass(bad, offs, P4, 0.002)
+    assert e.value.status == lib.ERR_INVALID
+    P5 = Phi0.clone()
+    t.cp_pass(bad, offs, P5, 0.002, wait=False)
+    with pytest.raises(lib.TLDAError) as e:
+        t.sync()
+    assert e.value.status == lib.ERR_INVALID
+    assert torch.equal(P4, P5)
+    t.sync()  # taken: nothing pending
+    host = lib.DeviceCSR.from_corpus(c, device="cpu", pin=True)
+    s = host.struct()
+    off = np.asarray(offs, dtype=np.int64)
+    st = t.lib.tlda_cp_pass(t.h, ctypes.byref(s), off.ctypes.data, nb, P5.data_ptr(), ctypes.c_float(0.002),
+                            lib.HOST_INPUT | lib.NO_WAIT, None)
+    assert st == lib.ERR_INVALID
+    t.close()
