@@ -410,12 +410,12 @@ struct Fused {
       float f = 0.f;
       if (j < nnz) {
         const int p = nz0 + j;
-        int lo = 0, hi = Te - 1;  // last document whose range starts at or before p
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (s_ptr[mid] <= p) lo = mid;
-          else hi = mid - 1;
-        }
+        // last document whose range starts at or before p: a fixed
+        // five-step search (Te <= kT = 32), so a thread's searches overlap
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (lo + step < Te && s_ptr[lo + step] <= p) lo += step;
         dd = lo;
         m = mr[u];
         const bool valid = m >= 0 && m < a.V && fr[u] > 0;
