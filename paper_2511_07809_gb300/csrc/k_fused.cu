@@ -403,6 +403,7 @@ struct Fused {
   __device__ void window_fill(const StepArgs &a, int nz0, int nnz, int Te, int w0, bool check, int gt, int bid,
                               const int (&mr)[kWin / kGn], const int (&fr)[kWin / kGn]) {
     constexpr int kPer = kWin / kGn;
+    int dds[kPer], ms[kPer];  // kept for the order check below
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int t = gt + u * kGn, j = w0 + t;
@@ -428,14 +429,17 @@ struct Fused {
       s_m[t] = m;
       s_f[t] = f;
       s_d[t] = dd;
+      dds[u] = dd;
+      ms[u] = m;
     }
     bar_sync_n(bid, kGn);
     if (check) {  // words strictly ascending within a document
-      for (int t = gt; t < kWin; t += kGn) {
-        const int j = w0 + t;
-        if (j < nnz && nz0 + j > s_ptr[s_d[t]]) {
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int t = gt + u * kGn, j = w0 + t;
+        if (j < nnz && nz0 + j > s_ptr[dds[u]]) {
           const int mp = t > 0 ? s_m[t - 1] : sh[2];
-          if (s_m[t] <= mp) sh[1] = 1;
+          if (ms[u] <= mp) sh[1] = 1;
         }
       }
       bar_sync_n(bid, kGn);
