@@ -311,19 +311,16 @@ struct Fused {
       // then copied out slice by slice: each slice's `per` entries are one
       // contiguous run in global memory, so the stores are whole lines
       float *stage = reinterpret_cast<float *>(sm + kOffU0);
-#pragma unroll 1
-      for (int p = 0; p < 4; ++p) {
-        const int c0 = half * 64 + p * 16;
-        if (c0 >= K) break;  // warp-uniform
-        float v[16];
-        if (g_init) tmem_ld16(colG + (static_cast<uint32_t>(quad * 32) << 16) + c0, v);
+      if (half * 64 < K) {  // warp-uniform: this warp's 64 columns, one TMEM wait
+        float v[64];
+        if (g_init) tmem_ld64(colG + (static_cast<uint32_t>(quad * 32) << 16) + half * 64, v);
         else
-          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+          for (int i = 0; i < 64; ++i) v[i] = 0.f;
         if (row < D) {
 #pragma unroll
-          for (int q = 0; q < 16; q += 4)
-            if (c0 + q < K)
-              *reinterpret_cast<float4 *>(stage + row * K + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+          for (int q = 0; q < 64; q += 4)
+            if (half * 64 + q < K)
+              *reinterpret_cast<float4 *>(stage + row * K + half * 64 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
         }
       }
       __syncthreads();
