@@ -1073,11 +1073,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pass(StepArgs a, PassArgs 
     ++nbar;
     // Between the arrival and phase B the block splits in two groups of four
     // warps.  Warps 4..7 do what needs nothing of this step's other blocks:
-    // the next step's first tile (header, first window, first U rows) and, in
-    // a Phi-only block, the CSR of the step after next into L2.  Warps 0..3
-    // wait for the barrier and run phase B (partial slices in the Q buffers,
-    // so the two do not touch the same shared memory).  They join before the
-    // end-of-step arrival; a failure is carried past the join in s_stop.
+    // the plan of the step after next, the next step's first tile (header,
+    // first window, first U rows) and, in a Phi-only block, the CSR of the
+    // step after next into L2.  Warps 0..3 wait for the barrier, run phase B
+    // (partial slices in the Q buffers, so the two do not touch the same
+    // shared memory) and make the end-of-step arrival.  The groups join after
+    // that; a failure is carried past the join in s_stop.
     BatchDesc bn;
     int tdn = 1, tsn = 0;
     const bool pf_next = s + 1 < p.s1 && !f.failed() && block_range(s + 1, bn, tdn, tsn);
