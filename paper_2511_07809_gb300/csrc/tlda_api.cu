@@ -439,13 +439,13 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
   // here after a pass that returned before it did
   // A short device-input pass hands its descriptors to the prologue kernel
   // in the launch parameters instead.
-  const bool inline_descs = !host && nb <= kInlineDescs;
+  // each launch (one per staged segment with host input) of at most
+  // kInlineDescs steps takes its descriptors in the prologue's parameters
+  bool inline_descs = true;
+  for (size_t g = 0; g + 1 < seg.size(); ++g)
+    if (seg[g + 1] - seg[g] > kInlineDescs) inline_descs = false;
   InlineDescs inl;
   inl.n = 0;
-  if (inline_descs) {
-    inl.n = nb;
-    std::memcpy(inl.d, hd.data(), sizeof(BatchDesc) * (size_t)nb);
-  }
   if (!inline_descs && ctx->descs_pin_busy) {
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaStreamSynchronize(ctx->pstream));
@@ -488,6 +488,10 @@ tlda_status cp_pass_persistent(tlda_ctx *ctx, const tlda_csr *corpus, const int6
     }
     // each batch's own tile size; the Phi^T image before the first segment
     // (each pass launch keeps it current)
+    if (inline_descs) {
+      inl.n = b1 - b0;
+      std::memcpy(inl.d, hd.data() + b0, sizeof(BatchDesc) * (size_t)inl.n);
+    }
     s = pass_launch(ctx, a, b0, b1, 0, no_wait ? loss_out : loss_out ? ctx->dlosses : nullptr, 1, g == 0, ps,
                     inline_descs ? &inl : nullptr);
     if (host && s == TLDA_OK) CK(cudaEventRecord(ctx->ev_seg[2 + (g & 1)], ps));
