@@ -116,8 +116,9 @@ __global__ void __launch_bounds__(kSplitThreads) k_pass_prep(StepArgs a, int ima
   // 128-nonzero chunk (or a second tile) than its neighbours: when the
   // batch averages at most one tile per block, each inner boundary may move
   // by up to two documents to lower the larger chunk count of its two
-  // ranges (ranges of more than cap documents count as eight more); even
-  // boundaries first, then odd ones (they share no range), twice.
+  // ranges (ranges of more than cap documents count as eight more); odd
+  // boundaries first, then even ones (boundaries of one parity share no
+  // range), twice.
   const int r_cap = min(p.tile_cap > 0 ? p.tile_cap : (b.tile_cap > 0 ? b.tile_cap : kPassTileDocs), kPassTileDocs);
   if (in_smem && nd > 0 && n_blocks > 1 && n_blocks < kSplitThreads && nd <= (long long)n_blocks * r_cap) {
     auto cost = [&](int da, int db) -> int {
